@@ -1,0 +1,185 @@
+"""Seeded synthetic inputs for the LBRMT time step.
+
+This module is the one place both the CUDA path and the FP64 oracle take their
+inputs from.  It holds no arithmetic of the method: it only draws solid
+placements and material constants and returns plain dictionaries.  Both sides
+consume the same dictionary (grid, walls, relaxation time, forcing, solids).
+
+Lattice units throughout: dx = dt = 1 and rho_f = 1 (paper, Sec. 4 intro and
+Appendix A).  The blur-zone half-width eps = 1.5 and the 11 extrapolation
+layers are the values the paper uses for every result (Sec. 4 intro).
+
+Scenario keys
+-------------
+nx, ny        grid nodes in x and y
+wall_x/wall_y 0 = periodic, 1 = no-slip halfway bounce-back walls (Sec. 3.5)
+tau, rho_f    BGK relaxation time and fluid density
+lid_u         speed of the top wall in +x (0 = static); lid-driven cavity, Sec. 4.1
+eps, n_layers blur-zone half-width and extrapolation layers
+eta           contact-stress constant of Eq. (3_6_collision_stress)
+gravity       g > 0 acting in -y; a solid feels (1 - rho_f/rho_s) g (Sec. 4.3)
+force_kind    0 none, 1 constant (force_a), 2 sinusoidal f_x = A sin(2 pi y / ny)
+              applied to all phases
+force_a       [fx, fy] for kind 1, [A, 0] for kind 2
+solids        list of {"x", "y", "r", "rho_s", "G"} disks (centre, radius,
+              density, small-strain shear modulus)
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+EPS = 1.5
+N_LAYERS = 11
+
+
+def _base(nx, ny, wall_x, wall_y, tau, lid_u=0.0, gravity=0.0, force_kind=0,
+          force_a=(0.0, 0.0), eta=1.0, name=""):
+    return {
+        "name": name, "nx": int(nx), "ny": int(ny),
+        "wall_x": int(wall_x), "wall_y": int(wall_y),
+        "tau": float(tau), "rho_f": 1.0, "lid_u": float(lid_u),
+        "eps": EPS, "n_layers": N_LAYERS, "eta": float(eta),
+        "gravity": float(gravity), "force_kind": int(force_kind),
+        "force_a": [float(force_a[0]), float(force_a[1])],
+        "solids": [],
+    }
+
+
+def _min_image(d, n, periodic):
+    if periodic:
+        d = (d + 0.5 * n) % n - 0.5 * n
+    return d
+
+
+def place_disks(rng, sc, count, r_lo, r_hi, rho_lo, rho_hi, g_lo, g_hi,
+                max_tries=200, r_choice=None):
+    """Rejection-sample non-overlapping disks.
+
+    Surface gap between disks >= 2*eps + 1 = 4 cells; gap to a no-slip wall
+    >= eps + 2 cells.  Disks that fail ``max_tries`` placements are dropped;
+    the realised count is len(sc["solids"]).
+    """
+    nx, ny = sc["nx"], sc["ny"]
+    px, py = sc["wall_x"] == 0, sc["wall_y"] == 0
+    gap = 2 * EPS + 1
+    wall_gap = EPS + 2
+    placed = sc["solids"]
+    for _ in range(count):
+        r = float(rng.uniform(r_lo, r_hi)) if r_choice is None else float(rng.choice(r_choice))
+        rho_s = float(rng.uniform(rho_lo, rho_hi))
+        G = float(rng.uniform(g_lo, g_hi))
+        for _t in range(max_tries):
+            lo_x = 0.0 if px else r + wall_gap - 0.5
+            hi_x = float(nx) if px else nx - 0.5 - r - wall_gap
+            lo_y = 0.0 if py else r + wall_gap - 0.5
+            hi_y = float(ny) if py else ny - 0.5 - r - wall_gap
+            if hi_x <= lo_x or hi_y <= lo_y:
+                break
+            x = float(rng.uniform(lo_x, hi_x))
+            y = float(rng.uniform(lo_y, hi_y))
+            ok = True
+            for s in placed:
+                dx = _min_image(x - s["x"], nx, px)
+                dy = _min_image(y - s["y"], ny, py)
+                if math.hypot(dx, dy) < r + s["r"] + gap:
+                    ok = False
+                    break
+            if ok:
+                placed.append({"x": x, "y": y, "r": r, "rho_s": rho_s, "G": G})
+                break
+    return sc
+
+
+# ---------------------------------------------------------------------------
+# The five workloads (deterministic given the seed)
+# ---------------------------------------------------------------------------
+
+def ldc_disk_64():
+    """Lid-driven cavity 64x64, lid 0.05, tau 0.8, one disk r=12 at (32,38),
+    rho_s/rho_f = 1, G = 0.01 (template: the paper's Sec. 4.1 benchmark)."""
+    sc = _base(64, 64, 1, 1, 0.8, lid_u=0.05, name="ldc_disk_64")
+    sc["solids"].append({"x": 32.0, "y": 38.0, "r": 12.0, "rho_s": 1.0, "G": 0.01})
+    return sc
+
+
+def settling_512(seed=0):
+    """512x512, periodic x, no-slip y, tau 0.7, 24 disks r~U[10,20],
+    rho_s~U[1.2,2.0], G~U[0.005,0.02], gravity 1e-5, contact on (Sec. 4.3-4.4)."""
+    rng = np.random.default_rng(seed)
+    sc = _base(512, 512, 0, 1, 0.7, gravity=1e-5, name=f"settling_512_s{seed}")
+    return place_disks(rng, sc, 24, 10, 20, 1.2, 2.0, 0.005, 0.02)
+
+
+def mixing_4096(seed=0, n=4096, count=1024):
+    """4096x4096 fully periodic, tau 0.6, f_x = 1e-5 sin(2 pi y/ny) on all
+    phases, 1024 disks r~U[8,24], rho_s~U[1.0,1.5], G~U[0.002,0.02]."""
+    rng = np.random.default_rng(seed)
+    sc = _base(n, n, 0, 0, 0.6, force_kind=2, force_a=(1e-5, 0.0),
+               name=f"mixing_{n}_s{seed}")
+    return place_disks(rng, sc, count, 8, 24, 1.0, 1.5, 0.002, 0.02)
+
+
+def ldc_ensemble(seed=0, count=96):
+    """96 lid-driven cavities, side ~ U{128,192,256,384,512}, 1-8 disks each
+    with r~U[8,40], G~U[0.005,0.05], lid_u~U[0.02,0.08]; tau 0.8, rho_s = 1."""
+    rng = np.random.default_rng(seed)
+    sims = []
+    for k in range(count):
+        side = int(rng.choice([128, 192, 256, 384, 512]))
+        lid = float(rng.uniform(0.02, 0.08))
+        sc = _base(side, side, 1, 1, 0.8, lid_u=lid, name=f"ldc_ens_{seed}_{k}")
+        nd = int(rng.integers(1, 9))
+        r_hi = min(40.0, side / 4.0)
+        place_disks(rng, sc, nd, 8, r_hi, 1.0, 1.0, 0.005, 0.05)
+        sims.append(sc)
+    return sims
+
+
+def adjoint_ldc_256():
+    """256x256 lid-driven cavity, tau 0.8, one disk r=40 at (0.6L, 0.5L)."""
+    sc = _base(256, 256, 1, 1, 0.8, lid_u=0.05, name="adjoint_ldc_256")
+    sc["solids"].append({"x": 0.6 * 256, "y": 0.5 * 256, "r": 40.0, "rho_s": 1.0, "G": 0.01})
+    return sc
+
+
+# ---------------------------------------------------------------------------
+# Small seeded cases for parity tests (sizes the oracle finishes in seconds)
+# ---------------------------------------------------------------------------
+
+def settling_small(seed=0, nx=96, ny=80, count=3, gravity=2e-4):
+    rng = np.random.default_rng(1000 + seed)
+    sc = _base(nx, ny, 0, 1, 0.7, gravity=gravity, name=f"settling_small_s{seed}")
+    return place_disks(rng, sc, count, 6, 10, 1.2, 2.0, 0.005, 0.02)
+
+
+def mixing_small(seed=0, n=96, count=5, amp=2e-4):
+    rng = np.random.default_rng(2000 + seed)
+    sc = _base(n, n, 0, 0, 0.6, force_kind=2, force_a=(amp, 0.0),
+               name=f"mixing_small_s{seed}")
+    return place_disks(rng, sc, count, 6, 12, 1.0, 1.5, 0.002, 0.02)
+
+
+def contact_pair(gap=1.0, nx=80, ny=48, speed=0.0):
+    """Two disks whose blur zones overlap (surface gap < 2 eps), periodic box,
+    pushed together by opposite body accelerations through gravity-free
+    sinusoidal forcing off; exercises the contact stress."""
+    sc = _base(nx, ny, 0, 0, 0.7, name=f"contact_pair_g{gap}")
+    r = 9.0
+    cx, cy = nx / 2.0, ny / 2.0 + 0.3
+    sc["solids"].append({"x": cx - r - gap / 2 - 0.2, "y": cy, "r": r, "rho_s": 1.3, "G": 0.02})
+    sc["solids"].append({"x": cx + r + gap / 2 + 0.1, "y": cy - 0.4, "r": r, "rho_s": 1.1, "G": 0.01})
+    return sc
+
+
+def fluid_only(nx, ny, wall_x, wall_y, tau, lid_u=0.0, force_kind=0, force_a=(0.0, 0.0)):
+    return _base(nx, ny, wall_x, wall_y, tau, lid_u=lid_u, force_kind=force_kind,
+                 force_a=force_a, name="fluid_only")
+
+
+ALL = {
+    "ldc_disk_64": ldc_disk_64,
+    "settling_512": settling_512,
+    "mixing_4096": mixing_4096,
+    "adjoint_ldc_256": adjoint_ldc_256,
+}

@@ -1,0 +1,429 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+printed tables and expanded formulas (tests/golden/), conservation laws the
+paper derives (Appendix C), closed-form flows (Couette, Poiseuille), exact
+properties of the discretisations (upwind stencil and least-squares fit are
+exact on linear fields, F = I gives zero stress) and brute force with an
+independent least-squares routine.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenarios
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+D2Q9 = _table("d2q9_table.txt")
+CX = D2Q9[:, 1]
+CY = D2Q9[:, 2]
+W = D2Q9[:, 3] / D2Q9[:, 4]
+
+
+# --------------------------------------------------------------------------
+# Equilibrium with smooth flux correction (Eqs. 2_3_feq_sfc, 3_4_feq; App. C)
+# --------------------------------------------------------------------------
+
+def test_d2q9_table_consistency():
+    # Table d2q9: weights sum to one, isotropy gives c_s^2 = 1/3 (Sec. 2.2)
+    assert abs(W.sum() - 1.0) < 1e-15
+    assert abs((W * CX * CX).sum() - 1.0 / 3.0) < 1e-15
+    assert abs((W * CX * CY).sum()) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_feq_moments_and_sfc_conservation(seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(50):
+        rho = rng.uniform(0.5, 2.0)
+        u, v = rng.uniform(-0.1, 0.1, 2)
+        drho = rng.uniform(-0.5, 1.0)
+        f = oracle.feq(rho, u, v, drho)
+        # Appendix C: the SFC terms cancel in mass and momentum
+        assert abs(f.sum() - rho) < 1e-14
+        assert abs((CX * f).sum() - rho * u) < 1e-15
+        assert abs((CY * f).sum() - rho * v) < 1e-15
+        # second moment of the uncorrected part: sum c c f = rho (cs2 I + v v)
+        f0 = oracle.feq(rho, u, v, 0.0)
+        assert abs((CX * CX * f0).sum() - rho * (1 / 3 + u * u)) < 1e-14
+        assert abs((CX * CY * f0).sum() - rho * u * v) < 1e-14
+
+
+def test_feq_matches_expanded_eq_3_4_feq():
+    T = _table("feq_expanded.txt")
+    rng = np.random.default_rng(7)
+    for _ in range(100):
+        rho = rng.uniform(0.5, 2.0)
+        u, v = rng.uniform(-0.2, 0.2, 2)
+        drho = rng.uniform(-0.5, 1.0)
+        f = oracle.feq(rho, u, v, drho)
+        for row in T:
+            i, den, a0, au, av, auu, avv, auv, kn, kd = row
+            e = rho * (a0 + au * u + av * v + auu * u * u + avv * v * v + auv * u * v) / den + kn / kd * drho
+            assert abs(f[int(i)] - e) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Guo forcing (Eqs. 2_2_Fi, 3_4_Fi)
+# --------------------------------------------------------------------------
+
+def test_guo_moments_and_expanded_form():
+    T = _table("guo_expanded.txt")
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        rho = rng.uniform(0.5, 2.0)
+        u, v = rng.uniform(-0.2, 0.2, 2)
+        fx, fy = rng.uniform(-1e-3, 1e-3, 2)
+        F = oracle.guo(rho, u, v, fx, fy)
+        assert abs(F.sum()) < 1e-18
+        assert abs((CX * F).sum() - rho * fx) < 1e-18
+        assert abs((CY * F).sum() - rho * fy) < 1e-18
+        # second moments of the Guo term: rho (v F + F v)
+        assert abs((CX * CX * F).sum() - 2 * rho * u * fx) < 1e-18
+        assert abs((CX * CY * F).sum() - rho * (u * fy + v * fx)) < 1e-18
+        assert abs((CY * CY * F).sum() - 2 * rho * v * fy) < 1e-18
+        for row in T:
+            i, den, bx, by, bux, bvx, buy, bvy = row
+            e = rho / den * (bx * fx + by * fy + bux * u * fx + bvx * v * fx + buy * u * fy + bvy * v * fy)
+            assert abs(F[int(i)] - e) < 1e-18
+
+
+def test_printed_F2_term_would_break_momentum():
+    # As printed, F_2 and F_4 of Eq. 3_4_Fi carry 9 v F_x; that version breaks
+    # the second moment sum c_y c_y F_i = 2 rho v F_y that Eq. 2_2_Fi gives,
+    # which is why the oracle reads 9 v F_y.
+    rho, u, v, fx, fy = 1.1, 0.03, -0.02, 1e-3, 2e-3
+    F = oracle.guo(rho, u, v, fx, fy).copy()
+    F_print = F.copy()
+    F_print[2] = rho / 9 * (-3 * u * fx + 3 * (1 - v) * fy + 9 * v * fx)
+    F_print[4] = rho / 9 * (-3 * u * fx + 3 * (-1 - v) * fy + 9 * v * fx)
+    assert abs((CY * CY * F).sum() - 2 * rho * v * fy) < 1e-18
+    assert abs((CY * CY * F_print).sum() - 2 * rho * v * fy) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Heaviside (Eq. 2_3_heaviside)
+# --------------------------------------------------------------------------
+
+def test_heaviside_properties():
+    eps = 1.5
+    H = oracle.heaviside
+    assert H(0.0, eps) == 0.5
+    assert H(-eps, eps) == 0.0 and H(eps, eps) == 1.0
+    xs = np.linspace(-2 * eps, 2 * eps, 401)
+    vals = np.array([H(x, eps) for x in xs])
+    assert np.all(np.diff(vals) >= -1e-16)
+    assert vals.min() >= 0 and vals.max() <= 1
+    for x in xs:
+        assert abs(H(x, eps) + H(-x, eps) - 1.0) < 1e-15
+    # continuity at the blur-zone edges
+    d = 1e-9
+    assert abs(H(eps - d, eps) - 1.0) < 1e-12
+    assert abs(H(-eps + d, eps)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Solid stress (Eqs. 3_3_refmap_deformation, 3_3_solid_stress) and contact
+# --------------------------------------------------------------------------
+
+def test_stress_zero_for_identity_and_rotation():
+    G = 0.37
+    assert np.all(oracle.stress_from_jacobian([[1, 0], [0, 1]], G) == 0.0)
+    for th in np.linspace(-3, 3, 13):
+        R = [[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]]
+        assert np.abs(oracle.stress_from_jacobian(R, G)).max() < 1e-15
+
+
+@pytest.mark.parametrize("a", [0.5, 0.9, 1.3, 2.0])
+def test_stress_uniaxial_stretch_closed_form(a):
+    G = 0.1
+    # J = d xi/dx = F^{-1} for F = diag(a, 1/a)
+    tau = oracle.stress_from_jacobian([[1 / a, 0], [0, a]], G)
+    tr = (a * a + 1 / (a * a) + 1) / 3
+    assert np.allclose(tau, [G * (a * a - tr), 0.0, G * (1 / (a * a) - tr)], rtol=1e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("gam", [-0.4, 0.05, 0.3])
+def test_stress_simple_shear_closed_form(gam):
+    G = 0.02
+    # F = [[1, gam], [0, 1]] => J = [[1, -gam], [0, 1]]; B = F F^T
+    tau = oracle.stress_from_jacobian([[1, -gam], [0, 1]], G)
+    assert np.allclose(tau, [2 / 3 * G * gam * gam, G * gam, -G * gam * gam / 3], rtol=1e-13, atol=1e-18)
+
+
+def test_contact_stress_properties():
+    eps, eta = 1.5, 1.0
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        ps, pt = rng.uniform(-1.4, 1.4, 2)
+        gx, gy = rng.normal(size=2)
+        t = oracle.contact_stress(ps, pt, 0.01, 0.02, eta, eps, gx, gy)
+        assert abs(t[0] + t[2]) < 1e-17          # traceless
+        t2 = oracle.contact_stress(pt, ps, 0.02, 0.01, eta, eps, -gx, -gy)
+        assert np.allclose(t, t2, rtol=0, atol=1e-18)  # swap invariance
+        # repulsive: normal stress along n is -k/2 < 0 times (-1) ... sign check
+        n = np.array([gx, gy]) / math.hypot(gx, gy)
+        tn = t[0] * n[0] ** 2 + 2 * t[1] * n[0] * n[1] + t[2] * n[1] ** 2
+        fm = min(0.5 * (1 - ps / eps), 0.5 * (1 - pt / eps))
+        assert abs(tn - (-eta * fm * 0.03 * 0.5)) < 1e-15
+    assert np.all(oracle.contact_stress(1.5, -1.0, 0.01, 0.01, eta, eps, 1, 0) == 0)
+    assert np.all(oracle.contact_stress(-1.0, 2.0, 0.01, 0.01, eta, eps, 1, 0) == 0)
+
+
+# --------------------------------------------------------------------------
+# Extrapolation (Sec. 3.2, Eq. 3_2_extrap_weight)
+# --------------------------------------------------------------------------
+
+def _lsq_reference(lab, X, tx, ty, layer, r, normal):
+    """Independent weighted least squares with numpy.linalg.lstsq."""
+    h, w = lab.shape
+    rows, rhs = [], []
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            x, y = tx + dx, ty + dy
+            if not (0 <= x < w and 0 <= y < h):
+                continue
+            if not (0 <= lab[y, x] < layer):
+                continue
+            wt = 2.0 ** -(abs(dx) + abs(dy))
+            if layer <= 2 and normal is not None:
+                d = np.array([-dx, -dy], float)
+                wt = max(0.0, d @ np.asarray(normal) / np.linalg.norm(d) * wt)
+            if wt <= 0:
+                continue
+            s = math.sqrt(wt)
+            rows.append([s * dx, s * dy, s])
+            rhs.append(s * X[y, x])
+    p = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]
+    return p[2]
+
+
+def _random_region(rng, h=13, w=13):
+    lab = -np.ones((h, w), np.int8)
+    cx, cy, R = rng.uniform(4, 8), rng.uniform(4, 8), rng.uniform(2.5, 4)
+    yy, xx = np.mgrid[0:h, 0:w]
+    lab[(xx - cx) ** 2 + (yy - cy) ** 2 < R * R] = 0
+    # two dilation layers
+    for l in (1, 2, 3):
+        prev = lab == l - 1
+        nb = np.zeros_like(prev)
+        nb[1:] |= prev[:-1]; nb[:-1] |= prev[1:]; nb[:, 1:] |= prev[:, :-1]; nb[:, :-1] |= prev[:, 1:]
+        lab[(lab == -1) & nb] = l
+    return lab, (cx, cy)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_extrapolation_exact_on_linear_fields(seed):
+    rng = np.random.default_rng(seed)
+    lab, (cx, cy) = _random_region(rng)
+    A = rng.normal(size=(2, 2)); b = rng.normal(size=2) * 10
+    yy, xx = np.mgrid[0:lab.shape[0], 0:lab.shape[1]].astype(float)
+    X = A[0, 0] * xx + A[0, 1] * yy + b[0]
+    Y = A[1, 0] * xx + A[1, 1] * yy + b[1]
+    for ty, tx in zip(*np.nonzero(lab > 0)):
+        l = int(lab[ty, tx])
+        n = np.array([tx - cx, ty - cy]); n /= np.linalg.norm(n)
+        r, ox, oy = oracle.extrap_target(lab, X, Y, tx, ty, l, normal=n)
+        assert r >= 2
+        assert abs(ox - X[ty, tx]) < 1e-12 and abs(oy - Y[ty, tx]) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_extrapolation_matches_independent_lstsq(seed):
+    rng = np.random.default_rng(100 + seed)
+    lab, (cx, cy) = _random_region(rng)
+    X = rng.normal(size=lab.shape)
+    Y = rng.normal(size=lab.shape)
+    for ty, tx in zip(*np.nonzero(lab > 0)):
+        l = int(lab[ty, tx])
+        n = np.array([tx - cx, ty - cy]); n /= np.linalg.norm(n)
+        r, ox, oy = oracle.extrap_target(lab, X, Y, tx, ty, l, normal=n)
+        assert abs(ox - _lsq_reference(lab, X, tx, ty, l, r, n)) < 1e-11
+        assert abs(oy - _lsq_reference(lab, Y, tx, ty, l, r, n)) < 1e-11
+
+
+def test_extrapolation_window_growth():
+    # fewer than three valid nodes within r = 2 -> r grows to 3
+    lab = -np.ones((9, 9), np.int8)
+    lab[4, 0] = 0; lab[4, 1] = 0; lab[0, 0] = 0
+    lab[4, 4] = 1
+    X = np.arange(81, dtype=float).reshape(9, 9)
+    r, ox, _ = oracle.extrap_target(lab, X, X, 4, 4, 3)
+    assert r == 4  # (0,0) is at Chebyshev distance 4
+    assert abs(ox - X[4, 4]) < 1e-12
+    # three collinear valid nodes: ill-posed fit, the window must grow
+    lab = -np.ones((9, 9), np.int8)
+    lab[4, 1] = lab[4, 2] = lab[4, 3] = 0
+    lab[1, 1] = 0
+    lab[4, 5] = 1
+    r, ox, _ = oracle.extrap_target(lab, X, X, 5, 4, 3)
+    assert r == 4 and abs(ox - X[4, 5]) < 1e-12
+    # the directional weight of layers 1-2 keeps only nodes behind the target
+    lab = -np.ones((9, 9), np.int8)
+    lab[3, 2] = lab[5, 2] = lab[4, 3] = 0   # behind the target (x < 4)
+    lab[3, 6] = lab[4, 6] = lab[5, 6] = 0   # ahead of the target
+    lab[0, 4] = 0                           # below, at Chebyshev distance 4
+    lab[4, 4] = 1
+    r, ox, _ = oracle.extrap_target(lab, X, X, 4, 4, 1, normal=(1.0, 0.0))
+    assert r == 2 and abs(ox - X[4, 4]) < 1e-12
+    # normal along +y: only (2,3), (6,3) have positive weight within r = 2, so
+    # the window grows until (4,0) joins at r = 4
+    r2, ox2, _ = oracle.extrap_target(lab, X, X, 4, 4, 1, normal=(0.0, 1.0))
+    assert r2 == 4 and abs(ox2 - X[4, 4]) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Whole-step invariants
+# --------------------------------------------------------------------------
+
+def _total(o):
+    return o.field("rho").sum()
+
+
+def test_rest_is_a_fixed_point():
+    sc = scenarios.settling_small(seed=1, gravity=0.0)
+    o = oracle.Oracle(sc)
+    f0 = o.populations()
+    o.step(30)
+    assert np.abs(o.populations() - f0).max() < 1e-12  # round-off over 30 steps
+    assert np.abs(o.field("ux")).max() < 1e-13 and np.abs(o.field("uy")).max() < 1e-13
+    x = np.arange(sc["nx"])[None, :].repeat(sc["ny"], 0)
+    for s in range(len(sc["solids"])):
+        xi = o.field("xi_x", s)
+        m = np.isfinite(xi)
+        d = (xi[m] - x[m] + sc["nx"] / 2) % sc["nx"] - sc["nx"] / 2  # unwrapped frame
+        assert np.abs(d).max() < 1e-10
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mass_conserved_periodic_with_forcing(seed):
+    sc = scenarios.mixing_small(seed=seed)
+    o = oracle.Oracle(sc)
+    m0 = _total(o)
+    o.step(40)
+    assert abs(_total(o) - m0) < 1e-11 * m0
+
+
+def test_momentum_gain_per_step():
+    # Periodic box.  The collision (Eq. 2_2_bgk_force) changes sum c_i f_i by
+    # (1/tau)(rho v - sum c f) + (1 - 1/(2 tau)) rho^n F^n (sum c F_i = rho F,
+    # Eq. 2_2_Fi); in Algorithm 1 the velocity v^n of f^eq carries the half-force
+    # of the previous step, rho v^n = sum c f + rho^{n-1} F^{n-1} / 2.  So the
+    # gain is exactly sum[rho^{n-1} F^{n-1} / (2 tau) + (1 - 1/(2 tau)) rho^n F^n].
+    sc = scenarios.mixing_small(seed=2)
+    tau = sc["tau"]
+    o = oracle.Oracle(sc)
+    o.step(4)
+    rho_prev = o.populations().sum(0)
+    o.step(1)
+    prev = (rho_prev * o.field("Fx"), rho_prev * o.field("Fy"))
+    for _ in range(3):
+        f = o.populations()
+        rho = f.sum(0)
+        px = (CX[:, None, None] * f).sum()
+        py = (CY[:, None, None] * f).sum()
+        o.step(1)
+        f1 = o.populations()
+        cur = (rho * o.field("Fx"), rho * o.field("Fy"))
+        gx = (prev[0] / (2 * tau) + (1 - 1 / (2 * tau)) * cur[0]).sum()
+        gy = (prev[1] / (2 * tau) + (1 - 1 / (2 * tau)) * cur[1]).sum()
+        assert abs(gx) > 1e-6
+        assert abs((CX[:, None, None] * f1).sum() - px - gx) < 1e-11
+        assert abs((CY[:, None, None] * f1).sum() - py - gy) < 1e-11
+        prev = cur
+
+
+def test_rigid_translation_keeps_xi_exact():
+    # neutrally buoyant disk in uniform flow: upwind advection and the LSQ fit are
+    # exact on linear xi, so xi = x - n U on the whole band; stress stays zero
+    sc = scenarios.fluid_only(64, 48, 0, 0, 0.7)
+    sc["solids"].append({"x": 30.3, "y": 23.6, "r": 9.0, "rho_s": 1.0, "G": 0.05})
+    o = oracle.Oracle(sc)
+    U, V = 0.02, -0.013
+    f = np.zeros((9, 48, 64))
+    feq = oracle.feq(1.0, U, V, 0.0)
+    f[:] = feq[:, None, None]
+    o.set_populations(f)
+    n = 6
+    o.step(n)
+    x = np.arange(64)[None, :].repeat(48, 0).astype(float)
+    y = np.arange(48)[:, None].repeat(64, 1).astype(float)
+    xi, yi = o.field("xi_x"), o.field("xi_y")
+    m = np.isfinite(xi)
+    assert m.sum() > 500
+    assert np.abs(xi[m] - (x[m] - n * U)).max() < 1e-10
+    assert np.abs(yi[m] - (y[m] - n * V)).max() < 1e-10
+    assert np.abs(o.field("Fx")).max() < 1e-12 and np.abs(o.field("Fy")).max() < 1e-12
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.0])
+def test_couette_exact_linear_profile(tau):
+    ny, U = 8, 0.01
+    o = oracle.Oracle(scenarios.fluid_only(4, ny, 0, 1, tau, lid_u=U))
+    o.step(5000)
+    u = o.field("ux")[:, 0]
+    assert np.abs(u - U * (np.arange(ny) + 0.5) / ny).max() < 1e-13
+    assert np.abs(o.field("uy")).max() < 1e-13
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0])
+def test_poiseuille_parabola(tau):
+    g = 1e-6
+    nu = (tau - 0.5) / 3
+    slips = []
+    for ny in (8, 16):
+        o = oracle.Oracle(scenarios.fluid_only(4, ny, 0, 1, tau, force_kind=1, force_a=(g, 0.0)))
+        o.step(int(12 * ny * ny / nu))
+        u = o.field("ux")[:, 0]
+        d2 = u[2:] - 2 * u[1:-1] + u[:-2]
+        assert np.abs(d2 * nu / g + 1.0).max() < 1e-8        # curvature exactly -g/nu
+        y = np.arange(ny) + 0.5
+        ex = g / (2 * nu) * y * (ny - y)
+        dev = u - ex
+        assert np.ptp(dev) < 1e-8 * ex.max()                  # uniform wall slip
+        slips.append(abs(dev.mean()) / ex.max())
+    assert slips[1] < slips[0] / 3.5                          # slip error is O(1/H^2)
+
+
+def test_mirror_symmetry_settling_disk():
+    nx, ny = 48, 64
+    sc = scenarios.fluid_only(nx, ny, 0, 1, 0.7)
+    sc["gravity"] = 5e-4
+    # centre on the mirror line x = (nx - 1)/2 of the node lattice
+    sc["solids"].append({"x": (nx - 1) / 2, "y": 30.4, "r": 8.5, "rho_s": 1.6, "G": 0.02})
+    o = oracle.Oracle(sc)
+    o.step(60)
+    u, v = o.field("ux"), o.field("uy")
+    assert np.abs(v).max() > 1e-4
+    assert np.abs(u + u[:, ::-1]).max() < 1e-10 * np.abs(v).max()
+    assert np.abs(v - v[:, ::-1]).max() < 1e-10 * np.abs(v).max()
+    xi = o.field("xi_x")
+    m = np.isfinite(xi)
+    assert np.array_equal(m, m[:, ::-1])
+    assert np.abs((xi - (nx - 1) / 2) + (xi[:, ::-1] - (nx - 1) / 2))[m].max() < 1e-10
+
+
+def test_band_has_eleven_layers_and_pads():
+    sc = scenarios.ldc_disk_64()
+    o = oracle.Oracle(sc)
+    lab = o.field("label")
+    assert lab.max() == 11
+    phi = o.field("phi")
+    assert np.all(phi[lab == 0] < 0)
+    o.step(3)
+    lab = o.field("label")
+    assert set(np.unique(lab[lab >= 0]).astype(int)) == set(range(12))
