@@ -21,7 +21,13 @@
  * benchmark load this file.  It shares no code, header or constant with the
  * CUDA path.  Where the paper is silent the readings are:
  *   - u == 0 takes the u > 0 (backward) upwind branch;
- *   - the advected set is {domain nodes with phi^n < 0};
+ *   - the advected set is {domain nodes with phi^n < 0}; a node whose level
+ *     set lies within PHI_TIE = 1e-9 of zero counts as not solid, so that
+ *     nodes exactly on the initial interface (a disk centred on a node) are
+ *     classified the same way whatever the rounding of later steps;
+ *   - a directional extrapolation weight whose cosine d.n/|d| is at most
+ *     COS_TIE = 1e-9 is zero (the same rule for a node exactly abeam the
+ *     target);
  *   - the extrapolation's "ill-defined" fit means fewer than three nodes of
  *     positive weight, or all of them on one line (det M = 0);
  *   - the surface normal of Eq. 3_2_extrap_weight is the central-difference
@@ -57,6 +63,8 @@ static const int CY[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WQ[NQ] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const int OPP[NQ] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#define PHI_TIE 1e-9
+#define COS_TIE 1e-9
 
 typedef struct {
     int nx, ny, wall_x, wall_y;
@@ -236,7 +244,7 @@ int oracle_extrap_target(int w, int h, const signed char *lab, const double *X,
                     /* d = target - valid node */
                     double ddx = -dx, ddy = -dy;
                     double dn = (ddx * nhx + ddy * nhy) / sqrt(ddx * ddx + ddy * ddy);
-                    wt = fmax(0.0, dn * wt);
+                    wt = dn > COS_TIE ? dn * wt : 0.0;
                 }
                 if (!(wt > 0.0)) continue;
                 /* collinearity bookkeeping on integer offsets */
@@ -403,7 +411,7 @@ static int init_solid(osim_t *m, osolid_t *s) {
     int sx0 = 1 << 30, sx1 = -(1 << 30), sy0 = 1 << 30, sy1 = -(1 << 30);
     for (int gy = by0; gy <= by1; gy++)
         for (int gx = bx0; gx <= bx1; gx++)
-            if (in_domain(c, gx, gy) && phi0(s, gx, gy) < 0.0) {
+            if (in_domain(c, gx, gy) && phi0(s, gx, gy) < -PHI_TIE) {
                 if (gx < sx0) { sx0 = gx; }
                 if (gx > sx1) { sx1 = gx; }
                 if (gy < sy0) { sy0 = gy; }
@@ -416,7 +424,7 @@ static int init_solid(osim_t *m, osolid_t *s) {
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
             int gx = x0 + x, gy = y0 + y;
-            if (in_domain(c, gx, gy) && phi0(s, gx, gy) < 0.0) {
+            if (in_domain(c, gx, gy) && phi0(s, gx, gy) < -PHI_TIE) {
                 int k = y * w + x;
                 s->lab[k] = 0; s->X[k] = gx; s->Y[k] = gy;
             }
@@ -433,7 +441,7 @@ static int update_solid(osim_t *m, osolid_t *s) {
     for (int y = 0; y < s->h; y++)
         for (int x = 0; x < s->w; x++) {
             int k = y * s->w + x, gx = s->x0 + x, gy = s->y0 + y;
-            if (s->lab[k] >= 0 && s->phi[k] < 0.0 && in_domain(c, gx, gy)) {
+            if (s->lab[k] >= 0 && s->phi[k] < -PHI_TIE && in_domain(c, gx, gy)) {
                 if (gx < sx0) { sx0 = gx; }
                 if (gx > sx1) { sx1 = gx; }
                 if (gy < sy0) { sy0 = gy; }
@@ -449,7 +457,7 @@ static int update_solid(osim_t *m, osolid_t *s) {
     for (int y = 0; y < s->h; y++)
         for (int x = 0; x < s->w; x++) {
             int k = y * s->w + x, gx = s->x0 + x, gy = s->y0 + y;
-            if (!(s->lab[k] >= 0 && s->phi[k] < 0.0 && in_domain(c, gx, gy))) continue;
+            if (!(s->lab[k] >= 0 && s->phi[k] < -PHI_TIE && in_domain(c, gx, gy))) continue;
             int cell = wrapi(gy, c->ny) * nx + wrapi(gx, nx);
             double u = m->ux[cell], v = m->uy[cell];
             int sx = (u >= 0.0) ? -1 : 1; /* backward for u >= 0 */

@@ -202,7 +202,8 @@ def _lsq_reference(lab, X, tx, ty, layer, r, normal):
             wt = 2.0 ** -(abs(dx) + abs(dy))
             if layer <= 2 and normal is not None:
                 d = np.array([-dx, -dy], float)
-                wt = max(0.0, d @ np.asarray(normal) / np.linalg.norm(d) * wt)
+                cos = d @ np.asarray(normal) / np.linalg.norm(d)
+                wt = cos * wt if cos > 1e-9 else 0.0
             if wt <= 0:
                 continue
             s = math.sqrt(wt)
