@@ -1,0 +1,304 @@
+"""Benchmark of the LBRMT time step on GB300.
+
+Default workload: the mixing suspension at scale -- a 4096 x 4096 periodic box,
+1024 soft disks (radii U[8,24], rho_s U[1.0,1.5], G U[0.002,0.02], seed 0),
+sinusoidal body force 1e-5, tau 0.6, FP32 (populations stored as FP32
+deviations from w_q rho_f).  One "step" is one full time step of Algorithm 1
+(reference-map kernel, stress/force kernel, fused lattice Boltzmann kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbrmt|reference]
+
+Prints one JSON line (rank 0).  value = lattice updates per second of all
+ranks (MLUPS) with the state resident in HBM, timed with CUDA events on the
+simulation's stream between a barrier + synchronize on both sides; the f
+planes (1.2 GB) are larger than L2.  For N > 1 each rank runs an independent
+replica (seed = rank), no collective on the data path.  The reference arm
+times the FP64 C oracle on the host cores on a bounded sample of the same
+workload (a 1024 x 1024 crop with the same disk density).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenarios  # noqa: E402
+
+METRIC = "LBRMT MLUPS on 1 GB300 (FP32 vs FP64/half-store) & % HBM roofline; adjoint cost"
+BASE_WORKLOAD = ("mixing_4096: 4096x4096 periodic box, 1024 disks r~U[8,24], rho_s~U[1.0,1.5], "
+                 "G~U[0.002,0.02], f_x = 1e-5 sin(2 pi y/ny), tau 0.6")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.gpu), "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def crop_sample(seed=0, n=1024):
+    """Bounded sample of the 4096^2 workload: same density (1024 disks / 4096^2)."""
+    count = int(round(1024 * (n / 4096) ** 2))
+    return scenarios.mixing_4096(seed=seed, n=n, count=count)
+
+
+def time_oracle(sc, steps, warmup):
+    import oracle
+    o = oracle.Oracle(sc)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return sc["nx"] * sc["ny"] * steps / dt / 1e6, dt, oracle.num_threads()
+
+
+def bench_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    sc = crop_sample(0)
+    value, dt, cores = time_oracle(sc, args.steps, args.warmup)
+    sample = (f"FP64 C oracle, {sc['nx']}x{sc['ny']} crop of the 4096^2 workload with "
+              f"{len(sc['solids'])} disks (same density), {args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": BASE_WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def bench_lbrmt(args):
+    import torch
+    import paper_2402_12696_gb300 as pkg
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    sc = scenarios.mixing_4096(seed=rank) if args.size == 4096 else crop_sample(rank, args.size)
+    N = sc["nx"] * sc["ny"]
+    stream = torch.cuda.Stream(dev)
+    sim = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream)
+    sim.init()
+    sim.step(args.warmup)
+    sim.sync()
+
+    # ---- timed region: K graph-replayed steps -------------------------------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    torch.cuda.synchronize(dev)
+    sim.sync()
+    launches = sim.last_launch_count
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms)
+    value = N * args.steps * ws / (ms_max / 1e3) / 1e6
+
+    # ---- per-kernel durations (CUDA events on the simulation stream) --------
+    kms = sim.step_timed(max(3, min(args.steps, 20)))
+    nact = sim.active_tiles()          # 32x8 tiles the LB kernel reads the force pool on
+    band_frac = min(1.0, nact * 256 / N)
+    sim.close()
+
+    # ---- e2e through the public API with host buffers -----------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        f0 = None
+        sim2 = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream)
+        sim2.init()
+        f0 = torch.from_numpy(sim2.populations_host()).pin_memory()
+        host_stats = torch.zeros((len(sc["solids"]), 8), dtype=torch.float64).pin_memory()
+        host_rho = torch.zeros(N, dtype=torch.float64).pin_memory()
+        ke = args.e2e_steps
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pkg.lbrmt_set_populations_host(sim2.h, f0.data_ptr())
+        for _ in range(ke):
+            pkg.lbrmt_step(sim2.h, 1)
+            pkg.lbrmt_solid_stats(sim2.h, 0, host_stats.data_ptr())
+        pkg.lbrmt_read_fields_host(sim2.h, 0, 0, 0, host_rho.data_ptr())
+        t1 = time.perf_counter()
+        barrier()
+        dt = max_over_ranks(t1 - t0)
+        h2d = f0.numel() * 8 / ke
+        d2h = host_stats.numel() * 8 + host_rho.numel() * 8 / ke
+        e2e = {"value": N * ke * ws / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": ke,
+               "note": "initial populations uploaded from pinned host memory, per-step solid stats "
+                       "read back, final density field read back; all inside the timed region"}
+        sim2.close()
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (fused LB kernel) ------------------
+    peak, peak_kind = _peaks()
+    sf = 4 if args.precision == "fp32" else 8
+    alg_bytes = N * (18 * sf + 4 * sf + 3 * sf * band_frac)
+    k1_ms = kms[2]
+    achieved = alg_bytes / (k1_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"lb_step_kernel_traffic_{args.precision}.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # ---- CPU baseline: the oracle on a bounded sample ------------------------
+    cpu = None
+    if not args.no_cpu_baseline:
+        csc = crop_sample(0)
+        v, dt, cores = time_oracle(csc, args.cpu_steps, 1)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{csc['nx']}x{csc['ny']} crop of the workload with {len(csc['solids'])} disks "
+                         f"(same density), {args.cpu_steps} timed steps after 1 warm-up, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": BASE_WORKLOAD if args.size == 4096 else
+                   f"{args.size}x{args.size} crop of " + BASE_WORKLOAD, "precision": args.precision, "seed": "rank",
+                   "nodes": N, "solids": len(sc["solids"]),
+                   "l2": f"inputs larger than L2 (population planes {2 * 9 * N * (4 if args.precision == 'fp32' else 8) / 1e9:.2f} GB)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "kernel_ms": {"rmt_solid_kernel": kms[0], "force_kernel": kms[1], "lb_step_kernel": kms[2]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "lb_step_kernel",
+                     "peak_source": peak_kind,
+                     "bytes_model": f"N*(18*{sf} + 4*{sf}) + 3*{sf}*256*active_tiles per launch",
+                     "active_tiles": nact, "active_frac": band_frac},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="lbrmt", choices=["lbrmt", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--size", type=int, default=4096,
+                    help="grid side; below 4096 a crop of the workload with the same disk density")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-steps", type=int, default=15)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_lbrmt(args)
+
+
+if __name__ == "__main__":
+    main()

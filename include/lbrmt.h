@@ -1,0 +1,178 @@
+/*
+ * lbrmt.h -- C ABI of the GB300 (sm_103a) LBRMT time step.
+ *
+ * The lattice Boltzmann reference map technique (Sun & Rycroft, arXiv
+ * 2402.12696) couples a D2Q9 lattice Boltzmann fluid with finite-strain
+ * neo-Hookean solids tracked by a reference map on one fixed grid.  One call
+ * of lbrmt_step advances every node by Algorithm 1 of the paper:
+ *   reference-map advection (Sec. 3.1), extrapolation into a band of layers
+ *   (Sec. 3.2), relabelling with phi = phi_0(xi), divergence of the blended
+ *   solid stress with contact (Secs. 3.3, 3.6, Eq. 2_4_F_divs), SFC
+ *   equilibrium (Eq. 2_3_feq_sfc), Guo forcing (Eq. 2_2_Fi / 3_4_Fi), BGK
+ *   collision (Eq. 2_2_bgk_force), wall conditions (Sec. 3.5), streaming and
+ *   the half-force moments (Sec. 3.4).
+ *
+ * Conventions for every entry point:
+ *   - Lattice units: dx = dt = 1.  Grid node (i, j) has linear index
+ *     j * nx + i; "field" outputs are nx*ny doubles in that order.
+ *   - The library owns all simulation state.  It allocates device memory
+ *     through the config's alloc/free callbacks when they are set (the
+ *     Python binding routes them to the PyTorch caching allocator), else
+ *     with cudaMalloc.  Pointers passed by the caller stay caller-owned.
+ *   - All work is enqueued asynchronously on the CUDA stream given to
+ *     lbrmt_create.  Calls named *_host copy to/from host memory and return
+ *     after the copy completed.
+ *   - Every call returns an lbrmt_status and never aborts.  Device-side
+ *     error flags (non-finite density, registry overflow, extrapolation
+ *     failure, tile overflow) are raised asynchronously and reported by the
+ *     next lbrmt_sync, read or stats call; lbrmt_last_error() gives text.
+ *   - A sim handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef LBRMT_H
+#define LBRMT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbrmt_sim lbrmt_sim;
+
+typedef enum {
+    LBRMT_OK = 0,
+    LBRMT_ERR_ARG = -1,         /* invalid argument */
+    LBRMT_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    LBRMT_ERR_NUMERIC = -3,     /* non-finite density or velocity */
+    LBRMT_ERR_OVERFLOW = -4,    /* solids-per-tile registry or solid tile overflow */
+    LBRMT_ERR_EXTRAP = -5,      /* extrapolation window exceeded rmax or stencil left the band */
+    LBRMT_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+    LBRMT_ERR_PARAM_RANGE = -7, /* parameter outside the limits of Appendix A (1/2 < tau <= 1, ...) */
+    LBRMT_ERR_STATE = -8        /* call not valid in the current state */
+} lbrmt_status;
+
+enum { LBRMT_PERIODIC = 0, LBRMT_WALL = 1 };
+enum { LBRMT_FP32 = 0, LBRMT_FP64 = 1, LBRMT_FP16_STORE = 2, LBRMT_BF16_STORE = 3 };
+enum { LBRMT_FORCE_NONE = 0, LBRMT_FORCE_CONST = 1, LBRMT_FORCE_SINE_X = 2 };
+enum { LBRMT_SHAPE_DISK = 0 };
+
+/* Field ids for lbrmt_read_fields.  RHO/UX/UY are the moments of the current
+ * populations (Sec. 3.4); FX/FY/DRHO are the force density F of Eq. 2_4_F_divs
+ * and the density difference of Eq. 2_3_drho used by the last step; XI_X,
+ * XI_Y, PHI are the reference map (absolute reference coordinates) and level
+ * set of one solid on its solid + band nodes (NaN elsewhere); POP0 + q is the
+ * population f_q. */
+enum {
+    LBRMT_FIELD_RHO = 0, LBRMT_FIELD_UX = 1, LBRMT_FIELD_UY = 2,
+    LBRMT_FIELD_FX = 3, LBRMT_FIELD_FY = 4, LBRMT_FIELD_DRHO = 5,
+    LBRMT_FIELD_XI_X = 10, LBRMT_FIELD_XI_Y = 11, LBRMT_FIELD_PHI = 12,
+    LBRMT_FIELD_POP0 = 20
+};
+
+typedef void *(*lbrmt_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbrmt_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+    int nx, ny;                 /* grid nodes; nx, ny >= 8 */
+    int bc_x, bc_y;             /* LBRMT_PERIODIC or LBRMT_WALL (halfway bounce-back, Sec. 3.5) */
+    double tau;                 /* BGK relaxation time; 1/2 < tau <= 1 (Appendix A) */
+    double rho_f;               /* fluid density (1 in the paper) */
+    double lid_u;               /* speed of the top (y = ny-1/2) wall in +x; needs bc_y = WALL */
+    double eps;                 /* blur-zone half-width (1.5 in the paper) */
+    int n_layers;               /* extrapolation layers (11 in the paper), 1..20 */
+    double eta;                 /* contact constant of Eq. 3_6_collision_stress */
+    double gravity;             /* g >= 0 acting in -y on solids: a = (1 - rho_f/rho_s) g (Sec. 4.3) */
+    int force_kind;             /* LBRMT_FORCE_*: body force on all phases */
+    double force_a[2];          /* (fx, fy) for CONST, (A, 0) for f_x = A sin(2 pi y / ny) */
+    int precision;              /* LBRMT_FP32, LBRMT_FP64 (FP16/BF16 storage: reserved) */
+    int max_solids_per_tile;    /* registry slots per 32x8 tile, 1..8 */
+    int rmax;                   /* largest extrapolation window half-width (>= 2) */
+    lbrmt_alloc_fn alloc;       /* optional device allocator */
+    lbrmt_free_fn free;
+    void *alloc_ctx;
+} lbrmt_config;
+
+/* Fill a config with the paper's defaults (eps 1.5, 11 layers, rho_f 1,
+ * eta 1, tau 1, periodic 64x64, FP32, 8 slots, rmax 11). */
+void lbrmt_default_config(lbrmt_config *cfg);
+
+/* Create a simulation on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream; then no CUDA graph is used).
+ * Checks the Appendix A limit 1/2 < tau <= 1 (LBRMT_ERR_PARAM_RANGE). */
+lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream, lbrmt_sim **out);
+
+/* Add a solid before the first step (Sec. 3.6: material and shape per
+ * object).  shape = LBRMT_SHAPE_DISK: level set phi_0(X) = |X - c| - radius
+ * (phi < 0 inside, Sec. 2.4); (cx, cy) in lattice units, rho_s > 0, G >= 0
+ * the small-strain shear modulus of Eq. 2_4_solid_const.  Returns the solid
+ * id (0, 1, ...) in *solid_id_out (may be NULL). */
+lbrmt_status lbrmt_add_solid(lbrmt_sim *sim, int shape, double cx, double cy, double radius,
+                             double rho_s, double G, int *solid_id_out);
+
+/* Initialise (Algorithm 1, initialisation): xi = x on each solid and its
+ * band, phi = phi_0(xi), rho = rho_t, v = 0, f = f^eq,SFC(rho_t, 0).  Called
+ * implicitly by the first step or read; allocates the solid tiles. */
+lbrmt_status lbrmt_init(lbrmt_sim *sim);
+
+/* Advance nsteps >= 0 time steps of Algorithm 1 (asynchronous). */
+lbrmt_status lbrmt_step(lbrmt_sim *sim, int nsteps);
+
+/* Write one field (ids above) as nx*ny doubles to the device buffer dev_out
+ * (caller-owned, nx*ny*8 bytes).  solid_id selects the solid for XI_X, XI_Y
+ * and PHI; sim_index must be 0. */
+lbrmt_status lbrmt_read_fields(lbrmt_sim *sim, int sim_index, int field, int solid_id,
+                               double *dev_out);
+
+/* Same as lbrmt_read_fields but into host memory (nx*ny doubles). */
+lbrmt_status lbrmt_read_fields_host(lbrmt_sim *sim, int sim_index, int field, int solid_id,
+                                    double *host_out);
+
+/* Overwrite the populations from host memory (9 planes of nx*ny doubles,
+ * plane q = f_q) and reset the stored half-force to zero. */
+lbrmt_status lbrmt_set_populations_host(lbrmt_sim *sim, const double *host_f);
+
+/* Per-solid FP64 statistics of the current state, S x 8 doubles into host
+ * memory: lambda-weighted area sum, centroid x, centroid y (unwrapped frame),
+ * mass sum(lambda rho), momentum sum(lambda rho u), sum(lambda rho v), and
+ * two reserved zeros; lambda = 1 - H_eps(phi) on domain nodes. */
+lbrmt_status lbrmt_solid_stats(lbrmt_sim *sim, int sim_index, double *host_out);
+
+/* Total mass sum_x rho over the domain after the last step (FP64, fixed
+ * summation order), into host memory. */
+lbrmt_status lbrmt_total_mass(lbrmt_sim *sim, int sim_index, double *host_out);
+
+/* Number of 32x8 tiles that the last step registered for the stress/force
+ * kernel (tiles touched by a blur zone), into host memory; 0 before the
+ * first step. */
+lbrmt_status lbrmt_active_tiles(lbrmt_sim *sim, int sim_index, long long *host_out);
+
+/* Wait for the stream and turn device error flags into a status. */
+lbrmt_status lbrmt_sync(lbrmt_sim *sim);
+
+/* Number of time steps taken, number of solids, kernel launches issued by
+ * the last lbrmt_step call (graph launches count their kernels). */
+long long lbrmt_steps_done(const lbrmt_sim *sim);
+int lbrmt_num_solids(const lbrmt_sim *sim);
+long long lbrmt_last_launch_count(const lbrmt_sim *sim);
+
+/* Advance nsteps >= 1 steps with direct launches and a CUDA event around
+ * every kernel (on the simulation's stream), then wait.  ms_out[k] receives
+ * the mean duration in milliseconds of kernel k of a step: 0 = reference-map
+ * kernel (advect, extrapolate, relabel), 1 = stress/force kernel, 2 = fused
+ * lattice Boltzmann kernel (host array of 3 floats; 0 where not launched). */
+lbrmt_status lbrmt_step_timed(lbrmt_sim *sim, int nsteps, float *ms_out);
+
+/* Use (1) or bypass (0) CUDA graphs for lbrmt_step; default 1. */
+lbrmt_status lbrmt_set_use_graphs(lbrmt_sim *sim, int enable);
+
+/* Text of the last error on this handle ("" if none). */
+const char *lbrmt_last_error(const lbrmt_sim *sim);
+
+/* Free the handle and all device memory it owns. */
+void lbrmt_destroy(lbrmt_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBRMT_H */

@@ -1,0 +1,306 @@
+"""Thin Python binding of the GB300 LBRMT library (C ABI of include/lbrmt.h).
+
+Every step of the time step runs in the CUDA kernels of ``liblbrmt.so``; this
+module only marshals arguments.  PyTorch supplies device memory (through the
+allocator callbacks of ``lbrmt_config``) and the CUDA stream.  There is no CPU
+fallback: importing the library on a machine where ``liblbrmt.so`` is missing
+or cannot be loaded raises.
+
+The module-level functions carry the C names (``lbrmt_create``,
+``lbrmt_add_solid``, ``lbrmt_step``, ``lbrmt_read_fields``, ...); the
+``Simulation`` class builds one simulation from a scenario dict of the
+``scenarios`` module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbrmt.so")
+
+LBRMT_OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NUMERIC", -4: "ERR_OVERFLOW",
+          -5: "ERR_EXTRAP", -6: "ERR_TIMEOUT", -7: "ERR_PARAM_RANGE", -8: "ERR_STATE"}
+PRECISION = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
+FIELDS = {"rho": 0, "ux": 1, "uy": 2, "Fx": 3, "Fy": 4, "drho": 5,
+          "xi_x": 10, "xi_y": 11, "phi": 12}
+EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_init", "lbrmt_step",
+           "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
+           "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
+           "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs",
+           "lbrmt_last_error", "lbrmt_destroy"]
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class lbrmt_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("bc_x", C.c_int), ("bc_y", C.c_int),
+                ("tau", C.c_double), ("rho_f", C.c_double), ("lid_u", C.c_double),
+                ("eps", C.c_double), ("n_layers", C.c_int), ("eta", C.c_double),
+                ("gravity", C.c_double), ("force_kind", C.c_int), ("force_a", C.c_double * 2),
+                ("precision", C.c_int), ("max_solids_per_tile", C.c_int), ("rmax", C.c_int),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class LbrmtError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load liblbrmt.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"liblbrmt.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    p, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    cfgp = C.POINTER(lbrmt_config)
+    L.lbrmt_default_config.argtypes = [cfgp]
+    L.lbrmt_default_config.restype = None
+    L.lbrmt_create.argtypes = [cfgp, p, C.POINTER(p)]
+    L.lbrmt_add_solid.argtypes = [p, i, d, d, d, d, d, C.POINTER(i)]
+    L.lbrmt_init.argtypes = [p]
+    L.lbrmt_step.argtypes = [p, i]
+    L.lbrmt_read_fields.argtypes = [p, i, i, i, p]
+    L.lbrmt_read_fields_host.argtypes = [p, i, i, i, p]
+    L.lbrmt_set_populations_host.argtypes = [p, p]
+    L.lbrmt_solid_stats.argtypes = [p, i, p]
+    L.lbrmt_total_mass.argtypes = [p, i, p]
+    L.lbrmt_sync.argtypes = [p]
+    L.lbrmt_active_tiles.argtypes = [p, i, C.POINTER(ll)]
+    L.lbrmt_step_timed.argtypes = [p, i, C.POINTER(C.c_float)]
+    L.lbrmt_steps_done.argtypes = [p]
+    L.lbrmt_steps_done.restype = ll
+    L.lbrmt_num_solids.argtypes = [p]
+    L.lbrmt_last_launch_count.argtypes = [p]
+    L.lbrmt_last_launch_count.restype = ll
+    L.lbrmt_set_use_graphs.argtypes = [p, i]
+    L.lbrmt_last_error.argtypes = [p]
+    L.lbrmt_last_error.restype = C.c_char_p
+    L.lbrmt_destroy.argtypes = [p]
+    L.lbrmt_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(h, st):
+    if st != LBRMT_OK:
+        msg = load().lbrmt_last_error(h).decode() if h else ""
+        raise LbrmtError(st, msg)
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers (argument marshalling only)
+# ---------------------------------------------------------------------------
+
+def lbrmt_default_config():
+    cfg = lbrmt_config()
+    load().lbrmt_default_config(C.byref(cfg))
+    return cfg
+
+
+def lbrmt_create(cfg, stream_ptr):
+    h = C.c_void_p()
+    _check(None, load().lbrmt_create(C.byref(cfg), C.c_void_p(stream_ptr), C.byref(h)))
+    return h
+
+
+def lbrmt_add_solid(h, shape, cx, cy, radius, rho_s, G):
+    sid = C.c_int()
+    _check(h, load().lbrmt_add_solid(h, shape, cx, cy, radius, rho_s, G, C.byref(sid)))
+    return sid.value
+
+
+def lbrmt_init(h):
+    _check(h, load().lbrmt_init(h))
+
+
+def lbrmt_step(h, nsteps):
+    _check(h, load().lbrmt_step(h, int(nsteps)))
+
+
+def lbrmt_read_fields(h, sim_index, field, solid_id, dev_ptr):
+    _check(h, load().lbrmt_read_fields(h, sim_index, field, solid_id, C.c_void_p(dev_ptr)))
+
+
+def lbrmt_read_fields_host(h, sim_index, field, solid_id, host_ptr):
+    _check(h, load().lbrmt_read_fields_host(h, sim_index, field, solid_id, C.c_void_p(host_ptr)))
+
+
+def lbrmt_set_populations_host(h, host_ptr):
+    _check(h, load().lbrmt_set_populations_host(h, C.c_void_p(host_ptr)))
+
+
+def lbrmt_solid_stats(h, sim_index, host_ptr):
+    _check(h, load().lbrmt_solid_stats(h, sim_index, C.c_void_p(host_ptr)))
+
+
+def lbrmt_total_mass(h, sim_index, host_ptr):
+    _check(h, load().lbrmt_total_mass(h, sim_index, C.c_void_p(host_ptr)))
+
+
+def lbrmt_sync(h):
+    _check(h, load().lbrmt_sync(h))
+
+
+def lbrmt_active_tiles(h, sim_index):
+    n = C.c_longlong()
+    _check(h, load().lbrmt_active_tiles(h, sim_index, C.byref(n)))
+    return n.value
+
+
+def lbrmt_step_timed(h, nsteps):
+    ms = (C.c_float * 3)()
+    _check(h, load().lbrmt_step_timed(h, int(nsteps), ms))
+    return [ms[0], ms[1], ms[2]]
+
+
+def lbrmt_destroy(h):
+    load().lbrmt_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Convenience class
+# ---------------------------------------------------------------------------
+
+class _TorchAllocator:
+    """Routes the library's device allocations to the PyTorch caching allocator."""
+
+    def __init__(self, torch, device, stream):
+        self.torch, self.device, self.stream = torch, device, stream
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            with self.torch.cuda.stream(self.stream):
+                t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        ptr = t.data_ptr()
+        self.live[ptr] = t
+        return ptr
+
+    def _free(self, ptr, ctx):
+        self.live.pop(ptr, None)
+
+
+class Simulation:
+    """One LBRMT simulation on a CUDA device, built from a scenario dict."""
+
+    def __init__(self, sc, precision="fp32", device="cuda:0", stream=None, use_graphs=True,
+                 max_solids_per_tile=8, rmax=11):
+        import torch
+        self.torch = torch
+        self.sc = sc
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.nx, self.ny = sc["nx"], sc["ny"]
+        self.nsolids = len(sc["solids"])
+        cfg = lbrmt_default_config()
+        cfg.nx, cfg.ny = sc["nx"], sc["ny"]
+        cfg.bc_x, cfg.bc_y = sc["wall_x"], sc["wall_y"]
+        cfg.tau, cfg.rho_f, cfg.lid_u = sc["tau"], sc["rho_f"], sc["lid_u"]
+        cfg.eps, cfg.n_layers, cfg.eta = sc["eps"], sc["n_layers"], sc["eta"]
+        cfg.gravity, cfg.force_kind = sc["gravity"], sc["force_kind"]
+        fa = sc.get("force_a", [0.0, 0.0])
+        cfg.force_a[0], cfg.force_a[1] = fa[0], fa[1]
+        cfg.precision = PRECISION[precision]
+        cfg.max_solids_per_tile = max_solids_per_tile
+        cfg.rmax = rmax
+        self._alloc = _TorchAllocator(torch, self.device, self.stream)
+        cfg.alloc = self._alloc.alloc_cb
+        cfg.free = self._alloc.free_cb
+        self._cfg = cfg
+        with torch.cuda.device(self.device):
+            self.h = lbrmt_create(cfg, self.stream.cuda_stream)
+            load().lbrmt_set_use_graphs(self.h, int(bool(use_graphs)))
+            for s in sc["solids"]:
+                lbrmt_add_solid(self.h, 0, s["x"], s["y"], s["r"], s["rho_s"], s["G"])
+
+    # -- time stepping ------------------------------------------------------
+    def init(self):
+        with self.torch.cuda.device(self.device):
+            lbrmt_init(self.h)
+
+    def step(self, n=1):
+        with self.torch.cuda.device(self.device):
+            lbrmt_step(self.h, n)
+
+    def sync(self):
+        lbrmt_sync(self.h)
+
+    def active_tiles(self):
+        return lbrmt_active_tiles(self.h, 0)
+
+    def step_timed(self, n):
+        """Run n steps with per-kernel CUDA events; mean ms of [K2, K3, K1]."""
+        with self.torch.cuda.device(self.device):
+            return lbrmt_step_timed(self.h, n)
+
+    @property
+    def steps_done(self):
+        return load().lbrmt_steps_done(self.h)
+
+    @property
+    def last_launch_count(self):
+        return load().lbrmt_last_launch_count(self.h)
+
+    # -- outputs ------------------------------------------------------------
+    def field(self, name, solid=0):
+        """Device tensor (float64, [ny, nx]) of one field."""
+        torch = self.torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            out = torch.empty(self.ny * self.nx, dtype=torch.float64, device=self.device)
+            fid = FIELDS[name] if isinstance(name, str) else int(name)
+            lbrmt_read_fields(self.h, 0, fid, solid, out.data_ptr())
+        return out.view(self.ny, self.nx)
+
+    def field_host(self, name, solid=0):
+        out = np.empty(self.ny * self.nx, dtype=np.float64)
+        fid = FIELDS[name] if isinstance(name, str) else int(name)
+        with self.torch.cuda.device(self.device):
+            lbrmt_read_fields_host(self.h, 0, fid, solid, out.ctypes.data)
+        return out.reshape(self.ny, self.nx)
+
+    def populations_host(self):
+        return np.stack([self.field_host(20 + q) for q in range(9)])
+
+    def set_populations_host(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        with self.torch.cuda.device(self.device):
+            lbrmt_set_populations_host(self.h, f.ctypes.data)
+
+    def solid_stats(self):
+        out = np.zeros((max(self.nsolids, 1), 8))
+        with self.torch.cuda.device(self.device):
+            lbrmt_solid_stats(self.h, 0, out.ctypes.data)
+        return out[: self.nsolids]
+
+    def total_mass(self):
+        out = np.zeros(1)
+        with self.torch.cuda.device(self.device):
+            lbrmt_total_mass(self.h, 0, out.ctypes.data)
+        return float(out[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbrmt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,490 @@
+// lbrmt_api.cu -- host runtime behind the C ABI of include/lbrmt.h.
+//
+// Owns the device state of one simulation, builds the solid tiles at
+// initialisation, enqueues the three kernels of a step on the caller's stream
+// and replays them through a two-step CUDA graph (the state is double-buffered
+// by step parity, so steps 2k and 2k+1 form a fixed launch sequence).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbrmt.h"
+#include "lbrmt_engine.cuh"
+
+using namespace lbrmt;
+
+namespace lbrmt {
+__global__ void mass_reduce_kernel(const double *partials, int n, double base, double *out) {
+    __shared__ double sh[1024];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = base + sh[0];
+}
+}  // namespace lbrmt
+
+struct SolidHost {
+    double xc, yc, R, rho_s, G;
+    int T;
+    long long off;
+};
+
+struct lbrmt_sim {
+    lbrmt_config cfg;
+    cudaStream_t stream = nullptr;
+    SimParams sp;
+    const EngineOps *eng = nullptr;
+    LaunchInfo li;
+    DevState d;
+    std::vector<SolidHost> solids;
+    bool inited = false;
+    long long steps = 0;
+    bool use_graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    long long last_launches = 0;
+    std::vector<void *> allocs;
+    double *scratch = nullptr;      // device: S*8 stats or 1 mass value
+    double *staging = nullptr;      // device: 9*P doubles for set_populations
+    std::string err;
+};
+
+static lbrmt_status fail(lbrmt_sim *s, lbrmt_status st, const std::string &msg) {
+    if (s) s->err = msg;
+    return st;
+}
+
+static lbrmt_status cuda_fail(lbrmt_sim *s, cudaError_t e, const char *where) {
+    return fail(s, LBRMT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static void *dalloc(lbrmt_sim *s, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (s->cfg.alloc) p = s->cfg.alloc(bytes, s->cfg.alloc_ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) s->allocs.push_back(p);
+    return p;
+}
+
+static void dfree_all(lbrmt_sim *s) {
+    for (void *p : s->allocs) {
+        if (s->cfg.free) s->cfg.free(p, s->cfg.alloc_ctx);
+        else cudaFree(p);
+    }
+    s->allocs.clear();
+}
+
+extern "C" void lbrmt_default_config(lbrmt_config *c) {
+    std::memset(c, 0, sizeof(*c));
+    c->nx = 64; c->ny = 64;
+    c->bc_x = LBRMT_PERIODIC; c->bc_y = LBRMT_PERIODIC;
+    c->tau = 1.0; c->rho_f = 1.0; c->lid_u = 0.0;
+    c->eps = 1.5; c->n_layers = 11; c->eta = 1.0;
+    c->gravity = 0.0; c->force_kind = LBRMT_FORCE_NONE;
+    c->precision = LBRMT_FP32;
+    c->max_solids_per_tile = KMAX;
+    c->rmax = 11;
+}
+
+extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream, lbrmt_sim **out) {
+    if (!cfg || !out) return LBRMT_ERR_ARG;
+    *out = nullptr;
+    const lbrmt_config &c = *cfg;
+    if (c.nx < 8 || c.ny < 8 || (long long)c.nx * c.ny > (1ll << 31)) return LBRMT_ERR_ARG;
+    if ((c.bc_x != 0 && c.bc_x != 1) || (c.bc_y != 0 && c.bc_y != 1)) return LBRMT_ERR_ARG;
+    if (!(c.tau > 0.5 && c.tau <= 1.0)) return LBRMT_ERR_PARAM_RANGE;  // Appendix A
+    if (!(c.rho_f > 0) || !(c.eps > 0) || c.n_layers < 1 || c.n_layers > 20) return LBRMT_ERR_ARG;
+    if (c.max_solids_per_tile < 1 || c.max_solids_per_tile > KMAX || c.rmax < 2 || c.rmax > 20) return LBRMT_ERR_ARG;
+    if (c.lid_u != 0.0 && c.bc_y != LBRMT_WALL) return LBRMT_ERR_ARG;
+    if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > 2) return LBRMT_ERR_ARG;
+    if (c.precision != LBRMT_FP32 && c.precision != LBRMT_FP64) return LBRMT_ERR_ARG;
+    if (std::fabs(c.lid_u) / std::sqrt(1.0 / 3.0) > 0.3) return LBRMT_ERR_PARAM_RANGE;  // Ma* <= 0.3
+
+    lbrmt_sim *s = new lbrmt_sim();
+    s->cfg = c;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->eng = c.precision == LBRMT_FP64 ? &engine_fp64 : &engine_fp32;
+    SimParams &sp = s->sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.nx = c.nx; sp.ny = c.ny; sp.wall_x = c.bc_x; sp.wall_y = c.bc_y;
+    sp.ntx = (c.nx + TILE_X - 1) / TILE_X;
+    sp.nty = (c.ny + TILE_Y - 1) / TILE_Y;
+    sp.P = (long long)c.nx * c.ny;
+    sp.tau = c.tau; sp.rho_f = c.rho_f; sp.lid_u = c.lid_u; sp.eps = c.eps; sp.eta = c.eta;
+    sp.gravity = c.gravity; sp.force_kind = c.force_kind; sp.fa0 = c.force_a[0]; sp.fa1 = c.force_a[1];
+    sp.n_layers = c.n_layers; sp.rmax = c.rmax; sp.kmax = c.max_solids_per_tile; sp.nsolids = 0;
+
+    const size_t P = (size_t)sp.P, ntiles = (size_t)sp.ntx * sp.nty;
+    const size_t rs = s->eng->real_size, ss = s->eng->store_size;
+    DevState &d = s->d;
+    std::memset(&d, 0, sizeof(d));
+    bool ok = true;
+    for (int k = 0; k < 2; k++) {
+        ok = ok && (d.f[k] = dalloc(s, 9 * P * ss));
+        ok = ok && (d.reg_count[k] = (int *)dalloc(s, ntiles * 4));
+        ok = ok && (d.reg_solids[k] = (int *)dalloc(s, ntiles * KMAX * 4));
+        ok = ok && (d.reg_active[k] = (int *)dalloc(s, ntiles * 4));
+        ok = ok && (d.reg_nactive[k] = (int *)dalloc(s, 16));
+        ok = ok && (d.pool[k] = dalloc(s, ntiles * POOL_STRIDE * rs));
+    }
+    ok = ok && (d.carry = dalloc(s, 2 * P * rs));
+    ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
+    ok = ok && (d.mass_partials = (double *)dalloc(s, ntiles * TILE_Y * 8));
+    ok = ok && (d.err = (unsigned *)dalloc(s, 16));
+    ok = ok && (s->scratch = (double *)dalloc(s, 64));
+    if (!ok) {
+        dfree_all(s);
+        delete s;
+        return LBRMT_ERR_CUDA;
+    }
+    cudaStream_t st = s->stream;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaMemsetAsync(d.reg_count[k], 0, ntiles * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[k], 0, 16, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.pool[k], 0, ntiles * POOL_STRIDE * rs, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, ntiles * TILE_Y * 8, st);
+    // body force per row (x component), Sec. 4 forcing on all phases
+    std::vector<double> fb(c.ny, 0.0);
+    for (int j = 0; j < c.ny; j++) {
+        if (c.force_kind == LBRMT_FORCE_CONST) fb[j] = c.force_a[0];
+        else if (c.force_kind == LBRMT_FORCE_SINE_X) fb[j] = c.force_a[0] * std::sin(2.0 * M_PI * j / c.ny);
+    }
+    if (e == cudaSuccess) {
+        if (rs == 4) {
+            std::vector<float> f32(fb.begin(), fb.end());
+            e = cudaMemcpy(d.fbody, f32.data(), c.ny * 4, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(d.fbody, fb.data(), c.ny * 8, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) {
+        dfree_all(s);
+        delete s;
+        return LBRMT_ERR_CUDA;
+    }
+    *out = s;
+    return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_add_solid(lbrmt_sim *s, int shape, double cx, double cy, double radius,
+                                        double rho_s, double G, int *id_out) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (s->inited) return fail(s, LBRMT_ERR_STATE, "solids must be added before the first step");
+    if (shape != LBRMT_SHAPE_DISK) return fail(s, LBRMT_ERR_ARG, "only disks are supported");
+    if (!(radius >= 1.0) || !(rho_s > 0) || !(G >= 0) || !std::isfinite(cx) || !std::isfinite(cy))
+        return fail(s, LBRMT_ERR_ARG, "bad solid parameters");
+    const int margin = 4 + (int)std::ceil(radius / 4.0);
+    int T = 2 * (int)std::ceil(radius) + 2 * (s->cfg.n_layers + margin) + 1;
+    T = (T + 7) & ~7;
+    if (T > 240) return fail(s, LBRMT_ERR_ARG, "solid too large for a tile");
+    if ((!s->cfg.bc_x && T >= s->cfg.nx) || (!s->cfg.bc_y && T >= s->cfg.ny))
+        return fail(s, LBRMT_ERR_ARG, "solid tile wider than the periodic domain");
+    SolidHost h{cx, cy, radius, rho_s, G, T, 0};
+    s->solids.push_back(h);
+    if (id_out) *id_out = (int)s->solids.size() - 1;
+    return LBRMT_OK;
+}
+
+static lbrmt_status check_flags(lbrmt_sim *s) {
+    unsigned h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream");
+    e = cudaMemcpy(h, s->d.err, 16, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "error flags");
+    const unsigned f = h[0];
+    if (!f) return LBRMT_OK;
+    if (f & ERR_NAN) return fail(s, LBRMT_ERR_NUMERIC, "non-finite density or velocity");
+    if (f & ERR_SLOT_OVERFLOW) return fail(s, LBRMT_ERR_OVERFLOW, "more solids on a 32x8 tile than max_solids_per_tile");
+    if (f & ERR_TILE_OVERFLOW) return fail(s, LBRMT_ERR_OVERFLOW, "a solid's band outgrew its tile");
+    if (f & ERR_EXTRAP) return fail(s, LBRMT_ERR_EXTRAP, "extrapolation window exceeded rmax");
+    if (f & ERR_STENCIL) return fail(s, LBRMT_ERR_EXTRAP, "advection stencil left the band");
+    if (f & ERR_SINGULAR) return fail(s, LBRMT_ERR_NUMERIC, "singular reference-map Jacobian");
+    return fail(s, LBRMT_ERR_NUMERIC, "device error flag");
+}
+
+extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (s->inited) return LBRMT_OK;
+    const int S = (int)s->solids.size();
+    s->sp.nsolids = S;
+    DevState &d = s->d;
+    long long total = 0;
+    int tmax = 8;
+    for (auto &h : s->solids) {
+        h.off = total;
+        total += 2ll * h.T * h.T;
+        tmax = std::max(tmax, h.T);
+    }
+    const size_t rs = s->eng->real_size;
+    bool ok = true;
+    for (int k = 0; k < 2; k++) {
+        ok = ok && (d.xi[k] = dalloc(s, (size_t)total * rs));
+        ok = ok && (d.origin[k] = (int2 *)dalloc(s, (size_t)S * sizeof(int2)));
+    }
+    ok = ok && (d.solids = (SolidDesc *)dalloc(s, (size_t)S * sizeof(SolidDesc)));
+    ok = ok && (d.stats_step = (double *)dalloc(s, (size_t)S * 64));
+    if (S > 1) {
+        double *sc = (double *)dalloc(s, (size_t)S * 64);
+        ok = ok && sc;
+        s->scratch = sc;
+    }
+    if (!ok) return fail(s, LBRMT_ERR_CUDA, "out of device memory for the solid tiles");
+    std::vector<SolidDesc> sd(S);
+    std::vector<int2> org(S);
+    for (int k = 0; k < S; k++) {
+        const SolidHost &h = s->solids[k];
+        org[k].x = (int)std::floor(h.xc) - h.T / 2;
+        org[k].y = (int)std::floor(h.yc) - h.T / 2;
+        sd[k].xc = h.xc; sd[k].yc = h.yc; sd[k].R = h.R; sd[k].rho_s = h.rho_s; sd[k].G = h.G;
+        sd[k].o0x = org[k].x; sd[k].o0y = org[k].y;
+        sd[k].offx = (double)org[k].x - h.xc; sd[k].offy = (double)org[k].y - h.yc;
+        sd[k].T = h.T; sd[k].pad = 0; sd[k].off = h.off;
+    }
+    cudaError_t e = cudaSuccess;
+    if (S > 0) {
+        e = cudaMemcpy(d.solids, sd.data(), S * sizeof(SolidDesc), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d.origin[0], org.data(), S * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d.origin[1], org.data(), S * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.stats_step, 0, (size_t)S * 64, s->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "upload solids");
+    e = s->eng->configure(s->sp, tmax, &s->li);
+    if (e != cudaSuccess) return cuda_fail(s, e, "configure kernels");
+    e = s->eng->init(s->sp, d, s->li, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "init kernels");
+    const size_t ntiles = (size_t)s->sp.ntx * s->sp.nty;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaMemsetAsync(d.reg_count[k], 0, ntiles * 4, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[k], 0, 16, s->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "clear registry");
+    s->inited = true;
+    s->steps = 0;
+    return check_flags(s);
+}
+
+static lbrmt_status direct_step(lbrmt_sim *s) {
+    cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    s->steps++;
+    s->last_launches += s->sp.nsolids > 0 ? 3 : 1;
+    return LBRMT_OK;
+}
+
+static lbrmt_status build_graph(lbrmt_sim *s) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
+    cudaError_t e0 = s->eng->step(s->sp, s->d, s->li, 0, s->stream, nullptr);
+    cudaError_t e1 = s->eng->step(s->sp, s->d, s->li, 1, s->stream, nullptr);
+    e = cudaStreamEndCapture(s->stream, &g);
+    if (e0 != cudaSuccess) e = e0;
+    if (e1 != cudaSuccess) e = e1;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(s, e, "capture");
+    }
+    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->gexec = nullptr;
+        return cuda_fail(s, e, "instantiate graph");
+    }
+    return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_step(lbrmt_sim *s, int nsteps) {
+    if (!s || nsteps < 0) return LBRMT_ERR_ARG;
+    if (!s->inited) {
+        lbrmt_status st = lbrmt_init(s);
+        if (st != LBRMT_OK) return st;
+    }
+    s->last_launches = 0;
+    int left = nsteps;
+    const bool graphs = s->use_graphs && s->stream != nullptr && nsteps >= 2;
+    if (graphs) {
+        if (s->steps & 1) {
+            lbrmt_status st = direct_step(s);
+            if (st != LBRMT_OK) return st;
+            left--;
+        }
+        if (left >= 2 && !s->gexec) {
+            lbrmt_status st = build_graph(s);
+            if (st != LBRMT_OK) return st;
+        }
+        while (left >= 2) {
+            cudaError_t e = cudaGraphLaunch(s->gexec, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
+            s->steps += 2;
+            s->last_launches += s->sp.nsolids > 0 ? 6 : 2;
+            left -= 2;
+        }
+    }
+    while (left > 0) {
+        lbrmt_status st = direct_step(s);
+        if (st != LBRMT_OK) return st;
+        left--;
+    }
+    return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_step_timed(lbrmt_sim *s, int nsteps, float *ms_out) {
+    if (!s || nsteps < 1 || !ms_out) return LBRMT_ERR_ARG;
+    if (!s->inited) {
+        lbrmt_status st = lbrmt_init(s);
+        if (st != LBRMT_OK) return st;
+    }
+    std::vector<cudaEvent_t> ev(4 * (size_t)nsteps, nullptr);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(s, LBRMT_ERR_CUDA, "event create");
+    s->last_launches = 0;
+    lbrmt_status status = LBRMT_OK;
+    for (int n = 0; n < nsteps; n++) {
+        cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, &ev[4 * (size_t)n]);
+        if (e != cudaSuccess) { status = cuda_fail(s, e, "timed step"); break; }
+        s->steps++;
+        s->last_launches += s->sp.nsolids > 0 ? 3 : 1;
+    }
+    double acc[3] = {0, 0, 0};
+    if (status == LBRMT_OK) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) status = cuda_fail(s, e, "timed sync");
+        for (int n = 0; n < nsteps && status == LBRMT_OK; n++)
+            for (int k = 0; k < 3; k++) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[4 * (size_t)n + k], ev[4 * (size_t)n + k + 1]);
+                acc[k] += ms;
+            }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < 3; k++) ms_out[k] = (float)(acc[k] / nsteps);
+    if (status != LBRMT_OK) return status;
+    return check_flags(s);
+}
+
+static bool field_ok(int f) { return (f >= 0 && f <= 5) || (f >= 10 && f <= 12) || (f >= 20 && f < 29); }
+
+extern "C" lbrmt_status lbrmt_read_fields(lbrmt_sim *s, int sim_index, int field, int solid_id, double *dev_out) {
+    if (!s || !dev_out || sim_index != 0 || !field_ok(field)) return LBRMT_ERR_ARG;
+    if (!s->inited) {
+        lbrmt_status st = lbrmt_init(s);
+        if (st != LBRMT_OK) return st;
+    }
+    const int cur = (int)(s->steps & 1);
+    const int lastreg = s->steps > 0 ? 1 - cur : -1;
+    if (field >= 10 && field <= 12) {
+        if (solid_id < 0 || solid_id >= (int)s->solids.size()) return fail(s, LBRMT_ERR_ARG, "bad solid id");
+        cudaError_t e = cudaMemsetAsync(dev_out, 0xFF, (size_t)s->sp.P * 8, s->stream);  // NaN
+        if (e != cudaSuccess) return cuda_fail(s, e, "clear field");
+    }
+    cudaError_t e = s->eng->field(s->sp, s->d, cur, lastreg, field, solid_id, dev_out, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "field kernel");
+    return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_read_fields_host(lbrmt_sim *s, int sim_index, int field, int solid_id,
+                                               double *host_out) {
+    if (!s || !host_out) return LBRMT_ERR_ARG;
+    if (!s->staging) {
+        s->staging = (double *)dalloc(s, (size_t)9 * s->sp.P * 8);
+        if (!s->staging) return fail(s, LBRMT_ERR_CUDA, "out of device memory");
+    }
+    lbrmt_status st = lbrmt_read_fields(s, sim_index, field, solid_id, s->staging);
+    if (st != LBRMT_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(host_out, s->staging, (size_t)s->sp.P * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy field");
+    return check_flags(s);
+}
+
+extern "C" lbrmt_status lbrmt_set_populations_host(lbrmt_sim *s, const double *host_f) {
+    if (!s || !host_f) return LBRMT_ERR_ARG;
+    if (!s->inited) {
+        lbrmt_status st = lbrmt_init(s);
+        if (st != LBRMT_OK) return st;
+    }
+    if (!s->staging) {
+        s->staging = (double *)dalloc(s, (size_t)9 * s->sp.P * 8);
+        if (!s->staging) return fail(s, LBRMT_ERR_CUDA, "out of device memory");
+    }
+    cudaError_t e = cudaMemcpyAsync(s->staging, host_f, (size_t)9 * s->sp.P * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy populations");
+    e = s->eng->set_pop(s->sp, s->d, (int)(s->steps & 1), s->staging, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set populations");
+    return check_flags(s);
+}
+
+extern "C" lbrmt_status lbrmt_solid_stats(lbrmt_sim *s, int sim_index, double *host_out) {
+    if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
+    if (!s->inited) {
+        lbrmt_status st = lbrmt_init(s);
+        if (st != LBRMT_OK) return st;
+    }
+    const int S = (int)s->solids.size();
+    if (S == 0) return LBRMT_OK;
+    cudaError_t e = s->eng->stats(s->sp, s->d, (int)(s->steps & 1), s->scratch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stats kernel");
+    e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * 64, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy stats");
+    return check_flags(s);
+}
+
+extern "C" lbrmt_status lbrmt_total_mass(lbrmt_sim *s, int sim_index, double *host_out) {
+    if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
+    if (s->steps == 0) return fail(s, LBRMT_ERR_STATE, "total mass is recorded by the first step");
+    const int n = s->sp.ntx * s->sp.nty * TILE_Y;
+    mass_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d.mass_partials, n, s->sp.rho_f * (double)s->sp.P, s->scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "mass kernel");
+    e = cudaMemcpyAsync(host_out, s->scratch, 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy mass");
+    return check_flags(s);
+}
+
+extern "C" lbrmt_status lbrmt_active_tiles(lbrmt_sim *s, int sim_index, long long *host_out) {
+    if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
+    *host_out = 0;
+    if (s->steps == 0 || s->sp.nsolids == 0) return LBRMT_OK;
+    const int r = 1 - (int)(s->steps & 1);
+    int n = 0;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&n, s->d.reg_nactive[r], 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "active tiles");
+    *host_out = n;
+    return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_sync(lbrmt_sim *s) {
+    if (!s) return LBRMT_ERR_ARG;
+    return check_flags(s);
+}
+
+extern "C" long long lbrmt_steps_done(const lbrmt_sim *s) { return s ? s->steps : -1; }
+extern "C" int lbrmt_num_solids(const lbrmt_sim *s) { return s ? (int)s->solids.size() : -1; }
+extern "C" long long lbrmt_last_launch_count(const lbrmt_sim *s) { return s ? s->last_launches : -1; }
+
+extern "C" lbrmt_status lbrmt_set_use_graphs(lbrmt_sim *s, int enable) {
+    if (!s) return LBRMT_ERR_ARG;
+    s->use_graphs = enable != 0;
+    return LBRMT_OK;
+}
+
+extern "C" const char *lbrmt_last_error(const lbrmt_sim *s) { return s ? s->err.c_str() : "null handle"; }
+
+extern "C" void lbrmt_destroy(lbrmt_sim *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    dfree_all(s);
+    delete s;
+}

@@ -1,0 +1,183 @@
+// lbrmt_engine.cuh -- launch sequences of the LBRMT kernels for one precision.
+#pragma once
+
+#include "lbrmt_kernels.cuh"
+
+namespace lbrmt {
+
+struct LaunchInfo {
+    int tmax;            // largest solid tile side
+    int force_blocks;    // persistent grid of K3
+    int rmt_smem;        // dynamic shared memory of K2
+    int force_smem;      // dynamic shared memory of K3
+};
+
+struct EngineOps {
+    cudaError_t (*configure)(const SimParams &, int tmax, LaunchInfo *);
+    cudaError_t (*init)(const SimParams &, const DevState &, const LaunchInfo &, cudaStream_t);
+    cudaError_t (*step)(const SimParams &, const DevState &, const LaunchInfo &, int parity, cudaStream_t,
+                        cudaEvent_t *ev);
+    cudaError_t (*field)(const SimParams &, const DevState &, int cur, int lastreg, int kind, int solid,
+                         double *out, cudaStream_t);
+    cudaError_t (*stats)(const SimParams &, const DevState &, int cur, double *out, cudaStream_t);
+    cudaError_t (*set_pop)(const SimParams &, const DevState &, int cur, const double *src, cudaStream_t);
+    int real_size, store_size;
+    int launches_per_step;
+};
+
+extern const EngineOps engine_fp32;
+extern const EngineOps engine_fp64;
+
+template <class R, class S>
+__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, R *carry) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= sp.P) return;
+    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f));
+    carry[c] = 0;
+    carry[sp.P + c] = 0;
+}
+
+template <class R, class S>
+struct Engine {
+    static cudaError_t configure(const SimParams &sp, int tmax, LaunchInfo *li) {
+        li->tmax = tmax;
+        li->rmt_smem = ((tmax * tmax + 15) & ~15) + 4 * LIST_CAP;
+        li->force_smem = (3 * KMAX * PATCH_N + 3 * (NXE + NYE)) * (int)sizeof(R);
+        cudaError_t e = cudaFuncSetAttribute(rmt_solid_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             li->rmt_smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(force_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, li->force_smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, nsm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_kernel<R>, TILE_N, li->force_smem);
+        if (e != cudaSuccess) return e;
+        li->force_blocks = nsm * (per > 0 ? per : 1);
+        (void)sp;
+        return cudaSuccess;
+    }
+
+    static RmtArgs<R, S> rmt_args(const DevState &d, int parity, int init) {
+        RmtArgs<R, S> a;
+        const int p = parity, q = 1 - parity;
+        a.f = (const S *)d.f[p];
+        a.carry = (const R *)d.carry;
+        a.xi_in = (const R *)d.xi[p];
+        a.origin_in = d.origin[p];
+        if (init) {
+            a.xi_out = (R *)d.xi[0];
+            a.origin_out = d.origin[0];
+            a.origin_next = d.origin[1];
+            a.stats = nullptr;
+        } else {
+            a.xi_out = (R *)d.xi[q];
+            a.origin_out = d.origin[q];
+            a.origin_next = d.origin[p];
+            a.stats = d.stats_step;
+        }
+        const int r = init ? 0 : p;
+        a.reg_count = d.reg_count[r];
+        a.reg_solids = d.reg_solids[r];
+        a.reg_active = d.reg_active[r];
+        a.reg_nactive = d.reg_nactive[r];
+        a.solids = d.solids;
+        a.err = d.err;
+        a.init = init;
+        return a;
+    }
+
+    static ForceArgs<R> force_args(const DevState &d, int xi_idx, int r) {
+        ForceArgs<R> a;
+        a.xi = (const R *)d.xi[xi_idx];
+        a.origin = d.origin[xi_idx];
+        a.reg_count = d.reg_count[r];
+        a.reg_solids = d.reg_solids[r];
+        a.reg_active = d.reg_active[r];
+        a.reg_nactive = d.reg_nactive[r];
+        a.pool = (R *)d.pool[r];
+        a.solids = d.solids;
+        a.err = d.err;
+        return a;
+    }
+
+    static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
+        if (sp.nsolids > 0) {
+            rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, 0, 1));
+            force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 0));
+        }
+        dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
+        init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (R *)d.carry, d.reg_count[0], (const R *)d.pool[0]);
+        return cudaGetLastError();
+    }
+
+    // ev (optional): four events recorded before K2, before K3, before K1 and after K1.
+    static cudaError_t step(const SimParams &sp, const DevState &d, const LaunchInfo &li, int parity,
+                            cudaStream_t st, cudaEvent_t *ev) {
+        const int p = parity, q = 1 - parity;
+        if (ev) cudaEventRecord(ev[0], st);
+        if (sp.nsolids > 0) rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, p, 0));
+        if (ev) cudaEventRecord(ev[1], st);
+        if (sp.nsolids > 0) force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, q, p));
+        if (ev) cudaEventRecord(ev[2], st);
+        LbArgs<R, S> a;
+        a.f_in = (const S *)d.f[p];
+        a.f_out = (S *)d.f[q];
+        a.carry = (R *)d.carry;
+        a.fbody = (const R *)d.fbody;
+        a.reg_count = d.reg_count[p];
+        a.pool = (const R *)d.pool[p];
+        a.clr_count = d.reg_count[q];
+        a.clr_nactive = d.reg_nactive[q];
+        a.mass_partials = d.mass_partials;
+        a.err = d.err;
+        dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
+        lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, a);
+        if (ev) cudaEventRecord(ev[3], st);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t field(const SimParams &sp, const DevState &d, int cur, int lastreg, int kind, int solid,
+                             double *out, cudaStream_t st) {
+        dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
+        if (kind >= 10 && kind <= 12) {
+            solid_field_kernel<R><<<64, 256, 0, st>>>(sp, (const R *)d.xi[cur], d.origin[cur], d.solids, solid,
+                                                      kind - 10, out);
+            return cudaGetLastError();
+        }
+        const int r = lastreg < 0 ? 0 : lastreg;
+        static_assert(sizeof(int) == 4, "");
+        field_kernel<R, S><<<grid, blk, 0, st>>>(sp, (const S *)d.f[cur], (const R *)d.carry, (const R *)d.fbody,
+                                                 d.reg_count[r], (const R *)d.pool[r], kind, out);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t stats(const SimParams &sp, const DevState &d, int cur, double *out, cudaStream_t st) {
+        if (sp.nsolids == 0) return cudaSuccess;
+        solid_stats_kernel<R, S><<<sp.nsolids, 256, 0, st>>>(sp, (const S *)d.f[cur], (const R *)d.carry,
+                                                             (const R *)d.xi[cur], d.origin[cur], d.solids, out);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t set_pop(const SimParams &sp, const DevState &d, int cur, const double *src, cudaStream_t st) {
+        const int nb = (int)((sp.P + 255) / 256);
+        set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (R *)d.carry);
+        return cudaGetLastError();
+    }
+
+    static EngineOps ops() {
+        EngineOps o;
+        o.configure = &configure;
+        o.init = &init;
+        o.step = &step;
+        o.field = &field;
+        o.stats = &stats;
+        o.set_pop = &set_pop;
+        o.real_size = sizeof(R);
+        o.store_size = sizeof(S);
+        o.launches_per_step = 3;
+        return o;
+    }
+};
+
+}  // namespace lbrmt

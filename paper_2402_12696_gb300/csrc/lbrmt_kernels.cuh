@@ -1,0 +1,838 @@
+// lbrmt_kernels.cuh -- device code of the LBRMT time step for sm_103a.
+//
+// Three kernels make one step of Algorithm 1 (Sun & Rycroft, arXiv 2402.12696):
+//   K2 rmt_solid_kernel   one CTA per solid: advect xi (Sec. 3.1), extrapolate
+//                         it layer by layer (Sec. 3.2), relabel, register the
+//                         32x8 tiles its blur zone touches, per-solid FP64 stats.
+//   K3 force_kernel       one CTA per registered tile: half-edge Jacobians and
+//                         neo-Hookean stresses (Sec. 3.3), multi-solid blend and
+//                         contact (Sec. 3.6), divergence (Eq. 3_3_div_solid_stress),
+//                         external accelerations and the SFC density difference.
+//   K1 lb_step_kernel     one thread per node: moments with the half-force
+//                         (Sec. 3.4), SFC equilibrium (Eq. 2_3_feq_sfc), Guo
+//                         forcing (Eq. 2_2_Fi x rho), BGK collision, wall
+//                         conditions (Sec. 3.5) and push streaming, FP64 mass.
+// Populations are stored as deviations f_q - w_q rho_f in structure-of-arrays
+// planes; the reference map of each solid lives in its own moving square tile
+// in solid-local coordinates xi - X_c.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace lbrmt {
+
+constexpr int TILE_X = 32, TILE_Y = 8, TILE_N = TILE_X * TILE_Y;
+constexpr int PATCH_X = TILE_X + 2, PATCH_Y = TILE_Y + 2, PATCH_N = PATCH_X * PATCH_Y;
+constexpr int NXE = (TILE_X + 1) * TILE_Y;  // x-edges of a tile
+constexpr int NYE = TILE_X * (TILE_Y + 1);  // y-edges of a tile
+constexpr int KMAX = 8;                     // registry slots per tile (upper bound)
+constexpr int RMT_THREADS = 256;
+constexpr int LIST_CAP = 2048;              // per-layer target list in shared memory
+constexpr int POOL_STRIDE = 3 * TILE_N;     // per tile: Fx, Fy, drho planes
+// Tie rules shared with the method's definition: a node with |phi| <= PHI_TIE
+// is not solid; a directional extrapolation weight with cosine <= COS_TIE is zero.
+constexpr double PHI_TIE = 1e-9;
+constexpr double COS_TIE = 1e-9;
+
+enum ErrBits : unsigned {
+    ERR_NAN = 1u, ERR_TILE_OVERFLOW = 2u, ERR_SLOT_OVERFLOW = 4u, ERR_EXTRAP = 8u,
+    ERR_SINGULAR = 16u, ERR_STENCIL = 32u
+};
+
+// Scalar parameters, passed by value.
+struct SimParams {
+    int nx, ny, wall_x, wall_y;
+    int ntx, nty;
+    long long P;  // plane size nx*ny
+    double tau, rho_f, lid_u, eps, eta, gravity;
+    int force_kind;
+    double fa0, fa1;
+    int n_layers, rmax, kmax, nsolids;
+};
+
+struct SolidDesc {
+    double xc, yc, R, rho_s, G;
+    double offx, offy;  // o0 - X_c: initial frame origin minus the reference centre
+    int T, o0x, o0y, pad;
+    long long off;      // element offset of the tile (eta_x plane, then eta_y plane)
+};
+
+// Device pointers of one simulation (type-erased; the kernels cast).
+struct DevState {
+    void *f[2];            // 9 planes each
+    void *carry;           // 2 planes: rho^n F^n / 2 of the last collision
+    void *xi[2];           // solid tiles
+    int2 *origin[2];       // frame of xi[k] per solid
+    int *reg_count[2];     // per tile: solids registered
+    int *reg_solids[2];    // per tile: KMAX ids
+    int *reg_active[2];    // list of tiles with count > 0
+    int *reg_nactive[2];
+    void *pool[2];         // per tile: Fx_pool, Fy_pool, drho (TILE_N each)
+    void *fbody;           // per row: body-force x component
+    double *mass_partials; // per LB block
+    double *stats_step;    // S x 8, stats of the state at the start of the last step
+    SolidDesc *solids;
+    unsigned *err;
+};
+
+// ---------------------------------------------------------------------------
+// D2Q9 (Table d2q9): c_q and weights; opposite directions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cxq(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
+__device__ __forceinline__ int cyq(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
+__device__ __forceinline__ int oppq(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) & 3) + 1 : ((q - 3) & 3) + 5); }
+template <class R> __device__ __forceinline__ R wq(int q) { return q == 0 ? R(4) / R(9) : (q <= 4 ? R(1) / R(9) : R(1) / R(36)); }
+
+__device__ __forceinline__ int wrapi(int g, int n) { int r = g % n; return r < 0 ? r + n : r; }
+__device__ __forceinline__ int floordiv(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
+
+template <class R> __device__ __forceinline__ R rsin(R x);
+template <> __device__ __forceinline__ float rsin<float>(float x) { return sinf(x); }
+template <> __device__ __forceinline__ double rsin<double>(double x) { return sin(x); }
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+template <class R> __device__ __forceinline__ R nanv();
+template <> __device__ __forceinline__ float nanv<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double nanv<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// Smoothed Heaviside, Eq. 2_3_heaviside.
+template <class R> __device__ __forceinline__ R heaviside(R phi, R eps) {
+    if (phi <= -eps) return R(0);
+    if (phi >= eps) return R(1);
+    const R pi = R(3.14159265358979323846);
+    return R(0.5) * (R(1) + phi / eps + rsin<R>(pi * phi / eps) / pi);
+}
+
+// Level set of a disk in solid-local reference coordinates, phi_0(X) = |X - c| - R.
+template <class R> __device__ __forceinline__ R phi_disk(R X, R Y, R rad) { return rsqrt_<R>(X * X + Y * Y) - rad; }
+
+template <class S, class R> __device__ __forceinline__ R ldS(const S *p) { return R(*p); }
+template <class S, class R> __device__ __forceinline__ void stS(S *p, R v) { *p = S(v); }
+
+__device__ __forceinline__ bool allowed_cell(const SimParams &sp, int gx, int gy) {
+    if (sp.wall_x && (gx < -2 || gx > sp.nx + 1)) return false;
+    if (sp.wall_y && (gy < -2 || gy > sp.ny + 1)) return false;
+    return true;
+}
+__device__ __forceinline__ bool domain_cell(const SimParams &sp, int gx, int gy) {
+    if (sp.wall_x && (gx < 0 || gx >= sp.nx)) return false;
+    if (sp.wall_y && (gy < 0 || gy >= sp.ny)) return false;
+    return true;
+}
+__device__ __forceinline__ long long grid_index(const SimParams &sp, int gx, int gy) {
+    return (long long)wrapi(gy, sp.ny) * sp.nx + wrapi(gx, sp.nx);
+}
+
+// Moments of node c: rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
+template <class R, class S>
+__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const R *carry, long long c,
+                                             R &rho, R &u, R &v) {
+    R fq[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) fq[q] = ldS<S, R>(f + q * sp.P + c);
+    R dr = ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
+    R jx = (fq[1] - fq[3]) + (fq[5] - fq[6]) + (fq[8] - fq[7]);
+    R jy = (fq[2] - fq[4]) + (fq[5] - fq[7]) + (fq[6] - fq[8]);
+    rho = R(sp.rho_f) + dr;
+    R inv = R(1) / rho;
+    u = (jx + carry[c]) * inv;
+    v = (jy + carry[sp.P + c]) * inv;
+}
+
+// Block-wide sum of NV doubles (blockDim.x multiple of 32, <= 1024).
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *sh /* 32*NV */) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; k++) sh[warp * NV + k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < NV; k++) {
+            double t = lane < nw ? sh[lane * NV + k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+    }
+}
+
+// ===========================================================================
+// K2: reference-map advection, extrapolation and relabel, one CTA per solid.
+// ===========================================================================
+template <class R, class S>
+struct RmtArgs {
+    const S *f;          // populations f^n
+    const R *carry;
+    const R *xi_in;      // xi^n tiles (unused at init)
+    R *xi_out;           // xi^{n+1} tiles
+    const int2 *origin_in, *origin_out;
+    int2 *origin_next;   // frame of the next step's output tile
+    int *reg_count, *reg_solids, *reg_active, *reg_nactive;
+    double *stats;       // S x 8 (state at time n), may be null at init
+    const SolidDesc *solids;
+    unsigned *err;
+    int init;
+};
+
+// Weighted least-squares fit of one target (Sec. 3.2, steps (i)-(iii)).
+template <class R>
+__device__ void extrapolate_target(const SimParams &sp, const signed char *lab, R *X, R *Y, int T, int t,
+                                   int l, bool use_n, R nhx, R nhy, unsigned *err) {
+    const int tx = t % T, ty = t / T;
+    for (int r = 2; r <= sp.rmax; r++) {
+        int nvalid = 0, npos = 0, p0x = 0, p0y = 0, p1x = 0, p1y = 0;
+        bool have1 = false, noncol = false;
+        R a = 0, b = 0, c = 0, d = 0, e = 0, fw = 0;  // M = [[a b c],[b d e],[c e fw]]
+        R bx0 = 0, bx1 = 0, bx2 = 0, by0 = 0, by1 = 0, by2 = 0;
+        R xref = 0, yref = 0;
+        bool haveref = false;
+        for (int dy = -r; dy <= r; dy++) {
+            const int yy = ty + dy;
+            if (yy < 0 || yy >= T) continue;
+            for (int dx = -r; dx <= r; dx++) {
+                const int xx = tx + dx;
+                if (xx < 0 || xx >= T) continue;
+                const int k = yy * T + xx;
+                const int L = lab[k];
+                if (!(L >= 0 && L < l)) continue;
+                nvalid++;
+                R wt = R(1) / R(1 << (abs(dx) + abs(dy)));  // 2^{-(r_i + r_j)}, exact
+                if (use_n) {
+                    const R ddx = R(-dx), ddy = R(-dy);
+                    const R dn = (ddx * nhx + ddy * nhy) / rsqrt_<R>(ddx * ddx + ddy * ddy);
+                    wt = dn > R(COS_TIE) ? dn * wt : R(0);
+                }
+                if (!(wt > R(0))) continue;
+                if (npos == 0) { p0x = dx; p0y = dy; }
+                else if (!have1) { p1x = dx; p1y = dy; have1 = true; }
+                else if (!noncol) {
+                    const int cr = (p1x - p0x) * (dy - p0y) - (p1y - p0y) * (dx - p0x);
+                    if (cr != 0) noncol = true;
+                }
+                npos++;
+                const R Xv = X[k], Yv = Y[k];
+                if (!haveref) { xref = Xv; yref = Yv; haveref = true; }
+                const R x = R(dx), y = R(dy);
+                const R wx = wt * x, wy = wt * y;
+                a += wx * x; b += wx * y; c += wx; d += wy * y; e += wy; fw += wt;
+                const R xv = Xv - xref, yv = Yv - yref;
+                bx0 += wx * xv; bx1 += wy * xv; bx2 += wt * xv;
+                by0 += wx * yv; by1 += wy * yv; by2 += wt * yv;
+            }
+        }
+        if (nvalid < 3 || npos < 3 || !noncol) continue;
+        // third row of M^{-1} from the cofactors of the symmetric M
+        const R c13 = b * e - c * d, c23 = b * c - a * e, c33 = a * d - b * b;
+        const R det = a * (d * fw - e * e) - b * (b * fw - c * e) + c * (b * e - c * d);
+        if (!(det != R(0))) continue;
+        X[t] = xref + (c13 * bx0 + c23 * bx1 + c33 * bx2) / det;
+        Y[t] = yref + (c13 * by0 + c23 * by1 + c33 * by2) / det;
+        return;
+    }
+    atomicOr(err, ERR_EXTRAP);
+    X[t] = nanv<R>();
+    Y[t] = nanv<R>();
+}
+
+// Per-solid constants of the stored reference map.  A tile node at local
+// coordinates l (frame origin o) stores eta = xi - (l + o0), o0 being the
+// frame origin at initialisation: eta = 0 at rest and stays small for a
+// translating solid, so Jacobians are differences of small numbers.  The same
+// node seen from a frame moved by D stores eta + D.  xi - X_c = eta + l + off,
+// off = o0 - X_c.
+template <class R>
+__device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const SolidDesc &sd) {
+    const R X = ex + (R(lx) + R(sd.offx)), Y = ey + (R(ly) + R(sd.offy));
+    return phi_disk(X, Y, R(sd.R));
+}
+
+__device__ __forceinline__ void warp_minmax(int &v, bool is_min) {
+    const unsigned u = (unsigned)(v + (1 << 30));  // shift to non-negative for the unsigned reduction
+    const unsigned r = is_min ? __reduce_min_sync(0xffffffffu, u) : __reduce_max_sync(0xffffffffu, u);
+    v = (int)r - (1 << 30);
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int nlist;
+    __shared__ int bb[12];  // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
+    __shared__ double red[32 * 6];
+    const int s = blockIdx.x;
+    const SolidDesc sd = a.solids[s];
+    const int T = sd.T, TT = T * T;
+    const int lane = threadIdx.x & 31;
+    signed char *lab = reinterpret_cast<signed char *>(smem);
+    int *list = reinterpret_cast<int *>(smem + ((TT + 15) & ~15));
+    const int2 oo = a.origin_out[s];
+    const int2 oi = a.init ? oo : a.origin_in[s];
+    const int shx = oo.x - oi.x, shy = oo.y - oi.y;  // frame shift: eta_out = eta_in + shift
+    R *Xo = a.xi_out + sd.off;
+    R *Yo = Xo + TT;
+    const R *Xi = a.init ? nullptr : a.xi_in + sd.off;
+    const R *Yi = a.init ? nullptr : Xi + TT;
+    const R eps = R(sp.eps);
+    if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
+    double st[6] = {0, 0, 0, 0, 0, 0};
+    int sb[4] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
+    __syncthreads();
+
+    // Pass 0: the advected set S = {domain nodes with phi^n < 0}, Eqs. 3_1_refmap_adv / 3_1_eno.
+    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+        const int lx = t % T, ly = t / T;
+        const int gx = oo.x + lx, gy = oo.y + ly;
+        signed char L = -1;
+        if (!allowed_cell(sp, gx, gy)) {
+            L = -2;
+        } else if (a.init) {
+            const R X = R((double)gx - sd.xc), Y = R((double)gy - sd.yc);
+            if (domain_cell(sp, gx, gy) && phi_disk(X, Y, R(sd.R)) < -R(PHI_TIE)) {
+                Xo[t] = R(0); Yo[t] = R(0); L = 0;
+            }
+        } else {
+            const int ix = lx + shx, iy = ly + shy;
+            if (ix >= 0 && iy >= 0 && ix < T && iy < T) {
+                const int k = iy * T + ix;
+                const R ex = Xi[k], ey = Yi[k];
+                if (ex == ex) {
+                    const R phi = phi_eta(ex, ey, ix, iy, sd);
+                    if (phi < eps && domain_cell(sp, gx, gy)) {
+                        const long long c = grid_index(sp, gx, gy);
+                        R rho, u, v;
+                        node_moments<R, S>(sp, a.f, a.carry, c, rho, u, v);
+                        const double lam = 1.0 - (double)heaviside<R>(phi, eps);
+                        st[0] += lam; st[1] += lam * gx; st[2] += lam * gy;
+                        st[3] += lam * (double)rho; st[4] += lam * (double)rho * (double)u;
+                        st[5] += lam * (double)rho * (double)v;
+                        if (phi < -R(PHI_TIE)) {
+                            const int sx = (u >= R(0)) ? -1 : 1, sy = (v >= R(0)) ? -1 : 1;
+                            const int x2 = ix + 2 * sx, y2 = iy + 2 * sy;
+                            if (x2 < 0 || x2 >= T || y2 < 0 || y2 >= T) {
+                                atomicOr(a.err, ERR_STENCIL);
+                            } else {
+                                const int k1 = k + sx, k2 = k + 2 * sx, k3 = k + sy * T, k4 = k + 2 * sy * T;
+                                const R X1 = Xi[k1], X2 = Xi[k2], X3 = Xi[k3], X4 = Xi[k4];
+                                const R Y1 = Yi[k1], Y2 = Yi[k2], Y3 = Yi[k3], Y4 = Yi[k4];
+                                if (!(X1 == X1 && X2 == X2 && X3 == X3 && X4 == X4)) atomicOr(a.err, ERR_STENCIL);
+                                // one-sided second-order differences of eta; xi = eta + position adds (1,0)/(0,1)
+                                const R hx = R(-sx) * R(0.5), hy = R(-sy) * R(0.5);
+                                const R dXdx = hx * (R(3) * ex - R(4) * X1 + X2), dYdx = hx * (R(3) * ey - R(4) * Y1 + Y2);
+                                const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
+                                Xo[t] = (ex - (u * dXdx + v * dXdy) - u) + R(shx);
+                                Yo[t] = (ey - (u * dYdx + v * dYdy) - v) + R(shy);
+                                L = 0;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        lab[t] = L;
+        if (L == 0) {
+            sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
+        }
+    }
+    for (int k = 0; k < 4; k++) warp_minmax(sb[k], (k & 1) == 0);
+    if (lane == 0) {
+        atomicMin(&bb[0], sb[0]); atomicMax(&bb[1], sb[1]); atomicMin(&bb[2], sb[2]); atomicMax(&bb[3], sb[3]);
+    }
+    __syncthreads();
+
+    // Layers 1..n_layers by 4-neighbour dilation; extrapolate each layer (Sec. 3.2).
+    const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
+    if (sx0 > sx1) {
+        if (threadIdx.x == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);  // the solid vanished
+    }
+    for (int l = 1; l <= sp.n_layers && sx0 <= sx1; l++) {
+        if (threadIdx.x == 0) nlist = 0;
+        __syncthreads();
+        // scan the S bbox grown by l, clipped to the tile
+        const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
+        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+        const int nround = (n + 31) & ~31;
+        for (int k = threadIdx.x; k < nround; k += blockDim.x) {
+            bool hit = false;
+            int t = 0;
+            if (k < n) {
+                const int lx = x0 + k % w, ly = y0 + k / w;
+                t = ly * T + lx;
+                if (lab[t] == -1)
+                    hit = (lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
+                          (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&nlist, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (hit) {
+                    lab[t] = (signed char)l;
+                    const int idx = base + __popc(m & ((1u << lane) - 1u));
+                    if (idx < LIST_CAP) list[idx] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const int nl = nlist;
+        const bool use_list = nl <= LIST_CAP;
+        const int nitems = use_list ? nl : TT;
+        for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
+            const int t = use_list ? list[k] : k;
+            if (!use_list && lab[t] != l) continue;
+            if (a.init) {  // xi = x on the band at initialisation
+                Xo[t] = R(0);
+                Yo[t] = R(0);
+                continue;
+            }
+            const int lx = t % T, ly = t / T;
+            bool use_n = false;
+            R nhx = 0, nhy = 0;
+            if (l <= 2) {
+                // surface normal: central difference of phi^n at the target (input frame)
+                const int ix = lx + shx, iy = ly + shy;
+                if (ix >= 1 && iy >= 1 && ix < T - 1 && iy < T - 1) {
+                    const int k0 = iy * T + ix;
+                    const R Xe = Xi[k0 + 1], Xw = Xi[k0 - 1], Xn = Xi[k0 + T], Xs = Xi[k0 - T];
+                    if (Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs) {
+                        const R pe = phi_eta(Xe, Yi[k0 + 1], ix + 1, iy, sd), pw = phi_eta(Xw, Yi[k0 - 1], ix - 1, iy, sd);
+                        const R pn = phi_eta(Xn, Yi[k0 + T], ix, iy + 1, sd), ps = phi_eta(Xs, Yi[k0 - T], ix, iy - 1, sd);
+                        const R gxp = (pe - pw) / R(2), gyp = (pn - ps) / R(2);
+                        const R nn = rsqrt_<R>(gxp * gxp + gyp * gyp);
+                        if (nn > R(0)) { use_n = true; nhx = gxp / nn; nhy = gyp / nn; }
+                    }
+                }
+            }
+            extrapolate_target<R>(sp, lab, Xo, Yo, T, t, l, use_n, nhx, nhy, a.err);
+        }
+        __syncthreads();
+    }
+
+    // Relabel phi^{n+1} = phi_0(xi^{n+1}); band and blur-zone bboxes; invalidate the rest.
+    int bx[8] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29), 1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
+    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+        const int lx = t % T, ly = t / T;
+        if (lab[t] >= 0) {
+            bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
+            if (phi_eta(Xo[t], Yo[t], lx, ly, sd) < eps) {
+                bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
+            }
+        } else {
+            Xo[t] = nanv<R>();
+            Yo[t] = nanv<R>();
+        }
+    }
+    for (int k = 0; k < 8; k++) warp_minmax(bx[k], (k & 1) == 0);
+    if (lane == 0)
+        for (int k = 0; k < 8; k += 2) { atomicMin(&bb[4 + k], bx[k]); atomicMax(&bb[5 + k], bx[k + 1]); }
+    if (a.stats) block_sum<6>(st, red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.stats) {
+            double *o = a.stats + 8 * s;
+            const double L = st[0];
+            o[0] = L; o[1] = st[1] / L; o[2] = st[2] / L; o[3] = st[3]; o[4] = st[4]; o[5] = st[5];
+            o[6] = 0; o[7] = 0;
+        }
+        int2 nx = oo;
+        if (bb[4] > bb[5]) {
+            atomicOr(a.err, ERR_TILE_OVERFLOW);
+        } else {
+            if (bb[4] < 1 || bb[6] < 1 || bb[5] > T - 2 || bb[7] > T - 2) atomicOr(a.err, ERR_TILE_OVERFLOW);
+            nx.x = oo.x + (bb[4] + bb[5]) / 2 - T / 2;
+            nx.y = oo.y + (bb[6] + bb[7]) / 2 - T / 2;
+        }
+        a.origin_next[s] = nx;
+    }
+    // Register the 32x8 tiles that the blur zone (grown by one node) touches.
+    if (bb[8] <= bb[9]) {
+        int x0 = oo.x + bb[8] - 1, x1 = oo.x + bb[9] + 1, y0 = oo.y + bb[10] - 1, y1 = oo.y + bb[11] + 1;
+        int sxa[2], sxb[2], sya[2], syb[2], nsx = 1, nsy = 1;
+        if (sp.wall_x) { sxa[0] = max(x0, 0); sxb[0] = min(x1, sp.nx - 1); }
+        else {
+            const int k0 = floordiv(x0, sp.nx), k1 = floordiv(x1, sp.nx);
+            if (k0 == k1) { sxa[0] = x0 - k0 * sp.nx; sxb[0] = x1 - k0 * sp.nx; }
+            else { sxa[0] = x0 - k0 * sp.nx; sxb[0] = sp.nx - 1; sxa[1] = 0; sxb[1] = x1 - k1 * sp.nx; nsx = 2; }
+        }
+        if (sp.wall_y) { sya[0] = max(y0, 0); syb[0] = min(y1, sp.ny - 1); }
+        else {
+            const int k0 = floordiv(y0, sp.ny), k1 = floordiv(y1, sp.ny);
+            if (k0 == k1) { sya[0] = y0 - k0 * sp.ny; syb[0] = y1 - k0 * sp.ny; }
+            else { sya[0] = y0 - k0 * sp.ny; syb[0] = sp.ny - 1; sya[1] = 0; syb[1] = y1 - k1 * sp.ny; nsy = 2; }
+        }
+        for (int ay = 0; ay < nsy; ay++)
+            for (int ax = 0; ax < nsx; ax++) {
+                if (sxa[ax] > sxb[ax] || sya[ay] > syb[ay]) continue;
+                const int tx0 = sxa[ax] / TILE_X, tx1 = sxb[ax] / TILE_X;
+                const int ty0 = sya[ay] / TILE_Y, ty1 = syb[ay] / TILE_Y;
+                const int ntxr = tx1 - tx0 + 1, nall = ntxr * (ty1 - ty0 + 1);
+                for (int k = threadIdx.x; k < nall; k += blockDim.x) {
+                    const int tile = (ty0 + k / ntxr) * sp.ntx + tx0 + k % ntxr;
+                    const int slot = atomicAdd(&a.reg_count[tile], 1);
+                    if (slot < sp.kmax) a.reg_solids[tile * KMAX + slot] = s;
+                    else atomicOr(a.err, ERR_SLOT_OVERFLOW);
+                    if (slot == 0) a.reg_active[atomicAdd(a.reg_nactive, 1)] = tile;
+                }
+            }
+    }
+}
+
+// ===========================================================================
+// K3: stress divergence, contact and node terms per registered 32x8 tile.
+// ===========================================================================
+template <class R>
+struct ForceArgs {
+    const R *xi;          // xi^{n+1} tiles
+    const int2 *origin;   // their frames
+    const int *reg_count, *reg_solids, *reg_active, *reg_nactive;
+    R *pool;
+    const SolidDesc *solids;
+    unsigned *err;
+};
+
+// Half-edge Jacobian of Eq. 3_3_refmap_jacobian from a 2x3 stencil: a = the
+// node on the low side of the edge, b = the high side, k = 0,1,2 across.
+template <class R>
+__device__ __forceinline__ void edge_grad(const R a0, const R a1, const R a2, const R b0, const R b1, const R b2,
+                                          R &dn, R &dt) {
+    dn = b1 - a1;
+    dt = (b2 + a2 - b0 - a0) / R(4);
+}
+
+// Neo-Hookean plane-strain deviatoric stress, Eq. 3_3_solid_stress, from J = d xi / dx.
+template <class R>
+__device__ __forceinline__ bool stress_from_j(R Jxx, R Jxy, R Jyx, R Jyy, R G, R &txx, R &txy, R &tyy) {
+    const R det = Jxx * Jyy - Jxy * Jyx;
+    if (det == R(0)) return false;
+    const R Fxx = Jyy / det, Fxy = -Jxy / det, Fyx = -Jyx / det, Fyy = Jxx / det;
+    const R Bxx = Fxx * Fxx + Fxy * Fxy, Bxy = Fxx * Fyx + Fxy * Fyy, Byy = Fyx * Fyx + Fyy * Fyy;
+    const R tr = (Bxx + Byy + R(1)) / R(3);
+    txx = G * (Bxx - tr); txy = G * Bxy; tyy = G * (Byy - tr);
+    return true;
+}
+
+template <class R>
+__global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    R *sX = reinterpret_cast<R *>(smem);          // [KMAX][PATCH_N]
+    R *sY = sX + KMAX * PATCH_N;
+    R *sP = sY + KMAX * PATCH_N;
+    R *eT = sP + KMAX * PATCH_N;                  // [(NXE + NYE) * 3] edge stresses
+    __shared__ int ids[KMAX];
+    __shared__ int nk;
+    const int nact = *a.reg_nactive;
+    const R eps = R(sp.eps), eta = R(sp.eta);
+    for (int it = blockIdx.x; it < nact; it += gridDim.x) {
+        const int tile = a.reg_active[it];
+        const int tx = tile % sp.ntx, ty = tile / sp.ntx;
+        const int i0 = tx * TILE_X, j0 = ty * TILE_Y;
+        if (threadIdx.x == 0) {
+            int n = min(a.reg_count[tile], sp.kmax);
+            for (int k = 0; k < n; k++) ids[k] = a.reg_solids[tile * KMAX + k];
+            for (int k = 1; k < n; k++) {  // sort by id: fixed summation order
+                int v = ids[k], m = k - 1;
+                while (m >= 0 && ids[m] > v) { ids[m + 1] = ids[m]; m--; }
+                ids[m + 1] = v;
+            }
+            nk = n;
+        }
+        __syncthreads();
+        const int n = nk;
+        // Stage each solid's xi (and phi) on the tile plus a one-node halo.
+        for (int idx = threadIdx.x; idx < n * PATCH_N; idx += blockDim.x) {
+            const int ks = idx / PATCH_N, p = idx % PATCH_N;
+            const int px = p % PATCH_X, py = p / PATCH_X;
+            const int gx = i0 - 1 + px, gy = j0 - 1 + py;
+            const SolidDesc sd = a.solids[ids[ks]];
+            const int2 o = a.origin[ids[ks]];
+            const int lx = sp.wall_x ? gx - o.x : wrapi(gx - o.x, sp.nx);
+            const int ly = sp.wall_y ? gy - o.y : wrapi(gy - o.y, sp.ny);
+            R X = nanv<R>(), Y = nanv<R>(), P = nanv<R>();
+            if (lx >= 0 && ly >= 0 && lx < sd.T && ly < sd.T) {
+                const R *Xs = a.xi + sd.off;
+                X = Xs[ly * sd.T + lx];
+                Y = Xs[sd.T * sd.T + ly * sd.T + lx];
+                if (X == X) P = phi_eta(X, Y, lx, ly, sd);
+            }
+            sX[ks * PATCH_N + p] = X; sY[ks * PATCH_N + p] = Y; sP[ks * PATCH_N + p] = P;
+        }
+        __syncthreads();
+        // Half-edge stresses: blended solid stress (Eq. 3_6_global_stress) plus contact.
+        for (int e = threadIdx.x; e < NXE + NYE; e += blockDim.x) {
+            int pa[3], pb[3];  // patch indices of the 2x3 stencil (a low side, b high side)
+            const bool xedge = e < NXE;
+            if (xedge) {
+                const int ex = e % (TILE_X + 1), ey = e / (TILE_X + 1);  // edge between col ex-1 and ex (tile coords)
+                for (int k = 0; k < 3; k++) { pa[k] = (ey + k) * PATCH_X + ex; pb[k] = (ey + k) * PATCH_X + ex + 1; }
+            } else {
+                const int f = e - NXE;
+                const int ex = f % TILE_X, ey = f / TILE_X;               // edge between row ey-1 and ey
+                for (int k = 0; k < 3; k++) { pa[k] = ey * PATCH_X + ex + k; pb[k] = (ey + 1) * PATCH_X + ex + k; }
+            }
+            R Sxx = 0, Sxy = 0, Syy = 0, L = 0, Cxx = 0, Cxy = 0, Cyy = 0;
+            bool okv[KMAX];
+            R phh[KMAX];
+            for (int ks = 0; ks < n; ks++) {
+                const R *X = sX + ks * PATCH_N, *Y = sY + ks * PATCH_N, *P = sP + ks * PATCH_N;
+                bool ok = true;
+                for (int k = 0; k < 3; k++) ok = ok && (P[pa[k]] == P[pa[k]]) && (P[pb[k]] == P[pb[k]]);
+                okv[ks] = ok;
+                if (!ok) continue;
+                const R ph = R(0.5) * (P[pa[1]] + P[pb[1]]);
+                phh[ks] = ph;
+                const R lam = R(1) - heaviside<R>(ph, eps);
+                R dXn, dXt, dYn, dYt, txx, txy, tyy;
+                edge_grad<R>(X[pa[0]], X[pa[1]], X[pa[2]], X[pb[0]], X[pb[1]], X[pb[2]], dXn, dXt);
+                edge_grad<R>(Y[pa[0]], Y[pa[1]], Y[pa[2]], Y[pb[0]], Y[pb[1]], Y[pb[2]], dYn, dYt);
+                const R G = R(a.solids[ids[ks]].G);
+                // J = d xi / dx = I + d eta / dx (the stored eta excludes the node position)
+                const bool good = xedge ? stress_from_j<R>(R(1) + dXn, dXt, dYn, R(1) + dYt, G, txx, txy, tyy)
+                                        : stress_from_j<R>(R(1) + dXt, dXn, dYt, R(1) + dYn, G, txx, txy, tyy);
+                if (!good) { atomicOr(a.err, ERR_SINGULAR); continue; }
+                Sxx += lam * txx; Sxy += lam * txy; Syy += lam * tyy; L += lam;
+            }
+            for (int ks = 0; ks < n; ks++) {
+                if (!okv[ks] || !(phh[ks] < eps)) continue;
+                for (int kt = ks + 1; kt < n; kt++) {
+                    if (!okv[kt] || !(phh[kt] < eps)) continue;
+                    const R fs = R(0.5) * (R(1) - phh[ks] / eps), ft = R(0.5) * (R(1) - phh[kt] / eps);
+                    const R fm = fs < ft ? fs : ft;
+                    const R *Ps = sP + ks * PATCH_N, *Pt = sP + kt * PATCH_N;
+                    R gn, gt;
+                    edge_grad<R>(Ps[pa[0]] - Pt[pa[0]], Ps[pa[1]] - Pt[pa[1]], Ps[pa[2]] - Pt[pa[2]],
+                                 Ps[pb[0]] - Pt[pb[0]], Ps[pb[1]] - Pt[pb[1]], Ps[pb[2]] - Pt[pb[2]], gn, gt);
+                    const R gxx = xedge ? gn : gt, gyy = xedge ? gt : gn;
+                    const R nrm = rsqrt_<R>(gxx * gxx + gyy * gyy);
+                    if (nrm == R(0)) continue;
+                    const R nx_ = gxx / nrm, ny_ = gyy / nrm;
+                    const R kk = -eta * fm * (R(a.solids[ids[ks]].G) + R(a.solids[ids[kt]].G));
+                    Cxx += kk * (nx_ * nx_ - R(0.5)); Cxy += kk * (nx_ * ny_); Cyy += kk * (ny_ * ny_ - R(0.5));
+                }
+            }
+            if (L > R(1)) { Sxx /= L; Sxy /= L; Syy /= L; }
+            eT[3 * e + 0] = Sxx + Cxx; eT[3 * e + 1] = Sxy + Cxy; eT[3 * e + 2] = Syy + Cyy;
+        }
+        __syncthreads();
+        // Node: divergence (Eq. 3_3_div_solid_stress), solid fraction, drho, solid acceleration.
+        {
+            const int cx = threadIdx.x % TILE_X, cy = threadIdx.x / TILE_X;
+            const int i = i0 + cx, j = j0 + cy;
+            if (i < sp.nx && j < sp.ny) {
+                const R *tl = eT + 3 * (cy * (TILE_X + 1) + cx), *tr = eT + 3 * (cy * (TILE_X + 1) + cx + 1);
+                const R *tb = eT + 3 * (NXE + cy * TILE_X + cx), *tt = eT + 3 * (NXE + (cy + 1) * TILE_X + cx);
+                const R fsx = (tr[0] - tl[0]) + (tt[1] - tb[1]);
+                const R fsy = (tr[1] - tl[1]) + (tt[2] - tb[2]);
+                const int p = (cy + 1) * PATCH_X + cx + 1;
+                R L = 0, D = 0, Ay = 0;
+                for (int ks = 0; ks < n; ks++) {
+                    const R ph = sP[ks * PATCH_N + p];
+                    if (!(ph == ph)) continue;
+                    const SolidDesc &sd = a.solids[ids[ks]];
+                    const R lam = R(1) - heaviside<R>(ph, eps);
+                    L += lam;
+                    D += lam * (R(sd.rho_s) - R(sp.rho_f));
+                    Ay += lam * (-(R(1) - R(sp.rho_f) / R(sd.rho_s)) * R(sp.gravity));
+                }
+                if (L > R(1)) { D /= L; Ay /= L; }
+                R *po = a.pool + (long long)tile * POOL_STRIDE + threadIdx.x;
+                po[0] = fsx;
+                po[TILE_N] = fsy + Ay;
+                po[2 * TILE_N] = D;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// K1: fused moments + SFC equilibrium + Guo forcing + BGK + walls + push stream.
+// ===========================================================================
+template <class R, class S>
+struct LbArgs {
+    const S *f_in;
+    S *f_out;
+    R *carry;
+    const R *fbody;            // per row x body force
+    const int *reg_count;      // registry of this step
+    const R *pool;
+    int *clr_count;            // registry of the next step (cleared here)
+    int *clr_nactive;
+    double *mass_partials;
+    unsigned *err;
+};
+
+template <class R, class S>
+__global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
+    const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+    const int tile = blockIdx.y * sp.ntx + blockIdx.x;
+    const int lt = threadIdx.y * TILE_X + threadIdx.x;
+    R dm = R(0);
+    if (i < sp.nx && j < sp.ny) {
+        const long long P = sp.P, c = (long long)j * sp.nx + i;
+        R f[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) f[q] = ldS<S, R>(a.f_in + q * P + c);
+        const R dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+        const R rho = R(sp.rho_f) + dr;
+        const R inv = R(1) / rho;
+        const R ux = (jx + a.carry[c]) * inv, uy = (jy + a.carry[P + c]) * inv;
+        R Fx = a.fbody[j], Fy = R(sp.force_kind == 1 ? sp.fa1 : 0.0), drt = R(0);
+        if (a.reg_count[tile] > 0) {
+            const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
+            Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
+        }
+        if (!(rho == rho) || !(ux == ux) || !(uy == uy)) atomicOr(a.err, ERR_NAN);
+        const R omega = R(1) / R(sp.tau), kf = R(1) - omega / R(2);
+        const R u2 = ux * ux + uy * uy;
+        const R uF = ux * Fx + uy * Fy;
+        R fh[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const R w = wq<R>(q);
+            const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
+            const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
+            // f^eq - w rho_f with the SFC correction (Eq. 2_3_feq_sfc): w (rho - rho_t) is
+            // formed first so the velocity terms do not sit on top of w drho
+            R feq = w * (dr - drt) + w * rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
+            if (q == 0) feq += drt;
+            // Guo term times rho (Eqs. 2_2_Fi, 3_4_Fi)
+            const R Fi = rho * w * (R(3) * (cF - uF) + R(9) * cu * cF);
+            fh[q] = f[q] - omega * (f[q] - feq) + kf * Fi;
+        }
+        a.carry[c] = R(0.5) * rho * Fx;
+        a.carry[P + c] = R(0.5) * rho * Fy;
+        stS<S, R>(a.f_out + c, fh[0]);
+#pragma unroll
+        for (int q = 1; q < 9; q++) {
+            int di = i + cxq(q), dj = j + cyq(q);
+            const bool ox = di < 0 || di >= sp.nx, oy = dj < 0 || dj >= sp.ny;
+            if ((ox && sp.wall_x) || (oy && sp.wall_y)) {
+                // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
+                const R uw = (oy && sp.wall_y && dj >= sp.ny) ? R(sp.lid_u) : R(0);
+                const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
+                stS<S, R>(a.f_out + oppq(q) * P + c, val);
+            } else {
+                if (ox) di = di < 0 ? di + sp.nx : di - sp.nx;
+                if (oy) dj = dj < 0 ? dj + sp.ny : dj - sp.ny;
+                stS<S, R>(a.f_out + q * P + (long long)dj * sp.nx + di, fh[q]);
+            }
+        }
+        dm = dr;
+    }
+    // total mass: rho - rho_f summed over the warp (one row of the tile), then FP64 per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
+    if (threadIdx.x == 0) a.mass_partials[(long long)tile * TILE_Y + threadIdx.y] = (double)dm;
+    if (lt == 0) {
+        a.clr_count[tile] = 0;
+        if (tile == 0) *a.clr_nactive = 0;
+    }
+}
+
+// Initial populations f = f^eq,SFC(rho_t, 0) as deviations; zero stored half-force.
+template <class R, class S>
+__global__ void init_f_kernel(SimParams sp, S *f, R *carry, const int *reg_count, const R *pool) {
+    const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+    if (i >= sp.nx || j >= sp.ny) return;
+    const int tile = blockIdx.y * sp.ntx + blockIdx.x;
+    const long long c = (long long)j * sp.nx + i;
+    R drt = 0;
+    if (reg_count[tile] > 0) drt = pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + threadIdx.y * TILE_X + threadIdx.x];
+    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, q == 0 ? drt : R(0));
+    carry[c] = 0;
+    carry[sp.P + c] = 0;
+}
+
+// Fields to a double grid.  kind: 0 rho, 1 ux, 2 uy, 3 Fx, 4 Fy, 5 drho, 20+q f_q.
+template <class R, class S>
+__global__ void field_kernel(SimParams sp, const S *f, const R *carry, const R *fbody, const int *reg_count,
+                             const R *pool, int kind, double *out) {
+    const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+    if (i >= sp.nx || j >= sp.ny) return;
+    const int tile = blockIdx.y * sp.ntx + blockIdx.x;
+    const long long c = (long long)j * sp.nx + i;
+    double v = 0;
+    if (kind <= 2) {
+        R rho, u, w;
+        node_moments<R, S>(sp, f, carry, c, rho, u, w);
+        v = kind == 0 ? (double)rho : kind == 1 ? (double)u : (double)w;
+    } else if (kind <= 5) {
+        R p = 0;
+        if (reg_count[tile] > 0) p = pool[(long long)tile * POOL_STRIDE + (kind - 3) * TILE_N + threadIdx.y * TILE_X + threadIdx.x];
+        if (kind == 3) v = (double)(fbody[j] + p);
+        else if (kind == 4) v = (double)(R(sp.force_kind == 1 ? sp.fa1 : 0.0) + p);
+        else v = (double)p;
+    } else {
+        const int q = kind - 20;
+        v = (double)ldS<S, R>(f + q * sp.P + c) + (double)wq<R>(q) * sp.rho_f;
+    }
+    out[c] = v;
+}
+
+// One solid's reference map / level set onto the grid (NaN where not in its band).
+template <class R>
+__global__ void solid_field_kernel(SimParams sp, const R *xi, const int2 *origin, const SolidDesc *solids, int s,
+                                   int kind, double *out) {
+    const SolidDesc sd = solids[s];
+    const int2 o = origin[s];
+    const int T = sd.T;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T * T; t += gridDim.x * blockDim.x) {
+        const int lx = t % T, ly = t / T;
+        const int gx = o.x + lx, gy = o.y + ly;
+        if (!domain_cell(sp, gx, gy)) continue;
+        const R X = xi[sd.off + t], Y = xi[sd.off + T * T + t];
+        if (!(X == X)) continue;
+        const long long c = grid_index(sp, gx, gy);
+        double v;
+        if (kind == 0) v = (double)X + (double)(lx + sd.o0x);
+        else if (kind == 1) v = (double)Y + (double)(ly + sd.o0y);
+        else v = (double)phi_eta(X, Y, lx, ly, sd);
+        out[c] = v;
+    }
+}
+
+// Per-solid FP64 statistics of the current state (one CTA per solid).
+template <class R, class S>
+__global__ void solid_stats_kernel(SimParams sp, const S *f, const R *carry, const R *xi, const int2 *origin,
+                                   const SolidDesc *solids, double *out) {
+    __shared__ double red[32 * 6];
+    const int s = blockIdx.x;
+    const SolidDesc sd = solids[s];
+    const int2 o = origin[s];
+    const int T = sd.T;
+    const R eps = R(sp.eps);
+    double st[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
+        const int lx = t % T, ly = t / T;
+        const int gx = o.x + lx, gy = o.y + ly;
+        const R X = xi[sd.off + t], Y = xi[sd.off + T * T + t];
+        if (!(X == X) || !domain_cell(sp, gx, gy)) continue;
+        const R phi = phi_eta(X, Y, lx, ly, sd);
+        if (!(phi < eps)) continue;
+        R rho, u, v;
+        node_moments<R, S>(sp, f, carry, grid_index(sp, gx, gy), rho, u, v);
+        const double lam = 1.0 - (double)heaviside<R>(phi, eps);
+        st[0] += lam; st[1] += lam * gx; st[2] += lam * gy;
+        st[3] += lam * (double)rho; st[4] += lam * (double)rho * (double)u; st[5] += lam * (double)rho * (double)v;
+    }
+    block_sum<6>(st, red);
+    if (threadIdx.x == 0) {
+        double *q = out + 8 * s;
+        q[0] = st[0]; q[1] = st[1] / st[0]; q[2] = st[2] / st[0]; q[3] = st[3]; q[4] = st[4]; q[5] = st[5];
+        q[6] = 0; q[7] = 0;
+    }
+}
+
+// Fixed-order FP64 sum of the per-block mass partials (single CTA).
+__global__ void mass_reduce_kernel(const double *partials, int n, double base, double *out);
+
+}  // namespace lbrmt

@@ -1,0 +1,98 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path and the FP64
+oracle on the same scenario and compare field by field.
+
+Error measure: relative L-infinity, max |gpu - oracle| / D, over nodes where
+both are finite.  Vector fields (u, v) and (F_x, F_y) are compared as vectors:
+D is the largest magnitude of the oracle's vector field.  D has a floor, the
+magnitude below which a field is at the level of round-off of the method
+itself (a fluid at rest, a force that is exactly zero after one step):
+  rho - rho_f : 1e-6 rho_f        velocity : 1e-6
+  force F     : 1e-8              drho     : 1e-6
+  xi - x      : 1 lattice spacing (so the xi error is absolute, in cells)
+"""
+import numpy as np
+
+import oracle
+import scenarios  # noqa: F401  (re-exported for the tests)
+
+FLOORS = {"rho": 1e-6, "u": 1e-6, "F": 1e-8, "drho": 1e-6, "xi": 1.0}
+
+
+def rel_linf(a, b, floor=0.0, mask=None):
+    m = np.isfinite(a) & np.isfinite(b)
+    if mask is not None:
+        m &= mask
+    if not m.any():
+        return 0.0
+    den = max(np.abs(b[m]).max(), floor)
+    return float(np.abs(a[m] - b[m]).max() / den) if den > 0 else float(np.abs(a[m] - b[m]).max())
+
+
+def rel_linf_vec(ax, ay, bx, by, floor):
+    m = np.isfinite(ax) & np.isfinite(bx) & np.isfinite(ay) & np.isfinite(by)
+    if not m.any():
+        return 0.0
+    den = max(np.hypot(bx[m], by[m]).max(), floor)
+    return float(np.hypot(ax[m] - bx[m], ay[m] - by[m]).max() / den)
+
+
+def grid_x(sc):
+    ny, nx = sc["ny"], sc["nx"]
+    return (np.arange(nx)[None, :].repeat(ny, 0).astype(float),
+            np.arange(ny)[:, None].repeat(nx, 1).astype(float))
+
+
+def compare(sim, ref, sc, core_layers=4):
+    """Per-field errors (see module doc) and band-label mismatch counts.
+
+    xi is compared on the solid and the first ``core_layers`` band layers
+    (the nodes whose values enter the stress stencils and the advection
+    stencils), and separately over the whole band (``xi_band``)."""
+    out = {}
+    rf = sc["rho_f"]
+    out["rho"] = rel_linf(sim.field_host("rho") - rf, ref.field("rho") - rf, FLOORS["rho"] * rf)
+    out["u"] = rel_linf_vec(sim.field_host("ux"), sim.field_host("uy"), ref.field("ux"), ref.field("uy"), FLOORS["u"])
+    out["F"] = rel_linf_vec(sim.field_host("Fx"), sim.field_host("Fy"), ref.field("Fx"), ref.field("Fy"), FLOORS["F"])
+    out["drho"] = rel_linf(sim.field_host("drho"), ref.field("drho"), FLOORS["drho"])
+    X, Y = grid_x(sc)
+    nx, ny = sc["nx"], sc["ny"]
+    core, band, mism = 0.0, 0.0, 0
+    for s in range(len(sc["solids"])):
+        xa, xb = sim.field_host("xi_x", s), ref.field("xi_x", s)
+        ya, yb = sim.field_host("xi_y", s), ref.field("xi_y", s)
+        lab = ref.field("label", s)
+        ma, mb = np.isfinite(xa), np.isfinite(xb)
+        mism += int((ma != mb).sum())
+        both = ma & mb
+        if not both.any():
+            continue
+        da = np.hypot(((xa - X + nx / 2) % nx - nx / 2) - ((xb - X + nx / 2) % nx - nx / 2),
+                      ((ya - Y + ny / 2) % ny - ny / 2) - ((yb - Y + ny / 2) % ny - ny / 2))
+        disp = np.hypot((xb - X + nx / 2) % nx - nx / 2, (yb - Y + ny / 2) % ny - ny / 2)
+        den = max(disp[both].max(), FLOORS["xi"])
+        band = max(band, float(da[both].max() / den))
+        c = both & (lab <= core_layers)
+        if c.any():
+            core = max(core, float(da[c].max() / den))
+    out["xi"] = core
+    out["xi_band"] = band
+    out["label_mismatch"] = mism
+    return out
+
+
+def run_pair(sc, precision, steps_list, **kw):
+    """Run GPU and oracle side by side; return {steps: compare()}."""
+    import paper_2402_12696_gb300 as pkg
+    sim = pkg.Simulation(sc, precision=precision, **kw)
+    ref = oracle.Oracle(sc)
+    res = {}
+    done = 0
+    for n in steps_list:
+        sim.step(n - done)
+        ref.step(n - done)
+        done = n
+        sim.sync()
+        res[n] = compare(sim, ref, sc)
+    sim.close()
+    ref.close()
+    return res
