@@ -73,7 +73,7 @@ typedef void *(*lbrmt_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*lbrmt_free_fn)(void *ptr, void *ctx);
 
 typedef struct {
-    int nx, ny;                 /* grid nodes; nx, ny >= 8 */
+    int nx, ny;                 /* grid nodes; nx, ny >= 8 and 9 nx ny < 2^31 */
     int bc_x, bc_y;             /* LBRMT_PERIODIC or LBRMT_WALL (halfway bounce-back, Sec. 3.5) */
     double tau;                 /* BGK relaxation time; 1/2 < tau <= 1 (Appendix A) */
     double rho_f;               /* fluid density (1 in the paper) */

@@ -97,7 +97,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (!cfg || !out) return LBRMT_ERR_ARG;
     *out = nullptr;
     const lbrmt_config &c = *cfg;
-    if (c.nx < 8 || c.ny < 8 || (long long)c.nx * c.ny > (1ll << 31)) return LBRMT_ERR_ARG;
+    if (c.nx < 8 || c.ny < 8 || 9ll * c.nx * c.ny >= (1ll << 31)) return LBRMT_ERR_ARG;
     if ((c.bc_x != 0 && c.bc_x != 1) || (c.bc_y != 0 && c.bc_y != 1)) return LBRMT_ERR_ARG;
     if (!(c.tau > 0.5 && c.tau <= 1.0)) return LBRMT_ERR_PARAM_RANGE;  // Appendix A
     if (!(c.rho_f > 0) || !(c.eps > 0) || c.n_layers < 1 || c.n_layers > 20) return LBRMT_ERR_ARG;

@@ -1,6 +1,8 @@
 // lbrmt_engine.cuh -- launch sequences of the LBRMT kernels for one precision.
 #pragma once
 
+#include <cmath>
+
 #include "lbrmt_kernels.cuh"
 
 namespace lbrmt {
@@ -41,7 +43,21 @@ template <class R, class S>
 struct Engine {
     static cudaError_t configure(const SimParams &sp, int tmax, LaunchInfo *li) {
         li->tmax = tmax;
-        li->rmt_smem = ((tmax * tmax + 15) & ~15) + 4 * LIST_CAP;
+        li->rmt_smem = 4 * tmax * tmax + 8 * LIST_CAP;
+        {
+            float tf[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+            double td[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+            for (int i = 0; i <= RMAX_TAB; i++)
+                for (int j = 0; j <= RMAX_TAB; j++) {
+                    const double r2 = (double)(i * i + j * j);
+                    td[i * (RMAX_TAB + 1) + j] = r2 > 0 ? 1.0 / std::sqrt(r2) : 0.0;
+                    tf[i * (RMAX_TAB + 1) + j] = (float)td[i * (RMAX_TAB + 1) + j];
+                }
+            cudaError_t e0 = cudaMemcpyToSymbol(c_rinv_f, tf, sizeof(tf));
+            if (e0 != cudaSuccess) return e0;
+            e0 = cudaMemcpyToSymbol(c_rinv_d, td, sizeof(td));
+            if (e0 != cudaSuccess) return e0;
+        }
         li->force_smem = (3 * KMAX * PATCH_N + 3 * (NXE + NYE)) * (int)sizeof(R);
         cudaError_t e = cudaFuncSetAttribute(rmt_solid_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              li->rmt_smem);

@@ -181,59 +181,103 @@ struct RmtArgs {
     int init;
 };
 
-// Weighted least-squares fit of one target (Sec. 3.2, steps (i)-(iii)).
+// 2^{-k} exactly, k in [0, 60].
+template <class R> __device__ __forceinline__ R pow2neg(int k);
+template <> __device__ __forceinline__ float pow2neg<float>(int k) { return __int_as_float((127 - k) << 23); }
+template <> __device__ __forceinline__ double pow2neg<double>(int k) {
+    return __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+// 1/|d| for |dx|, |dy| <= RMAX_TAB (filled by the host at configuration).
+constexpr int RMAX_TAB = 20;
+__constant__ float c_rinv_f[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+__constant__ double c_rinv_d[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+template <class R> __device__ __forceinline__ R rinv_tab(int dx, int dy);
+template <> __device__ __forceinline__ float rinv_tab<float>(int dx, int dy) { return c_rinv_f[abs(dx) * (RMAX_TAB + 1) + abs(dy)]; }
+template <> __device__ __forceinline__ double rinv_tab<double>(int dx, int dy) { return c_rinv_d[abs(dx) * (RMAX_TAB + 1) + abs(dy)]; }
+
+// Running sums of one weighted least-squares fit.  The positive-weight nodes
+// are collinear iff the Gram determinant of their integer offsets vanishes,
+// (n Sxx - Sx^2)(n Syy - Sy^2) - (n Sxy - Sx Sy)^2 = 0, an exact integer test.
 template <class R>
-__device__ void extrapolate_target(const SimParams &sp, const signed char *lab, R *X, R *Y, int T, int t,
-                                   int l, bool use_n, R nhx, R nhy, unsigned *err) {
+struct Lsq {
+    int nvalid, n, sx, sy, sxx, syy, sxy;
+    bool haveref;
+    R a, b, c, d, e, fw;            // M = [[a b c],[b d e],[c e fw]]
+    R bx0, bx1, bx2, by0, by1, by2; // right-hand sides for eta_x - xref and eta_y - yref
+    R xref, yref;                   // values of the first valid node (fit of differences)
+};
+
+template <class R>
+__device__ __forceinline__ void lsq_cell(Lsq<R> &A, const int *lab, const R *X, const R *Y, int k, int l, int dx,
+                                         int dy, bool use_n, R nhx, R nhy) {
+    const int L = lab[k];
+    if (!(L >= 0 && L < l)) return;
+    A.nvalid++;
+    R wt = pow2neg<R>(abs(dx) + abs(dy));  // 2^{-(r_i + r_j)}
+    if (use_n) {
+        const R dn = (R(-dx) * nhx + R(-dy) * nhy) * rinv_tab<R>(dx, dy);  // d = target - node
+        wt = dn > R(COS_TIE) ? dn * wt : R(0);
+    }
+    if (!(wt > R(0))) return;
+    A.n++; A.sx += dx; A.sy += dy; A.sxx += dx * dx; A.syy += dy * dy; A.sxy += dx * dy;
+    R Xv = X[k], Yv = Y[k];
+    if (!A.haveref) { A.xref = Xv; A.yref = Yv; A.haveref = true; }
+    Xv -= A.xref; Yv -= A.yref;
+    const R x = R(dx), y = R(dy);
+    const R wx = wt * x, wy = wt * y;
+    A.a += wx * x; A.b += wx * y; A.c += wx; A.d += wy * y; A.e += wy; A.fw += wt;
+    A.bx0 += wx * Xv; A.bx1 += wy * Xv; A.bx2 += wt * Xv;
+    A.by0 += wx * Yv; A.by1 += wy * Yv; A.by2 += wt * Yv;
+}
+
+// Weighted least-squares fit of one target (Sec. 3.2, steps (i)-(iii)).  The
+// weights do not depend on the window size, so growing r from r-1 only adds
+// the ring |dx| = r or |dy| = r to the sums of the smaller window.
+template <class R>
+__device__ void extrapolate_target(const SimParams &sp, const int *lab, R *X, R *Y, int T, int t, int l,
+                                   bool use_n, R nhx, R nhy, unsigned *err) {
     const int tx = t % T, ty = t / T;
+    Lsq<R> A;
+    A.nvalid = A.n = A.sx = A.sy = A.sxx = A.syy = A.sxy = 0;
+    A.haveref = false;
+    A.a = A.b = A.c = A.d = A.e = A.fw = R(0);
+    A.bx0 = A.bx1 = A.bx2 = A.by0 = A.by1 = A.by2 = R(0);
+    A.xref = A.yref = R(0);
+    if (tx >= 2 && ty >= 2 && tx < T - 2 && ty < T - 2) {
+#pragma unroll
+        for (int dy = -2; dy <= 2; dy++)
+#pragma unroll
+            for (int dx = -2; dx <= 2; dx++) lsq_cell<R>(A, lab, X, Y, t + dy * T + dx, l, dx, dy, use_n, nhx, nhy);
+    } else {
+        for (int dy = -2; dy <= 2; dy++)
+            for (int dx = -2; dx <= 2; dx++)
+                if (tx + dx >= 0 && ty + dy >= 0 && tx + dx < T && ty + dy < T)
+                    lsq_cell<R>(A, lab, X, Y, t + dy * T + dx, l, dx, dy, use_n, nhx, nhy);
+    }
     for (int r = 2; r <= sp.rmax; r++) {
-        int nvalid = 0, npos = 0, p0x = 0, p0y = 0, p1x = 0, p1y = 0;
-        bool have1 = false, noncol = false;
-        R a = 0, b = 0, c = 0, d = 0, e = 0, fw = 0;  // M = [[a b c],[b d e],[c e fw]]
-        R bx0 = 0, bx1 = 0, bx2 = 0, by0 = 0, by1 = 0, by2 = 0;
-        R xref = 0, yref = 0;
-        bool haveref = false;
-        for (int dy = -r; dy <= r; dy++) {
-            const int yy = ty + dy;
-            if (yy < 0 || yy >= T) continue;
-            for (int dx = -r; dx <= r; dx++) {
-                const int xx = tx + dx;
-                if (xx < 0 || xx >= T) continue;
-                const int k = yy * T + xx;
-                const int L = lab[k];
-                if (!(L >= 0 && L < l)) continue;
-                nvalid++;
-                R wt = R(1) / R(1 << (abs(dx) + abs(dy)));  // 2^{-(r_i + r_j)}, exact
-                if (use_n) {
-                    const R ddx = R(-dx), ddy = R(-dy);
-                    const R dn = (ddx * nhx + ddy * nhy) / rsqrt_<R>(ddx * ddx + ddy * ddy);
-                    wt = dn > R(COS_TIE) ? dn * wt : R(0);
+        if (r > 2) {
+            for (int q = -r; q <= r; q++) {
+                const int ring[4][2] = {{q, -r}, {q, r}, {-r, q}, {r, q}};
+                for (int m = 0; m < 4; m++) {
+                    if (m >= 2 && (q == -r || q == r)) continue;  // corners counted once
+                    const int dx = ring[m][0], dy = ring[m][1];
+                    if (tx + dx >= 0 && ty + dy >= 0 && tx + dx < T && ty + dy < T)
+                        lsq_cell<R>(A, lab, X, Y, t + dy * T + dx, l, dx, dy, use_n, nhx, nhy);
                 }
-                if (!(wt > R(0))) continue;
-                if (npos == 0) { p0x = dx; p0y = dy; }
-                else if (!have1) { p1x = dx; p1y = dy; have1 = true; }
-                else if (!noncol) {
-                    const int cr = (p1x - p0x) * (dy - p0y) - (p1y - p0y) * (dx - p0x);
-                    if (cr != 0) noncol = true;
-                }
-                npos++;
-                const R Xv = X[k], Yv = Y[k];
-                if (!haveref) { xref = Xv; yref = Yv; haveref = true; }
-                const R x = R(dx), y = R(dy);
-                const R wx = wt * x, wy = wt * y;
-                a += wx * x; b += wx * y; c += wx; d += wy * y; e += wy; fw += wt;
-                const R xv = Xv - xref, yv = Yv - yref;
-                bx0 += wx * xv; bx1 += wy * xv; bx2 += wt * xv;
-                by0 += wx * yv; by1 += wy * yv; by2 += wt * yv;
             }
         }
-        if (nvalid < 3 || npos < 3 || !noncol) continue;
+        if (A.nvalid < 3 || A.n < 3) continue;
+        const long long g1 = (long long)A.n * A.sxx - (long long)A.sx * A.sx;
+        const long long g2 = (long long)A.n * A.syy - (long long)A.sy * A.sy;
+        const long long g3 = (long long)A.n * A.sxy - (long long)A.sx * A.sy;
+        if (g1 * g2 - g3 * g3 == 0) continue;  // positive-weight nodes on one line
         // third row of M^{-1} from the cofactors of the symmetric M
-        const R c13 = b * e - c * d, c23 = b * c - a * e, c33 = a * d - b * b;
-        const R det = a * (d * fw - e * e) - b * (b * fw - c * e) + c * (b * e - c * d);
+        const R c13 = A.b * A.e - A.c * A.d, c23 = A.b * A.c - A.a * A.e, c33 = A.a * A.d - A.b * A.b;
+        const R det = A.a * (A.d * A.fw - A.e * A.e) - A.b * (A.b * A.fw - A.c * A.e) + A.c * (A.b * A.e - A.c * A.d);
         if (!(det != R(0))) continue;
-        X[t] = xref + (c13 * bx0 + c23 * bx1 + c33 * bx2) / det;
-        Y[t] = yref + (c13 * by0 + c23 * by1 + c33 * by2) / det;
+        X[t] = A.xref + (c13 * A.bx0 + c23 * A.bx1 + c33 * A.bx2) / det;
+        Y[t] = A.yref + (c13 * A.by0 + c23 * A.by1 + c33 * A.by2) / det;
         return;
     }
     atomicOr(err, ERR_EXTRAP);
@@ -260,7 +304,7 @@ __device__ __forceinline__ void warp_minmax(int &v, bool is_min) {
 }
 
 template <class R, class S>
-__global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
+__global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int nlist;
     __shared__ int bb[12];  // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
@@ -269,8 +313,8 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
     const SolidDesc sd = a.solids[s];
     const int T = sd.T, TT = T * T;
     const int lane = threadIdx.x & 31;
-    signed char *lab = reinterpret_cast<signed char *>(smem);
-    int *list = reinterpret_cast<int *>(smem + ((TT + 15) & ~15));
+    int *lab = reinterpret_cast<int *>(smem);       // -2 outside the pads, -1 free, 0 solid, l layer
+    int *lists = lab + TT;                          // two per-layer target lists of LIST_CAP
     const int2 oo = a.origin_out[s];
     const int2 oi = a.init ? oo : a.origin_in[s];
     const int shx = oo.x - oi.x, shy = oo.y - oi.y;  // frame shift: eta_out = eta_in + shift
@@ -280,7 +324,7 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
     const R *Yi = a.init ? nullptr : Xi + TT;
     const R eps = R(sp.eps);
     if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
-    double st[6] = {0, 0, 0, 0, 0, 0};
+    R stl[6] = {0, 0, 0, 0, 0, 0};  // sum lambda, lambda lx, lambda ly, lambda rho, lambda rho u, lambda rho v
     int sb[4] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
     __syncthreads();
 
@@ -288,7 +332,7 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
     for (int t = threadIdx.x; t < TT; t += blockDim.x) {
         const int lx = t % T, ly = t / T;
         const int gx = oo.x + lx, gy = oo.y + ly;
-        signed char L = -1;
+        int L = -1;
         if (!allowed_cell(sp, gx, gy)) {
             L = -2;
         } else if (a.init) {
@@ -307,10 +351,9 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
                         const long long c = grid_index(sp, gx, gy);
                         R rho, u, v;
                         node_moments<R, S>(sp, a.f, a.carry, c, rho, u, v);
-                        const double lam = 1.0 - (double)heaviside<R>(phi, eps);
-                        st[0] += lam; st[1] += lam * gx; st[2] += lam * gy;
-                        st[3] += lam * (double)rho; st[4] += lam * (double)rho * (double)u;
-                        st[5] += lam * (double)rho * (double)v;
+                        const R lam = R(1) - heaviside<R>(phi, eps);
+                        stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
+                        stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
                         if (phi < -R(PHI_TIE)) {
                             const int sx = (u >= R(0)) ? -1 : 1, sy = (v >= R(0)) ? -1 : 1;
                             const int x2 = ix + 2 * sx, y2 = iy + 2 * sy;
@@ -346,47 +389,71 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
     __syncthreads();
 
     // Layers 1..n_layers by 4-neighbour dilation; extrapolate each layer (Sec. 3.2).
+    // Layer 1 comes from a scan of the solid bbox grown by one; layer l > 1 from
+    // the free 4-neighbours of the layer l-1 list (claimed with a CAS).
     const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
     if (sx0 > sx1) {
         if (threadIdx.x == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);  // the solid vanished
     }
+    bool prev_full = true;  // previous list complete (no overflow)
+    int nl_prev = 0;        // size of the previous layer's list (same value in every thread)
     for (int l = 1; l <= sp.n_layers && sx0 <= sx1; l++) {
+        int *cur = lists + (l & 1) * LIST_CAP;
+        const int *prv = lists + ((l + 1) & 1) * LIST_CAP;
+        const int nprev = min(nl_prev, LIST_CAP);
+        __syncthreads();
         if (threadIdx.x == 0) nlist = 0;
         __syncthreads();
-        // scan the S bbox grown by l, clipped to the tile
-        const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
-        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
-        const int nround = (n + 31) & ~31;
-        for (int k = threadIdx.x; k < nround; k += blockDim.x) {
-            bool hit = false;
-            int t = 0;
-            if (k < n) {
-                const int lx = x0 + k % w, ly = y0 + k / w;
-                t = ly * T + lx;
-                if (lab[t] == -1)
-                    hit = (lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
-                          (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1);
+        if (l == 1 || !prev_full) {
+            const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
+            const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+            const int nround = (n + 31) & ~31;
+            for (int k = threadIdx.x; k < nround; k += blockDim.x) {
+                bool hit = false;
+                int t = 0;
+                if (k < n) {
+                    const int lx = x0 + k % w, ly = y0 + k / w;
+                    t = ly * T + lx;
+                    if (lab[t] == -1)
+                        hit = (lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
+                              (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&nlist, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (hit) {
+                        lab[t] = l;
+                        const int idx = base + __popc(m & ((1u << lane) - 1u));
+                        if (idx < LIST_CAP) cur[idx] = t;
+                    }
+                }
             }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&nlist, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (hit) {
-                    lab[t] = (signed char)l;
-                    const int idx = base + __popc(m & ((1u << lane) - 1u));
-                    if (idx < LIST_CAP) list[idx] = t;
+        } else {
+            for (int k = threadIdx.x; k < 4 * nprev; k += blockDim.x) {
+                const int p = prv[k >> 2], dir = k & 3;
+                const int lx = p % T, ly = p / T;
+                int q = -1;
+                if (dir == 0 && lx > 0) q = p - 1;
+                else if (dir == 1 && lx < T - 1) q = p + 1;
+                else if (dir == 2 && ly > 0) q = p - T;
+                else if (dir == 3 && ly < T - 1) q = p + T;
+                if (q >= 0 && lab[q] == -1 && atomicCAS(&lab[q], -1, l) == -1) {
+                    const int idx = atomicAdd(&nlist, 1);
+                    if (idx < LIST_CAP) cur[idx] = q;
                 }
             }
         }
         __syncthreads();
         const int nl = nlist;
-        const bool use_list = nl <= LIST_CAP;
-        const int nitems = use_list ? nl : TT;
+        nl_prev = nl;
+        prev_full = nl <= LIST_CAP;
+        const int nitems = prev_full ? nl : TT;
         for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
-            const int t = use_list ? list[k] : k;
-            if (!use_list && lab[t] != l) continue;
+            const int t = prev_full ? cur[k] : k;
+            if (!prev_full && lab[t] != l) continue;
             if (a.init) {  // xi = x on the band at initialisation
                 Xo[t] = R(0);
                 Yo[t] = R(0);
@@ -412,8 +479,8 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
             }
             extrapolate_target<R>(sp, lab, Xo, Yo, T, t, l, use_n, nhx, nhy, a.err);
         }
-        __syncthreads();
     }
+    __syncthreads();
 
     // Relabel phi^{n+1} = phi_0(xi^{n+1}); band and blur-zone bboxes; invalidate the rest.
     int bx[8] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29), 1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
@@ -432,13 +499,15 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
     for (int k = 0; k < 8; k++) warp_minmax(bx[k], (k & 1) == 0);
     if (lane == 0)
         for (int k = 0; k < 8; k += 2) { atomicMin(&bb[4 + k], bx[k]); atomicMax(&bb[5 + k], bx[k + 1]); }
+    double st[6];
+    for (int k = 0; k < 6; k++) st[k] = (double)stl[k];
     if (a.stats) block_sum<6>(st, red);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (a.stats) {
             double *o = a.stats + 8 * s;
             const double L = st[0];
-            o[0] = L; o[1] = st[1] / L; o[2] = st[2] / L; o[3] = st[3]; o[4] = st[4]; o[5] = st[5];
+            o[0] = L; o[1] = oo.x + st[1] / L; o[2] = oo.y + st[2] / L; o[3] = st[3]; o[4] = st[4]; o[5] = st[5];
             o[6] = 0; o[7] = 0;
         }
         int2 nx = oo;
@@ -446,8 +515,12 @@ __global__ void __launch_bounds__(RMT_THREADS) rmt_solid_kernel(SimParams sp, Rm
             atomicOr(a.err, ERR_TILE_OVERFLOW);
         } else {
             if (bb[4] < 1 || bb[6] < 1 || bb[5] > T - 2 || bb[7] > T - 2) atomicOr(a.err, ERR_TILE_OVERFLOW);
-            nx.x = oo.x + (bb[4] + bb[5]) / 2 - T / 2;
-            nx.y = oo.y + (bb[6] + bb[7]) / 2 - T / 2;
+            // centre the next frame on the solid (not on its band, which walls clip): the
+            // frame then follows the solid's translation and eta stays small
+            if (bb[0] <= bb[1]) {
+                nx.x = oo.x + (bb[0] + bb[1]) / 2 - T / 2;
+                nx.y = oo.y + (bb[2] + bb[3]) / 2 - T / 2;
+            }
         }
         a.origin_next[s] = nx;
     }
@@ -506,15 +579,25 @@ __device__ __forceinline__ void edge_grad(const R a0, const R a1, const R a2, co
     dt = (b2 + a2 - b0 - a0) / R(4);
 }
 
-// Neo-Hookean plane-strain deviatoric stress, Eq. 3_3_solid_stress, from J = d xi / dx.
+// Neo-Hookean plane-strain deviatoric stress, Eq. 3_3_solid_stress, for the
+// Jacobian J = d xi / dx = I + A.  Evaluated in the algebraically identical
+// small-strain form: with delta = det J - 1 = tr A + det A,
+//   F - I = (adj J - det J I) / det J = D,   E = F F^T - I = D + D^T + D D^T,
+//   tau = G (E - tr(E)/3 I),
+// so no O(1) terms cancel when the strain is small.
 template <class R>
-__device__ __forceinline__ bool stress_from_j(R Jxx, R Jxy, R Jyx, R Jyy, R G, R &txx, R &txy, R &tyy) {
-    const R det = Jxx * Jyy - Jxy * Jyx;
+__device__ __forceinline__ bool stress_from_grad(R Axx, R Axy, R Ayx, R Ayy, R G, R &txx, R &txy, R &tyy) {
+    const R dl = (Axx + Ayy) + (Axx * Ayy - Axy * Ayx);
+    const R det = R(1) + dl;
     if (det == R(0)) return false;
-    const R Fxx = Jyy / det, Fxy = -Jxy / det, Fyx = -Jyx / det, Fyy = Jxx / det;
-    const R Bxx = Fxx * Fxx + Fxy * Fxy, Bxy = Fxx * Fyx + Fxy * Fyy, Byy = Fyx * Fyx + Fyy * Fyy;
-    const R tr = (Bxx + Byy + R(1)) / R(3);
-    txx = G * (Bxx - tr); txy = G * Bxy; tyy = G * (Byy - tr);
+    const R inv = R(1) / det;
+    const R Dxx = (Ayy - dl) * inv, Dxy = -Axy * inv, Dyx = -Ayx * inv, Dyy = (Axx - dl) * inv;
+    const R Exx = R(2) * Dxx + (Dxx * Dxx + Dxy * Dxy);
+    const R Exy = (Dxy + Dyx) + (Dxx * Dyx + Dxy * Dyy);
+    const R Eyy = R(2) * Dyy + (Dyx * Dyx + Dyy * Dyy);
+    txx = G * (R(2) * Exx - Eyy) / R(3);
+    txy = G * Exy;
+    tyy = G * (R(2) * Eyy - Exx) / R(3);
     return true;
 }
 
@@ -593,8 +676,8 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                 edge_grad<R>(Y[pa[0]], Y[pa[1]], Y[pa[2]], Y[pb[0]], Y[pb[1]], Y[pb[2]], dYn, dYt);
                 const R G = R(a.solids[ids[ks]].G);
                 // J = d xi / dx = I + d eta / dx (the stored eta excludes the node position)
-                const bool good = xedge ? stress_from_j<R>(R(1) + dXn, dXt, dYn, R(1) + dYt, G, txx, txy, tyy)
-                                        : stress_from_j<R>(R(1) + dXt, dXn, dYt, R(1) + dYn, G, txx, txy, tyy);
+                const bool good = xedge ? stress_from_grad<R>(dXn, dXt, dYn, dYt, G, txx, txy, tyy)
+                                        : stress_from_grad<R>(dXt, dXn, dYt, dYn, G, txx, txy, tyy);
                 if (!good) { atomicOr(a.err, ERR_SINGULAR); continue; }
                 Sxx += lam * txx; Sxy += lam * txy; Syy += lam * tyy; L += lam;
             }
@@ -673,12 +756,16 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
     const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
     const int tile = blockIdx.y * sp.ntx + blockIdx.x;
     const int lt = threadIdx.y * TILE_X + threadIdx.x;
+    const int nx = sp.nx, ny = sp.ny, P = (int)sp.P;  // 9 P < 2^31 is checked at creation
+    // every push target of this block lies inside the domain
+    const bool interior = blockIdx.x > 0 && (blockIdx.x + 1) * TILE_X < nx && blockIdx.y > 0 &&
+                          (blockIdx.y + 1) * TILE_Y < ny;
     R dm = R(0);
-    if (i < sp.nx && j < sp.ny) {
-        const long long P = sp.P, c = (long long)j * sp.nx + i;
+    if (i < nx && j < ny) {
+        const int c = j * nx + i;
         R f[9];
 #pragma unroll
-        for (int q = 0; q < 9; q++) f[q] = ldS<S, R>(a.f_in + q * P + c);
+        for (int q = 0; q < 9; q++) f[q] = R(__ldg(a.f_in + q * P + c));
         const R dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
@@ -694,6 +781,7 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         const R omega = R(1) / R(sp.tau), kf = R(1) - omega / R(2);
         const R u2 = ux * ux + uy * uy;
         const R uF = ux * Fx + uy * Fy;
+        const R ddr = dr - drt;  // rho - rho_t
         R fh[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) {
@@ -702,7 +790,7 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
             const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
             // f^eq - w rho_f with the SFC correction (Eq. 2_3_feq_sfc): w (rho - rho_t) is
             // formed first so the velocity terms do not sit on top of w drho
-            R feq = w * (dr - drt) + w * rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
+            R feq = w * ddr + w * rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
             if (q == 0) feq += drt;
             // Guo term times rho (Eqs. 2_2_Fi, 3_4_Fi)
             const R Fi = rho * w * (R(3) * (cF - uF) + R(9) * cu * cF);
@@ -711,19 +799,24 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         a.carry[c] = R(0.5) * rho * Fx;
         a.carry[P + c] = R(0.5) * rho * Fy;
         stS<S, R>(a.f_out + c, fh[0]);
+        if (interior) {
 #pragma unroll
-        for (int q = 1; q < 9; q++) {
-            int di = i + cxq(q), dj = j + cyq(q);
-            const bool ox = di < 0 || di >= sp.nx, oy = dj < 0 || dj >= sp.ny;
-            if ((ox && sp.wall_x) || (oy && sp.wall_y)) {
-                // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
-                const R uw = (oy && sp.wall_y && dj >= sp.ny) ? R(sp.lid_u) : R(0);
-                const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
-                stS<S, R>(a.f_out + oppq(q) * P + c, val);
-            } else {
-                if (ox) di = di < 0 ? di + sp.nx : di - sp.nx;
-                if (oy) dj = dj < 0 ? dj + sp.ny : dj - sp.ny;
-                stS<S, R>(a.f_out + q * P + (long long)dj * sp.nx + di, fh[q]);
+            for (int q = 1; q < 9; q++) stS<S, R>(a.f_out + q * P + c + cyq(q) * nx + cxq(q), fh[q]);
+        } else {
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                int di = i + cxq(q), dj = j + cyq(q);
+                const bool ox = di < 0 || di >= nx, oy = dj < 0 || dj >= ny;
+                if ((ox && sp.wall_x) || (oy && sp.wall_y)) {
+                    // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
+                    const R uw = (oy && sp.wall_y && dj >= ny) ? R(sp.lid_u) : R(0);
+                    const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
+                    stS<S, R>(a.f_out + oppq(q) * P + c, val);
+                } else {
+                    if (ox) di = di < 0 ? di + nx : di - nx;
+                    if (oy) dj = dj < 0 ? dj + ny : dj - ny;
+                    stS<S, R>(a.f_out + q * P + dj * nx + di, fh[q]);
+                }
             }
         }
         dm = dr;

@@ -2,8 +2,9 @@
 
 Error measure: parity_util (relative L-infinity; vector fields as vectors;
 stated floors).  Tolerances:
-  FP64 GPU: 1e-9 on every field -- the two sides differ only in summation
-            order and in the 3x3 solve (cofactors vs. elimination).
+  FP64 GPU: 1e-8 on every field -- the two sides differ only in summation
+            order, in the 3x3 solve (cofactors vs. elimination) and in the
+            storage of xi (absolute in the oracle, eta on the GPU).
   FP32 GPU: 1e-5 on rho - rho_f, the velocity and xi - x on the solid and the
             first four band layers, the bound the FP32 path is built to.  The
             force density F is a difference of half-edge stresses that are
@@ -26,7 +27,7 @@ from parity_util import compare, rel_linf, run_pair
 
 pytestmark = pytest.mark.gpu
 
-FP64_TOL = 1e-9
+FP64_TOL = 1e-8
 FP32_TOL = 1e-5
 # |dF| <~ 8 G_max u_r |xi - X_c|_max / |F|_max with u_r = 2^-24; the cases here have
 # G_max |xi - X_c|_max ~ 0.3 and |F|_max ~ 1e-4 .. 1e-3, giving ~1e-2 .. 1e-1.
