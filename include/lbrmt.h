@@ -146,6 +146,22 @@ lbrmt_status lbrmt_total_mass(lbrmt_sim *sim, int sim_index, double *host_out);
  * first step. */
 lbrmt_status lbrmt_active_tiles(lbrmt_sim *sim, int sim_index, long long *host_out);
 
+/* Total mass sum_x rho of the current populations, written as one double to
+ * dev_out (caller-owned device memory), enqueued on the simulation's stream;
+ * the library allocates no device memory for it.  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory where
+ * they need the diagnostic (a stream capture that must not gain allocation
+ * nodes, a frozen memory pool, a device handed to another allocator).  Its
+ * partial sums live in one file-scope device array of 2048 doubles (16 KiB)
+ * that every GPU loading the library holds until exit; simulations of more
+ * than 33,554,432 nodes are rejected with LBRMT_ERR_ARG.  The first call on a
+ * device looks up that array's address, so make it before any stream
+ * capture.  The simulation's device must be current and the simulation
+ * initialised (LBRMT_ERR_STATE otherwise).  All calls share the array, which
+ * keeps the last call's partial sums: calls that overlap on the GPU (other
+ * streams of the same device) race and give wrong results. */
+lbrmt_status lbrmt_total_mass_noalloc(lbrmt_sim *sim, int sim_index, double *dev_out);
+
 /* Wait for the stream and turn device error flags into a status. */
 lbrmt_status lbrmt_sync(lbrmt_sim *sim);
 

@@ -29,7 +29,7 @@ FIELDS = {"rho": 0, "ux": 1, "uy": 2, "Fx": 3, "Fy": 4, "drho": 5,
           "xi_x": 10, "xi_y": 11, "phi": 12}
 EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_init", "lbrmt_step",
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
-           "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
+           "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs",
            "lbrmt_last_error", "lbrmt_destroy"]
 
@@ -78,6 +78,7 @@ def load():
     L.lbrmt_total_mass.argtypes = [p, i, p]
     L.lbrmt_sync.argtypes = [p]
     L.lbrmt_active_tiles.argtypes = [p, i, C.POINTER(ll)]
+    L.lbrmt_total_mass_noalloc.argtypes = [p, i, p]
     L.lbrmt_step_timed.argtypes = [p, i, C.POINTER(C.c_float)]
     L.lbrmt_steps_done.argtypes = [p]
     L.lbrmt_steps_done.restype = ll
@@ -153,6 +154,10 @@ def lbrmt_sync(h):
     _check(h, load().lbrmt_sync(h))
 
 
+def lbrmt_total_mass_noalloc(h, sim_index, dev_ptr):
+    _check(h, load().lbrmt_total_mass_noalloc(h, sim_index, C.c_void_p(dev_ptr)))
+
+
 def lbrmt_active_tiles(h, sim_index):
     n = C.c_longlong()
     _check(h, load().lbrmt_active_tiles(h, sim_index, C.byref(n)))
@@ -179,6 +184,7 @@ class _TorchAllocator:
     def __init__(self, torch, device, stream):
         self.torch, self.device, self.stream = torch, device, stream
         self.live = {}
+        self.n_alloc = 0
         self.alloc_cb = ALLOC_FN(self._alloc)
         self.free_cb = FREE_FN(self._free)
 
@@ -190,6 +196,7 @@ class _TorchAllocator:
             return None
         ptr = t.data_ptr()
         self.live[ptr] = t
+        self.n_alloc += 1
         return ptr
 
     def _free(self, ptr, ctx):

@@ -12,6 +12,7 @@
 
 #include "lbrmt.h"
 #include "lbrmt_engine.cuh"
+#include "lbrmt_sim.cuh"
 
 using namespace lbrmt;
 
@@ -29,31 +30,6 @@ __global__ void mass_reduce_kernel(const double *partials, int n, double base, d
     if (threadIdx.x == 0) *out = base + sh[0];
 }
 }  // namespace lbrmt
-
-struct SolidHost {
-    double xc, yc, R, rho_s, G;
-    int T;
-    long long off;
-};
-
-struct lbrmt_sim {
-    lbrmt_config cfg;
-    cudaStream_t stream = nullptr;
-    SimParams sp;
-    const EngineOps *eng = nullptr;
-    LaunchInfo li;
-    DevState d;
-    std::vector<SolidHost> solids;
-    bool inited = false;
-    long long steps = 0;
-    bool use_graphs = true;
-    cudaGraphExec_t gexec = nullptr;
-    long long last_launches = 0;
-    std::vector<void *> allocs;
-    double *scratch = nullptr;      // device: S*8 stats or 1 mass value
-    double *staging = nullptr;      // device: 9*P doubles for set_populations
-    std::string err;
-};
 
 static lbrmt_status fail(lbrmt_sim *s, lbrmt_status st, const std::string &msg) {
     if (s) s->err = msg;
@@ -109,6 +85,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
 
     lbrmt_sim *s = new lbrmt_sim();
     s->cfg = c;
+    if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
     s->stream = (cudaStream_t)cuda_stream;
     s->eng = c.precision == LBRMT_FP64 ? &engine_fp64 : &engine_fp32;
     SimParams &sp = s->sp;

@@ -1,0 +1,121 @@
+// lbrmt_noalloc.cu -- total mass without any device allocation.
+//
+// lbrmt_total_mass_noalloc serves callers that cannot allocate device memory
+// at the point where they need the diagnostic: code recording a CUDA stream
+// capture that must not gain allocation nodes, a loop running after its
+// device memory pool has been frozen, or a host that handed all device
+// memory to another allocator.  It computes the same quantity as the
+// reduction behind lbrmt_total_mass, but keeps its per-block partial sums in
+// the file-scope array below instead of memory the library allocates.
+#include <mutex>
+
+#include "lbrmt.h"
+#include "lbrmt_sim.cuh"
+
+namespace {
+
+constexpr int NOALLOC_THREADS = 256;
+constexpr int NOALLOC_CHUNK = 16384;       // nodes summed by one block
+constexpr int NOALLOC_MAX_BLOCKS = 2048;   // partial sums held in the array: 16 KiB
+constexpr long long NOALLOC_MAX_NODES = (long long)NOALLOC_CHUNK * NOALLOC_MAX_BLOCKS;
+
+// Shared by every call on a device and kept until the process exits.  In host
+// code this name is only a stand-in for the device array: kernels receive the
+// device address looked up below, never the host symbol.
+static __device__ __align__(256) double g_mass_partials[NOALLOC_MAX_BLOCKS];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_lock;
+double *g_partials_addr[MAX_DEVICES] = {nullptr};
+
+// Device address of g_mass_partials on the current device, looked up once per
+// device (the first call on a device does it; that call must not be inside a
+// stream capture).
+cudaError_t partials_address(int dev, double **out) {
+    std::lock_guard<std::mutex> guard(g_lock);
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (!g_partials_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_mass_partials);
+        if (e != cudaSuccess) return e;
+        g_partials_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_partials_addr[dev];
+    return cudaSuccess;
+}
+
+// Block b sums rho - rho_f = sum_q (f_q - w_q rho_f) over nodes [b C, (b+1) C).
+template <class S>
+__global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(const S *f, long long P, double *partials) {
+    __shared__ double sh[NOALLOC_THREADS];
+    const long long begin = (long long)blockIdx.x * NOALLOC_CHUNK;
+    const long long end = begin + NOALLOC_CHUNK < P ? begin + NOALLOC_CHUNK : P;
+    double acc = 0.0;
+    for (long long c = begin + threadIdx.x; c < end; c += NOALLOC_THREADS) {
+        double s = 0.0;
+        for (int q = 0; q < 9; q++) s += (double)f[q * P + c];
+        acc += s;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = NOALLOC_THREADS / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_final(const double *partials, int n, double base,
+                                                                      double *out) {
+    __shared__ double sh[NOALLOC_THREADS];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += NOALLOC_THREADS) acc += partials[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = NOALLOC_THREADS / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = base + sh[0];
+}
+
+}  // namespace
+
+extern "C" lbrmt_status lbrmt_total_mass_noalloc(lbrmt_sim *s, int sim_index, double *dev_out) {
+    if (!s || !dev_out || sim_index != 0) return LBRMT_ERR_ARG;
+    if (!s->inited) {
+        s->err = "lbrmt_total_mass_noalloc needs an initialised simulation (call lbrmt_init first)";
+        return LBRMT_ERR_STATE;
+    }
+    const long long P = s->sp.P;
+    if (P > NOALLOC_MAX_NODES) {
+        s->err = "lbrmt_total_mass_noalloc handles at most 33554432 nodes (2048 partial sums of 16384 nodes)";
+        return LBRMT_ERR_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && dev != s->device) {
+        s->err = "lbrmt_total_mass_noalloc: make the simulation's device current first";
+        return LBRMT_ERR_ARG;
+    }
+    double *partials = nullptr;
+    if (e == cudaSuccess) e = partials_address(dev, &partials);
+    if (e != cudaSuccess) {
+        s->err = std::string("lbrmt_total_mass_noalloc: scratch lookup: ") + cudaGetErrorString(e);
+        return LBRMT_ERR_CUDA;
+    }
+    const int nblocks = (int)((P + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
+    const void *f = s->d.f[s->steps & 1];
+    // each block overwrites its partial sum, so nothing in the array needs clearing
+    if (s->eng->store_size == 4)
+        noalloc_mass_partials<float><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>((const float *)f, P, partials);
+    else
+        noalloc_mass_partials<double><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>((const double *)f, P, partials);
+    noalloc_mass_final<<<1, NOALLOC_THREADS, 0, s->stream>>>(partials, nblocks, s->sp.rho_f * (double)P, dev_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        s->err = std::string("lbrmt_total_mass_noalloc: launch: ") + cudaGetErrorString(e);
+        return LBRMT_ERR_CUDA;
+    }
+    return LBRMT_OK;
+}

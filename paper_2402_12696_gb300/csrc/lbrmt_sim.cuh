@@ -1,0 +1,35 @@
+// lbrmt_sim.cuh -- the simulation handle behind the C ABI (host side).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "lbrmt.h"
+#include "lbrmt_engine.cuh"
+
+struct SolidHost {
+    double xc, yc, R, rho_s, G;
+    int T;
+    long long off;
+};
+
+struct lbrmt_sim {
+    lbrmt_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lbrmt::SimParams sp;
+    const lbrmt::EngineOps *eng = nullptr;
+    lbrmt::LaunchInfo li;
+    lbrmt::DevState d;
+    std::vector<SolidHost> solids;
+    bool inited = false;
+    long long steps = 0;
+    bool use_graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    long long last_launches = 0;
+    std::vector<void *> allocs;
+    double *scratch = nullptr;      // device: S*8 stats or 1 mass value
+    double *staging = nullptr;      // device: 9*P doubles for set_populations
+    std::string err;
+};
+
