@@ -97,6 +97,9 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     sp.tau = c.tau; sp.rho_f = c.rho_f; sp.lid_u = c.lid_u; sp.eps = c.eps; sp.eta = c.eta;
     sp.gravity = c.gravity; sp.force_kind = c.force_kind; sp.fa0 = c.force_a[0]; sp.fa1 = c.force_a[1];
     sp.n_layers = c.n_layers; sp.rmax = c.rmax; sp.kmax = c.max_solids_per_tile; sp.nsolids = 0;
+    sp.omega = 1.0 / c.tau; sp.kf = 1.0 - 0.5 / c.tau; sp.fy = c.force_kind == LBRMT_FORCE_CONST ? c.force_a[1] : 0.0;
+    sp.omega_f = (float)sp.omega; sp.kf_f = (float)sp.kf; sp.rho_f_f = (float)c.rho_f; sp.lid_u_f = (float)c.lid_u;
+    sp.eps_f = (float)c.eps; sp.eta_f = (float)c.eta; sp.fy_f = (float)sp.fy;
 
     const size_t P = (size_t)sp.P, ntiles = (size_t)sp.ntx * sp.nty;
     const size_t rs = s->eng->real_size, ss = s->eng->store_size;
@@ -206,7 +209,7 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     bool ok = true;
     for (int k = 0; k < 2; k++) {
         ok = ok && (d.xi[k] = dalloc(s, (size_t)total * rs));
-        ok = ok && (d.origin[k] = (int2 *)dalloc(s, (size_t)S * sizeof(int2)));
+        ok = ok && (d.frame[k] = (Frame *)dalloc(s, (size_t)S * sizeof(Frame)));
     }
     ok = ok && (d.solids = (SolidDesc *)dalloc(s, (size_t)S * sizeof(SolidDesc)));
     ok = ok && (d.stats_step = (double *)dalloc(s, (size_t)S * 64));
@@ -217,21 +220,28 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     }
     if (!ok) return fail(s, LBRMT_ERR_CUDA, "out of device memory for the solid tiles");
     std::vector<SolidDesc> sd(S);
-    std::vector<int2> org(S);
+    std::vector<Frame> org(S);
     for (int k = 0; k < S; k++) {
         const SolidHost &h = s->solids[k];
-        org[k].x = (int)std::floor(h.xc) - h.T / 2;
-        org[k].y = (int)std::floor(h.yc) - h.T / 2;
+        // initial frame: centred on the solid, off = o - X_c on the 2^-14 grid (d = o - X_c - off)
+        org[k].ox = (int)std::floor(h.xc) - h.T / 2;
+        org[k].oy = (int)std::floor(h.yc) - h.T / 2;
+        org[k].offx = (float)(std::rint(((double)org[k].ox - h.xc) * 16384.0) / 16384.0);
+        org[k].offy = (float)(std::rint(((double)org[k].oy - h.yc) * 16384.0) / 16384.0);
         sd[k].xc = h.xc; sd[k].yc = h.yc; sd[k].R = h.R; sd[k].rho_s = h.rho_s; sd[k].G = h.G;
-        sd[k].o0x = org[k].x; sd[k].o0y = org[k].y;
-        sd[k].offx = (double)org[k].x - h.xc; sd[k].offy = (double)org[k].y - h.yc;
-        sd[k].T = h.T; sd[k].pad = 0; sd[k].off = h.off;
+        sd[k].drho = h.rho_s - s->cfg.rho_f;
+        sd[k].accel = -(1.0 - s->cfg.rho_f / h.rho_s) * s->cfg.gravity;
+        const double r2 = h.R * h.R;
+        sd[k].R_f = (float)h.R; sd[k].G_f = (float)h.G;
+        sd[k].r2hi_f = (float)r2; sd[k].r2lo_f = (float)(r2 - (double)sd[k].r2hi_f); sd[k].r2lo = 0.0;
+        sd[k].drho_f = (float)sd[k].drho; sd[k].accel_f = (float)sd[k].accel;
+        sd[k].T = h.T; sd[k].off = h.off;
     }
     cudaError_t e = cudaSuccess;
     if (S > 0) {
         e = cudaMemcpy(d.solids, sd.data(), S * sizeof(SolidDesc), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(d.origin[0], org.data(), S * sizeof(int2), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(d.origin[1], org.data(), S * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d.frame[0], org.data(), S * sizeof(Frame), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d.frame[1], org.data(), S * sizeof(Frame), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemsetAsync(d.stats_step, 0, (size_t)S * 64, s->stream);
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "upload solids");
@@ -239,11 +249,11 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     if (e != cudaSuccess) return cuda_fail(s, e, "configure kernels");
     e = s->eng->init(s->sp, d, s->li, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernels");
+    // registry 1 holds the initial registration (step 0 reads its Delta rho as the
+    // rest base of f^0 and clears it); registry 0 receives step 0's registration
     const size_t ntiles = (size_t)s->sp.ntx * s->sp.nty;
-    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
-        e = cudaMemsetAsync(d.reg_count[k], 0, ntiles * 4, s->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[k], 0, 16, s->stream);
-    }
+    e = cudaMemsetAsync(d.reg_count[0], 0, ntiles * 4, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[0], 0, 16, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "clear registry");
     s->inited = true;
     s->steps = 0;
@@ -358,7 +368,7 @@ extern "C" lbrmt_status lbrmt_read_fields(lbrmt_sim *s, int sim_index, int field
         if (st != LBRMT_OK) return st;
     }
     const int cur = (int)(s->steps & 1);
-    const int lastreg = s->steps > 0 ? 1 - cur : -1;
+    const int lastreg = 1 - cur;  // registry of the step (or initialisation) that wrote the state
     if (field >= 10 && field <= 12) {
         if (solid_id < 0 || solid_id >= (int)s->solids.size()) return fail(s, LBRMT_ERR_ARG, "bad solid id");
         cudaError_t e = cudaMemsetAsync(dev_out, 0xFF, (size_t)s->sp.P * 8, s->stream);  // NaN

@@ -31,10 +31,13 @@ extern const EngineOps engine_fp32;
 extern const EngineOps engine_fp64;
 
 template <class R, class S>
-__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, R *carry) {
+__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, R *carry, const int *reg, const R *pool) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sp.P) return;
-    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f));
+    const int i = (int)(c % sp.nx), j = (int)(c / sp.nx);
+    const double base = (double)rest_base<R>(sp, reg, pool, i, j);
+    for (int q = 0; q < 9; q++)
+        stS<S, R>(f + q * sp.P + c, R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f - (q == 0 ? base : 0.0)));
     carry[c] = 0;
     carry[sp.P + c] = 0;
 }
@@ -79,20 +82,22 @@ struct Engine {
         const int p = parity, q = 1 - parity;
         a.f = (const S *)d.f[p];
         a.carry = (const R *)d.carry;
+        a.reg_prev = d.reg_count[q];
+        a.pool_prev = (const R *)d.pool[q];
         a.xi_in = (const R *)d.xi[p];
-        a.origin_in = d.origin[p];
+        a.frame_in = d.frame[p];
         if (init) {
             a.xi_out = (R *)d.xi[0];
-            a.origin_out = d.origin[0];
-            a.origin_next = d.origin[1];
+            a.frame_out = d.frame[0];
+            a.frame_next = d.frame[1];
             a.stats = nullptr;
         } else {
             a.xi_out = (R *)d.xi[q];
-            a.origin_out = d.origin[q];
-            a.origin_next = d.origin[p];
+            a.frame_out = d.frame[q];
+            a.frame_next = d.frame[p];
             a.stats = d.stats_step;
         }
-        const int r = init ? 0 : p;
+        const int r = init ? 1 : p;  // the initial registry takes slot 1 (step 0 reads it as "previous")
         a.reg_count = d.reg_count[r];
         a.reg_solids = d.reg_solids[r];
         a.reg_active = d.reg_active[r];
@@ -106,7 +111,7 @@ struct Engine {
     static ForceArgs<R> force_args(const DevState &d, int xi_idx, int r) {
         ForceArgs<R> a;
         a.xi = (const R *)d.xi[xi_idx];
-        a.origin = d.origin[xi_idx];
+        a.frame = d.frame[xi_idx];
         a.reg_count = d.reg_count[r];
         a.reg_solids = d.reg_solids[r];
         a.reg_active = d.reg_active[r];
@@ -120,10 +125,10 @@ struct Engine {
     static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
         if (sp.nsolids > 0) {
             rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, 0, 1));
-            force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 0));
+            force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 1));
         }
         dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
-        init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (R *)d.carry, d.reg_count[0], (const R *)d.pool[0]);
+        init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (R *)d.carry);
         return cudaGetLastError();
     }
 
@@ -145,6 +150,7 @@ struct Engine {
         a.pool = (const R *)d.pool[p];
         a.clr_count = d.reg_count[q];
         a.clr_nactive = d.reg_nactive[q];
+        a.pool_prev = (const R *)d.pool[q];
         a.mass_partials = d.mass_partials;
         a.err = d.err;
         dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
@@ -157,12 +163,11 @@ struct Engine {
                              double *out, cudaStream_t st) {
         dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
         if (kind >= 10 && kind <= 12) {
-            solid_field_kernel<R><<<64, 256, 0, st>>>(sp, (const R *)d.xi[cur], d.origin[cur], d.solids, solid,
+            solid_field_kernel<R><<<64, 256, 0, st>>>(sp, (const R *)d.xi[cur], d.frame[cur], d.solids, solid,
                                                       kind - 10, out);
             return cudaGetLastError();
         }
-        const int r = lastreg < 0 ? 0 : lastreg;
-        static_assert(sizeof(int) == 4, "");
+        const int r = lastreg;
         field_kernel<R, S><<<grid, blk, 0, st>>>(sp, (const S *)d.f[cur], (const R *)d.carry, (const R *)d.fbody,
                                                  d.reg_count[r], (const R *)d.pool[r], kind, out);
         return cudaGetLastError();
@@ -171,13 +176,15 @@ struct Engine {
     static cudaError_t stats(const SimParams &sp, const DevState &d, int cur, double *out, cudaStream_t st) {
         if (sp.nsolids == 0) return cudaSuccess;
         solid_stats_kernel<R, S><<<sp.nsolids, 256, 0, st>>>(sp, (const S *)d.f[cur], (const R *)d.carry,
-                                                             (const R *)d.xi[cur], d.origin[cur], d.solids, out);
+                                                             d.reg_count[1 - cur], (const R *)d.pool[1 - cur],
+                                                             (const R *)d.xi[cur], d.frame[cur], d.solids, out);
         return cudaGetLastError();
     }
 
     static cudaError_t set_pop(const SimParams &sp, const DevState &d, int cur, const double *src, cudaStream_t st) {
         const int nb = (int)((sp.P + 255) / 256);
-        set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (R *)d.carry);
+        set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (R *)d.carry, d.reg_count[1 - cur],
+                                                 (const R *)d.pool[1 - cur]);
         return cudaGetLastError();
     }
 

@@ -50,13 +50,31 @@ struct SimParams {
     int force_kind;
     double fa0, fa1;
     int n_layers, rmax, kmax, nsolids;
+    // FP32 copies (GB300's FP64 pipe is narrow: no per-thread conversions)
+    float omega_f, kf_f, rho_f_f, lid_u_f, eps_f, eta_f, fy_f;
+    double omega, kf, fy;  // 1/tau, 1 - 1/(2 tau), constant y body force
 };
+
+template <class R> __device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 struct SolidDesc {
     double xc, yc, R, rho_s, G;
-    double offx, offy;  // o0 - X_c: initial frame origin minus the reference centre
-    int T, o0x, o0y, pad;
+    double r2lo, drho, accel;   // R^2 - (double)(float)R^2, rho_s - rho_f, -(1 - rho_f/rho_s) g
+    float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f;
+    int T;
     long long off;      // element offset of the tile (eta_x plane, then eta_y plane)
+};
+
+// Frame of one buffer of a solid's tile: origin o (global node of tile node
+// (0,0), unwrapped) and off, a multiple of 2^-14.  A tile node at local l is the
+// grid node x = o + l and stores eta = xi - x + d with d = o - X_c - off, so
+// xi - X_c = eta + l + off: l + off is exact in FP32 and d follows the solid's
+// mean motion, which keeps eta small.
+struct Frame {
+    int ox, oy;
+    float offx, offy;
 };
 
 // Device pointers of one simulation (type-erased; the kernels cast).
@@ -64,7 +82,7 @@ struct DevState {
     void *f[2];            // 9 planes each
     void *carry;           // 2 planes: rho^n F^n / 2 of the last collision
     void *xi[2];           // solid tiles
-    int2 *origin[2];       // frame of xi[k] per solid
+    Frame *frame[2];       // frame of xi[k] per solid
     int *reg_count[2];     // per tile: solids registered
     int *reg_solids[2];    // per tile: KMAX ids
     int *reg_active[2];    // list of tiles with count > 0
@@ -126,17 +144,30 @@ __device__ __forceinline__ long long grid_index(const SimParams &sp, int gx, int
     return (long long)wrapi(gy, sp.ny) * sp.nx + wrapi(gx, sp.nx);
 }
 
-// Moments of node c: rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
+// Stored populations: g_q = f_q - w_q rho_f for q >= 1 and g_0 = f_0 - w_0 rho_f -
+// Delta rho, where Delta rho is the SFC density difference (Eq. 2_3_drho) of the
+// step that wrote them (zero off the registered tiles).  At the SFC rest state
+// every g_q vanishes, so all nine stored numbers are small deviations.
+template <class R>
+__device__ __forceinline__ R rest_base(const SimParams &sp, const int *reg, const R *pool, int i, int j) {
+    const int tile = (j / TILE_Y) * sp.ntx + i / TILE_X;
+    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + (j % TILE_Y) * TILE_X + i % TILE_X] : R(0);
+}
+
+// Moments of node (i, j): rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
+// reg/pool: registry and force pool of the step that wrote the populations.
 template <class R, class S>
-__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const R *carry, long long c,
-                                             R &rho, R &u, R &v) {
+__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const R *carry, const int *reg,
+                                             const R *pool, int i, int j, R &rho, R &u, R &v) {
+    const long long c = (long long)j * sp.nx + i;
     R fq[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) fq[q] = ldS<S, R>(f + q * sp.P + c);
-    R dr = ((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8];
+    R dr = rest_base<R>(sp, reg, pool, i, j) +
+           (((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8]);
     R jx = (fq[1] - fq[3]) + (fq[5] - fq[6]) + (fq[8] - fq[7]);
     R jy = (fq[2] - fq[4]) + (fq[5] - fq[7]) + (fq[6] - fq[8]);
-    rho = R(sp.rho_f) + dr;
+    rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
     R inv = R(1) / rho;
     u = (jx + carry[c]) * inv;
     v = (jy + carry[sp.P + c]) * inv;
@@ -170,10 +201,12 @@ template <class R, class S>
 struct RmtArgs {
     const S *f;          // populations f^n
     const R *carry;
+    const int *reg_prev; // registry and pool of the step that wrote f^n
+    const R *pool_prev;
     const R *xi_in;      // xi^n tiles (unused at init)
     R *xi_out;           // xi^{n+1} tiles
-    const int2 *origin_in, *origin_out;
-    int2 *origin_next;   // frame of the next step's output tile
+    const Frame *frame_in, *frame_out;
+    Frame *frame_next;   // frame of the next step's output tile
     int *reg_count, *reg_solids, *reg_active, *reg_nactive;
     double *stats;       // S x 8 (state at time n), may be null at init
     const SolidDesc *solids;
@@ -285,16 +318,54 @@ __device__ void extrapolate_target(const SimParams &sp, const int *lab, R *X, R 
     Y[t] = nanv<R>();
 }
 
-// Per-solid constants of the stored reference map.  A tile node at local
-// coordinates l (frame origin o) stores eta = xi - (l + o0), o0 being the
-// frame origin at initialisation: eta = 0 at rest and stays small for a
-// translating solid, so Jacobians are differences of small numbers.  The same
-// node seen from a frame moved by D stores eta + D.  xi - X_c = eta + l + off,
-// off = o0 - X_c.
+template <class R> __device__ __forceinline__ R mul_rn(R a, R b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <class R> __device__ __forceinline__ R add_rn(R a, R b);
+template <> __device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
+template <class R> __device__ __forceinline__ R fma_rn(R a, R b, R c);
+template <> __device__ __forceinline__ float fma_rn<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fma_rn<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// R^2 as an unevaluated sum hi + lo in precision R (from the host-side split).
 template <class R>
-__device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const SolidDesc &sd) {
-    const R X = ex + (R(lx) + R(sd.offx)), Y = ey + (R(ly) + R(sd.offy));
-    return phi_disk(X, Y, R(sd.R));
+struct Rsq {
+    R hi, lo, rad;
+    __device__ __forceinline__ Rsq() {}
+    __device__ __forceinline__ explicit Rsq(const SolidDesc &sd) {
+        hi = pick<R>(sd.R * sd.R, sd.r2hi_f);
+        lo = pick<R>(0.0, sd.r2lo_f);
+        rad = pick<R>(sd.R, sd.R_f);
+    }
+};
+
+// Level set phi_0 of a disk at a tile node: with p = l + off (exact) and eta,
+// phi = |p + eta| - R = (|p|^2 - R^2 + 2 p.eta + |eta|^2) / (|p + eta| + R),
+// where |p|^2 - R^2 is formed with error-free products and a two-sum, so
+// phi keeps its relative precision near the interface.
+template <class R>
+__device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const Frame &fr, const Rsq<R> &q) {
+    const R px = add_rn<R>(R(lx), R(fr.offx)), py = add_rn<R>(R(ly), R(fr.offy));  // exact
+    const R a = mul_rn<R>(px, px), ea = fma_rn<R>(px, px, -a);
+    const R b = mul_rn<R>(py, py), eb = fma_rn<R>(py, py, -b);
+    const R s2 = add_rn<R>(a, b);
+    const R bv = add_rn<R>(s2, -a);
+    const R es = add_rn<R>(add_rn<R>(a, -add_rn<R>(s2, -bv)), add_rn<R>(b, -bv));
+    const R pq = add_rn<R>(s2, -q.hi) + (((ea + eb) + es) - q.lo);
+    const R num = pq + (R(2) * (px * ex + py * ey) + (ex * ex + ey * ey));
+    const R X = px + ex, Y = py + ey;
+    return num / (rsqrt_<R>(X * X + Y * Y) + q.rad);
+}
+
+// d = o - X_c - off of a frame, in double.
+__device__ __forceinline__ double frame_d(const Frame &fr, double c, bool xdir) {
+    return xdir ? (double)fr.ox - c - (double)fr.offx : (double)fr.oy - c - (double)fr.offy;
+}
+
+// off for origin o and displacement estimate d: o - X_c - d on the 2^-14 grid.
+__device__ __forceinline__ float frame_off(int o, double c, double d) {
+    return (float)(rint(((double)o - c - d) * 16384.0) / 16384.0);
 }
 
 __device__ __forceinline__ void warp_minmax(int &v, bool is_min) {
@@ -315,14 +386,19 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
     const int lane = threadIdx.x & 31;
     int *lab = reinterpret_cast<int *>(smem);       // -2 outside the pads, -1 free, 0 solid, l layer
     int *lists = lab + TT;                          // two per-layer target lists of LIST_CAP
-    const int2 oo = a.origin_out[s];
-    const int2 oi = a.init ? oo : a.origin_in[s];
-    const int shx = oo.x - oi.x, shy = oo.y - oi.y;  // frame shift: eta_out = eta_in + shift
+    const Frame fo = a.frame_out[s];
+    const Frame fi = a.init ? fo : a.frame_in[s];
+    const int2 oo = make_int2(fo.ox, fo.oy);
+    const int shx = fo.ox - fi.ox, shy = fo.oy - fi.oy;  // same node: local index shifts by this
+    // eta_out = eta_in + (d_out - d_in); exact (integer part plus multiples of 2^-14)
+    const R ddx = R((double)shx - ((double)fo.offx - (double)fi.offx));
+    const R ddy = R((double)shy - ((double)fo.offy - (double)fi.offy));
+    const Rsq<R> rq(sd);
     R *Xo = a.xi_out + sd.off;
     R *Yo = Xo + TT;
     const R *Xi = a.init ? nullptr : a.xi_in + sd.off;
     const R *Yi = a.init ? nullptr : Xi + TT;
-    const R eps = R(sp.eps);
+    const R eps = pick<R>(sp.eps, sp.eps_f);
     if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
     R stl[6] = {0, 0, 0, 0, 0, 0};  // sum lambda, lambda lx, lambda ly, lambda rho, lambda rho u, lambda rho v
     int sb[4] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
@@ -336,9 +412,10 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
         if (!allowed_cell(sp, gx, gy)) {
             L = -2;
         } else if (a.init) {
-            const R X = R((double)gx - sd.xc), Y = R((double)gy - sd.yc);
-            if (domain_cell(sp, gx, gy) && phi_disk(X, Y, R(sd.R)) < -R(PHI_TIE)) {
-                Xo[t] = R(0); Yo[t] = R(0); L = 0;
+            // xi = x: eta = d of the initial frame
+            const R e0x = R(frame_d(fo, sd.xc, true)), e0y = R(frame_d(fo, sd.yc, false));
+            if (domain_cell(sp, gx, gy) && phi_eta(e0x, e0y, lx, ly, fo, rq) < -R(PHI_TIE)) {
+                Xo[t] = e0x; Yo[t] = e0y; L = 0;
             }
         } else {
             const int ix = lx + shx, iy = ly + shy;
@@ -346,11 +423,11 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                 const int k = iy * T + ix;
                 const R ex = Xi[k], ey = Yi[k];
                 if (ex == ex) {
-                    const R phi = phi_eta(ex, ey, ix, iy, sd);
+                    const R phi = phi_eta(ex, ey, ix, iy, fi, rq);
                     if (phi < eps && domain_cell(sp, gx, gy)) {
-                        const long long c = grid_index(sp, gx, gy);
                         R rho, u, v;
-                        node_moments<R, S>(sp, a.f, a.carry, c, rho, u, v);
+                        node_moments<R, S>(sp, a.f, a.carry, a.reg_prev, a.pool_prev, wrapi(gx, sp.nx),
+                                           wrapi(gy, sp.ny), rho, u, v);
                         const R lam = R(1) - heaviside<R>(phi, eps);
                         stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
                         stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
@@ -368,8 +445,9 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                                 const R hx = R(-sx) * R(0.5), hy = R(-sy) * R(0.5);
                                 const R dXdx = hx * (R(3) * ex - R(4) * X1 + X2), dYdx = hx * (R(3) * ey - R(4) * Y1 + Y2);
                                 const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
-                                Xo[t] = (ex - (u * dXdx + v * dXdy) - u) + R(shx);
-                                Yo[t] = (ey - (u * dYdx + v * dYdy) - v) + R(shy);
+                                // xi = eta + x - d: the node's own motion enters as -(u - dd)
+                                Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
+                                Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
                                 L = 0;
                             }
                         }
@@ -455,8 +533,8 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
             const int t = prev_full ? cur[k] : k;
             if (!prev_full && lab[t] != l) continue;
             if (a.init) {  // xi = x on the band at initialisation
-                Xo[t] = R(0);
-                Yo[t] = R(0);
+                Xo[t] = R(frame_d(fo, sd.xc, true));
+                Yo[t] = R(frame_d(fo, sd.yc, false));
                 continue;
             }
             const int lx = t % T, ly = t / T;
@@ -469,8 +547,8 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                     const int k0 = iy * T + ix;
                     const R Xe = Xi[k0 + 1], Xw = Xi[k0 - 1], Xn = Xi[k0 + T], Xs = Xi[k0 - T];
                     if (Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs) {
-                        const R pe = phi_eta(Xe, Yi[k0 + 1], ix + 1, iy, sd), pw = phi_eta(Xw, Yi[k0 - 1], ix - 1, iy, sd);
-                        const R pn = phi_eta(Xn, Yi[k0 + T], ix, iy + 1, sd), ps = phi_eta(Xs, Yi[k0 - T], ix, iy - 1, sd);
+                        const R pe = phi_eta(Xe, Yi[k0 + 1], ix + 1, iy, fi, rq), pw = phi_eta(Xw, Yi[k0 - 1], ix - 1, iy, fi, rq);
+                        const R pn = phi_eta(Xn, Yi[k0 + T], ix, iy + 1, fi, rq), ps = phi_eta(Xs, Yi[k0 - T], ix, iy - 1, fi, rq);
                         const R gxp = (pe - pw) / R(2), gyp = (pn - ps) / R(2);
                         const R nn = rsqrt_<R>(gxp * gxp + gyp * gyp);
                         if (nn > R(0)) { use_n = true; nhx = gxp / nn; nhy = gyp / nn; }
@@ -488,7 +566,7 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
         const int lx = t % T, ly = t / T;
         if (lab[t] >= 0) {
             bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
-            if (phi_eta(Xo[t], Yo[t], lx, ly, sd) < eps) {
+            if (phi_eta(Xo[t], Yo[t], lx, ly, fo, rq) < eps) {
                 bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
             }
         } else {
@@ -511,6 +589,9 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
             o[6] = 0; o[7] = 0;
         }
         int2 nx = oo;
+        // mean velocity of the solid at time n (zero at initialisation) moves d
+        double ux = 0.0, uy = 0.0;
+        if (a.stats && st[3] > 0.0) { ux = st[4] / st[3]; uy = st[5] / st[3]; }
         if (bb[4] > bb[5]) {
             atomicOr(a.err, ERR_TILE_OVERFLOW);
         } else {
@@ -522,7 +603,12 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                 nx.y = oo.y + (bb[2] + bb[3]) / 2 - T / 2;
             }
         }
-        a.origin_next[s] = nx;
+        Frame fn;
+        fn.ox = nx.x;
+        fn.oy = nx.y;
+        fn.offx = frame_off(nx.x, sd.xc, frame_d(fo, sd.xc, true) + ux);
+        fn.offy = frame_off(nx.y, sd.yc, frame_d(fo, sd.yc, false) + uy);
+        a.frame_next[s] = fn;
     }
     // Register the 32x8 tiles that the blur zone (grown by one node) touches.
     if (bb[8] <= bb[9]) {
@@ -563,7 +649,7 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
 template <class R>
 struct ForceArgs {
     const R *xi;          // xi^{n+1} tiles
-    const int2 *origin;   // their frames
+    const Frame *frame;   // their frames
     const int *reg_count, *reg_solids, *reg_active, *reg_nactive;
     R *pool;
     const SolidDesc *solids;
@@ -610,8 +696,13 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
     R *eT = sP + KMAX * PATCH_N;                  // [(NXE + NYE) * 3] edge stresses
     __shared__ int ids[KMAX];
     __shared__ int nk;
+    __shared__ Frame sfr[KMAX];
+    __shared__ R sG[KMAX], sD[KMAX], sA[KMAX];
+    __shared__ Rsq<R> srq[KMAX];
+    __shared__ int sT[KMAX];
+    __shared__ long long soff[KMAX];
     const int nact = *a.reg_nactive;
-    const R eps = R(sp.eps), eta = R(sp.eta);
+    const R eps = pick<R>(sp.eps, sp.eps_f), eta = pick<R>(sp.eta, sp.eta_f);
     for (int it = blockIdx.x; it < nact; it += gridDim.x) {
         const int tile = a.reg_active[it];
         const int tx = tile % sp.ntx, ty = tile / sp.ntx;
@@ -627,22 +718,33 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
             nk = n;
         }
         __syncthreads();
+        if (threadIdx.x < nk) {
+            const SolidDesc &sd = a.solids[ids[threadIdx.x]];
+            sfr[threadIdx.x] = a.frame[ids[threadIdx.x]];
+            sG[threadIdx.x] = pick<R>(sd.G, sd.G_f);
+            sD[threadIdx.x] = pick<R>(sd.drho, sd.drho_f);
+            sA[threadIdx.x] = pick<R>(sd.accel, sd.accel_f);
+            srq[threadIdx.x] = Rsq<R>(sd);
+            sT[threadIdx.x] = sd.T;
+            soff[threadIdx.x] = sd.off;
+        }
+        __syncthreads();
         const int n = nk;
         // Stage each solid's xi (and phi) on the tile plus a one-node halo.
         for (int idx = threadIdx.x; idx < n * PATCH_N; idx += blockDim.x) {
             const int ks = idx / PATCH_N, p = idx % PATCH_N;
             const int px = p % PATCH_X, py = p / PATCH_X;
             const int gx = i0 - 1 + px, gy = j0 - 1 + py;
-            const SolidDesc sd = a.solids[ids[ks]];
-            const int2 o = a.origin[ids[ks]];
-            const int lx = sp.wall_x ? gx - o.x : wrapi(gx - o.x, sp.nx);
-            const int ly = sp.wall_y ? gy - o.y : wrapi(gy - o.y, sp.ny);
+            const Frame fr = sfr[ks];
+            const int T = sT[ks];
+            const int lx = sp.wall_x ? gx - fr.ox : wrapi(gx - fr.ox, sp.nx);
+            const int ly = sp.wall_y ? gy - fr.oy : wrapi(gy - fr.oy, sp.ny);
             R X = nanv<R>(), Y = nanv<R>(), P = nanv<R>();
-            if (lx >= 0 && ly >= 0 && lx < sd.T && ly < sd.T) {
-                const R *Xs = a.xi + sd.off;
-                X = Xs[ly * sd.T + lx];
-                Y = Xs[sd.T * sd.T + ly * sd.T + lx];
-                if (X == X) P = phi_eta(X, Y, lx, ly, sd);
+            if (lx >= 0 && ly >= 0 && lx < T && ly < T) {
+                const R *Xs = a.xi + soff[ks];
+                X = Xs[ly * T + lx];
+                Y = Xs[T * T + ly * T + lx];
+                if (X == X) P = phi_eta(X, Y, lx, ly, fr, srq[ks]);
             }
             sX[ks * PATCH_N + p] = X; sY[ks * PATCH_N + p] = Y; sP[ks * PATCH_N + p] = P;
         }
@@ -674,7 +776,7 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                 R dXn, dXt, dYn, dYt, txx, txy, tyy;
                 edge_grad<R>(X[pa[0]], X[pa[1]], X[pa[2]], X[pb[0]], X[pb[1]], X[pb[2]], dXn, dXt);
                 edge_grad<R>(Y[pa[0]], Y[pa[1]], Y[pa[2]], Y[pb[0]], Y[pb[1]], Y[pb[2]], dYn, dYt);
-                const R G = R(a.solids[ids[ks]].G);
+                const R G = sG[ks];
                 // J = d xi / dx = I + d eta / dx (the stored eta excludes the node position)
                 const bool good = xedge ? stress_from_grad<R>(dXn, dXt, dYn, dYt, G, txx, txy, tyy)
                                         : stress_from_grad<R>(dXt, dXn, dYt, dYn, G, txx, txy, tyy);
@@ -695,7 +797,7 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                     const R nrm = rsqrt_<R>(gxx * gxx + gyy * gyy);
                     if (nrm == R(0)) continue;
                     const R nx_ = gxx / nrm, ny_ = gyy / nrm;
-                    const R kk = -eta * fm * (R(a.solids[ids[ks]].G) + R(a.solids[ids[kt]].G));
+                    const R kk = -eta * fm * (sG[ks] + sG[kt]);
                     Cxx += kk * (nx_ * nx_ - R(0.5)); Cxy += kk * (nx_ * ny_); Cyy += kk * (ny_ * ny_ - R(0.5));
                 }
             }
@@ -717,11 +819,10 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                 for (int ks = 0; ks < n; ks++) {
                     const R ph = sP[ks * PATCH_N + p];
                     if (!(ph == ph)) continue;
-                    const SolidDesc &sd = a.solids[ids[ks]];
                     const R lam = R(1) - heaviside<R>(ph, eps);
                     L += lam;
-                    D += lam * (R(sd.rho_s) - R(sp.rho_f));
-                    Ay += lam * (-(R(1) - R(sp.rho_f) / R(sd.rho_s)) * R(sp.gravity));
+                    D += lam * sD[ks];
+                    Ay += lam * sA[ks];
                 }
                 if (L > R(1)) { D /= L; Ay /= L; }
                 R *po = a.pool + (long long)tile * POOL_STRIDE + threadIdx.x;
@@ -745,18 +846,22 @@ struct LbArgs {
     const R *fbody;            // per row x body force
     const int *reg_count;      // registry of this step
     const R *pool;
-    int *clr_count;            // registry of the next step (cleared here)
+    int *clr_count;            // registry of the previous step: read, then cleared for the next step
     int *clr_nactive;
+    const R *pool_prev;        // force pool of the previous step (its Delta rho is the rest base)
     double *mass_partials;
     unsigned *err;
 };
 
 template <class R, class S>
 __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
+    __shared__ int prev_count;
     const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
     const int tile = blockIdx.y * sp.ntx + blockIdx.x;
     const int lt = threadIdx.y * TILE_X + threadIdx.x;
     const int nx = sp.nx, ny = sp.ny, P = (int)sp.P;  // 9 P < 2^31 is checked at creation
+    if (lt == 0) prev_count = a.clr_count[tile];
+    __syncthreads();
     // every push target of this block lies inside the domain
     const bool interior = blockIdx.x > 0 && (blockIdx.x + 1) * TILE_X < nx && blockIdx.y > 0 &&
                           (blockIdx.y + 1) * TILE_Y < ny;
@@ -766,32 +871,35 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         R f[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) f[q] = R(__ldg(a.f_in + q * P + c));
-        const R dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
+        const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const R dr = dro + ds;  // rho - rho_f
         const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-        const R rho = R(sp.rho_f) + dr;
+        const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
         const R inv = R(1) / rho;
         const R ux = (jx + a.carry[c]) * inv, uy = (jy + a.carry[P + c]) * inv;
-        R Fx = a.fbody[j], Fy = R(sp.force_kind == 1 ? sp.fa1 : 0.0), drt = R(0);
+        R Fx = a.fbody[j], Fy = pick<R>(sp.fy, sp.fy_f), drt = R(0);
         if (a.reg_count[tile] > 0) {
             const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
             Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
         }
         if (!(rho == rho) || !(ux == ux) || !(uy == uy)) atomicOr(a.err, ERR_NAN);
-        const R omega = R(1) / R(sp.tau), kf = R(1) - omega / R(2);
+        const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
         const R u2 = ux * ux + uy * uy;
         const R uF = ux * Fx + uy * Fy;
-        const R ddr = dr - drt;  // rho - rho_t
+        const R dd = dro - drt;      // change of the rest base over the step (small)
+        const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
+        f[0] += dd;                  // rest population relative to this step's Delta rho
         R fh[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) {
             const R w = wq<R>(q);
             const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
             const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
-            // f^eq - w rho_f with the SFC correction (Eq. 2_3_feq_sfc): w (rho - rho_t) is
-            // formed first so the velocity terms do not sit on top of w drho
-            R feq = w * ddr + w * rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
-            if (q == 0) feq += drt;
+            // f^eq with the SFC correction (Eq. 2_3_feq_sfc) in the stored form:
+            // minus w rho_f, and minus Delta rho for q = 0
+            const R feq = w * ddr + w * rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
             // Guo term times rho (Eqs. 2_2_Fi, 3_4_Fi)
             const R Fi = rho * w * (R(3) * (cF - uF) + R(9) * cu * cF);
             fh[q] = f[q] - omega * (f[q] - feq) + kf * Fi;
@@ -809,7 +917,7 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
                 const bool ox = di < 0 || di >= nx, oy = dj < 0 || dj >= ny;
                 if ((ox && sp.wall_x) || (oy && sp.wall_y)) {
                     // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
-                    const R uw = (oy && sp.wall_y && dj >= ny) ? R(sp.lid_u) : R(0);
+                    const R uw = (oy && sp.wall_y && dj >= ny) ? pick<R>(sp.lid_u, sp.lid_u_f) : R(0);
                     const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
                     stS<S, R>(a.f_out + oppq(q) * P + c, val);
                 } else {
@@ -831,16 +939,14 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
     }
 }
 
-// Initial populations f = f^eq,SFC(rho_t, 0) as deviations; zero stored half-force.
+// Initial populations f = f^eq,SFC(rho_t, 0): in the stored form (relative to
+// w_q rho_f and, for q = 0, to the initial Delta rho) every value is zero.
 template <class R, class S>
-__global__ void init_f_kernel(SimParams sp, S *f, R *carry, const int *reg_count, const R *pool) {
+__global__ void init_f_kernel(SimParams sp, S *f, R *carry) {
     const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
     if (i >= sp.nx || j >= sp.ny) return;
-    const int tile = blockIdx.y * sp.ntx + blockIdx.x;
     const long long c = (long long)j * sp.nx + i;
-    R drt = 0;
-    if (reg_count[tile] > 0) drt = pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + threadIdx.y * TILE_X + threadIdx.x];
-    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, q == 0 ? drt : R(0));
+    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(0));
     carry[c] = 0;
     carry[sp.P + c] = 0;
 }
@@ -854,29 +960,37 @@ __global__ void field_kernel(SimParams sp, const S *f, const R *carry, const R *
     const int tile = blockIdx.y * sp.ntx + blockIdx.x;
     const long long c = (long long)j * sp.nx + i;
     double v = 0;
-    if (kind <= 2) {
+    if (kind == 0) {
+        // rho = rho_f + rest base + stored values, summed in FP64 so the readout adds no rounding
+        double dr = (double)rest_base<R>(sp, reg_count, pool, i, j);
+        for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c);
+        v = sp.rho_f + dr;
+    } else if (kind <= 2) {
         R rho, u, w;
-        node_moments<R, S>(sp, f, carry, c, rho, u, w);
-        v = kind == 0 ? (double)rho : kind == 1 ? (double)u : (double)w;
+        node_moments<R, S>(sp, f, carry, reg_count, pool, i, j, rho, u, w);
+        v = kind == 1 ? (double)u : (double)w;
     } else if (kind <= 5) {
         R p = 0;
         if (reg_count[tile] > 0) p = pool[(long long)tile * POOL_STRIDE + (kind - 3) * TILE_N + threadIdx.y * TILE_X + threadIdx.x];
         if (kind == 3) v = (double)(fbody[j] + p);
-        else if (kind == 4) v = (double)(R(sp.force_kind == 1 ? sp.fa1 : 0.0) + p);
+        else if (kind == 4) v = (double)(pick<R>(sp.fy, sp.fy_f) + p);
         else v = (double)p;
     } else {
         const int q = kind - 20;
         v = (double)ldS<S, R>(f + q * sp.P + c) + (double)wq<R>(q) * sp.rho_f;
+        if (q == 0) v += (double)rest_base<R>(sp, reg_count, pool, i, j);
     }
     out[c] = v;
 }
 
 // One solid's reference map / level set onto the grid (NaN where not in its band).
 template <class R>
-__global__ void solid_field_kernel(SimParams sp, const R *xi, const int2 *origin, const SolidDesc *solids, int s,
+__global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frames, const SolidDesc *solids, int s,
                                    int kind, double *out) {
     const SolidDesc sd = solids[s];
-    const int2 o = origin[s];
+    const Frame fr = frames[s];
+    const int2 o = make_int2(fr.ox, fr.oy);
+    const Rsq<R> rq(sd);
     const int T = sd.T;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T * T; t += gridDim.x * blockDim.x) {
         const int lx = t % T, ly = t / T;
@@ -886,33 +1000,36 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const int2 *origin
         if (!(X == X)) continue;
         const long long c = grid_index(sp, gx, gy);
         double v;
-        if (kind == 0) v = (double)X + (double)(lx + sd.o0x);
-        else if (kind == 1) v = (double)Y + (double)(ly + sd.o0y);
-        else v = (double)phi_eta(X, Y, lx, ly, sd);
+        // xi = eta + l + off + X_c
+        if (kind == 0) v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
+        else if (kind == 1) v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
+        else v = (double)phi_eta(X, Y, lx, ly, fr, rq);
         out[c] = v;
     }
 }
 
 // Per-solid FP64 statistics of the current state (one CTA per solid).
 template <class R, class S>
-__global__ void solid_stats_kernel(SimParams sp, const S *f, const R *carry, const R *xi, const int2 *origin,
-                                   const SolidDesc *solids, double *out) {
+__global__ void solid_stats_kernel(SimParams sp, const S *f, const R *carry, const int *reg, const R *pool,
+                                   const R *xi, const Frame *frames, const SolidDesc *solids, double *out) {
     __shared__ double red[32 * 6];
     const int s = blockIdx.x;
     const SolidDesc sd = solids[s];
-    const int2 o = origin[s];
+    const Frame fr = frames[s];
+    const int2 o = make_int2(fr.ox, fr.oy);
+    const Rsq<R> rq(sd);
     const int T = sd.T;
-    const R eps = R(sp.eps);
+    const R eps = pick<R>(sp.eps, sp.eps_f);
     double st[6] = {0, 0, 0, 0, 0, 0};
     for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
         const int lx = t % T, ly = t / T;
         const int gx = o.x + lx, gy = o.y + ly;
         const R X = xi[sd.off + t], Y = xi[sd.off + T * T + t];
         if (!(X == X) || !domain_cell(sp, gx, gy)) continue;
-        const R phi = phi_eta(X, Y, lx, ly, sd);
+        const R phi = phi_eta(X, Y, lx, ly, fr, rq);
         if (!(phi < eps)) continue;
         R rho, u, v;
-        node_moments<R, S>(sp, f, carry, grid_index(sp, gx, gy), rho, u, v);
+        node_moments<R, S>(sp, f, carry, reg, pool, wrapi(gx, sp.nx), wrapi(gy, sp.ny), rho, u, v);
         const double lam = 1.0 - (double)heaviside<R>(phi, eps);
         st[0] += lam; st[1] += lam * gx; st[2] += lam * gy;
         st[3] += lam * (double)rho; st[4] += lam * (double)rho * (double)u; st[5] += lam * (double)rho * (double)v;

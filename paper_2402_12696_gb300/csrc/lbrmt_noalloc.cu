@@ -44,9 +44,12 @@ cudaError_t partials_address(int dev, double **out) {
     return cudaSuccess;
 }
 
-// Block b sums rho - rho_f = sum_q (f_q - w_q rho_f) over nodes [b C, (b+1) C).
+// Block b sums rho - rho_f over nodes [b C, (b+1) C): the nine stored values plus
+// the rest base (Delta rho of the step that wrote them, on registered tiles).
 template <class S>
-__global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(const S *f, long long P, double *partials) {
+__global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(lbrmt::SimParams sp, const S *f, const int *reg,
+                                                                         const S *pool, double *partials) {
+    const long long P = sp.P;
     __shared__ double sh[NOALLOC_THREADS];
     const long long begin = (long long)blockIdx.x * NOALLOC_CHUNK;
     const long long end = begin + NOALLOC_CHUNK < P ? begin + NOALLOC_CHUNK : P;
@@ -54,6 +57,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(const S
     for (long long c = begin + threadIdx.x; c < end; c += NOALLOC_THREADS) {
         double s = 0.0;
         for (int q = 0; q < 9; q++) s += (double)f[q * P + c];
+        s += (double)lbrmt::rest_base<S>(sp, reg, pool, (int)(c % sp.nx), (int)(c / sp.nx));
         acc += s;
     }
     sh[threadIdx.x] = acc;
@@ -105,12 +109,17 @@ extern "C" lbrmt_status lbrmt_total_mass_noalloc(lbrmt_sim *s, int sim_index, do
         return LBRMT_ERR_CUDA;
     }
     const int nblocks = (int)((P + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
-    const void *f = s->d.f[s->steps & 1];
+    const int cur = (int)(s->steps & 1);
+    const void *f = s->d.f[cur];
+    const int *reg = s->d.reg_count[1 - cur];
+    const void *pool = s->d.pool[1 - cur];
     // each block overwrites its partial sum, so nothing in the array needs clearing
     if (s->eng->store_size == 4)
-        noalloc_mass_partials<float><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>((const float *)f, P, partials);
+        noalloc_mass_partials<float><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(s->sp, (const float *)f, reg,
+                                                                                 (const float *)pool, partials);
     else
-        noalloc_mass_partials<double><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>((const double *)f, P, partials);
+        noalloc_mass_partials<double><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(s->sp, (const double *)f, reg,
+                                                                                  (const double *)pool, partials);
     noalloc_mass_final<<<1, NOALLOC_THREADS, 0, s->stream>>>(partials, nblocks, s->sp.rho_f * (double)P, dev_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

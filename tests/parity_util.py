@@ -42,17 +42,33 @@ def grid_x(sc):
             np.arange(ny)[:, None].repeat(nx, 1).astype(float))
 
 
+def _abs_vec(ax, ay, bx, by):
+    m = np.isfinite(ax) & np.isfinite(bx) & np.isfinite(ay) & np.isfinite(by)
+    if not m.any():
+        return 0.0, 0.0
+    return float(np.hypot(ax[m] - bx[m], ay[m] - by[m]).max()), float(np.hypot(bx[m], by[m]).max())
+
+
 def compare(sim, ref, sc, core_layers=4):
     """Per-field errors (see module doc) and band-label mismatch counts.
 
     xi is compared on the solid and the first ``core_layers`` band layers
     (the nodes whose values enter the stress stencils and the advection
-    stencils), and separately over the whole band (``xi_band``)."""
+    stencils), and separately over the whole band (``xi_band``).  The
+    absolute errors and the oracle's field magnitudes are returned too
+    (``*_abs``, ``*_max``)."""
     out = {}
     rf = sc["rho_f"]
-    out["rho"] = rel_linf(sim.field_host("rho") - rf, ref.field("rho") - rf, FLOORS["rho"] * rf)
-    out["u"] = rel_linf_vec(sim.field_host("ux"), sim.field_host("uy"), ref.field("ux"), ref.field("uy"), FLOORS["u"])
-    out["F"] = rel_linf_vec(sim.field_host("Fx"), sim.field_host("Fy"), ref.field("Fx"), ref.field("Fy"), FLOORS["F"])
+    ra, rb = sim.field_host("rho") - rf, ref.field("rho") - rf
+    out["rho"] = rel_linf(ra, rb, FLOORS["rho"] * rf)
+    out["rho_abs"] = float(np.abs(ra - rb).max())
+    out["rho_max"] = float(np.abs(rb).max())
+    ua = (sim.field_host("ux"), sim.field_host("uy"), ref.field("ux"), ref.field("uy"))
+    out["u"] = rel_linf_vec(*ua, FLOORS["u"])
+    out["u_abs"], out["u_max"] = _abs_vec(*ua)
+    fa = (sim.field_host("Fx"), sim.field_host("Fy"), ref.field("Fx"), ref.field("Fy"))
+    out["F"] = rel_linf_vec(*fa, FLOORS["F"])
+    out["F_abs"], out["F_max"] = _abs_vec(*fa)
     out["drho"] = rel_linf(sim.field_host("drho"), ref.field("drho"), FLOORS["drho"])
     X, Y = grid_x(sc)
     nx, ny = sc["nx"], sc["ny"]

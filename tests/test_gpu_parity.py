@@ -5,13 +5,18 @@ stated floors).  Tolerances:
   FP64 GPU: 1e-8 on every field -- the two sides differ only in summation
             order, in the 3x3 solve (cofactors vs. elimination) and in the
             storage of xi (absolute in the oracle, eta on the GPU).
-  FP32 GPU: 1e-5 on rho - rho_f, the velocity and xi - x on the solid and the
-            first four band layers, the bound the FP32 path is built to.  The
-            force density F is a difference of half-edge stresses that are
-            themselves differences of FP32 reference-map values, so its bound
-            is derived from the rounding of the stored map (FORCE_TOL_FP32);
-            the outer band layers are extrapolated from inner ones and amplify
-            the rounding of the inner layers (XI_BAND_TOL_FP32).
+  FP32 GPU: relative 1e-5 (the bound the FP32 path is built to) on rho - rho_f,
+            the velocity, the force density and xi - x on the solid and its
+            first four band layers, plus an absolute allowance for what FP32
+            cannot represent (u_32 = 2^-24): the SFC target density
+            Delta rho = sum lambda (rho_s - rho_f) (Eq. 2_3_drho) is an O(1)
+            number held to ~u_32 |rho_s - rho_f| per node and its noise drives
+            the pressure, and the stored populations (O(rho |u|) deviations)
+            round to ~u_32 |u| each step, a random walk over n steps: rho and u
+            get 4 u_32 (max|rho_s - rho_f| + max|u| sqrt(n)); the stress is G
+            times differences of FP32 Jacobian entries, so F gets 8 u_32 max G.
+            The outer band layers are extrapolated from inner ones and amplify
+            their rounding (XI_BAND_TOL_FP32).
 Band-label mismatches (nodes inside one side's band but not the other's) are
 counted; FP64 must have none.
 """
@@ -23,16 +28,21 @@ import pytest
 
 import oracle
 import scenarios
-from parity_util import compare, rel_linf, run_pair
+from parity_util import FLOORS, compare, rel_linf, run_pair
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-8
 FP32_TOL = 1e-5
-# |dF| <~ 8 G_max u_r |xi - X_c|_max / |F|_max with u_r = 2^-24; the cases here have
-# G_max |xi - X_c|_max ~ 0.3 and |F|_max ~ 1e-4 .. 1e-3, giving ~1e-2 .. 1e-1.
-FORCE_TOL_FP32 = 2e-1
-XI_BAND_TOL_FP32 = 1e-2
+U32 = 2.0 ** -24
+XI_BAND_TOL_FP32 = 1e-4
+
+
+def fp32_allowance(sc, r, n):
+    drho = max([abs(s["rho_s"] - sc["rho_f"]) for s in sc["solids"]] + [0.0])
+    gmax = max([s["G"] for s in sc["solids"]] + [0.0])
+    walk = 4 * U32 * (drho + r["u_max"] * np.sqrt(n))
+    return {"rho": walk, "u": walk, "F": 8 * U32 * gmax}
 
 OUT = os.environ.get("LBRMT_PARITY_LOG", "")
 
@@ -54,16 +64,18 @@ def _built():
     oracle.build()
 
 
-def _check(res, prec, fields_state=("rho", "u", "xi")):
+def _check(res, prec, sc):
     for n, r in res.items():
         if prec == "fp64":
             for k in ("rho", "u", "xi", "xi_band", "F", "drho"):
                 assert r[k] < FP64_TOL, (n, k, r)
             assert r["label_mismatch"] == 0, (n, r)
         else:
-            for k in fields_state:
-                assert r[k] < FP32_TOL, (n, k, r)
-            assert r["F"] < FORCE_TOL_FP32, (n, r)
+            allow = fp32_allowance(sc, r, n)
+            for k in ("rho", "u", "F"):
+                scale = max(r[k + "_max"], FLOORS[k] * (sc["rho_f"] if k == "rho" else 1.0))
+                assert r[k + "_abs"] <= FP32_TOL * scale + allow[k], (n, k, r)
+            assert r["xi"] < FP32_TOL, (n, r)
             assert r["xi_band"] < XI_BAND_TOL_FP32, (n, r)
 
 
@@ -83,7 +95,7 @@ def test_parity_1_10_100_steps(case, prec):
     sc = CASES[case]()
     res = run_pair(sc, prec, [1, 10, 100])
     _log(f"{case}/{prec}", res)
-    _check(res, prec)
+    _check(res, prec, sc)
 
 
 def test_contact_is_exercised():
@@ -102,10 +114,7 @@ def test_fluid_only_ragged_grid(prec):
     sc = scenarios.fluid_only(100, 60, 1, 0, 0.7, force_kind=1, force_a=(0.0, 2e-5))
     res = run_pair(sc, prec, [1, 50])
     _log(f"ragged/{prec}", res)
-    for n, r in res.items():
-        tol = FP64_TOL if prec == "fp64" else FP32_TOL
-        for k in ("rho", "u"):
-            assert r[k] < tol, (n, k, r)
+    _check(res, prec, sc)
 
 
 def test_couette_and_lid_fp64():
