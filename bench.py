@@ -237,11 +237,17 @@ def bench_lbrmt(args):
     alg_bytes = N * (18 * sf + 4 * sf + 3 * sf * band_frac)
     k1_ms = kms[2]
     achieved = alg_bytes / (k1_ms / 1e3) / 1e9
+    # DRAM traffic per launch from the committed ncu summary, valid only while the
+    # kernel source is the one that was profiled
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"lb_step_kernel_traffic_{args.precision}.json")
-    if os.path.exists(tfile):
+    tfile = os.path.join(ROOT, "profiles", f"lb_step_kernel_mixing4096_{args.precision}_traffic.json")
+    if os.path.exists(tfile) and args.size == 4096:
         try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
+            import hashlib
+            rec = json.load(open(tfile))
+            src = os.path.join(ROOT, "paper_2402_12696_gb300", "csrc", "lbrmt_kernels.cuh")
+            if hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] == rec.get("kernel_source_sha1"):
+                traffic = rec.get("bytes_per_launch")
         except Exception:
             traffic = None
 
