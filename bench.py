@@ -233,8 +233,9 @@ def bench_lbrmt(args):
 
     # ---- roofline of the dominant kernel (fused LB kernel) ------------------
     peak, peak_kind = _peaks()
-    sf = 4 if args.precision == "fp32" else 8
-    alg_bytes = N * (18 * sf + 4 * sf + 3 * sf * band_frac)
+    sf = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}[args.precision]   # stored population / carry
+    sr = 8 if args.precision == "fp64" else 4                            # force pool
+    alg_bytes = N * (18 * sf + 4 * sf + 3 * sr * band_frac)
     k1_ms = kms[2]
     achieved = alg_bytes / (k1_ms / 1e3) / 1e9
     # DRAM traffic per launch from the committed ncu summary, valid only while the
@@ -263,12 +264,13 @@ def bench_lbrmt(args):
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": BASE_WORKLOAD if args.size == 4096 else
                    f"{args.size}x{args.size} crop of " + BASE_WORKLOAD, "precision": args.precision, "seed": "rank",
                    "nodes": N, "solids": len(sc["solids"]),
-                   "l2": f"inputs larger than L2 (population planes {2 * 9 * N * (4 if args.precision == 'fp32' else 8) / 1e9:.2f} GB)",
+                   "l2": f"inputs larger than L2 (population planes {2 * 9 * N * sf / 1e9:.2f} GB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "kernel_ms": {"rmt_solid_kernel": kms[0], "force_kernel": kms[1], "lb_step_kernel": kms[2]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -293,7 +295,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="lbrmt", choices=["lbrmt", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--size", type=int, default=4096,
                     help="grid side; below 4096 a crop of the workload with the same disk density")
     ap.add_argument("--e2e-steps", type=int, default=50)

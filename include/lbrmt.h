@@ -84,7 +84,9 @@ typedef struct {
     double gravity;             /* g >= 0 acting in -y on solids: a = (1 - rho_f/rho_s) g (Sec. 4.3) */
     int force_kind;             /* LBRMT_FORCE_*: body force on all phases */
     double force_a[2];          /* (fx, fy) for CONST, (A, 0) for f_x = A sin(2 pi y / ny) */
-    int precision;              /* LBRMT_FP32, LBRMT_FP64 (FP16/BF16 storage: reserved) */
+    int precision;              /* LBRMT_FP32 / LBRMT_FP64 arithmetic and storage; LBRMT_FP16_STORE /
+                                   LBRMT_BF16_STORE: FP32 arithmetic, populations and half-force
+                                   stored in 16 bits (FP16 with power-of-two scales 2^10 and 2^14) */
     int max_solids_per_tile;    /* registry slots per 32x8 tile, 1..8 */
     int rmax;                   /* largest extrapolation window half-width (>= 2) */
     lbrmt_alloc_fn alloc;       /* optional device allocator */

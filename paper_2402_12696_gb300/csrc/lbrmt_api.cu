@@ -80,14 +80,17 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (c.max_solids_per_tile < 1 || c.max_solids_per_tile > KMAX || c.rmax < 2 || c.rmax > 20) return LBRMT_ERR_ARG;
     if (c.lid_u != 0.0 && c.bc_y != LBRMT_WALL) return LBRMT_ERR_ARG;
     if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > 2) return LBRMT_ERR_ARG;
-    if (c.precision != LBRMT_FP32 && c.precision != LBRMT_FP64) return LBRMT_ERR_ARG;
+    if (c.precision < LBRMT_FP32 || c.precision > LBRMT_BF16_STORE) return LBRMT_ERR_ARG;
     if (std::fabs(c.lid_u) / std::sqrt(1.0 / 3.0) > 0.3) return LBRMT_ERR_PARAM_RANGE;  // Ma* <= 0.3
 
     lbrmt_sim *s = new lbrmt_sim();
     s->cfg = c;
     if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
     s->stream = (cudaStream_t)cuda_stream;
-    s->eng = c.precision == LBRMT_FP64 ? &engine_fp64 : &engine_fp32;
+    s->eng = c.precision == LBRMT_FP64 ? &engine_fp64
+             : c.precision == LBRMT_FP16_STORE ? &engine_fp16
+             : c.precision == LBRMT_BF16_STORE ? &engine_bf16
+                                                : &engine_fp32;
     SimParams &sp = s->sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.nx = c.nx; sp.ny = c.ny; sp.wall_x = c.bc_x; sp.wall_y = c.bc_y;
@@ -114,7 +117,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         ok = ok && (d.reg_nactive[k] = (int *)dalloc(s, 16));
         ok = ok && (d.pool[k] = dalloc(s, ntiles * POOL_STRIDE * rs));
     }
-    ok = ok && (d.carry = dalloc(s, 2 * P * rs));
+    ok = ok && (d.carry = dalloc(s, 2 * P * ss));
     ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
     ok = ok && (d.mass_partials = (double *)dalloc(s, ntiles * TILE_Y * 8));
     ok = ok && (d.err = (unsigned *)dalloc(s, 16));
@@ -189,6 +192,7 @@ static lbrmt_status check_flags(lbrmt_sim *s) {
     if (f & ERR_EXTRAP) return fail(s, LBRMT_ERR_EXTRAP, "extrapolation window exceeded rmax");
     if (f & ERR_STENCIL) return fail(s, LBRMT_ERR_EXTRAP, "advection stencil left the band");
     if (f & ERR_SINGULAR) return fail(s, LBRMT_ERR_NUMERIC, "singular reference-map Jacobian");
+    if (f & ERR_OVERFLOW16) return fail(s, LBRMT_ERR_OVERFLOW, "a population exceeded the 16-bit storage range");
     return fail(s, LBRMT_ERR_NUMERIC, "device error flag");
 }
 

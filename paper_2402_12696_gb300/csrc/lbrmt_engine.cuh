@@ -29,17 +29,19 @@ struct EngineOps {
 
 extern const EngineOps engine_fp32;
 extern const EngineOps engine_fp64;
+extern const EngineOps engine_fp16;
+extern const EngineOps engine_bf16;
 
 template <class R, class S>
-__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, R *carry, const int *reg, const R *pool) {
+__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, const int *reg, const R *pool) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sp.P) return;
     const int i = (int)(c % sp.nx), j = (int)(c / sp.nx);
     const double base = (double)rest_base<R>(sp, reg, pool, i, j);
     for (int q = 0; q < 9; q++)
         stS<S, R>(f + q * sp.P + c, R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f - (q == 0 ? base : 0.0)));
-    carry[c] = 0;
-    carry[sp.P + c] = 0;
+    stC<S, R>(carry + c, R(0));
+    stC<S, R>(carry + sp.P + c, R(0));
 }
 
 template <class R, class S>
@@ -81,7 +83,7 @@ struct Engine {
         RmtArgs<R, S> a;
         const int p = parity, q = 1 - parity;
         a.f = (const S *)d.f[p];
-        a.carry = (const R *)d.carry;
+        a.carry = (const S *)d.carry;
         a.reg_prev = d.reg_count[q];
         a.pool_prev = (const R *)d.pool[q];
         a.xi_in = (const R *)d.xi[p];
@@ -128,7 +130,7 @@ struct Engine {
             force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 1));
         }
         dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
-        init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (R *)d.carry);
+        init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (S *)d.carry);
         return cudaGetLastError();
     }
 
@@ -144,7 +146,7 @@ struct Engine {
         LbArgs<R, S> a;
         a.f_in = (const S *)d.f[p];
         a.f_out = (S *)d.f[q];
-        a.carry = (R *)d.carry;
+        a.carry = (S *)d.carry;
         a.fbody = (const R *)d.fbody;
         a.reg_count = d.reg_count[p];
         a.pool = (const R *)d.pool[p];
@@ -168,14 +170,14 @@ struct Engine {
             return cudaGetLastError();
         }
         const int r = lastreg;
-        field_kernel<R, S><<<grid, blk, 0, st>>>(sp, (const S *)d.f[cur], (const R *)d.carry, (const R *)d.fbody,
+        field_kernel<R, S><<<grid, blk, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry, (const R *)d.fbody,
                                                  d.reg_count[r], (const R *)d.pool[r], kind, out);
         return cudaGetLastError();
     }
 
     static cudaError_t stats(const SimParams &sp, const DevState &d, int cur, double *out, cudaStream_t st) {
         if (sp.nsolids == 0) return cudaSuccess;
-        solid_stats_kernel<R, S><<<sp.nsolids, 256, 0, st>>>(sp, (const S *)d.f[cur], (const R *)d.carry,
+        solid_stats_kernel<R, S><<<sp.nsolids, 256, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry,
                                                              d.reg_count[1 - cur], (const R *)d.pool[1 - cur],
                                                              (const R *)d.xi[cur], d.frame[cur], d.solids, out);
         return cudaGetLastError();
@@ -183,7 +185,7 @@ struct Engine {
 
     static cudaError_t set_pop(const SimParams &sp, const DevState &d, int cur, const double *src, cudaStream_t st) {
         const int nb = (int)((sp.P + 255) / 256);
-        set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (R *)d.carry, d.reg_count[1 - cur],
+        set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (S *)d.carry, d.reg_count[1 - cur],
                                                  (const R *)d.pool[1 - cur]);
         return cudaGetLastError();
     }

@@ -17,6 +17,8 @@
 // in solid-local coordinates xi - X_c.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -38,7 +40,7 @@ constexpr double COS_TIE = 1e-9;
 
 enum ErrBits : unsigned {
     ERR_NAN = 1u, ERR_TILE_OVERFLOW = 2u, ERR_SLOT_OVERFLOW = 4u, ERR_EXTRAP = 8u,
-    ERR_SINGULAR = 16u, ERR_STENCIL = 32u
+    ERR_SINGULAR = 16u, ERR_STENCIL = 32u, ERR_OVERFLOW16 = 64u
 };
 
 // Scalar parameters, passed by value.
@@ -127,8 +129,47 @@ template <class R> __device__ __forceinline__ R heaviside(R phi, R eps) {
 // Level set of a disk in solid-local reference coordinates, phi_0(X) = |X - c| - R.
 template <class R> __device__ __forceinline__ R phi_disk(R X, R Y, R rad) { return rsqrt_<R>(X * X + Y * Y) - rad; }
 
-template <class S, class R> __device__ __forceinline__ R ldS(const S *p) { return R(*p); }
-template <class S, class R> __device__ __forceinline__ void stS(S *p, R v) { *p = S(v); }
+// Storage of the populations and of the half-force carry.  FP32/FP64 store the
+// values as they are.  The 16-bit variants store value x scale with a
+// power-of-two scale per field (exact): FP16 keeps populations x 2^10 and the
+// carry x 2^14, so deviations down to ~1e-11 stay normal and up to 64 fit;
+// BF16 has FP32's range and needs no scale.
+template <class S> struct StoreScale { static constexpr float pop = 1.0f, carry = 1.0f; };
+template <> struct StoreScale<__half> { static constexpr float pop = 1024.0f, carry = 16384.0f; };
+template <class S> __device__ __forceinline__ float to_f(S v) { return (float)v; }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class S> __device__ __forceinline__ S from_f(float v) { return S(v); }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <class S> __host__ __device__ constexpr bool is16() { return sizeof(S) == 2; }
+
+template <class S, class R> __device__ __forceinline__ R ldS(const S *p) {
+    if constexpr (is16<S>()) return R(to_f<S>(*p) * (1.0f / StoreScale<S>::pop));
+    else return R(*p);
+}
+template <class S, class R> __device__ __forceinline__ void stS(S *p, R v) {
+    if constexpr (is16<S>()) *p = from_f<S>(float(v) * StoreScale<S>::pop);
+    else *p = S(v);
+}
+template <class S, class R> __device__ __forceinline__ R ldC(const S *p) {
+    if constexpr (is16<S>()) return R(to_f<S>(*p) * (1.0f / StoreScale<S>::carry));
+    else return R(*p);
+}
+template <class S, class R> __device__ __forceinline__ void stC(S *p, R v) {
+    if constexpr (is16<S>()) *p = from_f<S>(float(v) * StoreScale<S>::carry);
+    else *p = S(v);
+}
+// read-only global load of a stored population
+template <class S, class R> __device__ __forceinline__ R ldG(const S *p) {
+    if constexpr (is16<S>()) return ldS<S, R>(p);
+    else return R(__ldg(p));
+}
+// a stored 16-bit population would exceed the format's range
+template <class S, class R> __device__ __forceinline__ bool store_overflow(R v) {
+    if constexpr (sizeof(S) == 2 && StoreScale<S>::pop != 1.0f) return fabsf(float(v)) * StoreScale<S>::pop > 60000.0f;
+    else return false;
+}
 
 __device__ __forceinline__ bool allowed_cell(const SimParams &sp, int gx, int gy) {
     if (sp.wall_x && (gx < -2 || gx > sp.nx + 1)) return false;
@@ -157,7 +198,7 @@ __device__ __forceinline__ R rest_base(const SimParams &sp, const int *reg, cons
 // Moments of node (i, j): rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
 // reg/pool: registry and force pool of the step that wrote the populations.
 template <class R, class S>
-__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const R *carry, const int *reg,
+__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const S *carry, const int *reg,
                                              const R *pool, int i, int j, R &rho, R &u, R &v) {
     const long long c = (long long)j * sp.nx + i;
     R fq[9];
@@ -169,8 +210,8 @@ __device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, co
     R jy = (fq[2] - fq[4]) + (fq[5] - fq[7]) + (fq[6] - fq[8]);
     rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
     R inv = R(1) / rho;
-    u = (jx + carry[c]) * inv;
-    v = (jy + carry[sp.P + c]) * inv;
+    u = (jx + ldC<S, R>(carry + c)) * inv;
+    v = (jy + ldC<S, R>(carry + sp.P + c)) * inv;
 }
 
 // Block-wide sum of NV doubles (blockDim.x multiple of 32, <= 1024).
@@ -200,7 +241,7 @@ __device__ void block_sum(double (&v)[NV], double *sh /* 32*NV */) {
 template <class R, class S>
 struct RmtArgs {
     const S *f;          // populations f^n
-    const R *carry;
+    const S *carry;
     const int *reg_prev; // registry and pool of the step that wrote f^n
     const R *pool_prev;
     const R *xi_in;      // xi^n tiles (unused at init)
@@ -842,7 +883,7 @@ template <class R, class S>
 struct LbArgs {
     const S *f_in;
     S *f_out;
-    R *carry;
+    S *carry;
     const R *fbody;            // per row x body force
     const int *reg_count;      // registry of this step
     const R *pool;
@@ -870,7 +911,7 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         const int c = j * nx + i;
         R f[9];
 #pragma unroll
-        for (int q = 0; q < 9; q++) f[q] = R(__ldg(a.f_in + q * P + c));
+        for (int q = 0; q < 9; q++) f[q] = ldG<S, R>(a.f_in + q * P + c);
         const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
         const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const R dr = dro + ds;  // rho - rho_f
@@ -878,7 +919,7 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
         const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
         const R inv = R(1) / rho;
-        const R ux = (jx + a.carry[c]) * inv, uy = (jy + a.carry[P + c]) * inv;
+        const R ux = (jx + ldC<S, R>(a.carry + c)) * inv, uy = (jy + ldC<S, R>(a.carry + P + c)) * inv;
         R Fx = a.fbody[j], Fy = pick<R>(sp.fy, sp.fy_f), drt = R(0);
         if (a.reg_count[tile] > 0) {
             const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
@@ -904,8 +945,14 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
             const R Fi = rho * w * (R(3) * (cF - uF) + R(9) * cu * cF);
             fh[q] = f[q] - omega * (f[q] - feq) + kf * Fi;
         }
-        a.carry[c] = R(0.5) * rho * Fx;
-        a.carry[P + c] = R(0.5) * rho * Fy;
+        stC<S, R>(a.carry + c, R(0.5) * rho * Fx);
+        stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy);
+        if constexpr (is16<S>()) {
+            bool ov = false;
+#pragma unroll
+            for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q]);
+            if (ov) atomicOr(a.err, ERR_OVERFLOW16);
+        }
         stS<S, R>(a.f_out + c, fh[0]);
         if (interior) {
 #pragma unroll
@@ -942,18 +989,18 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
 // Initial populations f = f^eq,SFC(rho_t, 0): in the stored form (relative to
 // w_q rho_f and, for q = 0, to the initial Delta rho) every value is zero.
 template <class R, class S>
-__global__ void init_f_kernel(SimParams sp, S *f, R *carry) {
+__global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
     const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
     if (i >= sp.nx || j >= sp.ny) return;
     const long long c = (long long)j * sp.nx + i;
     for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(0));
-    carry[c] = 0;
-    carry[sp.P + c] = 0;
+    stC<S, R>(carry + c, R(0));
+    stC<S, R>(carry + sp.P + c, R(0));
 }
 
 // Fields to a double grid.  kind: 0 rho, 1 ux, 2 uy, 3 Fx, 4 Fy, 5 drho, 20+q f_q.
 template <class R, class S>
-__global__ void field_kernel(SimParams sp, const S *f, const R *carry, const R *fbody, const int *reg_count,
+__global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *fbody, const int *reg_count,
                              const R *pool, int kind, double *out) {
     const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
     if (i >= sp.nx || j >= sp.ny) return;
@@ -1010,7 +1057,7 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
 
 // Per-solid FP64 statistics of the current state (one CTA per solid).
 template <class R, class S>
-__global__ void solid_stats_kernel(SimParams sp, const S *f, const R *carry, const int *reg, const R *pool,
+__global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, const int *reg, const R *pool,
                                    const R *xi, const Frame *frames, const SolidDesc *solids, double *out) {
     __shared__ double red[32 * 6];
     const int s = blockIdx.x;

@@ -46,9 +46,9 @@ cudaError_t partials_address(int dev, double **out) {
 
 // Block b sums rho - rho_f over nodes [b C, (b+1) C): the nine stored values plus
 // the rest base (Delta rho of the step that wrote them, on registered tiles).
-template <class S>
+template <class R, class S>
 __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(lbrmt::SimParams sp, const S *f, const int *reg,
-                                                                         const S *pool, double *partials) {
+                                                                         const R *pool, double *partials) {
     const long long P = sp.P;
     __shared__ double sh[NOALLOC_THREADS];
     const long long begin = (long long)blockIdx.x * NOALLOC_CHUNK;
@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(lbrmt::
     double acc = 0.0;
     for (long long c = begin + threadIdx.x; c < end; c += NOALLOC_THREADS) {
         double s = 0.0;
-        for (int q = 0; q < 9; q++) s += (double)f[q * P + c];
-        s += (double)lbrmt::rest_base<S>(sp, reg, pool, (int)(c % sp.nx), (int)(c / sp.nx));
+        for (int q = 0; q < 9; q++) s += (double)lbrmt::ldS<S, R>(f + q * P + c);
+        s += (double)lbrmt::rest_base<R>(sp, reg, pool, (int)(c % sp.nx), (int)(c / sp.nx));
         acc += s;
     }
     sh[threadIdx.x] = acc;
@@ -114,12 +114,24 @@ extern "C" lbrmt_status lbrmt_total_mass_noalloc(lbrmt_sim *s, int sim_index, do
     const int *reg = s->d.reg_count[1 - cur];
     const void *pool = s->d.pool[1 - cur];
     // each block overwrites its partial sum, so nothing in the array needs clearing
-    if (s->eng->store_size == 4)
-        noalloc_mass_partials<float><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(s->sp, (const float *)f, reg,
-                                                                                 (const float *)pool, partials);
-    else
-        noalloc_mass_partials<double><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(s->sp, (const double *)f, reg,
-                                                                                  (const double *)pool, partials);
+    switch (s->cfg.precision) {
+    case LBRMT_FP64:
+        noalloc_mass_partials<double, double><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(
+            s->sp, (const double *)f, reg, (const double *)pool, partials);
+        break;
+    case LBRMT_FP16_STORE:
+        noalloc_mass_partials<float, __half><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(
+            s->sp, (const __half *)f, reg, (const float *)pool, partials);
+        break;
+    case LBRMT_BF16_STORE:
+        noalloc_mass_partials<float, __nv_bfloat16><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(
+            s->sp, (const __nv_bfloat16 *)f, reg, (const float *)pool, partials);
+        break;
+    default:
+        noalloc_mass_partials<float, float><<<nblocks, NOALLOC_THREADS, 0, s->stream>>>(
+            s->sp, (const float *)f, reg, (const float *)pool, partials);
+        break;
+    }
     noalloc_mass_final<<<1, NOALLOC_THREADS, 0, s->stream>>>(partials, nblocks, s->sp.rho_f * (double)P, dev_out);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
