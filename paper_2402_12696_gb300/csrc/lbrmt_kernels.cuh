@@ -114,6 +114,9 @@ template <> __device__ __forceinline__ double rsin<double>(double x) { return si
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+template <class R> __device__ __forceinline__ R rcp_rn(R x);
+template <> __device__ __forceinline__ float rcp_rn<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp_rn<double>(double x) { return __drcp_rn(x); }
 template <class R> __device__ __forceinline__ R nanv();
 template <> __device__ __forceinline__ float nanv<float>() { return __int_as_float(0x7fc00000); }
 template <> __device__ __forceinline__ double nanv<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
@@ -918,7 +921,7 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
         const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
-        const R inv = R(1) / rho;
+        const R inv = rcp_rn<R>(rho);
         const R ux = (jx + ldC<S, R>(a.carry + c)) * inv, uy = (jy + ldC<S, R>(a.carry + P + c)) * inv;
         R Fx = a.fbody[j], Fy = pick<R>(sp.fy, sp.fy_f), drt = R(0);
         if (a.reg_count[tile] > 0) {
@@ -932,18 +935,28 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         const R dd = dro - drt;      // change of the rest base over the step (small)
         const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
         f[0] += dd;                  // rest population relative to this step's Delta rho
+        // Collision f^ = f - omega (f - f^eq) + (1 - omega/2) F_i (Eq. 2_2_bgk_force) with
+        // f^eq of Eq. 2_3_feq_sfc in the stored form (minus w rho_f, minus Delta rho for
+        // q = 0) and the Guo term of Eq. 2_2_Fi times rho.  Opposite directions share the
+        // even parts (in c) of f^eq and F_i and differ in the sign of the odd parts.
+        const R om1 = R(1) - omega;
+        const R r15u2 = R(1.5) * u2, r3uF = R(3) * uF;
         R fh[9];
+        {
+            const R w = R(4) / R(9), rw = rho * w;
+            fh[0] = om1 * f[0] + omega * (w * ddr - rw * r15u2) - kf * rw * r3uF;
+        }
 #pragma unroll
-        for (int q = 0; q < 9; q++) {
-            const R w = wq<R>(q);
+        for (int pr = 0; pr < 4; pr++) {
+            const int q = pr + 1 + (pr >= 2 ? 2 : 0);  // 1, 2, 5, 6; partners 3, 4, 7, 8
+            const int qo = oppq(q);
+            const R w = wq<R>(q), rw = rho * w;
             const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
             const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
-            // f^eq with the SFC correction (Eq. 2_3_feq_sfc) in the stored form:
-            // minus w rho_f, and minus Delta rho for q = 0
-            const R feq = w * ddr + w * rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
-            // Guo term times rho (Eqs. 2_2_Fi, 3_4_Fi)
-            const R Fi = rho * w * (R(3) * (cF - uF) + R(9) * cu * cF);
-            fh[q] = f[q] - omega * (f[q] - feq) + kf * Fi;
+            const R even = omega * (w * ddr + rw * (R(4.5) * cu * cu - r15u2)) + kf * rw * (R(9) * cu * cF - r3uF);
+            const R odd = R(3) * rw * (omega * cu + kf * cF);
+            fh[q] = om1 * f[q] + even + odd;
+            fh[qo] = om1 * f[qo] + even - odd;
         }
         stC<S, R>(a.carry + c, R(0.5) * rho * Fx);
         stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy);
