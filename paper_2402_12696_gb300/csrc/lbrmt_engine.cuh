@@ -48,7 +48,7 @@ template <class R, class S>
 struct Engine {
     static cudaError_t configure(const SimParams &sp, int tmax, LaunchInfo *li) {
         li->tmax = tmax;
-        li->rmt_smem = 4 * tmax * tmax + 8 * LIST_CAP;
+        li->rmt_smem = ((tmax * tmax + 15) & ~15) + 8 * LIST_CAP;
         {
             float tf[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
             double td[(RMAX_TAB + 1) * (RMAX_TAB + 1)];

@@ -31,6 +31,9 @@ constexpr int NXE = (TILE_X + 1) * TILE_Y;  // x-edges of a tile
 constexpr int NYE = TILE_X * (TILE_Y + 1);  // y-edges of a tile
 constexpr int KMAX = 8;                     // registry slots per tile (upper bound)
 constexpr int RMT_THREADS = 256;
+#ifndef RMT_MIN_BLOCKS
+#define RMT_MIN_BLOCKS 4
+#endif
 constexpr int LIST_CAP = 2048;              // per-layer target list in shared memory
 constexpr int POOL_STRIDE = 3 * TILE_N;     // per tile: Fx, Fy, drho planes
 // Tie rules shared with the method's definition: a node with |phi| <= PHI_TIE
@@ -77,7 +80,13 @@ struct SolidDesc {
 struct Frame {
     int ox, oy;
     float offx, offy;
+    // box (local, inclusive) holding every solid and band node of the tile;
+    // values outside it are stale and never read
+    short bx0, bx1, by0, by1;
 };
+__host__ __device__ __forceinline__ bool in_box(const Frame &f, int x, int y) {
+    return x >= f.bx0 && x <= f.bx1 && y >= f.by0 && y <= f.by1;
+}
 
 // Device pointers of one simulation (type-erased; the kernels cast).
 struct DevState {
@@ -249,7 +258,8 @@ struct RmtArgs {
     const R *pool_prev;
     const R *xi_in;      // xi^n tiles (unused at init)
     R *xi_out;           // xi^{n+1} tiles
-    const Frame *frame_in, *frame_out;
+    const Frame *frame_in;
+    Frame *frame_out;    // origin read at entry; its box is written at exit
     Frame *frame_next;   // frame of the next step's output tile
     int *reg_count, *reg_solids, *reg_active, *reg_nactive;
     double *stats;       // S x 8 (state at time n), may be null at init
@@ -286,7 +296,7 @@ struct Lsq {
 };
 
 template <class R>
-__device__ __forceinline__ void lsq_cell(Lsq<R> &A, const int *lab, const R *X, const R *Y, int k, int l, int dx,
+__device__ __forceinline__ void lsq_cell(Lsq<R> &A, const signed char *lab, const R *X, const R *Y, int k, int l, int dx,
                                          int dy, bool use_n, R nhx, R nhy) {
     const int L = lab[k];
     if (!(L >= 0 && L < l)) return;
@@ -312,9 +322,9 @@ __device__ __forceinline__ void lsq_cell(Lsq<R> &A, const int *lab, const R *X, 
 // weights do not depend on the window size, so growing r from r-1 only adds
 // the ring |dx| = r or |dy| = r to the sums of the smaller window.
 template <class R>
-__device__ void extrapolate_target(const SimParams &sp, const int *lab, R *X, R *Y, int T, int t, int l,
-                                   bool use_n, R nhx, R nhy, unsigned *err) {
-    const int tx = t % T, ty = t / T;
+__device__ void extrapolate_target(const SimParams &sp, const signed char *lab, R *X, R *Y, int T, int tx, int ty,
+                                   int l, bool use_n, R nhx, R nhy, unsigned *err) {
+    const int t = ty * T + tx;
     Lsq<R> A;
     A.nvalid = A.n = A.sx = A.sy = A.sxx = A.syy = A.sxy = 0;
     A.haveref = false;
@@ -418,8 +428,30 @@ __device__ __forceinline__ void warp_minmax(int &v, bool is_min) {
     v = (int)r - (1 << 30);
 }
 
+// Claim a free label byte (-1 -> l) with a CAS on the 32-bit word holding it.
+__device__ __forceinline__ bool claim_label(signed char *lab, int q, int l) {
+    unsigned *w = reinterpret_cast<unsigned *>(lab + (q & ~3));
+    const int sh = (q & 3) * 8;
+    unsigned old = *reinterpret_cast<volatile unsigned *>(w), assumed;
+    do {
+        assumed = old;
+        if (((assumed >> sh) & 0xffu) != 0xffu) return false;
+        old = atomicCAS(w, assumed, (assumed & ~(0xffu << sh)) | ((unsigned)l << sh));
+    } while (old != assumed);
+    return true;
+}
+
+// Row-major walk of a w-wide box by a CTA: (c, r) of item k, advanced by blockDim.x items at a time.
+struct BoxWalk {
+    int c, r, dc, dr, w;
+    __device__ __forceinline__ BoxWalk(int w_) : w(w_ > 0 ? w_ : 1) {
+        c = threadIdx.x % w; r = threadIdx.x / w; dc = blockDim.x % w; dr = blockDim.x / w;
+    }
+    __device__ __forceinline__ void next() { c += dc; r += dr; if (c >= w) { c -= w; r++; } }
+};
+
 template <class R, class S>
-__global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
+__global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int nlist;
     __shared__ int bb[12];  // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
@@ -428,8 +460,8 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
     const SolidDesc sd = a.solids[s];
     const int T = sd.T, TT = T * T;
     const int lane = threadIdx.x & 31;
-    int *lab = reinterpret_cast<int *>(smem);       // -2 outside the pads, -1 free, 0 solid, l layer
-    int *lists = lab + TT;                          // two per-layer target lists of LIST_CAP
+    signed char *lab = reinterpret_cast<signed char *>(smem);        // -1 free, 0 solid, l layer
+    int *lists = reinterpret_cast<int *>(smem + ((TT + 15) & ~15));  // two per-layer lists of packed (lx, ly)
     const Frame fo = a.frame_out[s];
     const Frame fi = a.init ? fo : a.frame_in[s];
     const int2 oo = make_int2(fo.ox, fo.oy);
@@ -444,63 +476,65 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
     const R *Yi = a.init ? nullptr : Xi + TT;
     const R eps = pick<R>(sp.eps, sp.eps_f);
     if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
+    for (int k = threadIdx.x; k < (TT + 15) >> 4; k += blockDim.x)
+        reinterpret_cast<int4 *>(lab)[k] = make_int4(-1, -1, -1, -1);
     R stl[6] = {0, 0, 0, 0, 0, 0};  // sum lambda, lambda lx, lambda ly, lambda rho, lambda rho u, lambda rho v
     int sb[4] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
     __syncthreads();
 
-    // Pass 0: the advected set S = {domain nodes with phi^n < 0}, Eqs. 3_1_refmap_adv / 3_1_eno.
-    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
-        const int lx = t % T, ly = t / T;
-        const int gx = oo.x + lx, gy = oo.y + ly;
-        int L = -1;
-        if (!allowed_cell(sp, gx, gy)) {
-            L = -2;
-        } else if (a.init) {
-            // xi = x: eta = d of the initial frame
-            const R e0x = R(frame_d(fo, sd.xc, true)), e0y = R(frame_d(fo, sd.yc, false));
-            if (domain_cell(sp, gx, gy) && phi_eta(e0x, e0y, lx, ly, fo, rq) < -R(PHI_TIE)) {
-                Xo[t] = e0x; Yo[t] = e0y; L = 0;
-            }
-        } else {
-            const int ix = lx + shx, iy = ly + shy;
-            if (ix >= 0 && iy >= 0 && ix < T && iy < T) {
-                const int k = iy * T + ix;
-                const R ex = Xi[k], ey = Yi[k];
-                if (ex == ex) {
-                    const R phi = phi_eta(ex, ey, ix, iy, fi, rq);
-                    if (phi < eps && domain_cell(sp, gx, gy)) {
-                        R rho, u, v;
-                        node_moments<R, S>(sp, a.f, a.carry, a.reg_prev, a.pool_prev, wrapi(gx, sp.nx),
-                                           wrapi(gy, sp.ny), rho, u, v);
-                        const R lam = R(1) - heaviside<R>(phi, eps);
-                        stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
-                        stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
-                        if (phi < -R(PHI_TIE)) {
-                            const int sx = (u >= R(0)) ? -1 : 1, sy = (v >= R(0)) ? -1 : 1;
-                            const int x2 = ix + 2 * sx, y2 = iy + 2 * sy;
-                            if (x2 < 0 || x2 >= T || y2 < 0 || y2 >= T) {
-                                atomicOr(a.err, ERR_STENCIL);
-                            } else {
-                                const int k1 = k + sx, k2 = k + 2 * sx, k3 = k + sy * T, k4 = k + 2 * sy * T;
-                                const R X1 = Xi[k1], X2 = Xi[k2], X3 = Xi[k3], X4 = Xi[k4];
-                                const R Y1 = Yi[k1], Y2 = Yi[k2], Y3 = Yi[k3], Y4 = Yi[k4];
-                                if (!(X1 == X1 && X2 == X2 && X3 == X3 && X4 == X4)) atomicOr(a.err, ERR_STENCIL);
-                                // one-sided second-order differences of eta; xi = eta + position adds (1,0)/(0,1)
-                                const R hx = R(-sx) * R(0.5), hy = R(-sy) * R(0.5);
-                                const R dXdx = hx * (R(3) * ex - R(4) * X1 + X2), dYdx = hx * (R(3) * ey - R(4) * Y1 + Y2);
-                                const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
-                                // xi = eta + x - d: the node's own motion enters as -(u - dd)
-                                Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
-                                Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
-                                L = 0;
-                            }
-                        }
-                    }
+    // Pass 0: the advected set S = {domain nodes with phi^n < 0}, Eqs. 3_1_refmap_adv / 3_1_eno,
+    // over the input tile's box (the whole tile at initialisation).
+    {
+        const int ib0 = a.init ? 0 : fi.bx0, ib1 = a.init ? T - 1 : fi.bx1;
+        const int jb0 = a.init ? 0 : fi.by0, jb1 = a.init ? T - 1 : fi.by1;
+        const int bw = ib1 - ib0 + 1, bn = (ib1 >= ib0 && jb1 >= jb0) ? bw * (jb1 - jb0 + 1) : 0;
+        BoxWalk wk(bw);
+        for (int kk = threadIdx.x; kk < bn; kk += blockDim.x, wk.next()) {
+            const int ix = ib0 + wk.c, iy = jb0 + wk.r;  // input-tile coordinates
+            const int lx = ix - shx, ly = iy - shy;      // output-tile coordinates
+            const int gx = oo.x + lx, gy = oo.y + ly;
+            if (a.init) {
+                // xi = x: eta = d of the initial frame
+                const R e0x = R(frame_d(fo, sd.xc, true)), e0y = R(frame_d(fo, sd.yc, false));
+                if (domain_cell(sp, gx, gy) && phi_eta(e0x, e0y, lx, ly, fo, rq) < -R(PHI_TIE)) {
+                    const int t = ly * T + lx;
+                    Xo[t] = e0x; Yo[t] = e0y; lab[t] = 0;
+                    sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
                 }
+                continue;
             }
-        }
-        lab[t] = L;
-        if (L == 0) {
+            const int k = iy * T + ix;
+            const R ex = Xi[k], ey = Yi[k];
+            if (!(ex == ex)) continue;
+            const R phi = phi_eta(ex, ey, ix, iy, fi, rq);
+            if (!(phi < eps) || !domain_cell(sp, gx, gy)) continue;
+            if (lx < 0 || ly < 0 || lx >= T || ly >= T) { atomicOr(a.err, ERR_TILE_OVERFLOW); continue; }
+            R rho, u, v;
+            node_moments<R, S>(sp, a.f, a.carry, a.reg_prev, a.pool_prev, wrapi(gx, sp.nx), wrapi(gy, sp.ny),
+                               rho, u, v);
+            const R lam = R(1) - heaviside<R>(phi, eps);
+            stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
+            stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
+            if (!(phi < -R(PHI_TIE))) continue;
+            const int sx = (u >= R(0)) ? -1 : 1, sy = (v >= R(0)) ? -1 : 1;
+            const int x2 = ix + 2 * sx, y2 = iy + 2 * sy;
+            if (x2 < fi.bx0 || x2 > fi.bx1 || y2 < fi.by0 || y2 > fi.by1) {
+                atomicOr(a.err, ERR_STENCIL);
+                continue;
+            }
+            const int k1 = k + sx, k2 = k + 2 * sx, k3 = k + sy * T, k4 = k + 2 * sy * T;
+            const R X1 = Xi[k1], X2 = Xi[k2], X3 = Xi[k3], X4 = Xi[k4];
+            const R Y1 = Yi[k1], Y2 = Yi[k2], Y3 = Yi[k3], Y4 = Yi[k4];
+            if (!(X1 == X1 && X2 == X2 && X3 == X3 && X4 == X4)) atomicOr(a.err, ERR_STENCIL);
+            // one-sided second-order differences of eta; xi = eta + position adds (1,0)/(0,1)
+            const R hx = R(-sx) * R(0.5), hy = R(-sy) * R(0.5);
+            const R dXdx = hx * (R(3) * ex - R(4) * X1 + X2), dYdx = hx * (R(3) * ey - R(4) * Y1 + Y2);
+            const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
+            // xi = eta + x - d: the node's own motion enters as -(u - dd)
+            const int t = ly * T + lx;
+            Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
+            Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
+            lab[t] = 0;
             sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
         }
     }
@@ -512,7 +546,8 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
 
     // Layers 1..n_layers by 4-neighbour dilation; extrapolate each layer (Sec. 3.2).
     // Layer 1 comes from a scan of the solid bbox grown by one; layer l > 1 from
-    // the free 4-neighbours of the layer l-1 list (claimed with a CAS).
+    // the free 4-neighbours of the layer l-1 list (claimed with a CAS).  Nodes
+    // beyond the pad of a no-slip side are never labelled.
     const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
     if (sx0 > sx1) {
         if (threadIdx.x == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);  // the solid vanished
@@ -530,16 +565,14 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
             const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
             const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
             const int nround = (n + 31) & ~31;
-            for (int k = threadIdx.x; k < nround; k += blockDim.x) {
+            BoxWalk wk(w);
+            for (int k = threadIdx.x; k < nround; k += blockDim.x, wk.next()) {
                 bool hit = false;
-                int t = 0;
-                if (k < n) {
-                    const int lx = x0 + k % w, ly = y0 + k / w;
-                    t = ly * T + lx;
-                    if (lab[t] == -1)
-                        hit = (lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
-                              (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1);
-                }
+                const int lx = x0 + wk.c, ly = y0 + wk.r;
+                const int t = ly * T + lx;
+                if (k < n && lab[t] == -1 && allowed_cell(sp, oo.x + lx, oo.y + ly))
+                    hit = (lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
+                          (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1);
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
                 if (m) {
                     const int leader = __ffs(m) - 1;
@@ -547,24 +580,25 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                     if (lane == leader) base = atomicAdd(&nlist, __popc(m));
                     base = __shfl_sync(0xffffffffu, base, leader);
                     if (hit) {
-                        lab[t] = l;
+                        lab[t] = (signed char)l;
                         const int idx = base + __popc(m & ((1u << lane) - 1u));
-                        if (idx < LIST_CAP) cur[idx] = t;
+                        if (idx < LIST_CAP) cur[idx] = lx | (ly << 16);
                     }
                 }
             }
         } else {
             for (int k = threadIdx.x; k < 4 * nprev; k += blockDim.x) {
                 const int p = prv[k >> 2], dir = k & 3;
-                const int lx = p % T, ly = p / T;
-                int q = -1;
-                if (dir == 0 && lx > 0) q = p - 1;
-                else if (dir == 1 && lx < T - 1) q = p + 1;
-                else if (dir == 2 && ly > 0) q = p - T;
-                else if (dir == 3 && ly < T - 1) q = p + T;
-                if (q >= 0 && lab[q] == -1 && atomicCAS(&lab[q], -1, l) == -1) {
+                int lx = p & 0xffff, ly = p >> 16;
+                if (dir == 0) lx--;
+                else if (dir == 1) lx++;
+                else if (dir == 2) ly--;
+                else ly++;
+                if (lx < 0 || ly < 0 || lx >= T || ly >= T) continue;
+                const int q = ly * T + lx;
+                if (lab[q] == -1 && allowed_cell(sp, oo.x + lx, oo.y + ly) && claim_label(lab, q, l)) {
                     const int idx = atomicAdd(&nlist, 1);
-                    if (idx < LIST_CAP) cur[idx] = q;
+                    if (idx < LIST_CAP) cur[idx] = lx | (ly << 16);
                 }
             }
         }
@@ -574,20 +608,25 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
         prev_full = nl <= LIST_CAP;
         const int nitems = prev_full ? nl : TT;
         for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
-            const int t = prev_full ? cur[k] : k;
-            if (!prev_full && lab[t] != l) continue;
+            int lx, ly;
+            if (prev_full) {
+                lx = cur[k] & 0xffff; ly = cur[k] >> 16;
+            } else {  // overflowed list: scan the tile
+                lx = k % T; ly = k / T;
+                if (lab[k] != l) continue;
+            }
+            const int t = ly * T + lx;
             if (a.init) {  // xi = x on the band at initialisation
                 Xo[t] = R(frame_d(fo, sd.xc, true));
                 Yo[t] = R(frame_d(fo, sd.yc, false));
                 continue;
             }
-            const int lx = t % T, ly = t / T;
             bool use_n = false;
             R nhx = 0, nhy = 0;
             if (l <= 2) {
                 // surface normal: central difference of phi^n at the target (input frame)
                 const int ix = lx + shx, iy = ly + shy;
-                if (ix >= 1 && iy >= 1 && ix < T - 1 && iy < T - 1) {
+                if (ix > fi.bx0 && iy > fi.by0 && ix < fi.bx1 && iy < fi.by1) {
                     const int k0 = iy * T + ix;
                     const R Xe = Xi[k0 + 1], Xw = Xi[k0 - 1], Xn = Xi[k0 + T], Xs = Xi[k0 - T];
                     if (Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs) {
@@ -599,23 +638,31 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                     }
                 }
             }
-            extrapolate_target<R>(sp, lab, Xo, Yo, T, t, l, use_n, nhx, nhy, a.err);
+            extrapolate_target<R>(sp, lab, Xo, Yo, T, lx, ly, l, use_n, nhx, nhy, a.err);
         }
     }
     __syncthreads();
 
-    // Relabel phi^{n+1} = phi_0(xi^{n+1}); band and blur-zone bboxes; invalidate the rest.
+    // Relabel phi^{n+1} = phi_0(xi^{n+1}) over the box that can hold band nodes
+    // (layer l lies within l of the solid bbox); band and blur-zone bboxes;
+    // invalidate the free nodes of the box.
     int bx[8] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29), 1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
-    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
-        const int lx = t % T, ly = t / T;
-        if (lab[t] >= 0) {
-            bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
-            if (phi_eta(Xo[t], Yo[t], lx, ly, fo, rq) < eps) {
-                bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
+    if (sx0 <= sx1) {
+        const int x0 = max(sx0 - sp.n_layers, 0), x1 = min(sx1 + sp.n_layers, T - 1);
+        const int y0 = max(sy0 - sp.n_layers, 0), y1 = min(sy1 + sp.n_layers, T - 1);
+        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+        BoxWalk wk(w);
+        for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
+            const int lx = x0 + wk.c, ly = y0 + wk.r, t = ly * T + lx;
+            if (lab[t] >= 0) {
+                bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
+                if (phi_eta(Xo[t], Yo[t], lx, ly, fo, rq) < eps) {
+                    bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
+                }
+            } else {
+                Xo[t] = nanv<R>();
+                Yo[t] = nanv<R>();
             }
-        } else {
-            Xo[t] = nanv<R>();
-            Yo[t] = nanv<R>();
         }
     }
     for (int k = 0; k < 8; k++) warp_minmax(bx[k], (k & 1) == 0);
@@ -636,10 +683,13 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
         // mean velocity of the solid at time n (zero at initialisation) moves d
         double ux = 0.0, uy = 0.0;
         if (a.stats && st[3] > 0.0) { ux = st[4] / st[3]; uy = st[5] / st[3]; }
+        Frame fb = fo;
         if (bb[4] > bb[5]) {
             atomicOr(a.err, ERR_TILE_OVERFLOW);
+            fb.bx0 = fb.by0 = 1; fb.bx1 = fb.by1 = 0;
         } else {
             if (bb[4] < 1 || bb[6] < 1 || bb[5] > T - 2 || bb[7] > T - 2) atomicOr(a.err, ERR_TILE_OVERFLOW);
+            fb.bx0 = (short)bb[4]; fb.bx1 = (short)bb[5]; fb.by0 = (short)bb[6]; fb.by1 = (short)bb[7];
             // centre the next frame on the solid (not on its band, which walls clip): the
             // frame then follows the solid's translation and eta stays small
             if (bb[0] <= bb[1]) {
@@ -647,11 +697,13 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? 4 : 2) rmt_solid
                 nx.y = oo.y + (bb[2] + bb[3]) / 2 - T / 2;
             }
         }
+        a.frame_out[s] = fb;
         Frame fn;
         fn.ox = nx.x;
         fn.oy = nx.y;
         fn.offx = frame_off(nx.x, sd.xc, frame_d(fo, sd.xc, true) + ux);
         fn.offy = frame_off(nx.y, sd.yc, frame_d(fo, sd.yc, false) + uy);
+        fn.bx0 = fn.by0 = 1; fn.bx1 = fn.by1 = 0;  // filled by the step that writes that tile
         a.frame_next[s] = fn;
     }
     // Register the 32x8 tiles that the blur zone (grown by one node) touches.
@@ -784,7 +836,7 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
             const int lx = sp.wall_x ? gx - fr.ox : wrapi(gx - fr.ox, sp.nx);
             const int ly = sp.wall_y ? gy - fr.oy : wrapi(gy - fr.oy, sp.ny);
             R X = nanv<R>(), Y = nanv<R>(), P = nanv<R>();
-            if (lx >= 0 && ly >= 0 && lx < T && ly < T) {
+            if (in_box(fr, lx, ly)) {
                 const R *Xs = a.xi + soff[ks];
                 X = Xs[ly * T + lx];
                 Y = Xs[T * T + ly * T + lx];
@@ -1055,7 +1107,7 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T * T; t += gridDim.x * blockDim.x) {
         const int lx = t % T, ly = t / T;
         const int gx = o.x + lx, gy = o.y + ly;
-        if (!domain_cell(sp, gx, gy)) continue;
+        if (!in_box(fr, lx, ly) || !domain_cell(sp, gx, gy)) continue;
         const R X = xi[sd.off + t], Y = xi[sd.off + T * T + t];
         if (!(X == X)) continue;
         const long long c = grid_index(sp, gx, gy);
@@ -1084,6 +1136,7 @@ __global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, con
     for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
         const int lx = t % T, ly = t / T;
         const int gx = o.x + lx, gy = o.y + ly;
+        if (!in_box(fr, lx, ly)) continue;
         const R X = xi[sd.off + t], Y = xi[sd.off + T * T + t];
         if (!(X == X) || !domain_cell(sp, gx, gy)) continue;
         const R phi = phi_eta(X, Y, lx, ly, fr, rq);
