@@ -87,15 +87,17 @@ typedef struct {
     int precision;              /* LBRMT_FP32 / LBRMT_FP64 arithmetic and storage; LBRMT_FP16_STORE /
                                    LBRMT_BF16_STORE: FP32 arithmetic, populations and half-force
                                    stored in 16 bits (FP16 with power-of-two scales 2^10 and 2^14) */
-    int max_solids_per_tile;    /* registry slots per 32x8 tile, 1..8 */
+    int max_solids_per_tile;    /* registry slots per tile, 1..8 */
     int rmax;                   /* largest extrapolation window half-width (>= 2) */
+    int tile_x;                 /* registry / LB tile width: 16, 32, 64 or 128 nodes (height 256 /
+                                   tile_x); 0 selects 32.  Results do not depend on it. */
     lbrmt_alloc_fn alloc;       /* optional device allocator */
     lbrmt_free_fn free;
     void *alloc_ctx;
 } lbrmt_config;
 
 /* Fill a config with the paper's defaults (eps 1.5, 11 layers, rho_f 1,
- * eta 1, tau 1, periodic 64x64, FP32, 8 slots, rmax 11). */
+ * eta 1, tau 1, periodic 64x64, FP32, 8 slots, rmax 11, 32x8 tiles). */
 void lbrmt_default_config(lbrmt_config *cfg);
 
 /* Create a simulation on the current CUDA device.  cuda_stream is a
@@ -188,6 +190,63 @@ const char *lbrmt_last_error(const lbrmt_sim *sim);
 
 /* Free the handle and all device memory it owns. */
 void lbrmt_destroy(lbrmt_sim *sim);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent simulations advanced together.  The paper has no
+ * counterpart (it runs one instance of Algorithm 1 at a time); every member of
+ * a batch computes exactly what it would compute alone (bit-identical fields),
+ * but a batch step is one persistent launch per kernel of the step over the
+ * work of all members, replayed through CUDA graphs.
+ * ------------------------------------------------------------------------- */
+typedef struct lbrmt_batch lbrmt_batch;
+
+/* Create a batch of nsim (1..1024) simulations, one per config (all with the
+ * same precision; tile_x 0 selects 32), on the given CUDA stream (NULL: the
+ * legacy default stream, stepped without graphs).  Configs are validated as
+ * by lbrmt_create; the allocator of cfgs[0] also holds the batch's own lists.
+ * The batch owns its members. */
+lbrmt_status lbrmt_create_batch(const lbrmt_config *cfgs, int nsim, void *cuda_stream, lbrmt_batch **out);
+
+/* Add a solid to member sim_index (before lbrmt_batch_init); as lbrmt_add_solid. */
+lbrmt_status lbrmt_batch_add_solid(lbrmt_batch *batch, int sim_index, int shape, double cx, double cy,
+                                   double radius, double rho_s, double G, int *solid_id_out);
+
+/* Initialise every member (Algorithm 1, initialisation).  With
+ * autotune_steps > 0, first choose each grid size's tile shape among
+ * tile_x = 16, 32, 64, 128 by timing whole batch steps (autotune_steps timed
+ * steps per trial, greedy over grid sizes), then start every member again
+ * from its initial state with the chosen shapes.  Synchronous. */
+lbrmt_status lbrmt_batch_init(lbrmt_batch *batch, int autotune_steps);
+
+/* Advance every member nsteps >= 0 steps (asynchronous). */
+lbrmt_status lbrmt_batch_step(lbrmt_batch *batch, int nsteps);
+
+/* As lbrmt_step_timed, for the batched kernels (ms_out: 3 floats, mean ms of
+ * the reference-map, force and lattice Boltzmann launches of a batch step). */
+lbrmt_status lbrmt_batch_step_timed(lbrmt_batch *batch, int nsteps, float *ms_out);
+
+/* Wait for the stream and check every member's device error flags. */
+lbrmt_status lbrmt_batch_sync(lbrmt_batch *batch);
+
+/* Borrowed handle of member sim_index (after lbrmt_batch_init) for
+ * lbrmt_read_fields*, lbrmt_solid_stats, lbrmt_total_mass and the other
+ * queries; lbrmt_step on it returns LBRMT_ERR_STATE.  Do not destroy it. */
+lbrmt_status lbrmt_batch_member(lbrmt_batch *batch, int sim_index, lbrmt_sim **out);
+
+/* Number of members; tile_x in use by member sim_index. */
+int lbrmt_batch_size(const lbrmt_batch *batch);
+int lbrmt_batch_tile_x(const lbrmt_batch *batch, int sim_index);
+
+/* Autotuner trials: fills up to cap entries of (nx, ny, tile_x, ms per batch
+ * step) host arrays (any may be NULL) and returns the number of trials. */
+int lbrmt_batch_tune_log(const lbrmt_batch *batch, int *nx, int *ny, int *tile_x, double *ms, int cap);
+
+long long lbrmt_batch_steps_done(const lbrmt_batch *batch);
+long long lbrmt_batch_last_launch_count(const lbrmt_batch *batch);
+const char *lbrmt_batch_last_error(const lbrmt_batch *batch);
+
+/* Free the batch, its members and all device memory they own. */
+void lbrmt_destroy_batch(lbrmt_batch *batch);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,11 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_ini
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs",
-           "lbrmt_last_error", "lbrmt_destroy"]
+           "lbrmt_last_error", "lbrmt_destroy",
+           "lbrmt_create_batch", "lbrmt_batch_add_solid", "lbrmt_batch_init", "lbrmt_batch_step",
+           "lbrmt_batch_step_timed", "lbrmt_batch_sync", "lbrmt_batch_member", "lbrmt_batch_size",
+           "lbrmt_batch_tile_x", "lbrmt_batch_tune_log", "lbrmt_batch_steps_done",
+           "lbrmt_batch_last_launch_count", "lbrmt_batch_last_error", "lbrmt_destroy_batch"]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -43,7 +47,7 @@ class lbrmt_config(C.Structure):
                 ("eps", C.c_double), ("n_layers", C.c_int), ("eta", C.c_double),
                 ("gravity", C.c_double), ("force_kind", C.c_int), ("force_a", C.c_double * 2),
                 ("precision", C.c_int), ("max_solids_per_tile", C.c_int), ("rmax", C.c_int),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("tile_x", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class LbrmtError(RuntimeError):
@@ -90,6 +94,24 @@ def load():
     L.lbrmt_last_error.restype = C.c_char_p
     L.lbrmt_destroy.argtypes = [p]
     L.lbrmt_destroy.restype = None
+    L.lbrmt_create_batch.argtypes = [cfgp, i, p, C.POINTER(p)]
+    L.lbrmt_batch_add_solid.argtypes = [p, i, i, d, d, d, d, d, C.POINTER(i)]
+    L.lbrmt_batch_init.argtypes = [p, i]
+    L.lbrmt_batch_step.argtypes = [p, i]
+    L.lbrmt_batch_step_timed.argtypes = [p, i, C.POINTER(C.c_float)]
+    L.lbrmt_batch_sync.argtypes = [p]
+    L.lbrmt_batch_member.argtypes = [p, i, C.POINTER(p)]
+    L.lbrmt_batch_size.argtypes = [p]
+    L.lbrmt_batch_tile_x.argtypes = [p, i]
+    L.lbrmt_batch_tune_log.argtypes = [p, p, p, p, p, i]
+    L.lbrmt_batch_steps_done.argtypes = [p]
+    L.lbrmt_batch_steps_done.restype = ll
+    L.lbrmt_batch_last_launch_count.argtypes = [p]
+    L.lbrmt_batch_last_launch_count.restype = ll
+    L.lbrmt_batch_last_error.argtypes = [p]
+    L.lbrmt_batch_last_error.restype = C.c_char_p
+    L.lbrmt_destroy_batch.argtypes = [p]
+    L.lbrmt_destroy_batch.restype = None
     _lib = L
     return L
 
@@ -174,6 +196,62 @@ def lbrmt_destroy(h):
     load().lbrmt_destroy(h)
 
 
+def _bcheck(b, st):
+    if st != LBRMT_OK:
+        msg = load().lbrmt_batch_last_error(b).decode() if b else ""
+        raise LbrmtError(st, msg)
+
+
+def lbrmt_create_batch(cfgs, stream_ptr):
+    arr = (lbrmt_config * len(cfgs))(*cfgs)
+    b = C.c_void_p()
+    _bcheck(None, load().lbrmt_create_batch(arr, len(cfgs), C.c_void_p(stream_ptr), C.byref(b)))
+    return b
+
+
+def lbrmt_batch_add_solid(b, sim_index, shape, cx, cy, radius, rho_s, G):
+    sid = C.c_int()
+    _bcheck(b, load().lbrmt_batch_add_solid(b, sim_index, shape, cx, cy, radius, rho_s, G, C.byref(sid)))
+    return sid.value
+
+
+def lbrmt_batch_init(b, autotune_steps):
+    _bcheck(b, load().lbrmt_batch_init(b, int(autotune_steps)))
+
+
+def lbrmt_batch_step(b, nsteps):
+    _bcheck(b, load().lbrmt_batch_step(b, int(nsteps)))
+
+
+def lbrmt_batch_step_timed(b, nsteps):
+    ms = (C.c_float * 3)()
+    _bcheck(b, load().lbrmt_batch_step_timed(b, int(nsteps), ms))
+    return [ms[0], ms[1], ms[2]]
+
+
+def lbrmt_batch_sync(b):
+    _bcheck(b, load().lbrmt_batch_sync(b))
+
+
+def lbrmt_batch_member(b, sim_index):
+    h = C.c_void_p()
+    _bcheck(b, load().lbrmt_batch_member(b, sim_index, C.byref(h)))
+    return h
+
+
+def lbrmt_batch_tune_log(b):
+    L = load()
+    n = L.lbrmt_batch_tune_log(b, None, None, None, None, 0)
+    nx, ny, tx = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))()
+    ms = (C.c_double * max(n, 1))()
+    L.lbrmt_batch_tune_log(b, nx, ny, tx, ms, n)
+    return [(nx[k], ny[k], tx[k], ms[k]) for k in range(n)]
+
+
+def lbrmt_destroy_batch(b):
+    load().lbrmt_destroy_batch(b)
+
+
 # ---------------------------------------------------------------------------
 # Convenience class
 # ---------------------------------------------------------------------------
@@ -203,11 +281,28 @@ class _TorchAllocator:
         self.live.pop(ptr, None)
 
 
+def scenario_config(sc, precision="fp32", max_solids_per_tile=8, rmax=11, tile_x=32):
+    """lbrmt_config of a scenario dict (without allocator callbacks)."""
+    cfg = lbrmt_default_config()
+    cfg.nx, cfg.ny = sc["nx"], sc["ny"]
+    cfg.bc_x, cfg.bc_y = sc["wall_x"], sc["wall_y"]
+    cfg.tau, cfg.rho_f, cfg.lid_u = sc["tau"], sc["rho_f"], sc["lid_u"]
+    cfg.eps, cfg.n_layers, cfg.eta = sc["eps"], sc["n_layers"], sc["eta"]
+    cfg.gravity, cfg.force_kind = sc["gravity"], sc["force_kind"]
+    fa = sc.get("force_a", [0.0, 0.0])
+    cfg.force_a[0], cfg.force_a[1] = fa[0], fa[1]
+    cfg.precision = PRECISION[precision]
+    cfg.max_solids_per_tile = max_solids_per_tile
+    cfg.rmax = rmax
+    cfg.tile_x = tile_x
+    return cfg
+
+
 class Simulation:
     """One LBRMT simulation on a CUDA device, built from a scenario dict."""
 
     def __init__(self, sc, precision="fp32", device="cuda:0", stream=None, use_graphs=True,
-                 max_solids_per_tile=8, rmax=11):
+                 max_solids_per_tile=8, rmax=11, tile_x=32):
         import torch
         self.torch = torch
         self.sc = sc
@@ -215,17 +310,7 @@ class Simulation:
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         self.nx, self.ny = sc["nx"], sc["ny"]
         self.nsolids = len(sc["solids"])
-        cfg = lbrmt_default_config()
-        cfg.nx, cfg.ny = sc["nx"], sc["ny"]
-        cfg.bc_x, cfg.bc_y = sc["wall_x"], sc["wall_y"]
-        cfg.tau, cfg.rho_f, cfg.lid_u = sc["tau"], sc["rho_f"], sc["lid_u"]
-        cfg.eps, cfg.n_layers, cfg.eta = sc["eps"], sc["n_layers"], sc["eta"]
-        cfg.gravity, cfg.force_kind = sc["gravity"], sc["force_kind"]
-        fa = sc.get("force_a", [0.0, 0.0])
-        cfg.force_a[0], cfg.force_a[1] = fa[0], fa[1]
-        cfg.precision = PRECISION[precision]
-        cfg.max_solids_per_tile = max_solids_per_tile
-        cfg.rmax = rmax
+        cfg = scenario_config(sc, precision, max_solids_per_tile, rmax, tile_x)
         self._alloc = _TorchAllocator(torch, self.device, self.stream)
         cfg.alloc = self._alloc.alloc_cb
         cfg.free = self._alloc.free_cb
@@ -305,6 +390,100 @@ class Simulation:
         if getattr(self, "h", None):
             lbrmt_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Member(Simulation):
+    """Borrowed view of one member of a Batch (reads only; the batch steps it)."""
+
+    def __init__(self, batch, k):  # noqa: D401  (no Simulation.__init__: the batch owns the handle)
+        self.torch, self.device, self.stream = batch.torch, batch.device, batch.stream
+        self.sc = batch.scs[k]
+        self.nx, self.ny = self.sc["nx"], self.sc["ny"]
+        self.nsolids = len(self.sc["solids"])
+        self.h = lbrmt_batch_member(batch.b, k)
+        self._batch = batch
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Many independent LBRMT simulations advanced by one persistent launch per
+    kernel of the step (lbrmt_create_batch).  ``tile_x`` is one value or one per
+    member; ``autotune_steps`` > 0 lets the library choose each grid size's tile
+    shape by timing batch steps."""
+
+    def __init__(self, scs, precision="fp32", device="cuda:0", stream=None, tile_x=32, autotune_steps=0,
+                 max_solids_per_tile=8, rmax=11):
+        import torch
+        self.torch = torch
+        self.scs = list(scs)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        txs = list(tile_x) if isinstance(tile_x, (list, tuple)) else [tile_x] * len(self.scs)
+        self._alloc = _TorchAllocator(torch, self.device, self.stream)
+        cfgs = []
+        for sc, tx in zip(self.scs, txs):
+            cfg = scenario_config(sc, precision, max_solids_per_tile, rmax, tx)
+            cfg.alloc = self._alloc.alloc_cb
+            cfg.free = self._alloc.free_cb
+            cfgs.append(cfg)
+        self._cfgs = cfgs
+        with torch.cuda.device(self.device):
+            self.b = lbrmt_create_batch(cfgs, self.stream.cuda_stream)
+            for k, sc in enumerate(self.scs):
+                for s in sc["solids"]:
+                    lbrmt_batch_add_solid(self.b, k, 0, s["x"], s["y"], s["r"], s["rho_s"], s["G"])
+            lbrmt_batch_init(self.b, autotune_steps)
+        self.members = [_Member(self, k) for k in range(len(self.scs))]
+
+    def __len__(self):
+        return len(self.scs)
+
+    def __getitem__(self, k):
+        return self.members[k]
+
+    def step(self, n=1):
+        with self.torch.cuda.device(self.device):
+            lbrmt_batch_step(self.b, n)
+
+    def step_timed(self, n):
+        with self.torch.cuda.device(self.device):
+            return lbrmt_batch_step_timed(self.b, n)
+
+    def sync(self):
+        lbrmt_batch_sync(self.b)
+
+    def tile_x(self, k):
+        return load().lbrmt_batch_tile_x(self.b, k)
+
+    def tune_log(self):
+        return lbrmt_batch_tune_log(self.b)
+
+    @property
+    def steps_done(self):
+        return load().lbrmt_batch_steps_done(self.b)
+
+    @property
+    def last_launch_count(self):
+        return load().lbrmt_batch_last_launch_count(self.b)
+
+    @property
+    def nodes(self):
+        return sum(sc["nx"] * sc["ny"] for sc in self.scs)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for m in self.members:
+                m.close()
+            lbrmt_destroy_batch(self.b)
+            self.b = None
 
     def __del__(self):
         try:

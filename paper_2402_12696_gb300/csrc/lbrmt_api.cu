@@ -67,6 +67,7 @@ extern "C" void lbrmt_default_config(lbrmt_config *c) {
     c->precision = LBRMT_FP32;
     c->max_solids_per_tile = KMAX;
     c->rmax = 11;
+    c->tile_x = 32;
 }
 
 extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream, lbrmt_sim **out) {
@@ -81,6 +82,8 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (c.lid_u != 0.0 && c.bc_y != LBRMT_WALL) return LBRMT_ERR_ARG;
     if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > 2) return LBRMT_ERR_ARG;
     if (c.precision < LBRMT_FP32 || c.precision > LBRMT_BF16_STORE) return LBRMT_ERR_ARG;
+    const int tx = c.tile_x == 0 ? 32 : c.tile_x;
+    if (tx != 16 && tx != 32 && tx != 64 && tx != 128) return LBRMT_ERR_ARG;
     if (std::fabs(c.lid_u) / std::sqrt(1.0 / 3.0) > 0.3) return LBRMT_ERR_PARAM_RANGE;  // Ma* <= 0.3
 
     lbrmt_sim *s = new lbrmt_sim();
@@ -94,8 +97,10 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     SimParams &sp = s->sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.nx = c.nx; sp.ny = c.ny; sp.wall_x = c.bc_x; sp.wall_y = c.bc_y;
-    sp.ntx = (c.nx + TILE_X - 1) / TILE_X;
-    sp.nty = (c.ny + TILE_Y - 1) / TILE_Y;
+    sp.tx = tx; sp.ty = TILE_N / tx;
+    sp.lx = __builtin_ctz((unsigned)sp.tx); sp.ly = __builtin_ctz((unsigned)sp.ty);
+    sp.ntx = (c.nx + sp.tx - 1) / sp.tx;
+    sp.nty = (c.ny + sp.ty - 1) / sp.ty;
     sp.P = (long long)c.nx * c.ny;
     sp.tau = c.tau; sp.rho_f = c.rho_f; sp.lid_u = c.lid_u; sp.eps = c.eps; sp.eta = c.eta;
     sp.gravity = c.gravity; sp.force_kind = c.force_kind; sp.fa0 = c.force_a[0]; sp.fa1 = c.force_a[1];
@@ -119,7 +124,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     }
     ok = ok && (d.carry = dalloc(s, 2 * P * ss));
     ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
-    ok = ok && (d.mass_partials = (double *)dalloc(s, ntiles * TILE_Y * 8));
+    ok = ok && (d.mass_partials = (double *)dalloc(s, ntiles * (TILE_N / 32) * 8));
     ok = ok && (d.err = (unsigned *)dalloc(s, 16));
     ok = ok && (s->scratch = (double *)dalloc(s, 64));
     if (!ok) {
@@ -135,7 +140,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         if (e == cudaSuccess) e = cudaMemsetAsync(d.pool[k], 0, ntiles * POOL_STRIDE * rs, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, ntiles * TILE_Y * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, ntiles * (TILE_N / 32) * 8, st);
     // body force per row (x component), Sec. 4 forcing on all phases
     std::vector<double> fb(c.ny, 0.0);
     for (int j = 0; j < c.ny; j++) {
@@ -169,7 +174,7 @@ extern "C" lbrmt_status lbrmt_add_solid(lbrmt_sim *s, int shape, double cx, doub
     const int margin = 4 + (int)std::ceil(radius / 4.0);
     int T = 2 * (int)std::ceil(radius) + 2 * (s->cfg.n_layers + margin) + 1;
     T = (T + 7) & ~7;
-    if (T > 240) return fail(s, LBRMT_ERR_ARG, "solid too large for a tile");
+    if (T > TILE_SIDE_MAX) return fail(s, LBRMT_ERR_ARG, "solid too large for a tile");
     if ((!s->cfg.bc_x && T >= s->cfg.nx) || (!s->cfg.bc_y && T >= s->cfg.ny))
         return fail(s, LBRMT_ERR_ARG, "solid tile wider than the periodic domain");
     SolidHost h{cx, cy, radius, rho_s, G, T, 0};
@@ -187,7 +192,7 @@ static lbrmt_status check_flags(lbrmt_sim *s) {
     const unsigned f = h[0];
     if (!f) return LBRMT_OK;
     if (f & ERR_NAN) return fail(s, LBRMT_ERR_NUMERIC, "non-finite density or velocity");
-    if (f & ERR_SLOT_OVERFLOW) return fail(s, LBRMT_ERR_OVERFLOW, "more solids on a 32x8 tile than max_solids_per_tile");
+    if (f & ERR_SLOT_OVERFLOW) return fail(s, LBRMT_ERR_OVERFLOW, "more solids on a tile than max_solids_per_tile");
     if (f & ERR_TILE_OVERFLOW) return fail(s, LBRMT_ERR_OVERFLOW, "a solid's band outgrew its tile");
     if (f & ERR_EXTRAP) return fail(s, LBRMT_ERR_EXTRAP, "extrapolation window exceeded rmax");
     if (f & ERR_STENCIL) return fail(s, LBRMT_ERR_EXTRAP, "advection stencil left the band");
@@ -195,6 +200,8 @@ static lbrmt_status check_flags(lbrmt_sim *s) {
     if (f & ERR_OVERFLOW16) return fail(s, LBRMT_ERR_OVERFLOW, "a population exceeded the 16-bit storage range");
     return fail(s, LBRMT_ERR_NUMERIC, "device error flag");
 }
+
+lbrmt_status lbrmt_internal_check_flags(lbrmt_sim *s) { return check_flags(s); }
 
 extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     if (!s) return LBRMT_ERR_ARG;
@@ -297,6 +304,7 @@ static lbrmt_status build_graph(lbrmt_sim *s) {
 
 extern "C" lbrmt_status lbrmt_step(lbrmt_sim *s, int nsteps) {
     if (!s || nsteps < 0) return LBRMT_ERR_ARG;
+    if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
     if (!s->inited) {
         lbrmt_status st = lbrmt_init(s);
         if (st != LBRMT_OK) return st;
@@ -332,6 +340,7 @@ extern "C" lbrmt_status lbrmt_step(lbrmt_sim *s, int nsteps) {
 
 extern "C" lbrmt_status lbrmt_step_timed(lbrmt_sim *s, int nsteps, float *ms_out) {
     if (!s || nsteps < 1 || !ms_out) return LBRMT_ERR_ARG;
+    if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
     if (!s->inited) {
         lbrmt_status st = lbrmt_init(s);
         if (st != LBRMT_OK) return st;
@@ -433,7 +442,7 @@ extern "C" lbrmt_status lbrmt_solid_stats(lbrmt_sim *s, int sim_index, double *h
 extern "C" lbrmt_status lbrmt_total_mass(lbrmt_sim *s, int sim_index, double *host_out) {
     if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
     if (s->steps == 0) return fail(s, LBRMT_ERR_STATE, "total mass is recorded by the first step");
-    const int n = s->sp.ntx * s->sp.nty * TILE_Y;
+    const int n = s->sp.ntx * s->sp.nty * (TILE_N / 32);
     mass_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d.mass_partials, n, s->sp.rho_f * (double)s->sp.P, s->scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "mass kernel");

@@ -1,8 +1,11 @@
 // lbrmt_engine.cuh -- launch sequences of the LBRMT kernels for one precision.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 
+#include "lbrmt_batch.cuh"
 #include "lbrmt_kernels.cuh"
 
 namespace lbrmt {
@@ -14,6 +17,13 @@ struct LaunchInfo {
     int force_smem;      // dynamic shared memory of K3
 };
 
+// Launch shape of the batched kernels.
+struct BatchLaunch {
+    int rmt_blocks, rmt_smem;      // K2: persistent grid, dynamic shared memory (largest solid tile)
+    int force_blocks, force_smem;  // K3 (widest tile shape)
+    int lb_blocks;                 // K1
+};
+
 struct EngineOps {
     cudaError_t (*configure)(const SimParams &, int tmax, LaunchInfo *);
     cudaError_t (*init)(const SimParams &, const DevState &, const LaunchInfo &, cudaStream_t);
@@ -23,6 +33,13 @@ struct EngineOps {
                          double *out, cudaStream_t);
     cudaError_t (*stats)(const SimParams &, const DevState &, int cur, double *out, cudaStream_t);
     cudaError_t (*set_pop)(const SimParams &, const DevState &, int cur, const double *src, cudaStream_t);
+    // batches: descriptor of one simulation (host image of BatchSimDesc<R, S>)
+    size_t desc_size;
+    void (*fill_desc)(void *dst, const SimParams &, const DevState &);
+    cudaError_t (*batch_configure)(int tmax, int force_smem_elems, int nitems_rmt, BatchLaunch *);
+    // ev (optional): events before K2, before K3, before K1 and after K1
+    cudaError_t (*batch_step)(const void *descs, int nsim, const int2 *rmt_items, int n_rmt, const int2 *lb_items,
+                              int n_lb, const BatchLaunch &, int parity, cudaStream_t, cudaEvent_t *ev);
     int real_size, store_size;
     int launches_per_step;
 };
@@ -63,11 +80,13 @@ struct Engine {
             e0 = cudaMemcpyToSymbol(c_rinv_d, td, sizeof(td));
             if (e0 != cudaSuccess) return e0;
         }
-        li->force_smem = (3 * KMAX * PATCH_N + 3 * (NXE + NYE)) * (int)sizeof(R);
+        li->force_smem = force_smem_elems(sp.tx, sp.ty) * (int)sizeof(R);
+        // the attribute is per kernel, shared by every simulation: set the largest any may need
         cudaError_t e = cudaFuncSetAttribute(rmt_solid_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             li->rmt_smem);
+                                             RMT_SMEM_MAX);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(force_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, li->force_smem);
+        e = cudaFuncSetAttribute(force_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 force_smem_max() * (int)sizeof(R));
         if (e != cudaSuccess) return e;
         int dev = 0, nsm = 0, per = 0;
         cudaGetDevice(&dev);
@@ -75,7 +94,6 @@ struct Engine {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_kernel<R>, TILE_N, li->force_smem);
         if (e != cudaSuccess) return e;
         li->force_blocks = nsm * (per > 0 ? per : 1);
-        (void)sp;
         return cudaSuccess;
     }
 
@@ -124,12 +142,78 @@ struct Engine {
         return a;
     }
 
+    static LbArgs<R, S> lb_args(const DevState &d, int parity) {
+        const int p = parity, q = 1 - parity;
+        LbArgs<R, S> a;
+        a.f_in = (const S *)d.f[p];
+        a.f_out = (S *)d.f[q];
+        a.carry = (S *)d.carry;
+        a.fbody = (const R *)d.fbody;
+        a.reg_count = d.reg_count[p];
+        a.pool = (const R *)d.pool[p];
+        a.clr_count = d.reg_count[q];
+        a.clr_nactive = d.reg_nactive[q];
+        a.pool_prev = (const R *)d.pool[q];
+        a.mass_partials = d.mass_partials;
+        a.err = d.err;
+        return a;
+    }
+
+    static void fill_desc(void *dst, const SimParams &sp, const DevState &d) {
+        BatchSimDesc<R, S> b;
+        std::memset(&b, 0, sizeof(b));
+        b.sp = sp;
+        for (int p = 0; p < 2; p++) {
+            b.rmt[p] = rmt_args(d, p, 0);
+            b.frc[p] = force_args(d, 1 - p, p);
+            b.lb[p] = lb_args(d, p);
+        }
+        std::memcpy(dst, &b, sizeof(b));
+    }
+
+    static cudaError_t batch_configure(int tmax, int fs_elems, int nitems_rmt, BatchLaunch *bl) {
+        int dev = 0, nsm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        bl->rmt_smem = ((tmax * tmax + 15) & ~15) + 8 * LIST_CAP;
+        bl->force_smem = fs_elems * (int)sizeof(R);
+        cudaError_t e = cudaFuncSetAttribute(rmt_batch_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             RMT_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(force_batch_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 force_smem_max() * (int)sizeof(R));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rmt_batch_kernel<R, S>, RMT_THREADS, bl->rmt_smem);
+        if (e != cudaSuccess) return e;
+        bl->rmt_blocks = std::max(1, std::min(nitems_rmt, nsm * std::max(per, 1)));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_batch_kernel<R, S>, TILE_N, bl->force_smem);
+        if (e != cudaSuccess) return e;
+        bl->force_blocks = nsm * std::max(per, 1);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lb_batch_kernel<R, S>, TILE_N, 0);
+        if (e != cudaSuccess) return e;
+        bl->lb_blocks = nsm * std::max(per, 1);
+        return cudaSuccess;
+    }
+
+    static cudaError_t batch_step(const void *descs, int nsim, const int2 *rmt_items, int n_rmt, const int2 *lb_items,
+                                  int n_lb, const BatchLaunch &bl, int parity, cudaStream_t st, cudaEvent_t *ev) {
+        const BatchSimDesc<R, S> *ds = static_cast<const BatchSimDesc<R, S> *>(descs);
+        if (ev) cudaEventRecord(ev[0], st);
+        if (n_rmt > 0) rmt_batch_kernel<R, S><<<bl.rmt_blocks, RMT_THREADS, bl.rmt_smem, st>>>(ds, rmt_items, n_rmt, parity);
+        if (ev) cudaEventRecord(ev[1], st);
+        if (n_rmt > 0) force_batch_kernel<R, S><<<bl.force_blocks, TILE_N, bl.force_smem, st>>>(ds, nsim, parity);
+        if (ev) cudaEventRecord(ev[2], st);
+        lb_batch_kernel<R, S><<<bl.lb_blocks, TILE_N, 0, st>>>(ds, lb_items, n_lb, parity);
+        if (ev) cudaEventRecord(ev[3], st);
+        return cudaGetLastError();
+    }
+
     static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
         if (sp.nsolids > 0) {
             rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, 0, 1));
             force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 1));
         }
-        dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
+        dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
         init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (S *)d.carry);
         return cudaGetLastError();
     }
@@ -143,27 +227,15 @@ struct Engine {
         if (ev) cudaEventRecord(ev[1], st);
         if (sp.nsolids > 0) force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, q, p));
         if (ev) cudaEventRecord(ev[2], st);
-        LbArgs<R, S> a;
-        a.f_in = (const S *)d.f[p];
-        a.f_out = (S *)d.f[q];
-        a.carry = (S *)d.carry;
-        a.fbody = (const R *)d.fbody;
-        a.reg_count = d.reg_count[p];
-        a.pool = (const R *)d.pool[p];
-        a.clr_count = d.reg_count[q];
-        a.clr_nactive = d.reg_nactive[q];
-        a.pool_prev = (const R *)d.pool[q];
-        a.mass_partials = d.mass_partials;
-        a.err = d.err;
-        dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
-        lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, a);
+        dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
+        lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, lb_args(d, p));
         if (ev) cudaEventRecord(ev[3], st);
         return cudaGetLastError();
     }
 
     static cudaError_t field(const SimParams &sp, const DevState &d, int cur, int lastreg, int kind, int solid,
                              double *out, cudaStream_t st) {
-        dim3 grid(sp.ntx, sp.nty), blk(TILE_X, TILE_Y);
+        dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
         if (kind >= 10 && kind <= 12) {
             solid_field_kernel<R><<<64, 256, 0, st>>>(sp, (const R *)d.xi[cur], d.frame[cur], d.solids, solid,
                                                       kind - 10, out);
@@ -198,6 +270,10 @@ struct Engine {
         o.field = &field;
         o.stats = &stats;
         o.set_pop = &set_pop;
+        o.desc_size = sizeof(BatchSimDesc<R, S>);
+        o.fill_desc = &fill_desc;
+        o.batch_configure = &batch_configure;
+        o.batch_step = &batch_step;
         o.real_size = sizeof(R);
         o.store_size = sizeof(S);
         o.launches_per_step = 3;

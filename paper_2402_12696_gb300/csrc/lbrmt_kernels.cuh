@@ -25,16 +25,17 @@
 
 namespace lbrmt {
 
-constexpr int TILE_X = 32, TILE_Y = 8, TILE_N = TILE_X * TILE_Y;
-constexpr int PATCH_X = TILE_X + 2, PATCH_Y = TILE_Y + 2, PATCH_N = PATCH_X * PATCH_Y;
-constexpr int NXE = (TILE_X + 1) * TILE_Y;  // x-edges of a tile
-constexpr int NYE = TILE_X * (TILE_Y + 1);  // y-edges of a tile
+// Registry tiles are tile_x x tile_y nodes with tile_x * tile_y = TILE_N, one
+// thread per node; tile_x in {16, 32, 64, 128} is chosen per simulation.
+constexpr int TILE_N = 256;
 constexpr int KMAX = 8;                     // registry slots per tile (upper bound)
 constexpr int RMT_THREADS = 256;
 #ifndef RMT_MIN_BLOCKS
 #define RMT_MIN_BLOCKS 4
 #endif
 constexpr int LIST_CAP = 2048;              // per-layer target list in shared memory
+constexpr int TILE_SIDE_MAX = 240;          // largest solid tile side
+constexpr int RMT_SMEM_MAX = ((TILE_SIDE_MAX * TILE_SIDE_MAX + 15) & ~15) + 8 * LIST_CAP;
 constexpr int POOL_STRIDE = 3 * TILE_N;     // per tile: Fx, Fy, drho planes
 // Tie rules shared with the method's definition: a node with |phi| <= PHI_TIE
 // is not solid; a directional extrapolation weight with cosine <= COS_TIE is zero.
@@ -50,6 +51,7 @@ enum ErrBits : unsigned {
 struct SimParams {
     int nx, ny, wall_x, wall_y;
     int ntx, nty;
+    int tx, ty, lx, ly;  // registry tile shape and log2 of each side
     long long P;  // plane size nx*ny
     double tau, rho_f, lid_u, eps, eta, gravity;
     int force_kind;
@@ -203,8 +205,9 @@ __device__ __forceinline__ long long grid_index(const SimParams &sp, int gx, int
 // every g_q vanishes, so all nine stored numbers are small deviations.
 template <class R>
 __device__ __forceinline__ R rest_base(const SimParams &sp, const int *reg, const R *pool, int i, int j) {
-    const int tile = (j / TILE_Y) * sp.ntx + i / TILE_X;
-    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + (j % TILE_Y) * TILE_X + i % TILE_X] : R(0);
+    const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))]
+                         : R(0);
 }
 
 // Moments of node (i, j): rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
@@ -428,6 +431,27 @@ __device__ __forceinline__ void warp_minmax(int &v, bool is_min) {
     v = (int)r - (1 << 30);
 }
 
+// Disjoint ranges of tile indices (side 2^shift, ntiles per row or column) that
+// cover the node interval [lo, hi] of one axis of extent n: clipped at walls,
+// wrapped (and merged where the two wrapped pieces share tiles) when periodic.
+__device__ __forceinline__ int tile_ranges(int lo, int hi, int n, int wall, int shift, int ntiles, int r0[2],
+                                           int r1[2]) {
+    if (wall) {
+        lo = max(lo, 0);
+        hi = min(hi, n - 1);
+        if (lo > hi) return 0;
+        r0[0] = lo >> shift; r1[0] = hi >> shift;
+        return 1;
+    }
+    if (hi - lo + 1 >= n) { r0[0] = 0; r1[0] = ntiles - 1; return 1; }
+    const int k0 = floordiv(lo, n), k1 = floordiv(hi, n);
+    const int a = (lo - k0 * n) >> shift, b = (hi - k1 * n) >> shift;
+    if (k0 == k1) { r0[0] = a; r1[0] = b; return 1; }
+    if (b + 1 >= a) { r0[0] = 0; r1[0] = ntiles - 1; return 1; }
+    r0[0] = 0; r1[0] = b; r0[1] = a; r1[1] = ntiles - 1;
+    return 2;
+}
+
 // Claim a free label byte (-1 -> l) with a CAS on the 32-bit word holding it.
 __device__ __forceinline__ bool claim_label(signed char *lab, int q, int l) {
     unsigned *w = reinterpret_cast<unsigned *>(lab + (q & ~3));
@@ -451,12 +475,12 @@ struct BoxWalk {
 };
 
 template <class R, class S>
-__global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
+__device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int s) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int nlist;
     __shared__ int bb[12];  // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
     __shared__ double red[32 * 6];
-    const int s = blockIdx.x;
+    __syncthreads();  // the shared state of a previous solid is no longer read
     const SolidDesc sd = a.solids[s];
     const int T = sd.T, TT = T * T;
     const int lane = threadIdx.x & 31;
@@ -706,28 +730,15 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS :
         fn.bx0 = fn.by0 = 1; fn.bx1 = fn.by1 = 0;  // filled by the step that writes that tile
         a.frame_next[s] = fn;
     }
-    // Register the 32x8 tiles that the blur zone (grown by one node) touches.
+    // Register the tiles that the blur zone (grown by one node) touches, each once.
     if (bb[8] <= bb[9]) {
-        int x0 = oo.x + bb[8] - 1, x1 = oo.x + bb[9] + 1, y0 = oo.y + bb[10] - 1, y1 = oo.y + bb[11] + 1;
-        int sxa[2], sxb[2], sya[2], syb[2], nsx = 1, nsy = 1;
-        if (sp.wall_x) { sxa[0] = max(x0, 0); sxb[0] = min(x1, sp.nx - 1); }
-        else {
-            const int k0 = floordiv(x0, sp.nx), k1 = floordiv(x1, sp.nx);
-            if (k0 == k1) { sxa[0] = x0 - k0 * sp.nx; sxb[0] = x1 - k0 * sp.nx; }
-            else { sxa[0] = x0 - k0 * sp.nx; sxb[0] = sp.nx - 1; sxa[1] = 0; sxb[1] = x1 - k1 * sp.nx; nsx = 2; }
-        }
-        if (sp.wall_y) { sya[0] = max(y0, 0); syb[0] = min(y1, sp.ny - 1); }
-        else {
-            const int k0 = floordiv(y0, sp.ny), k1 = floordiv(y1, sp.ny);
-            if (k0 == k1) { sya[0] = y0 - k0 * sp.ny; syb[0] = y1 - k0 * sp.ny; }
-            else { sya[0] = y0 - k0 * sp.ny; syb[0] = sp.ny - 1; sya[1] = 0; syb[1] = y1 - k1 * sp.ny; nsy = 2; }
-        }
-        for (int ay = 0; ay < nsy; ay++)
-            for (int ax = 0; ax < nsx; ax++) {
-                if (sxa[ax] > sxb[ax] || sya[ay] > syb[ay]) continue;
-                const int tx0 = sxa[ax] / TILE_X, tx1 = sxb[ax] / TILE_X;
-                const int ty0 = sya[ay] / TILE_Y, ty1 = syb[ay] / TILE_Y;
-                const int ntxr = tx1 - tx0 + 1, nall = ntxr * (ty1 - ty0 + 1);
+        int rx0[2], rx1[2], ry0[2], ry1[2];
+        const int nrx = tile_ranges(oo.x + bb[8] - 1, oo.x + bb[9] + 1, sp.nx, sp.wall_x, sp.lx, sp.ntx, rx0, rx1);
+        const int nry = tile_ranges(oo.y + bb[10] - 1, oo.y + bb[11] + 1, sp.ny, sp.wall_y, sp.ly, sp.nty, ry0, ry1);
+        for (int ay = 0; ay < nry; ay++)
+            for (int ax = 0; ax < nrx; ax++) {
+                const int tx0 = rx0[ax], ty0 = ry0[ay];
+                const int ntxr = rx1[ax] - tx0 + 1, nall = ntxr * (ry1[ay] - ty0 + 1);
                 for (int k = threadIdx.x; k < nall; k += blockDim.x) {
                     const int tile = (ty0 + k / ntxr) * sp.ntx + tx0 + k % ntxr;
                     const int slot = atomicAdd(&a.reg_count[tile], 1);
@@ -739,8 +750,13 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS :
     }
 }
 
+template <class R, class S>
+__global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
+    rmt_solid<R, S>(sp, a, blockIdx.x);
+}
+
 // ===========================================================================
-// K3: stress divergence, contact and node terms per registered 32x8 tile.
+// K3: stress divergence, contact and node terms per registered tile.
 // ===========================================================================
 template <class R>
 struct ForceArgs {
@@ -783,26 +799,48 @@ __device__ __forceinline__ bool stress_from_grad(R Axx, R Axy, R Ayx, R Ayy, R G
     return true;
 }
 
+// Per-tile constants of the registered solids (static shared memory of K3).
 template <class R>
-__global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R> a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    R *sX = reinterpret_cast<R *>(smem);          // [KMAX][PATCH_N]
-    R *sY = sX + KMAX * PATCH_N;
-    R *sP = sY + KMAX * PATCH_N;
-    R *eT = sP + KMAX * PATCH_N;                  // [(NXE + NYE) * 3] edge stresses
-    __shared__ int ids[KMAX];
-    __shared__ int nk;
-    __shared__ Frame sfr[KMAX];
-    __shared__ R sG[KMAX], sD[KMAX], sA[KMAX];
-    __shared__ Rsq<R> srq[KMAX];
-    __shared__ int sT[KMAX];
-    __shared__ long long soff[KMAX];
-    const int nact = *a.reg_nactive;
+struct ForceShared {
+    int ids[KMAX];
+    int nk;
+    Frame sfr[KMAX];
+    R sG[KMAX], sD[KMAX], sA[KMAX];
+    Rsq<R> srq[KMAX];
+    int sT[KMAX];
+    long long soff[KMAX];
+};
+
+// Dynamic shared memory of K3 for a tile shape: xi_x, xi_y, phi per slot on the
+// tile plus a one-node halo, and three stress components per half-edge.
+__host__ __device__ __forceinline__ int force_patch_n(int tx, int ty) { return (tx + 2) * (ty + 2); }
+__host__ __device__ __forceinline__ int force_smem_elems(int tx, int ty) {
+    return 3 * KMAX * force_patch_n(tx, ty) + 3 * ((tx + 1) * ty + tx * (ty + 1));
+}
+__host__ __device__ __forceinline__ int force_smem_max() {
+    int m = 0;
+    for (int tx = 16; tx <= 128; tx *= 2) m = force_smem_elems(tx, TILE_N / tx) > m ? force_smem_elems(tx, TILE_N / tx) : m;
+    return m;
+}
+
+template <class R>
+__device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int tile, ForceShared<R> &fs, R *dyn) {
+    const int TX = sp.tx, PX = TX + 2, PN = force_patch_n(TX, sp.ty);
+    const int NXE = (TX + 1) * sp.ty, NYE = TX * (sp.ty + 1);
+    R *sX = dyn;                       // [KMAX][PN]
+    R *sY = sX + KMAX * PN;
+    R *sP = sY + KMAX * PN;
+    R *eT = sP + KMAX * PN;            // [(NXE + NYE) * 3] edge stresses
+    int *ids = fs.ids;
+    Frame *sfr = fs.sfr;
+    R *sG = fs.sG, *sD = fs.sD, *sA = fs.sA;
+    Rsq<R> *srq = fs.srq;
+    int *sT = fs.sT;
+    long long *soff = fs.soff;
     const R eps = pick<R>(sp.eps, sp.eps_f), eta = pick<R>(sp.eta, sp.eta_f);
-    for (int it = blockIdx.x; it < nact; it += gridDim.x) {
-        const int tile = a.reg_active[it];
+    {
         const int tx = tile % sp.ntx, ty = tile / sp.ntx;
-        const int i0 = tx * TILE_X, j0 = ty * TILE_Y;
+        const int i0 = tx * TX, j0 = ty * sp.ty;
         if (threadIdx.x == 0) {
             int n = min(a.reg_count[tile], sp.kmax);
             for (int k = 0; k < n; k++) ids[k] = a.reg_solids[tile * KMAX + k];
@@ -811,10 +849,10 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                 while (m >= 0 && ids[m] > v) { ids[m + 1] = ids[m]; m--; }
                 ids[m + 1] = v;
             }
-            nk = n;
+            fs.nk = n;
         }
         __syncthreads();
-        if (threadIdx.x < nk) {
+        if (threadIdx.x < fs.nk) {
             const SolidDesc &sd = a.solids[ids[threadIdx.x]];
             sfr[threadIdx.x] = a.frame[ids[threadIdx.x]];
             sG[threadIdx.x] = pick<R>(sd.G, sd.G_f);
@@ -825,11 +863,11 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
             soff[threadIdx.x] = sd.off;
         }
         __syncthreads();
-        const int n = nk;
+        const int n = fs.nk;
         // Stage each solid's xi (and phi) on the tile plus a one-node halo.
-        for (int idx = threadIdx.x; idx < n * PATCH_N; idx += blockDim.x) {
-            const int ks = idx / PATCH_N, p = idx % PATCH_N;
-            const int px = p % PATCH_X, py = p / PATCH_X;
+        for (int idx = threadIdx.x; idx < n * PN; idx += blockDim.x) {
+            const int ks = idx / PN, p = idx % PN;
+            const int px = p % PX, py = p / PX;
             const int gx = i0 - 1 + px, gy = j0 - 1 + py;
             const Frame fr = sfr[ks];
             const int T = sT[ks];
@@ -842,7 +880,7 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                 Y = Xs[T * T + ly * T + lx];
                 if (X == X) P = phi_eta(X, Y, lx, ly, fr, srq[ks]);
             }
-            sX[ks * PATCH_N + p] = X; sY[ks * PATCH_N + p] = Y; sP[ks * PATCH_N + p] = P;
+            sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
         }
         __syncthreads();
         // Half-edge stresses: blended solid stress (Eq. 3_6_global_stress) plus contact.
@@ -850,18 +888,18 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
             int pa[3], pb[3];  // patch indices of the 2x3 stencil (a low side, b high side)
             const bool xedge = e < NXE;
             if (xedge) {
-                const int ex = e % (TILE_X + 1), ey = e / (TILE_X + 1);  // edge between col ex-1 and ex (tile coords)
-                for (int k = 0; k < 3; k++) { pa[k] = (ey + k) * PATCH_X + ex; pb[k] = (ey + k) * PATCH_X + ex + 1; }
+                const int ex = e % (TX + 1), ey = e / (TX + 1);  // edge between col ex-1 and ex (tile coords)
+                for (int k = 0; k < 3; k++) { pa[k] = (ey + k) * PX + ex; pb[k] = (ey + k) * PX + ex + 1; }
             } else {
                 const int f = e - NXE;
-                const int ex = f % TILE_X, ey = f / TILE_X;               // edge between row ey-1 and ey
-                for (int k = 0; k < 3; k++) { pa[k] = ey * PATCH_X + ex + k; pb[k] = (ey + 1) * PATCH_X + ex + k; }
+                const int ex = f % TX, ey = f / TX;               // edge between row ey-1 and ey
+                for (int k = 0; k < 3; k++) { pa[k] = ey * PX + ex + k; pb[k] = (ey + 1) * PX + ex + k; }
             }
             R Sxx = 0, Sxy = 0, Syy = 0, L = 0, Cxx = 0, Cxy = 0, Cyy = 0;
             bool okv[KMAX];
             R phh[KMAX];
             for (int ks = 0; ks < n; ks++) {
-                const R *X = sX + ks * PATCH_N, *Y = sY + ks * PATCH_N, *P = sP + ks * PATCH_N;
+                const R *X = sX + ks * PN, *Y = sY + ks * PN, *P = sP + ks * PN;
                 bool ok = true;
                 for (int k = 0; k < 3; k++) ok = ok && (P[pa[k]] == P[pa[k]]) && (P[pb[k]] == P[pb[k]]);
                 okv[ks] = ok;
@@ -885,7 +923,7 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
                     if (!okv[kt] || !(phh[kt] < eps)) continue;
                     const R fs = R(0.5) * (R(1) - phh[ks] / eps), ft = R(0.5) * (R(1) - phh[kt] / eps);
                     const R fm = fs < ft ? fs : ft;
-                    const R *Ps = sP + ks * PATCH_N, *Pt = sP + kt * PATCH_N;
+                    const R *Ps = sP + ks * PN, *Pt = sP + kt * PN;
                     R gn, gt;
                     edge_grad<R>(Ps[pa[0]] - Pt[pa[0]], Ps[pa[1]] - Pt[pa[1]], Ps[pa[2]] - Pt[pa[2]],
                                  Ps[pb[0]] - Pt[pb[0]], Ps[pb[1]] - Pt[pb[1]], Ps[pb[2]] - Pt[pb[2]], gn, gt);
@@ -903,17 +941,17 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
         __syncthreads();
         // Node: divergence (Eq. 3_3_div_solid_stress), solid fraction, drho, solid acceleration.
         {
-            const int cx = threadIdx.x % TILE_X, cy = threadIdx.x / TILE_X;
+            const int cx = threadIdx.x & (TX - 1), cy = threadIdx.x >> sp.lx;
             const int i = i0 + cx, j = j0 + cy;
             if (i < sp.nx && j < sp.ny) {
-                const R *tl = eT + 3 * (cy * (TILE_X + 1) + cx), *tr = eT + 3 * (cy * (TILE_X + 1) + cx + 1);
-                const R *tb = eT + 3 * (NXE + cy * TILE_X + cx), *tt = eT + 3 * (NXE + (cy + 1) * TILE_X + cx);
+                const R *tl = eT + 3 * (cy * (TX + 1) + cx), *tr = eT + 3 * (cy * (TX + 1) + cx + 1);
+                const R *tb = eT + 3 * (NXE + cy * TX + cx), *tt = eT + 3 * (NXE + (cy + 1) * TX + cx);
                 const R fsx = (tr[0] - tl[0]) + (tt[1] - tb[1]);
                 const R fsy = (tr[1] - tl[1]) + (tt[2] - tb[2]);
-                const int p = (cy + 1) * PATCH_X + cx + 1;
+                const int p = (cy + 1) * PX + cx + 1;
                 R L = 0, D = 0, Ay = 0;
                 for (int ks = 0; ks < n; ks++) {
-                    const R ph = sP[ks * PATCH_N + p];
+                    const R ph = sP[ks * PN + p];
                     if (!(ph == ph)) continue;
                     const R lam = R(1) - heaviside<R>(ph, eps);
                     L += lam;
@@ -929,6 +967,15 @@ __global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R
         }
         __syncthreads();
     }
+}
+
+template <class R>
+__global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ForceShared<R> fs;
+    const int nact = *a.reg_nactive;
+    for (int it = blockIdx.x; it < nact; it += gridDim.x)
+        force_tile<R>(sp, a, a.reg_active[it], fs, reinterpret_cast<R *>(smem));
 }
 
 // ===========================================================================
@@ -949,18 +996,16 @@ struct LbArgs {
     unsigned *err;
 };
 
+// One registry tile (bx, by) of K1, one thread per node.
 template <class R, class S>
-__global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
-    __shared__ int prev_count;
-    const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
-    const int tile = blockIdx.y * sp.ntx + blockIdx.x;
-    const int lt = threadIdx.y * TILE_X + threadIdx.x;
+__device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> &a, const int bx, const int by) {
+    const int lt = threadIdx.x;
+    const int i = bx * sp.tx + (lt & (sp.tx - 1)), j = by * sp.ty + (lt >> sp.lx);
+    const int tile = by * sp.ntx + bx;
     const int nx = sp.nx, ny = sp.ny, P = (int)sp.P;  // 9 P < 2^31 is checked at creation
-    if (lt == 0) prev_count = a.clr_count[tile];
-    __syncthreads();
-    // every push target of this block lies inside the domain
-    const bool interior = blockIdx.x > 0 && (blockIdx.x + 1) * TILE_X < nx && blockIdx.y > 0 &&
-                          (blockIdx.y + 1) * TILE_Y < ny;
+    const int prev_count = a.clr_count[tile];  // cleared below, after every thread has read it
+    // every push target of this tile lies inside the domain
+    const bool interior = bx > 0 && (bx + 1) * sp.tx < nx && by > 0 && (by + 1) * sp.ty < ny;
     R dm = R(0);
     if (i < nx && j < ny) {
         const int c = j * nx + i;
@@ -1041,21 +1086,27 @@ __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R,
         }
         dm = dr;
     }
-    // total mass: rho - rho_f summed over the warp (one row of the tile), then FP64 per warp
+    // total mass: rho - rho_f summed over the warp, then FP64 per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
-    if (threadIdx.x == 0) a.mass_partials[(long long)tile * TILE_Y + threadIdx.y] = (double)dm;
+    if ((lt & 31) == 0) a.mass_partials[(long long)tile * (TILE_N / 32) + (lt >> 5)] = (double)dm;
+    __syncthreads();
     if (lt == 0) {
         a.clr_count[tile] = 0;
         if (tile == 0) *a.clr_nactive = 0;
     }
 }
 
+template <class R, class S>
+__global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
+    lb_tile<R, S>(sp, a, blockIdx.x, blockIdx.y);
+}
+
 // Initial populations f = f^eq,SFC(rho_t, 0): in the stored form (relative to
 // w_q rho_f and, for q = 0, to the initial Delta rho) every value is zero.
 template <class R, class S>
 __global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
-    const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+    const int i = blockIdx.x * sp.tx + (threadIdx.x & (sp.tx - 1)), j = blockIdx.y * sp.ty + (threadIdx.x >> sp.lx);
     if (i >= sp.nx || j >= sp.ny) return;
     const long long c = (long long)j * sp.nx + i;
     for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(0));
@@ -1067,7 +1118,7 @@ __global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
 template <class R, class S>
 __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *fbody, const int *reg_count,
                              const R *pool, int kind, double *out) {
-    const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+    const int i = blockIdx.x * sp.tx + (threadIdx.x & (sp.tx - 1)), j = blockIdx.y * sp.ty + (threadIdx.x >> sp.lx);
     if (i >= sp.nx || j >= sp.ny) return;
     const int tile = blockIdx.y * sp.ntx + blockIdx.x;
     const long long c = (long long)j * sp.nx + i;
@@ -1083,7 +1134,7 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
         v = kind == 1 ? (double)u : (double)w;
     } else if (kind <= 5) {
         R p = 0;
-        if (reg_count[tile] > 0) p = pool[(long long)tile * POOL_STRIDE + (kind - 3) * TILE_N + threadIdx.y * TILE_X + threadIdx.x];
+        if (reg_count[tile] > 0) p = pool[(long long)tile * POOL_STRIDE + (kind - 3) * TILE_N + threadIdx.x];
         if (kind == 3) v = (double)(fbody[j] + p);
         else if (kind == 4) v = (double)(pick<R>(sp.fy, sp.fy_f) + p);
         else v = (double)p;

@@ -25,6 +25,7 @@ struct lbrmt_sim {
     bool inited = false;
     long long steps = 0;
     bool use_graphs = true;
+    bool in_batch = false;          // stepped by a batch: lbrmt_step is refused
     cudaGraphExec_t gexec = nullptr;
     long long last_launches = 0;
     std::vector<void *> allocs;
@@ -33,3 +34,5 @@ struct lbrmt_sim {
     std::string err;
 };
 
+// Wait for the simulation's stream and map its device error flags to a status.
+lbrmt_status lbrmt_internal_check_flags(lbrmt_sim *s);

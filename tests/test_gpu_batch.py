@@ -1,0 +1,181 @@
+"""Tile shapes and batches of simulations on the GPU.
+
+* The registry / LB tile shape (tile_x x 256/tile_x) changes only which CTA
+  computes a node, never its arithmetic: every shape gives bit-identical fields.
+* A member of a batch computes exactly what the same scenario computes alone
+  (bit-identical fields), whatever the other members and the tile shapes.
+* Batched FP64 members match the FP64 oracle like single simulations do.
+* The 96-cavity ensemble (sides 128..512, 1-8 disks of radius 8-40) runs in one
+  batch; sampled members are checked against single runs and the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenarios
+from parity_util import compare
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho", "ux", "uy", "Fx", "Fy", "drho")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_12696_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _snapshot(sim, sc):
+    out = [sim.field_host(n) for n in FIELDS]
+    for s in range(len(sc["solids"])):
+        out += [sim.field_host("xi_x", s), sim.field_host("xi_y", s)]
+    return out
+
+
+def _same(a, b):
+    return all(np.array_equal(x, y, equal_nan=True) for x, y in zip(a, b))
+
+
+SHAPE_CASES = {
+    "settling_small_0": lambda: scenarios.settling_small(0),
+    "mixing_small_1": lambda: scenarios.mixing_small(1),
+    "contact_pair": lambda: scenarios.contact_pair(gap=0.8, nx=96, ny=64),
+    "ragged": lambda: scenarios.fluid_only(100, 60, 1, 0, 0.7, force_kind=1, force_a=(0.0, 2e-5)),
+}
+
+
+@pytest.mark.parametrize("case", list(SHAPE_CASES))
+def test_tile_shapes_bit_identical(case):
+    import paper_2402_12696_gb300 as pkg
+    sc = SHAPE_CASES[case]()
+    snaps = {}
+    for tx in (32, 16, 64, 128):
+        sim = pkg.Simulation(sc, precision="fp32", tile_x=tx)
+        sim.step(13)
+        snaps[tx] = _snapshot(sim, sc)
+        sim.close()
+    for tx in (16, 64, 128):
+        assert _same(snaps[32], snaps[tx]), tx
+
+
+@pytest.mark.parametrize("case", ["settling_small_0", "mixing_small_1"])
+def test_tile_shape_fp64_oracle(case):
+    # 128-wide tiles on 96-wide periodic grids: one tile spans the width, so a
+    # blur zone that wraps the periodic edge must still register its tile once
+    import paper_2402_12696_gb300 as pkg
+    sc = SHAPE_CASES[case]()
+    sim = pkg.Simulation(sc, precision="fp64", tile_x=128)
+    ref = oracle.Oracle(sc)
+    sim.step(10)
+    ref.step(10)
+    r = compare(sim, ref, sc)
+    for k in ("rho", "u", "xi", "F", "drho"):
+        assert r[k] < 1e-8, (k, r)
+    sim.close()
+    ref.close()
+
+
+def _batch_scs():
+    return [scenarios.mixing_small(0), scenarios.settling_small(1), scenarios.ldc_disk_64(),
+            scenarios.fluid_only(100, 60, 1, 0, 0.7, force_kind=1, force_a=(0.0, 2e-5)),
+            scenarios.contact_pair(gap=0.8, nx=96, ny=64)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_members_match_single_runs(prec):
+    import paper_2402_12696_gb300 as pkg
+    scs = _batch_scs()
+    txs = [32, 16, 64, 128, 32]
+    b = pkg.Batch(scs, precision=prec, tile_x=txs)
+    b.step(23)  # one 20-step graph, one 2-step graph, one direct step
+    b.sync()
+    assert b.steps_done == 23
+    for k, sc in enumerate(scs):
+        assert b[k].steps_done == 23
+        sim = pkg.Simulation(sc, precision=prec, tile_x=32)
+        sim.step(23)
+        assert _same(_snapshot(sim, sc), _snapshot(b[k], sc)), k
+        np.testing.assert_array_equal(sim.solid_stats(), b[k].solid_stats())
+        sim.close()
+    b.close()
+
+
+def test_batch_fp64_oracle():
+    import paper_2402_12696_gb300 as pkg
+    scs = [scenarios.ldc_disk_64(), scenarios.mixing_small(1), scenarios.contact_pair(gap=0.8, nx=96, ny=64)]
+    b = pkg.Batch(scs, precision="fp64", tile_x=[16, 64, 32])
+    refs = [oracle.Oracle(sc) for sc in scs]
+    done = 0
+    for n in (1, 10):
+        b.step(n - done)
+        for r in refs:
+            r.step(n - done)
+        done = n
+        b.sync()
+        for k, sc in enumerate(scs):
+            res = compare(b[k], refs[k], sc)
+            for f in ("rho", "u", "xi", "xi_band", "F", "drho"):
+                assert res[f] < 1e-8, (k, n, f, res)
+            assert res["label_mismatch"] == 0
+    for r in refs:
+        r.close()
+    b.close()
+
+
+def test_batch_autotune_and_restart():
+    import paper_2402_12696_gb300 as pkg
+    scs = [scenarios.mixing_small(0), scenarios.mixing_small(1), scenarios.settling_small(0),
+           scenarios.settling_small(2)]
+    b = pkg.Batch(scs, precision="fp32", autotune_steps=3)
+    log = b.tune_log()
+    sizes = {(sc["nx"], sc["ny"]) for sc in scs}
+    assert len(log) == 4 * len(sizes)  # the starting shape, then 3 others per grid size
+    assert all(ms > 0 for (_, _, _, ms) in log)
+    assert b.steps_done == 0
+    for k in range(len(scs)):
+        assert b.tile_x(k) in (16, 32, 64, 128)
+        assert b[k].steps_done == 0
+    b.step(6)
+    for k, sc in enumerate(scs):
+        sim = pkg.Simulation(sc, precision="fp32", tile_x=b.tile_x(k))
+        sim.step(6)
+        assert _same(_snapshot(sim, sc), _snapshot(b[k], sc)), k
+        sim.close()
+    b.close()
+
+
+def test_member_cannot_be_stepped_alone():
+    import paper_2402_12696_gb300 as pkg
+    b = pkg.Batch([scenarios.ldc_disk_64(), scenarios.mixing_small(0)], precision="fp32")
+    with pytest.raises(pkg.LbrmtError, match="ERR_STATE"):
+        b[0].step(1)
+    b.close()
+
+
+def test_ldc_ensemble_96():
+    import paper_2402_12696_gb300 as pkg
+    scs = scenarios.ldc_ensemble(0)
+    assert len(scs) == 96
+    b = pkg.Batch(scs, precision="fp32")
+    b.step(4)
+    b.sync()
+    # the smallest member against the oracle after 4 steps, and two members
+    # against single runs
+    k_small = min(range(96), key=lambda k: scs[k]["nx"] * scs[k]["ny"] * 10 + len(scs[k]["solids"]))
+    ref = oracle.Oracle(scs[k_small])
+    ref.step(4)
+    r = compare(b[k_small], ref, scs[k_small])
+    assert r["xi"] < 1e-5 and r["label_mismatch"] == 0, r
+    assert r["u_abs"] < 1e-5 * max(r["u_max"], 1e-6) + 1e-7, r
+    ref.close()
+    for k in (0, 95):
+        sim = pkg.Simulation(scs[k], precision="fp32")
+        sim.step(4)
+        assert _same(_snapshot(sim, scs[k]), _snapshot(b[k], scs[k])), k
+        sim.close()
+    b.close()
