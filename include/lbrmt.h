@@ -53,7 +53,7 @@ typedef enum {
 
 enum { LBRMT_PERIODIC = 0, LBRMT_WALL = 1 };
 enum { LBRMT_FP32 = 0, LBRMT_FP64 = 1, LBRMT_FP16_STORE = 2, LBRMT_BF16_STORE = 3 };
-enum { LBRMT_FORCE_NONE = 0, LBRMT_FORCE_CONST = 1, LBRMT_FORCE_SINE_X = 2 };
+enum { LBRMT_FORCE_NONE = 0, LBRMT_FORCE_CONST = 1, LBRMT_FORCE_SINE_X = 2, LBRMT_FORCE_FIELD = 3 };
 enum { LBRMT_SHAPE_DISK = 0 };
 
 /* Field ids for lbrmt_read_fields.  RHO/UX/UY are the moments of the current
@@ -83,7 +83,8 @@ typedef struct {
     double eta;                 /* contact constant of Eq. 3_6_collision_stress */
     double gravity;             /* g >= 0 acting in -y on solids: a = (1 - rho_f/rho_s) g (Sec. 4.3) */
     int force_kind;             /* LBRMT_FORCE_*: body force on all phases */
-    double force_a[2];          /* (fx, fy) for CONST, (A, 0) for f_x = A sin(2 pi y / ny) */
+    double force_a[2];          /* (fx, fy) for CONST, (A, 0) for f_x = A sin(2 pi y / ny);
+                                   FIELD: a per-node field set by lbrmt_set_body_force_field (0 at creation) */
     int precision;              /* LBRMT_FP32 / LBRMT_FP64 arithmetic and storage; LBRMT_FP16_STORE /
                                    LBRMT_BF16_STORE: FP32 arithmetic, populations and half-force
                                    stored in 16 bits (FP16 with power-of-two scales 2^10 and 2^14) */
@@ -112,6 +113,20 @@ lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream, lbrmt_sim 
  * id (0, 1, ...) in *solid_id_out (may be NULL). */
 lbrmt_status lbrmt_add_solid(lbrmt_sim *sim, int shape, double cx, double cy, double radius,
                              double rho_s, double G, int *solid_id_out);
+
+/* Body force field f(x) of Eq. 2_4_F_divs for force_kind LBRMT_FORCE_FIELD:
+ * dev_xy is a device array of 2*nx*ny doubles (x components, then y
+ * components, row-major), copied (and rounded to the arithmetic precision);
+ * caller-owned.  Acts on all phases from the next step on.  sim_index must be 0. */
+lbrmt_status lbrmt_set_body_force_field(lbrmt_sim *sim, int sim_index, const double *dev_xy);
+
+/* Change a solid's density and shear modulus.  After initialisation this
+ * also returns the simulation to its initial state (lbrmt_reset). */
+lbrmt_status lbrmt_set_solid_params(lbrmt_sim *sim, int solid_id, double rho_s, double G);
+
+/* Return to the initial state of Algorithm 1 with the current parameters
+ * (keeps the allocations and the body force field). */
+lbrmt_status lbrmt_reset(lbrmt_sim *sim);
 
 /* Initialise (Algorithm 1, initialisation): xi = x on each solid and its
  * band, phi = phi_0(xi), rho = rho_t, v = 0, f = f^eq,SFC(rho_t, 0).  Called
@@ -190,6 +205,34 @@ const char *lbrmt_last_error(const lbrmt_sim *sim);
 
 /* Free the handle and all device memory it owns. */
 void lbrmt_destroy(lbrmt_sim *sim);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint.  The paper has no counterpart (it runs the method forward only).
+ * The loss L is any function of the solids' centroids at the final step,
+ * c_s = sum_x lambda_s(x) x / sum_x lambda_s(x), lambda_s = 1 - H_eps(phi_s)
+ * over the domain nodes of the solid's tile (unwrapped coordinates).  The
+ * reverse sweep applies the transposed Jacobian of every kernel of the step
+ * (the branch decisions of the forward step held fixed) with checkpointing.
+ * FP32 and FP64 arithmetic only.
+ * ------------------------------------------------------------------------- */
+
+/* Return to the initial state, run nsteps >= 1 steps keeping a copy of the
+ * device state every checkpoint_every >= 1 steps and at the end, and write the
+ * final centroids (S x 2 host doubles, may be NULL).  Synchronous.  Needs
+ * about (nsteps / checkpoint_every + 1) times the simulation's state memory. */
+lbrmt_status lbrmt_forward_checkpointed(lbrmt_sim *sim, int nsteps, int checkpoint_every, double *centroids_out);
+
+/* Gradients of L through the last lbrmt_forward_checkpointed run, given
+ * dL_dcentroid = dL/dc_s (S x 2 host doubles): dL_dG[s] = dL/dG_s and
+ * dL_dratio[s] = dL/d(rho_s / rho_f) (S host doubles each, may be NULL), and
+ * dL_dbody_dev = dL/df(x) for the body force field (2 nx ny device doubles,
+ * x plane then y plane; needs force_kind LBRMT_FORCE_FIELD; may be NULL), and
+ * dL_df0_dev = dL/df_q(x, t = 0) for the initial populations (9 nx ny device
+ * doubles, plane q at offset q nx ny; may be NULL).
+ * Recomputes each segment from its checkpoint (about one extra forward run);
+ * leaves the simulation in the final state of the forward run.  Synchronous. */
+lbrmt_status lbrmt_backward(lbrmt_sim *sim, const double *dL_dcentroid, double *dL_dG, double *dL_dratio,
+                            double *dL_dbody_dev, double *dL_df0_dev);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent simulations advanced together.  The paper has no

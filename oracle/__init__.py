@@ -48,6 +48,7 @@ def lib():
         L.oracle_create.restype = p
         L.oracle_create.argtypes = [i, i, i, i, d, d, d, d, i, d, d, i, d, d, i]
         L.oracle_add_solid.argtypes = [p, d, d, d, d, d]
+        L.oracle_set_body_force.argtypes = [p, dp]
         L.oracle_init.argtypes = [p]
         L.oracle_step.argtypes = [p, i]
         L.oracle_read_field.argtypes = [p, i, i, dp]
@@ -142,6 +143,10 @@ class Oracle:
             raise OracleError("oracle_create failed (out of memory?)")
         for s in sc["solids"]:
             if L.oracle_add_solid(self.h, s["x"], s["y"], s["r"], s["rho_s"], s["G"]) < 0:
+                self._raise()
+        if sc["force_kind"] == 3:
+            bf = np.ascontiguousarray(sc["body_field"], dtype=np.float64).reshape(2, self.ny, self.nx)
+            if L.oracle_set_body_force(self.h, _dp(bf)) != 0:
                 self._raise()
         if L.oracle_init(self.h) != 0:
             self._raise()

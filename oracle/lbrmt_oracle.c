@@ -74,6 +74,7 @@ typedef struct {
     int force_kind;
     double force_a[2];
     int rmax;
+    double *bfield;  /* force_kind 3: per-node body force, x plane then y plane */
 } ocfg_t;
 
 typedef struct {
@@ -491,10 +492,16 @@ static int update_solid(osim_t *m, osolid_t *s) {
 
 #define EV 7 /* per edge: sum lambda*tau (3), sum lambda, contact tau (3) */
 
-static void body_force(const ocfg_t *c, int j, double *fx, double *fy) {
+/* External body force of node (i, j) (Eq. 2_4_F_divs), acting on all phases. */
+static void body_force(const ocfg_t *c, int i, int j, double *fx, double *fy) {
     *fx = *fy = 0.0;
     if (c->force_kind == 1) { *fx = c->force_a[0]; *fy = c->force_a[1]; }
     else if (c->force_kind == 2) *fx = c->force_a[0] * sin(2.0 * M_PI * j / c->ny);
+    else if (c->force_kind == 3 && c->bfield) {
+        long cell = (long)j * c->nx + i;
+        *fx = c->bfield[cell];
+        *fy = c->bfield[(long)c->nx * c->ny + cell];
+    }
 }
 
 /* Edge array index of the x-edge (dir 0) between (gx-1, gy) and (gx, gy), or the
@@ -572,7 +579,7 @@ static void compute_force(osim_t *m) {
                 int cell = wrapi(gy, ny) * nx + wrapi(gx, nx);
                 double lam = 1.0 - oracle_heaviside(s->phi[k], c->eps);
                 double fbx, fby;
-                body_force(c, wrapi(gy, ny), &fbx, &fby);
+                body_force(c, wrapi(gx, nx), wrapi(gy, ny), &fbx, &fby);
                 double ax = fbx, ay = fby - (1.0 - c->rho_f / s->rho_s) * c->gravity;
                 m->nl[cell] += lam;
                 m->nd[cell] += lam * (s->rho_s - c->rho_f);
@@ -639,7 +646,7 @@ static void compute_force(osim_t *m) {
             if (L > 1.0) { ax /= L; ay /= L; dr /= L; }
             double Hf = 1.0 - fmin(1.0, L);
             double fbx, fby;
-            body_force(c, j, &fbx, &fby);
+            body_force(c, i, j, &fbx, &fby);
             m->Fx[cell] = fsx + ax + Hf * fbx;
             m->Fy[cell] = fsy + ay + Hf * fby;
             m->drho[cell] = dr;
@@ -884,7 +891,19 @@ void oracle_destroy(void *h) {
     free(m->f); free(m->fh); free(m->Fi); free(m->rho); free(m->ux); free(m->uy);
     free(m->Fx); free(m->Fy); free(m->drho); free(m->ex); free(m->ey);
     free(m->nl); free(m->nd); free(m->na);
+    free(m->c.bfield);
     free(m);
+}
+
+/* force_kind 3: copy the body force field (2*nx*ny doubles, x plane then y plane). */
+int oracle_set_body_force(void *h, const double *bxy) {
+    osim_t *m = h;
+    long n = 2L * m->c.nx * m->c.ny;
+    if (m->c.force_kind != 3) return seterr(m, "force_kind is not 3 (field)");
+    if (!m->c.bfield) m->c.bfield = malloc(n * sizeof(double));
+    if (!m->c.bfield) return seterr(m, "out of memory");
+    memcpy(m->c.bfield, bxy, n * sizeof(double));
+    return 0;
 }
 
 int oracle_num_threads(void) {

@@ -31,7 +31,8 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_ini
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs",
-           "lbrmt_last_error", "lbrmt_destroy",
+           "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
+           "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward",
            "lbrmt_create_batch", "lbrmt_batch_add_solid", "lbrmt_batch_init", "lbrmt_batch_step",
            "lbrmt_batch_step_timed", "lbrmt_batch_sync", "lbrmt_batch_member", "lbrmt_batch_size",
            "lbrmt_batch_tile_x", "lbrmt_batch_tune_log", "lbrmt_batch_steps_done",
@@ -94,6 +95,11 @@ def load():
     L.lbrmt_last_error.restype = C.c_char_p
     L.lbrmt_destroy.argtypes = [p]
     L.lbrmt_destroy.restype = None
+    L.lbrmt_set_body_force_field.argtypes = [p, i, p]
+    L.lbrmt_set_solid_params.argtypes = [p, i, d, d]
+    L.lbrmt_reset.argtypes = [p]
+    L.lbrmt_forward_checkpointed.argtypes = [p, i, i, p]
+    L.lbrmt_backward.argtypes = [p, p, p, p, p, p]
     L.lbrmt_create_batch.argtypes = [cfgp, i, p, C.POINTER(p)]
     L.lbrmt_batch_add_solid.argtypes = [p, i, i, d, d, d, d, d, C.POINTER(i)]
     L.lbrmt_batch_init.argtypes = [p, i]
@@ -194,6 +200,27 @@ def lbrmt_step_timed(h, nsteps):
 
 def lbrmt_destroy(h):
     load().lbrmt_destroy(h)
+
+
+def lbrmt_set_body_force_field(h, sim_index, dev_ptr):
+    _check(h, load().lbrmt_set_body_force_field(h, sim_index, C.c_void_p(dev_ptr)))
+
+
+def lbrmt_set_solid_params(h, solid_id, rho_s, G):
+    _check(h, load().lbrmt_set_solid_params(h, solid_id, rho_s, G))
+
+
+def lbrmt_reset(h):
+    _check(h, load().lbrmt_reset(h))
+
+
+def lbrmt_forward_checkpointed(h, nsteps, checkpoint_every, host_ptr):
+    _check(h, load().lbrmt_forward_checkpointed(h, int(nsteps), int(checkpoint_every), C.c_void_p(host_ptr)))
+
+
+def lbrmt_backward(h, dLdc_ptr, dG_ptr, dratio_ptr, dbody_dev_ptr, df0_dev_ptr=0):
+    _check(h, load().lbrmt_backward(h, C.c_void_p(dLdc_ptr), C.c_void_p(dG_ptr), C.c_void_p(dratio_ptr),
+                                    C.c_void_p(dbody_dev_ptr), C.c_void_p(df0_dev_ptr)))
 
 
 def _bcheck(b, st):
@@ -320,6 +347,25 @@ class Simulation:
             load().lbrmt_set_use_graphs(self.h, int(bool(use_graphs)))
             for s in sc["solids"]:
                 lbrmt_add_solid(self.h, 0, s["x"], s["y"], s["r"], s["rho_s"], s["G"])
+            if sc["force_kind"] == 3:
+                self.set_body_force_field(sc["body_field"])
+
+    def set_body_force_field(self, field):
+        """Body force field (2, ny, nx) of a force_kind 3 scenario (array or tensor)."""
+        torch = self.torch
+        t = torch.as_tensor(field, dtype=torch.float64).reshape(2, self.ny, self.nx)
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            t = t.to(self.device, non_blocking=False).contiguous()
+            lbrmt_set_body_force_field(self.h, 0, t.data_ptr())
+            self._bfield = t  # kept alive until the copy kernel has run
+
+    def set_solid_params(self, solid, rho_s, G):
+        with self.torch.cuda.device(self.device):
+            lbrmt_set_solid_params(self.h, solid, rho_s, G)
+
+    def reset(self):
+        with self.torch.cuda.device(self.device):
+            lbrmt_reset(self.h)
 
     # -- time stepping ------------------------------------------------------
     def init(self):
@@ -348,6 +394,33 @@ class Simulation:
     @property
     def last_launch_count(self):
         return load().lbrmt_last_launch_count(self.h)
+
+    # -- adjoint --------------------------------------------------------------
+    def forward_checkpointed(self, nsteps, checkpoint_every):
+        """Run from the initial state; the solids' final centroids (S, 2)."""
+        out = np.zeros((max(self.nsolids, 1), 2))
+        with self.torch.cuda.device(self.device):
+            lbrmt_forward_checkpointed(self.h, nsteps, checkpoint_every, out.ctypes.data)
+        return out[: self.nsolids]
+
+    def backward(self, dLdc, body=False, f0=False):
+        """Gradients through the last forward_checkpointed run for dL/dc (S, 2):
+        (dL/dG (S,), dL/d(rho_s/rho_f) (S,), dL/df body field (2, ny, nx) device
+        tensor or None), and with ``f0`` also dL/df_q(t=0) (9, ny, nx)."""
+        torch = self.torch
+        g = np.ascontiguousarray(dLdc, dtype=np.float64).reshape(self.nsolids, 2)
+        dG = np.zeros(max(self.nsolids, 1))
+        dr = np.zeros(max(self.nsolids, 1))
+        db = None
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            if body:
+                db = torch.zeros((2, self.ny, self.nx), dtype=torch.float64, device=self.device)
+            d0 = torch.zeros((9, self.ny, self.nx), dtype=torch.float64, device=self.device) if f0 else None
+            lbrmt_backward(self.h, g.ctypes.data, dG.ctypes.data, dr.ctypes.data, db.data_ptr() if body else 0,
+                           d0.data_ptr() if f0 else 0)
+        if f0:
+            return dG[: self.nsolids], dr[: self.nsolids], db, d0
+        return dG[: self.nsolids], dr[: self.nsolids], db
 
     # -- outputs ------------------------------------------------------------
     def field(self, name, solid=0):
@@ -490,3 +563,44 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _make_function():
+    import torch
+
+    class LBRMTFunction(torch.autograd.Function):
+        """Final solid centroids c (S, 2) of a Simulation as a differentiable
+        function of the shear moduli G (S,), the density ratios rho_s / rho_f
+        (S,) and the body force field (2, ny, nx) (force_kind 3 scenarios; may
+        be None).  ``apply(G, ratio, body, sim, nsteps, checkpoint_every)``;
+        the backward pass is the library's adjoint sweep (lbrmt_backward)."""
+
+        @staticmethod
+        def forward(ctx, G, ratio, body, sim, nsteps, checkpoint_every):
+            rho_f = sim.sc["rho_f"]
+            for k in range(sim.nsolids):
+                sim.set_solid_params(k, float(ratio[k]) * rho_f, float(G[k]))
+            if body is not None:
+                sim.set_body_force_field(body.detach())
+            c = sim.forward_checkpointed(nsteps, checkpoint_every)
+            ctx.sim = sim
+            ctx.has_body = body is not None
+            ctx.body_device = body.device if body is not None else None
+            return torch.as_tensor(c, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_c):
+            dG, dr, db = ctx.sim.backward(grad_c.detach().cpu().numpy(), body=ctx.has_body)
+            gb = db.to(ctx.body_device) if ctx.has_body else None
+            return (torch.as_tensor(dG, dtype=torch.float64), torch.as_tensor(dr, dtype=torch.float64), gb,
+                    None, None, None)
+
+    return LBRMTFunction
+
+
+def __getattr__(name):
+    if name == "LBRMTFunction":
+        fn = _make_function()
+        globals()["LBRMTFunction"] = fn
+        return fn
+    raise AttributeError(name)

@@ -4,6 +4,7 @@
 // initialisation, enqueues the three kernels of a step on the caller's stream
 // and replays them through a two-step CUDA graph (the state is double-buffered
 // by step parity, so steps 2k and 2k+1 form a fixed launch sequence).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,7 +81,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (!(c.rho_f > 0) || !(c.eps > 0) || c.n_layers < 1 || c.n_layers > 20) return LBRMT_ERR_ARG;
     if (c.max_solids_per_tile < 1 || c.max_solids_per_tile > KMAX || c.rmax < 2 || c.rmax > 20) return LBRMT_ERR_ARG;
     if (c.lid_u != 0.0 && c.bc_y != LBRMT_WALL) return LBRMT_ERR_ARG;
-    if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > 2) return LBRMT_ERR_ARG;
+    if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > LBRMT_FORCE_FIELD) return LBRMT_ERR_ARG;
     if (c.precision < LBRMT_FP32 || c.precision > LBRMT_BF16_STORE) return LBRMT_ERR_ARG;
     const int tx = c.tile_x == 0 ? 32 : c.tile_x;
     if (tx != 16 && tx != 32 && tx != 64 && tx != 128) return LBRMT_ERR_ARG;
@@ -124,6 +125,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     }
     ok = ok && (d.carry = dalloc(s, 2 * P * ss));
     ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
+    if (c.force_kind == LBRMT_FORCE_FIELD) ok = ok && (d.bfield = dalloc(s, 2 * P * rs));
     ok = ok && (d.mass_partials = (double *)dalloc(s, ntiles * (TILE_N / 32) * 8));
     ok = ok && (d.err = (unsigned *)dalloc(s, 16));
     ok = ok && (s->scratch = (double *)dalloc(s, 64));
@@ -140,6 +142,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         if (e == cudaSuccess) e = cudaMemsetAsync(d.pool[k], 0, ntiles * POOL_STRIDE * rs, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, st);
+    if (e == cudaSuccess && d.bfield) e = cudaMemsetAsync(d.bfield, 0, 2 * P * rs, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, ntiles * (TILE_N / 32) * 8, st);
     // body force per row (x component), Sec. 4 forcing on all phases
     std::vector<double> fb(c.ny, 0.0);
@@ -202,34 +205,16 @@ static lbrmt_status check_flags(lbrmt_sim *s) {
 }
 
 lbrmt_status lbrmt_internal_check_flags(lbrmt_sim *s) { return check_flags(s); }
+void *lbrmt_internal_alloc(lbrmt_sim *s, size_t bytes) { return dalloc(s, bytes); }
+lbrmt_status lbrmt_internal_fail(lbrmt_sim *s, lbrmt_status st, const std::string &msg) { return fail(s, st, msg); }
 
-extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
-    if (!s) return LBRMT_ERR_ARG;
-    if (s->inited) return LBRMT_OK;
+// Solid descriptors and initial frames from the host solids; configure and run
+// the initialisation kernels (Algorithm 1, initialisation) on the allocated state.
+static lbrmt_status run_init(lbrmt_sim *s) {
     const int S = (int)s->solids.size();
-    s->sp.nsolids = S;
     DevState &d = s->d;
-    long long total = 0;
     int tmax = 8;
-    for (auto &h : s->solids) {
-        h.off = total;
-        total += 2ll * h.T * h.T;
-        tmax = std::max(tmax, h.T);
-    }
-    const size_t rs = s->eng->real_size;
-    bool ok = true;
-    for (int k = 0; k < 2; k++) {
-        ok = ok && (d.xi[k] = dalloc(s, (size_t)total * rs));
-        ok = ok && (d.frame[k] = (Frame *)dalloc(s, (size_t)S * sizeof(Frame)));
-    }
-    ok = ok && (d.solids = (SolidDesc *)dalloc(s, (size_t)S * sizeof(SolidDesc)));
-    ok = ok && (d.stats_step = (double *)dalloc(s, (size_t)S * 64));
-    if (S > 1) {
-        double *sc = (double *)dalloc(s, (size_t)S * 64);
-        ok = ok && sc;
-        s->scratch = sc;
-    }
-    if (!ok) return fail(s, LBRMT_ERR_CUDA, "out of device memory for the solid tiles");
+    for (auto &h : s->solids) tmax = std::max(tmax, h.T);
     std::vector<SolidDesc> sd(S);
     std::vector<Frame> org(S);
     for (int k = 0; k < S; k++) {
@@ -249,8 +234,8 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
         sd[k].drho_f = (float)sd[k].drho; sd[k].accel_f = (float)sd[k].accel;
         sd[k].T = h.T; sd[k].off = h.off;
     }
-    cudaError_t e = cudaSuccess;
-    if (S > 0) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess && S > 0) {
         e = cudaMemcpy(d.solids, sd.data(), S * sizeof(SolidDesc), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d.frame[0], org.data(), S * sizeof(Frame), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d.frame[1], org.data(), S * sizeof(Frame), cudaMemcpyHostToDevice);
@@ -259,11 +244,19 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     if (e != cudaSuccess) return cuda_fail(s, e, "upload solids");
     e = s->eng->configure(s->sp, tmax, &s->li);
     if (e != cudaSuccess) return cuda_fail(s, e, "configure kernels");
+    // both registries start empty; the initialisation registers into registry 1
+    // (step 0 reads its Delta rho as the rest base of f^0 and clears it) and
+    // step 0 registers into registry 0
+    const size_t ntiles = (size_t)s->sp.ntx * s->sp.nty;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        e = cudaMemsetAsync(d.reg_count[k], 0, ntiles * 4, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[k], 0, 16, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.carry, 0, 2 * (size_t)s->sp.P * s->eng->store_size, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "clear registry");
     e = s->eng->init(s->sp, d, s->li, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernels");
-    // registry 1 holds the initial registration (step 0 reads its Delta rho as the
-    // rest base of f^0 and clears it); registry 0 receives step 0's registration
-    const size_t ntiles = (size_t)s->sp.ntx * s->sp.nty;
     e = cudaMemsetAsync(d.reg_count[0], 0, ntiles * 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[0], 0, 16, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "clear registry");
@@ -272,8 +265,76 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     return check_flags(s);
 }
 
+extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (s->inited) return LBRMT_OK;
+    const int S = (int)s->solids.size();
+    s->sp.nsolids = S;
+    DevState &d = s->d;
+    long long total = 0;
+    for (auto &h : s->solids) {
+        h.off = total;
+        total += 2ll * h.T * h.T;
+    }
+    s->xi_total = total;
+    const size_t rs = s->eng->real_size;
+    bool ok = true;
+    for (int k = 0; k < 2; k++) {
+        ok = ok && (d.xi[k] = dalloc(s, (size_t)total * rs));
+        ok = ok && (d.frame[k] = (Frame *)dalloc(s, (size_t)S * sizeof(Frame)));
+    }
+    ok = ok && (d.solids = (SolidDesc *)dalloc(s, (size_t)S * sizeof(SolidDesc)));
+    ok = ok && (d.stats_step = (double *)dalloc(s, (size_t)S * 64));
+    if (S > 1) {
+        double *sc = (double *)dalloc(s, (size_t)S * 64);
+        ok = ok && sc;
+        s->scratch = sc;
+    }
+    if (!ok) return fail(s, LBRMT_ERR_CUDA, "out of device memory for the solid tiles");
+    return run_init(s);
+}
+
+extern "C" lbrmt_status lbrmt_reset(lbrmt_sim *s) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
+    if (!s->inited) return lbrmt_init(s);
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return run_init(s);
+}
+
+extern "C" lbrmt_status lbrmt_set_solid_params(lbrmt_sim *s, int solid_id, double rho_s, double G) {
+    if (!s || solid_id < 0 || solid_id >= (int)s->solids.size()) return LBRMT_ERR_ARG;
+    if (!(rho_s > 0) || !(G >= 0)) return fail(s, LBRMT_ERR_ARG, "bad solid parameters");
+    s->solids[solid_id].rho_s = rho_s;
+    s->solids[solid_id].G = G;
+    if (!s->inited) return LBRMT_OK;
+    return lbrmt_reset(s);
+}
+
+namespace lbrmt {
+template <class R>
+__global__ void body_field_kernel(const double *src, R *dst, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = R(src[k]);
+}
+}  // namespace lbrmt
+
+extern "C" lbrmt_status lbrmt_set_body_force_field(lbrmt_sim *s, int sim_index, const double *dev_xy) {
+    if (!s || !dev_xy || sim_index != 0) return LBRMT_ERR_ARG;
+    if (s->cfg.force_kind != LBRMT_FORCE_FIELD) return fail(s, LBRMT_ERR_STATE, "force_kind is not LBRMT_FORCE_FIELD");
+    const long long n = 2 * s->sp.P;
+    if (s->eng->real_size == 8) body_field_kernel<double><<<256, 256, 0, s->stream>>>(dev_xy, (double *)s->d.bfield, n);
+    else body_field_kernel<float><<<256, 256, 0, s->stream>>>(dev_xy, (float *)s->d.bfield, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "body force field");
+    return LBRMT_OK;
+}
+
 static lbrmt_status direct_step(lbrmt_sim *s) {
-    cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, nullptr);
+    cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, nullptr, nullptr);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->steps++;
     s->last_launches += s->sp.nsolids > 0 ? 3 : 1;
@@ -284,8 +345,8 @@ static lbrmt_status build_graph(lbrmt_sim *s) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
-    cudaError_t e0 = s->eng->step(s->sp, s->d, s->li, 0, s->stream, nullptr);
-    cudaError_t e1 = s->eng->step(s->sp, s->d, s->li, 1, s->stream, nullptr);
+    cudaError_t e0 = s->eng->step(s->sp, s->d, s->li, 0, s->stream, nullptr, nullptr);
+    cudaError_t e1 = s->eng->step(s->sp, s->d, s->li, 1, s->stream, nullptr, nullptr);
     e = cudaStreamEndCapture(s->stream, &g);
     if (e0 != cudaSuccess) e = e0;
     if (e1 != cudaSuccess) e = e1;
@@ -351,7 +412,7 @@ extern "C" lbrmt_status lbrmt_step_timed(lbrmt_sim *s, int nsteps, float *ms_out
     s->last_launches = 0;
     lbrmt_status status = LBRMT_OK;
     for (int n = 0; n < nsteps; n++) {
-        cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, &ev[4 * (size_t)n]);
+        cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, &ev[4 * (size_t)n], nullptr);
         if (e != cudaSuccess) { status = cuda_fail(s, e, "timed step"); break; }
         s->steps++;
         s->last_launches += s->sp.nsolids > 0 ? 3 : 1;
@@ -486,6 +547,7 @@ extern "C" void lbrmt_destroy(lbrmt_sim *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->adj) lbrmt_internal_adjoint_free(s);
     dfree_all(s);
     delete s;
 }

@@ -27,8 +27,9 @@ struct BatchLaunch {
 struct EngineOps {
     cudaError_t (*configure)(const SimParams &, int tmax, LaunchInfo *);
     cudaError_t (*init)(const SimParams &, const DevState &, const LaunchInfo &, cudaStream_t);
+    // tape (optional): per-node rho, ux, uy, Fx, Fy of the step (5 planes of reals)
     cudaError_t (*step)(const SimParams &, const DevState &, const LaunchInfo &, int parity, cudaStream_t,
-                        cudaEvent_t *ev);
+                        cudaEvent_t *ev, void *tape);
     cudaError_t (*field)(const SimParams &, const DevState &, int cur, int lastreg, int kind, int solid,
                          double *out, cudaStream_t);
     cudaError_t (*stats)(const SimParams &, const DevState &, int cur, double *out, cudaStream_t);
@@ -67,17 +68,7 @@ struct Engine {
         li->tmax = tmax;
         li->rmt_smem = ((tmax * tmax + 15) & ~15) + 8 * LIST_CAP;
         {
-            float tf[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
-            double td[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
-            for (int i = 0; i <= RMAX_TAB; i++)
-                for (int j = 0; j <= RMAX_TAB; j++) {
-                    const double r2 = (double)(i * i + j * j);
-                    td[i * (RMAX_TAB + 1) + j] = r2 > 0 ? 1.0 / std::sqrt(r2) : 0.0;
-                    tf[i * (RMAX_TAB + 1) + j] = (float)td[i * (RMAX_TAB + 1) + j];
-                }
-            cudaError_t e0 = cudaMemcpyToSymbol(c_rinv_f, tf, sizeof(tf));
-            if (e0 != cudaSuccess) return e0;
-            e0 = cudaMemcpyToSymbol(c_rinv_d, td, sizeof(td));
+            cudaError_t e0 = upload_rinv_tables();
             if (e0 != cudaSuccess) return e0;
         }
         li->force_smem = force_smem_elems(sp.tx, sp.ty) * (int)sizeof(R);
@@ -149,6 +140,8 @@ struct Engine {
         a.f_out = (S *)d.f[q];
         a.carry = (S *)d.carry;
         a.fbody = (const R *)d.fbody;
+        a.bfield = (const R *)d.bfield;
+        a.tape = nullptr;
         a.reg_count = d.reg_count[p];
         a.pool = (const R *)d.pool[p];
         a.clr_count = d.reg_count[q];
@@ -220,7 +213,7 @@ struct Engine {
 
     // ev (optional): four events recorded before K2, before K3, before K1 and after K1.
     static cudaError_t step(const SimParams &sp, const DevState &d, const LaunchInfo &li, int parity,
-                            cudaStream_t st, cudaEvent_t *ev) {
+                            cudaStream_t st, cudaEvent_t *ev, void *tape) {
         const int p = parity, q = 1 - parity;
         if (ev) cudaEventRecord(ev[0], st);
         if (sp.nsolids > 0) rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, p, 0));
@@ -228,7 +221,9 @@ struct Engine {
         if (sp.nsolids > 0) force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, q, p));
         if (ev) cudaEventRecord(ev[2], st);
         dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
-        lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, lb_args(d, p));
+        LbArgs<R, S> la = lb_args(d, p);
+        la.tape = static_cast<R *>(tape);
+        lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, la);
         if (ev) cudaEventRecord(ev[3], st);
         return cudaGetLastError();
     }
@@ -243,6 +238,7 @@ struct Engine {
         }
         const int r = lastreg;
         field_kernel<R, S><<<grid, blk, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry, (const R *)d.fbody,
+                                                 (const R *)d.bfield,
                                                  d.reg_count[r], (const R *)d.pool[r], kind, out);
         return cudaGetLastError();
     }

@@ -101,6 +101,7 @@ struct DevState {
     int *reg_active[2];    // list of tiles with count > 0
     int *reg_nactive[2];
     void *pool[2];         // per tile: Fx_pool, Fy_pool, drho (TILE_N each)
+    void *bfield;          // force_kind 3: body force field, x plane then y plane (nx*ny each)
     void *fbody;           // per row: body-force x component
     double *mass_partials; // per LB block
     double *stats_step;    // S x 8, stats of the state at the start of the last step
@@ -224,7 +225,7 @@ __device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, co
     R jx = (fq[1] - fq[3]) + (fq[5] - fq[6]) + (fq[8] - fq[7]);
     R jy = (fq[2] - fq[4]) + (fq[5] - fq[7]) + (fq[6] - fq[8]);
     rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
-    R inv = R(1) / rho;
+    R inv = rcp_rn<R>(rho);  // as the LB kernel
     u = (jx + ldC<S, R>(carry + c)) * inv;
     v = (jy + ldC<S, R>(carry + sp.P + c)) * inv;
 }
@@ -282,6 +283,21 @@ template <> __device__ __forceinline__ double pow2neg<double>(int k) {
 constexpr int RMAX_TAB = 20;
 __constant__ float c_rinv_f[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
 __constant__ double c_rinv_d[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+// The tables live in each translation unit that includes this header: every
+// unit that launches a kernel reading them fills its own copy with this.
+static inline cudaError_t upload_rinv_tables() {
+    float tf[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+    double td[(RMAX_TAB + 1) * (RMAX_TAB + 1)];
+    for (int i = 0; i <= RMAX_TAB; i++)
+        for (int j = 0; j <= RMAX_TAB; j++) {
+            const double r2 = (double)(i * i + j * j);
+            td[i * (RMAX_TAB + 1) + j] = r2 > 0 ? 1.0 / sqrt(r2) : 0.0;
+            tf[i * (RMAX_TAB + 1) + j] = (float)td[i * (RMAX_TAB + 1) + j];
+        }
+    cudaError_t e = cudaMemcpyToSymbol(c_rinv_f, tf, sizeof(tf));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_rinv_d, td, sizeof(td));
+}
 template <class R> __device__ __forceinline__ R rinv_tab(int dx, int dy);
 template <> __device__ __forceinline__ float rinv_tab<float>(int dx, int dy) { return c_rinv_f[abs(dx) * (RMAX_TAB + 1) + abs(dy)]; }
 template <> __device__ __forceinline__ double rinv_tab<double>(int dx, int dy) { return c_rinv_d[abs(dx) * (RMAX_TAB + 1) + abs(dy)]; }
@@ -987,6 +1003,8 @@ struct LbArgs {
     S *f_out;
     S *carry;
     const R *fbody;            // per row x body force
+    const R *bfield;           // force_kind 3: per-node body force (x plane, y plane)
+    R *tape;                   // optional: rho, ux, uy, Fx, Fy of every node (5 planes)
     const int *reg_count;      // registry of this step
     const R *pool;
     int *clr_count;            // registry of the previous step: read, then cleared for the next step
@@ -1020,7 +1038,14 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
         const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
         const R inv = rcp_rn<R>(rho);
         const R ux = (jx + ldC<S, R>(a.carry + c)) * inv, uy = (jy + ldC<S, R>(a.carry + P + c)) * inv;
-        R Fx = a.fbody[j], Fy = pick<R>(sp.fy, sp.fy_f), drt = R(0);
+        R Fx, Fy, drt = R(0);
+        if (sp.force_kind == 3) {
+            Fx = a.bfield[c];
+            Fy = a.bfield[P + c];
+        } else {
+            Fx = a.fbody[j];
+            Fy = pick<R>(sp.fy, sp.fy_f);
+        }
         if (a.reg_count[tile] > 0) {
             const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
             Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
@@ -1054,6 +1079,10 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
             const R odd = R(3) * rw * (omega * cu + kf * cF);
             fh[q] = om1 * f[q] + even + odd;
             fh[qo] = om1 * f[qo] + even - odd;
+        }
+        if (a.tape) {
+            a.tape[c] = rho; a.tape[P + c] = ux; a.tape[2 * P + c] = uy;
+            a.tape[3 * P + c] = Fx; a.tape[4 * P + c] = Fy;
         }
         stC<S, R>(a.carry + c, R(0.5) * rho * Fx);
         stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy);
@@ -1116,7 +1145,7 @@ __global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
 
 // Fields to a double grid.  kind: 0 rho, 1 ux, 2 uy, 3 Fx, 4 Fy, 5 drho, 20+q f_q.
 template <class R, class S>
-__global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *fbody, const int *reg_count,
+__global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *fbody, const R *bfield, const int *reg_count,
                              const R *pool, int kind, double *out) {
     const int i = blockIdx.x * sp.tx + (threadIdx.x & (sp.tx - 1)), j = blockIdx.y * sp.ty + (threadIdx.x >> sp.lx);
     if (i >= sp.nx || j >= sp.ny) return;
@@ -1135,8 +1164,10 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
     } else if (kind <= 5) {
         R p = 0;
         if (reg_count[tile] > 0) p = pool[(long long)tile * POOL_STRIDE + (kind - 3) * TILE_N + threadIdx.x];
-        if (kind == 3) v = (double)(fbody[j] + p);
-        else if (kind == 4) v = (double)(pick<R>(sp.fy, sp.fy_f) + p);
+        const R bx = sp.force_kind == 3 ? bfield[c] : fbody[j];
+        const R by = sp.force_kind == 3 ? bfield[sp.P + c] : pick<R>(sp.fy, sp.fy_f);
+        if (kind == 3) v = (double)(bx + p);
+        else if (kind == 4) v = (double)(by + p);
         else v = (double)p;
     } else {
         const int q = kind - 20;

@@ -13,6 +13,8 @@ struct SolidHost {
     long long off;
 };
 
+struct AdjointStore;
+
 struct lbrmt_sim {
     lbrmt_config cfg;
     int device = 0;
@@ -22,6 +24,7 @@ struct lbrmt_sim {
     lbrmt::LaunchInfo li;
     lbrmt::DevState d;
     std::vector<SolidHost> solids;
+    long long xi_total = 0;         // reals in one xi buffer (all solid tiles)
     bool inited = false;
     long long steps = 0;
     bool use_graphs = true;
@@ -32,7 +35,13 @@ struct lbrmt_sim {
     double *scratch = nullptr;      // device: S*8 stats or 1 mass value
     double *staging = nullptr;      // device: 9*P doubles for set_populations
     std::string err;
+    AdjointStore *adj = nullptr;    // checkpoints and buffers of the adjoint (lbrmt_adjoint.cu)
 };
 
 // Wait for the simulation's stream and map its device error flags to a status.
 lbrmt_status lbrmt_internal_check_flags(lbrmt_sim *s);
+
+// Device allocation owned by the simulation (freed with it), and error recording.
+void *lbrmt_internal_alloc(lbrmt_sim *s, size_t bytes);
+lbrmt_status lbrmt_internal_fail(lbrmt_sim *s, lbrmt_status st, const std::string &msg);
+void lbrmt_internal_adjoint_free(lbrmt_sim *s);

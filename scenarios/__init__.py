@@ -143,6 +143,31 @@ def adjoint_ldc_256():
     return sc
 
 
+def adjoint_ldc(n=256, r=40.0, G=0.01, rho_ratio=1.0, lid_u=0.05, body=None):
+    """Lid-driven cavity of side n (tau 0.8) with one disk of radius r at
+    (0.6n, 0.5n) and a per-node body force field (force_kind 3): ``body`` of
+    shape (2, n, n), zero by default."""
+    sc = _base(n, n, 1, 1, 0.8, lid_u=lid_u, force_kind=3, name=f"adjoint_ldc_{n}")
+    sc["solids"].append({"x": 0.6 * n, "y": 0.5 * n, "r": float(r), "rho_s": float(rho_ratio) * sc["rho_f"],
+                         "G": float(G)})
+    sc["body_field"] = np.zeros((2, n, n)) if body is None else np.asarray(body, dtype=np.float64).reshape(2, n, n)
+    return sc
+
+
+def smooth_body_field(seed, n, amp=1e-5, modes=3):
+    """Seeded smooth body force field (2, n, n): a few low Fourier modes per
+    component with amplitudes up to ``amp``."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:n, 0:n] / float(n)
+    out = np.zeros((2, n, n))
+    for c in range(2):
+        for _ in range(modes):
+            kx, ky = rng.integers(1, 4, size=2)
+            ph = rng.uniform(0, 2 * np.pi)
+            out[c] += rng.uniform(-amp, amp) * np.sin(2 * np.pi * (kx * x + ky * y) + ph)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Small seeded cases for parity tests (sizes the oracle finishes in seconds)
 # ---------------------------------------------------------------------------

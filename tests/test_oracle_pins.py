@@ -428,3 +428,47 @@ def test_band_has_eleven_layers_and_pads():
     o.step(3)
     lab = o.field("label")
     assert set(np.unique(lab[lab >= 0]).astype(int)) == set(range(12))
+
+
+def test_body_force_field_uniform_equals_constant_force():
+    # A per-node body force field (force_kind 3) that is uniform must give
+    # exactly the pinned constant-force path (force_kind 1): the field only
+    # replaces where f of Eq. 2_4_F_divs is read from.
+    sc1 = scenarios.mixing_small(seed=3)
+    sc1["force_kind"], sc1["force_a"] = 1, [2e-5, -1e-5]
+    sc3 = dict(sc1)
+    sc3["force_kind"] = 3
+    n = sc1["nx"] * sc1["ny"]
+    sc3["body_field"] = np.concatenate([np.full(n, 2e-5), np.full(n, -1e-5)])
+    a, b = oracle.Oracle(sc1), oracle.Oracle(sc3)
+    a.step(15)
+    b.step(15)
+    for name in ("rho", "ux", "uy", "Fx", "Fy"):
+        assert np.array_equal(a.field(name), b.field(name)), name
+    assert np.array_equal(a.field("xi_x", 1), b.field("xi_x", 1), equal_nan=True)
+
+
+def test_body_force_field_momentum_gain():
+    # Momentum gain per step with a non-uniform field (periodic box): the
+    # identity of test_momentum_gain_per_step with F including the field.
+    sc = scenarios.fluid_only(48, 40, 0, 0, 0.7)
+    sc["force_kind"] = 3
+    sc["body_field"] = scenarios.smooth_body_field(5, 48, amp=3e-5)[:, :40, :]
+    tau = sc["tau"]
+    o = oracle.Oracle(sc)
+    o.step(2)
+    rho_prev = o.populations().sum(0)
+    o.step(1)
+    prev = (rho_prev * o.field("Fx"), rho_prev * o.field("Fy"))
+    f = o.populations()
+    rho = f.sum(0)
+    px, py = (CX[:, None, None] * f).sum(), (CY[:, None, None] * f).sum()
+    o.step(1)
+    f1 = o.populations()
+    # no solid: F is the field itself
+    assert np.array_equal(o.field("Fx"), sc["body_field"][0])
+    cur = (rho * o.field("Fx"), rho * o.field("Fy"))
+    gx = (prev[0] / (2 * tau) + (1 - 1 / (2 * tau)) * cur[0]).sum()
+    gy = (prev[1] / (2 * tau) + (1 - 1 / (2 * tau)) * cur[1]).sum()
+    assert abs((CX[:, None, None] * f1).sum() - px - gx) < 1e-11
+    assert abs((CY[:, None, None] * f1).sum() - py - gy) < 1e-11
