@@ -177,6 +177,42 @@ def bench_batch(args, dev):
     return out
 
 
+def bench_adjoint(args, dev):
+    """Adjoint cost on the 256^2 lid-driven cavity with one disk of radius 40
+    (tau 0.8, lid 0.05, G 0.01, rho_s / rho_f 1, zero body force field), FP32:
+    a checkpointed forward run of T steps (a copy of the state every 100
+    steps), then the reverse sweep for L = |c(T) - c(0) - (8, -8)|^2, which
+    returns dL/dG, dL/d(rho_s/rho_f) and dL/df(x).  Wall-clock seconds of both
+    calls (each synchronous) and their ratio."""
+    import torch
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.adjoint_ldc(256, r=40.0, G=0.01, rho_ratio=1.0)
+    stream = torch.cuda.Stream(dev)
+    sim = pkg.Simulation(sc, precision="fp32", device=str(dev), stream=stream)
+    c0 = sim.forward_checkpointed(1, 1)
+    target = c0 + np.array([[8.0, -8.0]])
+    sim.forward_checkpointed(args.adjoint_steps, 100)  # warm-up (allocations, graph)
+    sim.backward(2 * (sim.solid_stats()[:, 1:3] - target), body=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    cT = sim.forward_checkpointed(args.adjoint_steps, 100)
+    t1 = time.perf_counter()
+    dG, dr, db = sim.backward(2 * (cT - target), body=True)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    n = sc["nx"] * sc["ny"]
+    out = {"workload": "256x256 lid-driven cavity, one disk r=40 at (0.6L, 0.5L), G 0.01, rho_s/rho_f 1, "
+                       "FP32, L = |c(T) - c(0) - (8,-8)|^2, checkpoint every 100 steps",
+           "steps": args.adjoint_steps, "forward_s": t1 - t0, "backward_s": t2 - t1,
+           "backward_over_forward": (t2 - t1) / (t1 - t0),
+           "forward_mlups": n * args.adjoint_steps / (t1 - t0) / 1e6,
+           "loss": float(((cT - target) ** 2).sum()), "dL_dG": float(dG[0]), "dL_dratio": float(dr[0]),
+           "dL_dbody_max": float(db.abs().max().item()),
+           "note": "backward = recompute of every segment from its checkpoint + reverse kernels"}
+    sim.close()
+    return out
+
+
 def bench_lbrmt(args):
     import torch
     import paper_2402_12696_gb300 as pkg
@@ -263,6 +299,7 @@ def bench_lbrmt(args):
         sim2.close()
 
     batched = bench_batch(args, dev) if args.batch_steps > 0 and rank == 0 else None
+    adjoint = bench_adjoint(args, dev) if args.adjoint_steps > 0 and rank == 0 else None
 
     if rank != 0:
         if ws > 1:
@@ -322,6 +359,7 @@ def bench_lbrmt(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "batched": batched,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -344,6 +382,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="timed steps of the 96-cavity batch (0: skip)")
     ap.add_argument("--autotune-steps", type=int, default=5)
+    ap.add_argument("--adjoint-steps", type=int, default=3000,
+                    help="steps of the adjoint-cost measurement (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
