@@ -234,9 +234,14 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         sd[k].drho_f = (float)sd[k].drho; sd[k].accel_f = (float)sd[k].accel;
         sd[k].T = h.T; sd[k].off = h.off;
     }
+    // solid kernel launch order: largest tiles first, so the last CTAs to start are short
+    std::vector<int> order(S);
+    for (int k = 0; k < S; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s->solids[a].T > s->solids[b].T; });
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess && S > 0) {
-        e = cudaMemcpy(d.solids, sd.data(), S * sizeof(SolidDesc), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(d.order, order.data(), S * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d.solids, sd.data(), S * sizeof(SolidDesc), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d.frame[0], org.data(), S * sizeof(Frame), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d.frame[1], org.data(), S * sizeof(Frame), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemsetAsync(d.stats_step, 0, (size_t)S * 64, s->stream);
@@ -284,6 +289,7 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
         ok = ok && (d.frame[k] = (Frame *)dalloc(s, (size_t)S * sizeof(Frame)));
     }
     ok = ok && (d.solids = (SolidDesc *)dalloc(s, (size_t)S * sizeof(SolidDesc)));
+    ok = ok && (d.order = (int *)dalloc(s, (size_t)std::max(S, 1) * sizeof(int)));
     ok = ok && (d.stats_step = (double *)dalloc(s, (size_t)S * 64));
     if (S > 1) {
         double *sc = (double *)dalloc(s, (size_t)S * 64);

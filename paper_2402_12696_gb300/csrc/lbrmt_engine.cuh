@@ -114,6 +114,7 @@ struct Engine {
         a.reg_active = d.reg_active[r];
         a.reg_nactive = d.reg_nactive[r];
         a.solids = d.solids;
+        a.order = d.order;
         a.err = d.err;
         a.init = init;
         return a;

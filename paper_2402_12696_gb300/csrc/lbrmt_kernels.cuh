@@ -102,6 +102,7 @@ struct DevState {
     int *reg_nactive[2];
     void *pool[2];         // per tile: Fx_pool, Fy_pool, drho (TILE_N each)
     void *bfield;          // force_kind 3: body force field, x plane then y plane (nx*ny each)
+    int *order;            // solids by decreasing tile side (launch order of the solid kernel)
     void *fbody;           // per row: body-force x component
     double *mass_partials; // per LB block
     double *stats_step;    // S x 8, stats of the state at the start of the last step
@@ -268,6 +269,7 @@ struct RmtArgs {
     int *reg_count, *reg_solids, *reg_active, *reg_nactive;
     double *stats;       // S x 8 (state at time n), may be null at init
     const SolidDesc *solids;
+    const int *order;    // CTA -> solid (largest tiles first), or null
     unsigned *err;
     int init;
 };
@@ -337,24 +339,63 @@ __device__ __forceinline__ void lsq_cell(Lsq<R> &A, const signed char *lab, cons
     A.by0 += wx * Yv; A.by1 += wy * Yv; A.by2 += wt * Yv;
 }
 
+// The 5x5 window of a target away from the tile edge, without branches on
+// the node's validity (weights are zero for the nodes that do not count).
+template <class R, bool USE_N>
+__device__ __forceinline__ void lsq_window5(Lsq<R> &A, const signed char *lab, const R *X, const R *Y, int t, int T,
+                                            int l, R nhx, R nhy) {
+#pragma unroll
+    for (int dy = -2; dy <= 2; dy++)
+#pragma unroll
+        for (int dx = -2; dx <= 2; dx++) {
+            if (dx == 0 && dy == 0) continue;  // the target itself (layer l) never counts
+            const int k = t + dy * T + dx;
+            const int L = lab[k];
+            const bool valid = (unsigned)L < (unsigned)l;  // 0 <= L < l
+            R wt = valid ? pow2neg<R>(abs(dx) + abs(dy)) : R(0);
+            if (USE_N) {
+                const R dn = (R(-dx) * nhx + R(-dy) * nhy) * rinv_tab<R>(dx, dy);
+                wt = dn > R(COS_TIE) ? dn * wt : R(0);
+            }
+            A.nvalid += valid ? 1 : 0;
+            const bool pos = wt > R(0);
+            A.n += pos ? 1 : 0;
+            A.sx += pos ? dx : 0; A.sy += pos ? dy : 0;
+            A.sxx += pos ? dx * dx : 0; A.syy += pos ? dy * dy : 0; A.sxy += pos ? dx * dy : 0;
+            R Xv = R(0), Yv = R(0);
+            if (pos) { Xv = X[k] - A.xref; Yv = Y[k] - A.yref; }
+            const R wx = wt * R(dx), wy = wt * R(dy);
+            A.a += wx * R(dx); A.b += wx * R(dy); A.c += wx; A.d += wy * R(dy); A.e += wy; A.fw += wt;
+            A.bx0 += wx * Xv; A.bx1 += wy * Xv; A.bx2 += wt * Xv;
+            A.by0 += wx * Yv; A.by1 += wy * Yv; A.by2 += wt * Yv;
+        }
+}
+
 // Weighted least-squares fit of one target (Sec. 3.2, steps (i)-(iii)).  The
 // weights do not depend on the window size, so growing r from r-1 only adds
-// the ring |dx| = r or |dy| = r to the sums of the smaller window.
+// the ring |dx| = r or |dy| = r to the sums of the smaller window.  The fit is
+// of differences from the value at the target's 4-neighbour in layer l - 1
+// (a valid node by construction), which keeps the sums small.
 template <class R>
 __device__ void extrapolate_target(const SimParams &sp, const signed char *lab, R *X, R *Y, int T, int tx, int ty,
                                    int l, bool use_n, R nhx, R nhy, unsigned *err) {
     const int t = ty * T + tx;
     Lsq<R> A;
     A.nvalid = A.n = A.sx = A.sy = A.sxx = A.syy = A.sxy = 0;
-    A.haveref = false;
     A.a = A.b = A.c = A.d = A.e = A.fw = R(0);
     A.bx0 = A.bx1 = A.bx2 = A.by0 = A.by1 = A.by2 = R(0);
-    A.xref = A.yref = R(0);
+    {
+        int kref = t + T;
+        if (tx > 0 && lab[t - 1] == l - 1) kref = t - 1;
+        else if (tx < T - 1 && lab[t + 1] == l - 1) kref = t + 1;
+        else if (ty > 0 && lab[t - T] == l - 1) kref = t - T;
+        A.xref = X[kref];
+        A.yref = Y[kref];
+        A.haveref = true;
+    }
     if (tx >= 2 && ty >= 2 && tx < T - 2 && ty < T - 2) {
-#pragma unroll
-        for (int dy = -2; dy <= 2; dy++)
-#pragma unroll
-            for (int dx = -2; dx <= 2; dx++) lsq_cell<R>(A, lab, X, Y, t + dy * T + dx, l, dx, dy, use_n, nhx, nhy);
+        if (use_n) lsq_window5<R, true>(A, lab, X, Y, t, T, l, nhx, nhy);
+        else lsq_window5<R, false>(A, lab, X, Y, t, T, l, nhx, nhy);
     } else {
         for (int dy = -2; dy <= 2; dy++)
             for (int dx = -2; dx <= 2; dx++)
@@ -493,8 +534,8 @@ struct BoxWalk {
 template <class R, class S>
 __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int s) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int nlist;
-    __shared__ int bb[12];  // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
+    __shared__ int nlist[2];  // list lengths of alternate layers
+    __shared__ int bb[12];    // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
     __shared__ double red[32 * 6];
     __syncthreads();  // the shared state of a previous solid is no longer read
     const SolidDesc sd = a.solids[s];
@@ -516,6 +557,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     const R *Yi = a.init ? nullptr : Xi + TT;
     const R eps = pick<R>(sp.eps, sp.eps_f);
     if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
+    if (threadIdx.x < 2) nlist[threadIdx.x] = 0;
     for (int k = threadIdx.x; k < (TT + 15) >> 4; k += blockDim.x)
         reinterpret_cast<int4 *>(lab)[k] = make_int4(-1, -1, -1, -1);
     R stl[6] = {0, 0, 0, 0, 0, 0};  // sum lambda, lambda lx, lambda ly, lambda rho, lambda rho u, lambda rho v
@@ -598,8 +640,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
         int *cur = lists + (l & 1) * LIST_CAP;
         const int *prv = lists + ((l + 1) & 1) * LIST_CAP;
         const int nprev = min(nl_prev, LIST_CAP);
-        __syncthreads();
-        if (threadIdx.x == 0) nlist = 0;
+        int *cnt = &nlist[l & 1];  // zero: reset after the layer two back was read
         __syncthreads();
         if (l == 1 || !prev_full) {
             const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
@@ -617,7 +658,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                 if (m) {
                     const int leader = __ffs(m) - 1;
                     int base = 0;
-                    if (lane == leader) base = atomicAdd(&nlist, __popc(m));
+                    if (lane == leader) base = atomicAdd(cnt, __popc(m));
                     base = __shfl_sync(0xffffffffu, base, leader);
                     if (hit) {
                         lab[t] = (signed char)l;
@@ -637,13 +678,14 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                 if (lx < 0 || ly < 0 || lx >= T || ly >= T) continue;
                 const int q = ly * T + lx;
                 if (lab[q] == -1 && allowed_cell(sp, oo.x + lx, oo.y + ly) && claim_label(lab, q, l)) {
-                    const int idx = atomicAdd(&nlist, 1);
+                    const int idx = atomicAdd(cnt, 1);
                     if (idx < LIST_CAP) cur[idx] = lx | (ly << 16);
                 }
             }
         }
         __syncthreads();
-        const int nl = nlist;
+        const int nl = *cnt;
+        if (threadIdx.x == 0) nlist[(l + 1) & 1] = 0;  // every thread read it before this layer's first barrier
         nl_prev = nl;
         prev_full = nl <= LIST_CAP;
         const int nitems = prev_full ? nl : TT;
@@ -768,7 +810,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
 
 template <class R, class S>
 __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
-    rmt_solid<R, S>(sp, a, blockIdx.x);
+    rmt_solid<R, S>(sp, a, a.order ? a.order[blockIdx.x] : (int)blockIdx.x);
 }
 
 // ===========================================================================
