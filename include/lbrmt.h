@@ -200,6 +200,13 @@ lbrmt_status lbrmt_step_timed(lbrmt_sim *sim, int nsteps, float *ms_out);
 /* Use (1) or bypass (0) CUDA graphs for lbrmt_step; default 1. */
 lbrmt_status lbrmt_set_use_graphs(lbrmt_sim *sim, int enable);
 
+/* Load the populations of the lattice Boltzmann kernel with tensor-memory
+ * copies into shared memory (1, default) or directly (0).  The results are the
+ * same bit for bit.  The tensor path needs nx times the storage size to be a
+ * multiple of 16 bytes; lbrmt_uses_tma tells whether it is in use. */
+lbrmt_status lbrmt_set_use_tma(lbrmt_sim *sim, int enable);
+int lbrmt_uses_tma(const lbrmt_sim *sim);
+
 /* Text of the last error on this handle ("" if none). */
 const char *lbrmt_last_error(const lbrmt_sim *sim);
 

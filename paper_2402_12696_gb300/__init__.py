@@ -30,7 +30,8 @@ FIELDS = {"rho": 0, "ux": 1, "uy": 2, "Fx": 3, "Fy": 4, "drho": 5,
 EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_init", "lbrmt_step",
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
-           "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs",
+           "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
+           "lbrmt_uses_tma",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
            "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward",
            "lbrmt_create_batch", "lbrmt_batch_add_solid", "lbrmt_batch_init", "lbrmt_batch_step",
@@ -91,6 +92,8 @@ def load():
     L.lbrmt_last_launch_count.argtypes = [p]
     L.lbrmt_last_launch_count.restype = ll
     L.lbrmt_set_use_graphs.argtypes = [p, i]
+    L.lbrmt_set_use_tma.argtypes = [p, i]
+    L.lbrmt_uses_tma.argtypes = [p]
     L.lbrmt_last_error.argtypes = [p]
     L.lbrmt_last_error.restype = C.c_char_p
     L.lbrmt_destroy.argtypes = [p]
@@ -329,7 +332,7 @@ class Simulation:
     """One LBRMT simulation on a CUDA device, built from a scenario dict."""
 
     def __init__(self, sc, precision="fp32", device="cuda:0", stream=None, use_graphs=True,
-                 max_solids_per_tile=8, rmax=11, tile_x=32):
+                 max_solids_per_tile=8, rmax=11, tile_x=32, use_tma=True):
         import torch
         self.torch = torch
         self.sc = sc
@@ -345,6 +348,7 @@ class Simulation:
         with torch.cuda.device(self.device):
             self.h = lbrmt_create(cfg, self.stream.cuda_stream)
             load().lbrmt_set_use_graphs(self.h, int(bool(use_graphs)))
+            load().lbrmt_set_use_tma(self.h, int(bool(use_tma)))
             for s in sc["solids"]:
                 lbrmt_add_solid(self.h, 0, s["x"], s["y"], s["r"], s["rho_s"], s["G"])
             if sc["force_kind"] == 3:
@@ -390,6 +394,10 @@ class Simulation:
     @property
     def steps_done(self):
         return load().lbrmt_steps_done(self.h)
+
+    @property
+    def uses_tma(self):
+        return bool(load().lbrmt_uses_tma(self.h))
 
     @property
     def last_launch_count(self):

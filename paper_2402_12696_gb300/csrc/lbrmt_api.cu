@@ -201,6 +201,8 @@ static lbrmt_status check_flags(lbrmt_sim *s) {
     if (f & ERR_STENCIL) return fail(s, LBRMT_ERR_EXTRAP, "advection stencil left the band");
     if (f & ERR_SINGULAR) return fail(s, LBRMT_ERR_NUMERIC, "singular reference-map Jacobian");
     if (f & ERR_OVERFLOW16) return fail(s, LBRMT_ERR_OVERFLOW, "a population exceeded the 16-bit storage range");
+    if (f & ERR_TIMEOUT) return fail(s, LBRMT_ERR_TIMEOUT, "a bounded wait on a tensor copy gave up");
+    if (f & ERR_ALIGN) return fail(s, LBRMT_ERR_CUDA, "misaligned shared-memory stage (tensor copies skipped)");
     return fail(s, LBRMT_ERR_NUMERIC, "device error flag");
 }
 
@@ -247,7 +249,9 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         if (e == cudaSuccess) e = cudaMemsetAsync(d.stats_step, 0, (size_t)S * 64, s->stream);
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "upload solids");
-    e = s->eng->configure(s->sp, tmax, &s->li);
+    const bool use_tma = s->li.use_tma;
+    e = s->eng->configure(s->sp, d, tmax, &s->li);
+    s->li.use_tma = use_tma;
     if (e != cudaSuccess) return cuda_fail(s, e, "configure kernels");
     // both registries start empty; the initialisation registers into registry 1
     // (step 0 reads its Delta rho as the rest base of f^0 and clears it) and
@@ -545,6 +549,19 @@ extern "C" lbrmt_status lbrmt_set_use_graphs(lbrmt_sim *s, int enable) {
     s->use_graphs = enable != 0;
     return LBRMT_OK;
 }
+
+extern "C" lbrmt_status lbrmt_set_use_tma(lbrmt_sim *s, int enable) {
+    if (!s) return LBRMT_ERR_ARG;
+    s->li.use_tma = enable != 0;
+    if (s->gexec) {
+        cudaStreamSynchronize(s->stream);
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return LBRMT_OK;
+}
+
+extern "C" int lbrmt_uses_tma(const lbrmt_sim *s) { return s && s->inited && s->li.tma && s->li.use_tma ? 1 : 0; }
 
 extern "C" const char *lbrmt_last_error(const lbrmt_sim *s) { return s ? s->err.c_str() : "null handle"; }
 

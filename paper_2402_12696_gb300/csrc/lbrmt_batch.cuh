@@ -22,6 +22,9 @@ struct BatchSimDesc {
 };
 
 // K2 over every solid of every simulation: item = (simulation, solid).
+// Same launch bounds as the single-simulation kernel: the same register budget
+// gives the same instruction selection, so batch members stay bit-identical to
+// single runs.
 template <class R, class S>
 __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2)
     rmt_batch_kernel(const BatchSimDesc<R, S> *sims, const int2 *items, int nitems, int parity) {
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(TILE_N) lb_batch_kernel(const BatchSimDesc<R, 
             __syncthreads();
             cur = w.x;
         }
-        lb_tile<R, S>(sp, la, w.y & 0xffff, w.y >> 16);
+        lb_tile<R, S, false>(sp, la, w.y & 0xffff, w.y >> 16, nullptr);
     }
 }
 

@@ -15,7 +15,34 @@ struct LaunchInfo {
     int force_blocks;    // persistent grid of K3
     int rmt_smem;        // dynamic shared memory of K2
     int force_smem;      // dynamic shared memory of K3
+    bool tma = false;    // tensor maps of the populations and half-force are valid
+    bool use_tma = true; // K1 with TMA staging (else the direct-load kernel)
+    int lb_blocks = 0, lb_smem = 0;
+    CUtensorMap tm_f[2], tm_c;
 };
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+template <class S> inline CUtensorMapDataType tma_dtype();
+template <> inline CUtensorMapDataType tma_dtype<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> inline CUtensorMapDataType tma_dtype<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+template <> inline CUtensorMapDataType tma_dtype<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+template <> inline CUtensorMapDataType tma_dtype<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
 
 // Launch shape of the batched kernels.
 struct BatchLaunch {
@@ -25,7 +52,7 @@ struct BatchLaunch {
 };
 
 struct EngineOps {
-    cudaError_t (*configure)(const SimParams &, int tmax, LaunchInfo *);
+    cudaError_t (*configure)(const SimParams &, const DevState &, int tmax, LaunchInfo *);
     cudaError_t (*init)(const SimParams &, const DevState &, const LaunchInfo &, cudaStream_t);
     // tape (optional): per-node rho, ux, uy, Fx, Fy of the step (5 planes of reals)
     cudaError_t (*step)(const SimParams &, const DevState &, const LaunchInfo &, int parity, cudaStream_t,
@@ -64,7 +91,40 @@ __global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, 
 
 template <class R, class S>
 struct Engine {
-    static cudaError_t configure(const SimParams &sp, int tmax, LaunchInfo *li) {
+    // Tensor maps over the population buffers (nx x ny x 9) and the half-force
+    // (nx x ny x 2) with one registry tile per box; needs rows of 16-byte multiples.
+    static void configure_tma(const SimParams &sp, const DevState &d, LaunchInfo *li, int nsm) {
+        li->tma = false;
+        EncodeTiledFn enc = encode_tiled_fn();
+        const size_t ss = sizeof(S);
+        if (!enc || ((size_t)sp.nx * ss) % 16 != 0) return;
+        const cuuint64_t dimf[3] = {(cuuint64_t)sp.nx, (cuuint64_t)sp.ny, 9};
+        const cuuint64_t dimc[3] = {(cuuint64_t)sp.nx, (cuuint64_t)sp.ny, 2};
+        const cuuint64_t str[2] = {(cuuint64_t)sp.nx * ss, (cuuint64_t)sp.P * ss};
+        const cuuint32_t boxf[3] = {(cuuint32_t)sp.tx, (cuuint32_t)sp.ty, 9}, boxc[3] = {(cuuint32_t)sp.tx, (cuuint32_t)sp.ty, 2};
+        const cuuint32_t es[3] = {1, 1, 1};
+        bool ok = true;
+        for (int k = 0; k < 2 && ok; k++)
+            ok = enc(&li->tm_f[k], tma_dtype<S>(), 3, d.f[k], dimf, str, boxf, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+                 CUDA_SUCCESS;
+        ok = ok && enc(&li->tm_c, tma_dtype<S>(), 3, d.carry, dimc, str, boxc, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        if (!ok) return;
+        li->lb_smem = 2 * 11 * TILE_N * (int)ss + 128;  // + alignment of the stages
+        if (cudaFuncSetAttribute(lb_tma_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, li->lb_smem) !=
+            cudaSuccess)
+            return;
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lb_tma_kernel<R, S>, TILE_N, li->lb_smem) != cudaSuccess ||
+            per < 1)
+            return;
+        li->lb_blocks = nsm * per;
+        li->tma = true;
+    }
+
+    static cudaError_t configure(const SimParams &sp, const DevState &d, int tmax, LaunchInfo *li) {
         li->tmax = tmax;
         li->rmt_smem = ((tmax * tmax + 15) & ~15) + 8 * LIST_CAP;
         {
@@ -85,6 +145,7 @@ struct Engine {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_kernel<R>, TILE_N, li->force_smem);
         if (e != cudaSuccess) return e;
         li->force_blocks = nsm * (per > 0 ? per : 1);
+        configure_tma(sp, d, li, nsm);
         return cudaSuccess;
     }
 
@@ -224,7 +285,10 @@ struct Engine {
         dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
         LbArgs<R, S> la = lb_args(d, p);
         la.tape = static_cast<R *>(tape);
-        lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, la);
+        if (li.tma && li.use_tma)
+            lb_tma_kernel<R, S><<<li.lb_blocks, TILE_N, li.lb_smem, st>>>(sp, la, li.tm_f[p], li.tm_c, sp.ntx * sp.nty);
+        else
+            lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, la);
         if (ev) cudaEventRecord(ev[3], st);
         return cudaGetLastError();
     }

@@ -17,6 +17,7 @@
 // in solid-local coordinates xi - X_c.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the tensor maps are encoded through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -44,7 +45,7 @@ constexpr double COS_TIE = 1e-9;
 
 enum ErrBits : unsigned {
     ERR_NAN = 1u, ERR_TILE_OVERFLOW = 2u, ERR_SLOT_OVERFLOW = 4u, ERR_EXTRAP = 8u,
-    ERR_SINGULAR = 16u, ERR_STENCIL = 32u, ERR_OVERFLOW16 = 64u
+    ERR_SINGULAR = 16u, ERR_STENCIL = 32u, ERR_OVERFLOW16 = 64u, ERR_TIMEOUT = 128u, ERR_ALIGN = 256u
 };
 
 // Scalar parameters, passed by value.
@@ -1056,9 +1057,12 @@ struct LbArgs {
     unsigned *err;
 };
 
-// One registry tile (bx, by) of K1, one thread per node.
-template <class R, class S>
-__device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> &a, const int bx, const int by) {
+// One registry tile (bx, by) of K1, one thread per node.  STAGED: the tile's
+// populations and half-force were staged in shared memory (9 + 2 planes of
+// TILE_N values, node lt at offset lt), else they are read from global memory.
+template <class R, class S, bool STAGED>
+__device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> &a, const int bx, const int by,
+                                        const S *stage) {
     const int lt = threadIdx.x;
     const int i = bx * sp.tx + (lt & (sp.tx - 1)), j = by * sp.ty + (lt >> sp.lx);
     const int tile = by * sp.ntx + bx;
@@ -1071,7 +1075,8 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
         const int c = j * nx + i;
         R f[9];
 #pragma unroll
-        for (int q = 0; q < 9; q++) f[q] = ldG<S, R>(a.f_in + q * P + c);
+        for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
+            f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.f_in + q * P + c);
         const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
         const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const R dr = dro + ds;  // rho - rho_f
@@ -1079,7 +1084,9 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
         const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
         const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
         const R inv = rcp_rn<R>(rho);
-        const R ux = (jx + ldC<S, R>(a.carry + c)) * inv, uy = (jy + ldC<S, R>(a.carry + P + c)) * inv;
+        const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt) : ldC<S, R>(a.carry + c);
+        const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt) : ldC<S, R>(a.carry + P + c);
+        const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
         R Fx, Fy, drt = R(0);
         if (sp.force_kind == 3) {
             Fx = a.bfield[c];
@@ -1170,7 +1177,99 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
 
 template <class R, class S>
 __global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
-    lb_tile<R, S>(sp, a, blockIdx.x, blockIdx.y);
+    lb_tile<R, S, false>(sp, a, blockIdx.x, blockIdx.y, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// K1 with TMA staging: persistent CTAs walk the tiles with a grid stride; one
+// thread loads each tile's 9 population planes and 2 half-force planes with
+// two 3-D bulk tensor copies (boxes tile_x x tile_y x 9 and x 2) into one of
+// two shared-memory stages, completing on an mbarrier, so the copies of the
+// next tile overlap the collision of the current one.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// Wait for the phase with the given parity to complete; false after ~2^31 cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(TILE_N) lb_tma_kernel(SimParams sp, LbArgs<R, S> a,
+                                                        const __grid_constant__ CUtensorMap tm_f,
+                                                        const __grid_constant__ CUtensorMap tm_c, int ntiles) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int ok;
+    // the stages start on a 128-byte boundary of the shared window (the launch
+    // reserves 128 bytes for this): tensor copies write to 128-byte aligned addresses
+    const unsigned pad = (128u - (smem_u32(smem) & 127u)) & 127u;
+    S *stage0 = reinterpret_cast<S *>(smem + pad);
+    const unsigned stage_elems = 11u * TILE_N, stage_bytes = stage_elems * (unsigned)sizeof(S);
+    const int lt = threadIdx.x;
+    if (lt == 0) {
+        ok = ((smem_u32(stage0) & 127u) == 0u && ((stage_bytes & 127u) == 0u)) ? 1 : 0;
+        if (!ok) atomicOr(a.err, ERR_ALIGN);
+        mbar_init(smem_u32(&bar[0]), 1);
+        mbar_init(smem_u32(&bar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (!ok) return;  // nothing issued yet
+    auto issue = [&](int tile, int st) {
+        const int bx = tile % sp.ntx, by = tile / sp.ntx;
+        const unsigned b = smem_u32(&bar[st]);
+        const unsigned dst = smem_u32(stage0 + st * stage_elems);
+        mbar_expect_tx(b, stage_bytes);
+        tma_load_3d(dst, &tm_f, bx * sp.tx, by * sp.ty, 0, b);
+        tma_load_3d(dst + 9u * TILE_N * (unsigned)sizeof(S), &tm_c, bx * sp.tx, by * sp.ty, 0, b);
+    };
+    int tile = blockIdx.x;
+    if (lt == 0) {
+        if (tile < ntiles) issue(tile, 0);
+        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, 1);
+    }
+    for (int it = 0; tile < ntiles; tile += gridDim.x, it++) {
+        const int st = it & 1;
+        if (lt == 0) ok = mbar_wait_bounded(smem_u32(&bar[st]), (it >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!ok) {
+            if (lt == 0) {
+                atomicOr(a.err, ERR_TIMEOUT);
+                // let the other stage's copy (if one was issued) land before leaving
+                if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(smem_u32(&bar[st ^ 1]), ((it + 1) >> 1) & 1);
+            }
+            return;
+        }
+        lb_tile<R, S, true>(sp, a, tile % sp.ntx, tile / sp.ntx, stage0 + st * stage_elems);
+        // every thread has read stage st (lb_tile ends with a barrier): refill it
+        if (lt == 0 && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, st);
+    }
 }
 
 // Initial populations f = f^eq,SFC(rho_t, 0): in the stored form (relative to

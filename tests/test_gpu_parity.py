@@ -192,3 +192,20 @@ def test_rest_state_fixed_point_gpu():
     assert np.abs(sim.populations_host() - f0).max() < 5e-6
     assert np.abs(sim.field_host("ux")).max() < 1e-7
     sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16", "bf16"])
+def test_tma_and_direct_loads_bit_identical(prec):
+    # the LB kernel with tensor-memory staging computes exactly what the
+    # direct-load kernel computes
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.mixing_small(1)
+    outs = []
+    for tma in (True, False):
+        sim = pkg.Simulation(sc, precision=prec, use_tma=tma)
+        sim.step(9)
+        assert sim.uses_tma == tma
+        outs.append([sim.field_host(n) for n in ("rho", "ux", "uy", "Fx")] + [sim.field_host("xi_x", 0)])
+        sim.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b, equal_nan=True)
