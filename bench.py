@@ -241,8 +241,15 @@ def bench_lbrmt(args):
     sc = scenarios.mixing_4096(seed=rank) if args.size == 4096 else crop_sample(rank, args.size)
     N = sc["nx"] * sc["ny"]
     stream = torch.cuda.Stream(dev)
-    sim = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream)
+    sim = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream,
+                         use_tma=args.lb_loads == "tma", tile_x=args.tile_x or 32)
     sim.init()
+    tune = None
+    if args.tile_x == 0:  # the library's tile-shape autotuner (state back to initial afterwards)
+        (best, staged), tms = sim.autotune_tile(20)
+        tune = {"tile_x": best, "lb_loads": "tma" if staged else "direct",
+                "ms_per_step": {f"{k[0]}/{'tma' if k[1] else 'direct'}": round(v, 4) for k, v in tms.items()}}
+    tile_used, tma_used = sim.tile_x, sim.uses_tma
     sim.step(args.warmup)
     sim.sync()
 
@@ -273,7 +280,8 @@ def bench_lbrmt(args):
     e2e = None
     if args.e2e_steps > 0:
         f0 = None
-        sim2 = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream)
+        sim2 = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream, tile_x=tile_used,
+                              use_tma=tma_used)
         sim2.init()
         f0 = torch.from_numpy(sim2.populations_host()).pin_memory()
         host_stats = torch.zeros((len(sc["solids"]), 8), dtype=torch.float64).pin_memory()
@@ -345,7 +353,7 @@ def bench_lbrmt(args):
         "data": "synthetic",
         "config": {"workload": BASE_WORKLOAD if args.size == 4096 else
                    f"{args.size}x{args.size} crop of " + BASE_WORKLOAD, "precision": args.precision, "seed": "rank",
-                   "nodes": N, "solids": len(sc["solids"]),
+                   "nodes": N, "solids": len(sc["solids"]), "tile_x": tile_used, "tile_autotune": tune,
                    "l2": f"inputs larger than L2 (population planes {2 * 9 * N * sf / 1e9:.2f} GB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "kernel_ms": {"rmt_solid_kernel": kms[0], "force_kernel": kms[1], "lb_step_kernel": kms[2]},
@@ -382,6 +390,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="timed steps of the 96-cavity batch (0: skip)")
     ap.add_argument("--autotune-steps", type=int, default=5)
+    ap.add_argument("--tile-x", type=int, default=0, choices=[0, 16, 32, 64, 128],
+                    help="registry / LB tile width (height 256 / tile_x); 0: autotuned")
+    ap.add_argument("--lb-loads", default="tma", choices=["tma", "direct"],
+                    help="LB kernel loads when the tile shape is fixed: tensor-memory staging or direct")
     ap.add_argument("--adjoint-steps", type=int, default=3000,
                     help="steps of the adjoint-cost measurement (0: skip)")
     args = ap.parse_args()

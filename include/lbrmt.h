@@ -128,6 +128,21 @@ lbrmt_status lbrmt_set_solid_params(lbrmt_sim *sim, int solid_id, double rho_s, 
  * (keeps the allocations and the body force field). */
 lbrmt_status lbrmt_reset(lbrmt_sim *sim);
 
+/* Registry / lattice Boltzmann tile shape: tile_x in {16, 32, 64, 128} (0:
+ * 32), height 256 / tile_x.  After initialisation this returns the
+ * simulation to its initial state.  The results do not depend on it. */
+lbrmt_status lbrmt_set_tile_x(lbrmt_sim *sim, int tile_x);
+int lbrmt_tile_x(const lbrmt_sim *sim);
+
+/* Autotuner of the tile shape and of the lattice Boltzmann loads: time
+ * `steps` graph-replayed steps (best of two, after 4 warm-up steps) for each
+ * tile_x in {16, 32, 64, 128} with tensor-memory staging and with direct
+ * loads, keep the fastest and return to the initial state with it.  The
+ * results do not depend on the choice.  best_tile_x / best_tma (may be NULL)
+ * receive the choice; ms_out (8 doubles, may be NULL) the ms per step of
+ * (16, staged), (16, direct), (32, staged), ... (-1 where not applicable). */
+lbrmt_status lbrmt_autotune_tile(lbrmt_sim *sim, int steps, int *best_tile_x, int *best_tma, double *ms_out);
+
 /* Initialise (Algorithm 1, initialisation): xi = x on each solid and its
  * band, phi = phi_0(xi), rho = rho_t, v = 0, f = f^eq,SFC(rho_t, 0).  Called
  * implicitly by the first step or read; allocates the solid tiles. */

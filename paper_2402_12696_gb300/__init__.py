@@ -33,7 +33,8 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_ini
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
            "lbrmt_uses_tma",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
-           "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward",
+           "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward", "lbrmt_set_tile_x", "lbrmt_tile_x",
+           "lbrmt_autotune_tile",
            "lbrmt_create_batch", "lbrmt_batch_add_solid", "lbrmt_batch_init", "lbrmt_batch_step",
            "lbrmt_batch_step_timed", "lbrmt_batch_sync", "lbrmt_batch_member", "lbrmt_batch_size",
            "lbrmt_batch_tile_x", "lbrmt_batch_tune_log", "lbrmt_batch_steps_done",
@@ -101,6 +102,9 @@ def load():
     L.lbrmt_set_body_force_field.argtypes = [p, i, p]
     L.lbrmt_set_solid_params.argtypes = [p, i, d, d]
     L.lbrmt_reset.argtypes = [p]
+    L.lbrmt_set_tile_x.argtypes = [p, i]
+    L.lbrmt_tile_x.argtypes = [p]
+    L.lbrmt_autotune_tile.argtypes = [p, i, C.POINTER(i), C.POINTER(i), p]
     L.lbrmt_forward_checkpointed.argtypes = [p, i, i, p]
     L.lbrmt_backward.argtypes = [p, p, p, p, p, p]
     L.lbrmt_create_batch.argtypes = [cfgp, i, p, C.POINTER(p)]
@@ -370,6 +374,24 @@ class Simulation:
     def reset(self):
         with self.torch.cuda.device(self.device):
             lbrmt_reset(self.h)
+
+    @property
+    def tile_x(self):
+        return load().lbrmt_tile_x(self.h)
+
+    def set_tile_x(self, tx):
+        with self.torch.cuda.device(self.device):
+            _check(self.h, load().lbrmt_set_tile_x(self.h, int(tx)))
+
+    def autotune_tile(self, steps=20):
+        """Time each tile shape with staged and direct LB loads; keep the fastest
+        (state back to initial).  Returns ((tile_x, staged), {(tile_x, staged): ms})."""
+        best, tma = C.c_int(), C.c_int()
+        ms = (C.c_double * 8)()
+        with self.torch.cuda.device(self.device):
+            _check(self.h, load().lbrmt_autotune_tile(self.h, int(steps), C.byref(best), C.byref(tma), ms))
+        table = {(tx, st): ms[2 * k + (0 if st else 1)] for k, tx in enumerate((16, 32, 64, 128)) for st in (True, False)}
+        return (best.value, bool(tma.value)), table
 
     # -- time stepping ------------------------------------------------------
     def init(self):

@@ -85,6 +85,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (c.precision < LBRMT_FP32 || c.precision > LBRMT_BF16_STORE) return LBRMT_ERR_ARG;
     const int tx = c.tile_x == 0 ? 32 : c.tile_x;
     if (tx != 16 && tx != 32 && tx != 64 && tx != 128) return LBRMT_ERR_ARG;
+
     if (std::fabs(c.lid_u) / std::sqrt(1.0 / 3.0) > 0.3) return LBRMT_ERR_PARAM_RANGE;  // Ma* <= 0.3
 
     lbrmt_sim *s = new lbrmt_sim();
@@ -110,7 +111,13 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     sp.omega_f = (float)sp.omega; sp.kf_f = (float)sp.kf; sp.rho_f_f = (float)c.rho_f; sp.lid_u_f = (float)c.lid_u;
     sp.eps_f = (float)c.eps; sp.eta_f = (float)c.eta; sp.fy_f = (float)sp.fy;
 
-    const size_t P = (size_t)sp.P, ntiles = (size_t)sp.ntx * sp.nty;
+    // registry and pool sized for the largest tile count over the tile shapes, so
+    // the shape can change later (lbrmt_set_tile_x) without reallocation
+    size_t ntiles = 0;
+    for (int w = 16; w <= 128; w *= 2)
+        ntiles = std::max(ntiles, (size_t)((c.nx + w - 1) / w) * (size_t)((c.ny + TILE_N / w - 1) / (TILE_N / w)));
+    s->ntiles_cap = (long long)ntiles;
+    const size_t P = (size_t)sp.P;
     const size_t rs = s->eng->real_size, ss = s->eng->store_size;
     DevState &d = s->d;
     std::memset(&d, 0, sizeof(d));
@@ -313,6 +320,76 @@ extern "C" lbrmt_status lbrmt_reset(lbrmt_sim *s) {
         s->gexec = nullptr;
     }
     return run_init(s);
+}
+
+static void set_tile_shape(lbrmt_sim *s, int tx) {
+    SimParams &sp = s->sp;
+    s->cfg.tile_x = tx;
+    sp.tx = tx; sp.ty = TILE_N / tx;
+    sp.lx = __builtin_ctz((unsigned)sp.tx); sp.ly = __builtin_ctz((unsigned)sp.ty);
+    sp.ntx = (s->cfg.nx + sp.tx - 1) / sp.tx;
+    sp.nty = (s->cfg.ny + sp.ty - 1) / sp.ty;
+}
+
+extern "C" lbrmt_status lbrmt_set_tile_x(lbrmt_sim *s, int tile_x) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (tile_x == 0) tile_x = 32;
+    if (tile_x != 16 && tile_x != 32 && tile_x != 64 && tile_x != 128) return fail(s, LBRMT_ERR_ARG, "tile_x must be 16, 32, 64 or 128");
+    if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member's tile shape is set by its batch");
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    if (s->adj) lbrmt_internal_adjoint_free(s);  // its recording buffers are sized by the tile count
+    set_tile_shape(s, tile_x);
+    if (!s->inited) return LBRMT_OK;
+    return run_init(s);
+}
+
+extern "C" int lbrmt_tile_x(const lbrmt_sim *s) { return s ? s->sp.tx : 0; }
+
+extern "C" lbrmt_status lbrmt_autotune_tile(lbrmt_sim *s, int steps, int *best_tile_x, int *best_tma, double *ms_out) {
+    if (!s || steps < 1) return LBRMT_ERR_ARG;
+    const int cand[4] = {16, 32, 64, 128};
+    int best = s->sp.tx, best_t = s->li.use_tma ? 1 : 0;
+    double best_ms = 1e30;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(s, LBRMT_ERR_CUDA, "event create");
+    lbrmt_status st = LBRMT_OK;
+    for (int k = 0; k < 8 && st == LBRMT_OK; k++) {
+        const int tx = cand[k >> 1], tma = (k & 1) ? 0 : 1;
+        double ms = 1e30;
+        s->li.use_tma = tma != 0;
+        st = lbrmt_set_tile_x(s, tx);
+        if (st == LBRMT_OK && !s->inited) st = lbrmt_init(s);
+        const bool runs = st == LBRMT_OK && (tma == 0 || s->li.tma);  // the tensor path may not apply
+        if (runs) st = lbrmt_step(s, 4);  // warm-up (graph capture)
+        for (int rep = 0; rep < 2 && runs && st == LBRMT_OK; rep++) {
+            cudaEventRecord(e0, s->stream);
+            st = lbrmt_step(s, steps);
+            cudaEventRecord(e1, s->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(s, LBRMT_ERR_CUDA, "autotune");
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            ms = std::min(ms, (double)f / steps);
+        }
+        if (st == LBRMT_OK && runs) st = check_flags(s);
+        if (ms_out) ms_out[k] = runs ? ms : -1.0;
+        if (st == LBRMT_OK && runs && ms < best_ms) {
+            best_ms = ms;
+            best = tx;
+            best_t = tma;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBRMT_OK) return st;
+    if (best_tile_x) *best_tile_x = best;
+    if (best_tma) *best_tma = best_t;
+    s->li.use_tma = best_t != 0;
+    return lbrmt_set_tile_x(s, best);  // back to the initial state with the chosen variant
 }
 
 extern "C" lbrmt_status lbrmt_set_solid_params(lbrmt_sim *s, int solid_id, double rho_s, double G) {

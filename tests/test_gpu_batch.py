@@ -179,3 +179,28 @@ def test_ldc_ensemble_96():
         assert _same(_snapshot(sim, scs[k]), _snapshot(b[k], scs[k])), k
         sim.close()
     b.close()
+
+
+def test_set_tile_x_and_autotune_single_simulation():
+    # changing the tile shape of an initialised simulation restarts it; the
+    # autotuner leaves it in the initial state with the fastest shape; results
+    # are those of any fixed shape
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.mixing_small(0)
+    ref = pkg.Simulation(sc, precision="fp32", tile_x=32)
+    ref.step(7)
+    want = _snapshot(ref, sc)
+    ref.close()
+    sim = pkg.Simulation(sc, precision="fp32", tile_x=128)
+    sim.step(3)
+    sim.set_tile_x(16)
+    assert sim.steps_done == 0 and sim.tile_x == 16
+    sim.step(7)
+    assert _same(want, _snapshot(sim, sc))
+    (best, staged), ms = sim.autotune_tile(3)
+    assert best in (16, 32, 64, 128) and sim.tile_x == best and sim.steps_done == 0
+    assert sim.uses_tma == staged
+    assert all(v > 0 for (tx, st), v in ms.items() if not st)
+    sim.step(7)
+    assert _same(want, _snapshot(sim, sc))
+    sim.close()
