@@ -60,12 +60,16 @@ enum { LBRMT_SHAPE_DISK = 0 };
  * populations (Sec. 3.4); FX/FY/DRHO are the force density F of Eq. 2_4_F_divs
  * and the density difference of Eq. 2_3_drho used by the last step; XI_X,
  * XI_Y, PHI are the reference map (absolute reference coordinates) and level
- * set of one solid on its solid + band nodes (NaN elsewhere); POP0 + q is the
- * population f_q. */
+ * set of one solid on its solid + band nodes (NaN elsewhere); DET_F_DEV and
+ * VON_MISES are det F - 1 (F = J^-1, J = d xi / dx by central differences over
+ * the 4-neighbours; the volumetric deviation of Sec. 4.1) and the von Mises
+ * stress of the neo-Hookean stress of Eq. 3_3_solid_stress in plane strain, on
+ * the solid's nodes (phi < 0; NaN elsewhere); POP0 + q is the population f_q. */
 enum {
     LBRMT_FIELD_RHO = 0, LBRMT_FIELD_UX = 1, LBRMT_FIELD_UY = 2,
     LBRMT_FIELD_FX = 3, LBRMT_FIELD_FY = 4, LBRMT_FIELD_DRHO = 5,
     LBRMT_FIELD_XI_X = 10, LBRMT_FIELD_XI_Y = 11, LBRMT_FIELD_PHI = 12,
+    LBRMT_FIELD_DET_F_DEV = 14, LBRMT_FIELD_VON_MISES = 15,
     LBRMT_FIELD_POP0 = 20
 };
 
@@ -167,8 +171,9 @@ lbrmt_status lbrmt_set_populations_host(lbrmt_sim *sim, const double *host_f);
 
 /* Per-solid FP64 statistics of the current state, S x 8 doubles into host
  * memory: lambda-weighted area sum, centroid x, centroid y (unwrapped frame),
- * mass sum(lambda rho), momentum sum(lambda rho u), sum(lambda rho v), and
- * two reserved zeros; lambda = 1 - H_eps(phi) on domain nodes. */
+ * mass sum(lambda rho), momentum sum(lambda rho u), sum(lambda rho v), the
+ * maximum of |det F - 1| over the solid nodes (phi < 0) and its lambda-weighted
+ * mean over them; lambda = 1 - H_eps(phi) on domain nodes. */
 lbrmt_status lbrmt_solid_stats(lbrmt_sim *sim, int sim_index, double *host_out);
 
 /* Total mass sum_x rho over the domain after the last step (FP64, fixed

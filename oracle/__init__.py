@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liblbrmt_oracle.so")
 _lib = None
 
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "Fx": 3, "Fy": 4, "drho": 5,
-          "xi_x": 10, "xi_y": 11, "phi": 12, "label": 13}
+          "xi_x": 10, "xi_y": 11, "phi": 12, "label": 13, "detF_dev": 14, "von_mises": 15}
 RMAX = 11
 
 
@@ -49,6 +49,7 @@ def lib():
         L.oracle_create.argtypes = [i, i, i, i, d, d, d, d, i, d, d, i, d, d, i]
         L.oracle_add_solid.argtypes = [p, d, d, d, d, d]
         L.oracle_set_body_force.argtypes = [p, dp]
+        L.oracle_deformation.argtypes = [dp, d, dp]
         L.oracle_init.argtypes = [p]
         L.oracle_step.argtypes = [p, i]
         L.oracle_read_field.argtypes = [p, i, i, dp]
@@ -75,6 +76,15 @@ def lib():
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def deformation(J, G):
+    """(det F - 1, von Mises stress) for the Jacobian J = d xi / dx (2x2)."""
+    j = np.ascontiguousarray(np.asarray(J, dtype=np.float64).reshape(4))
+    out = np.empty(2)
+    if lib().oracle_deformation(_dp(j), float(G), _dp(out)) != 0:
+        raise OracleError("singular Jacobian")
+    return float(out[0]), float(out[1])
 
 
 def heaviside(phi, eps):

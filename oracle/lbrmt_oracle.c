@@ -800,6 +800,39 @@ int oracle_step(void *h, int nsteps) {
 /* Fields: 0 rho, 1 ux, 2 uy, 3 Fx, 4 Fy, 5 drho (last step's force density and
  * density difference), 10 xi_x, 11 xi_y, 12 phi, 13 layer label (per solid,
  * NaN / -1 where the node is not in the solid's band), 20+q population q. */
+/* Deformation measures for a Jacobian J = d xi / dx (row-major, J[0] = dX/dx,
+ * J[1] = dX/dy, J[2] = dY/dx, J[3] = dY/dy): out[0] = det F - 1 with F = J^-1
+ * (volumetric deviation), out[1] = von Mises stress of the neo-Hookean stress
+ * tau = G (F F^T - (tr(F F^T) + 1)/3 I) of Eq. 3_3_solid_stress in plane strain,
+ * whose out-of-plane component is G (1 - (tr(F F^T) + 1)/3).  Returns -1 if J
+ * is singular. */
+int oracle_deformation(const double *J, double G, double *out) {
+    double det = J[0] * J[3] - J[1] * J[2];
+    if (det == 0.0) return -1;
+    double F[4] = {J[3] / det, -J[1] / det, -J[2] / det, J[0] / det};
+    double Bxx = F[0] * F[0] + F[1] * F[1], Bxy = F[0] * F[2] + F[1] * F[3], Byy = F[2] * F[2] + F[3] * F[3];
+    double tr = (Bxx + Byy + 1.0) / 3.0;
+    double txx = G * (Bxx - tr), tyy = G * (Byy - tr), tzz = G * (1.0 - tr), txy = G * Bxy;
+    out[0] = 1.0 / det - 1.0;
+    out[1] = sqrt(1.5 * (txx * txx + tyy * tyy + tzz * tzz + 2.0 * txy * txy));
+    return 0;
+}
+
+/* Central-difference Jacobian of solid s's reference map at window node (x, y);
+ * -1 unless the node is solid (phi < 0) and its four neighbours are in the band. */
+static int node_jacobian(const osim_t *m, const osolid_t *s, int x, int y, double *J) {
+    const ocfg_t *c = &m->c;
+    if (x < 1 || y < 1 || x >= s->w - 1 || y >= s->h - 1) return -1;
+    int k = y * s->w + x;
+    if (s->lab[k] < 0 || !(s->phi[k] < -PHI_TIE) || !in_domain(c, s->x0 + x, s->y0 + y)) return -1;
+    if (s->lab[k - 1] < 0 || s->lab[k + 1] < 0 || s->lab[k - s->w] < 0 || s->lab[k + s->w] < 0) return -1;
+    J[0] = 0.5 * (s->X[k + 1] - s->X[k - 1]);
+    J[1] = 0.5 * (s->X[k + s->w] - s->X[k - s->w]);
+    J[2] = 0.5 * (s->Y[k + 1] - s->Y[k - 1]);
+    J[3] = 0.5 * (s->Y[k + s->w] - s->Y[k - s->w]);
+    return 0;
+}
+
 int oracle_read_field(void *h, int field, int solid, double *out) {
     osim_t *m = h;
     const ocfg_t *c = &m->c;
@@ -817,6 +850,19 @@ int oracle_read_field(void *h, int field, int solid, double *out) {
     }
     if (src) { memcpy(out, src, N * sizeof(double)); return 0; }
     if (field >= 20 && field < 20 + NQ) { memcpy(out, m->f + (field - 20) * N, N * sizeof(double)); return 0; }
+    if (field == 14 || field == 15) {
+        if (solid < 0 || solid >= m->ns) return seterr(m, "bad solid id");
+        const osolid_t *s = &m->s[solid];
+        for (long k = 0; k < N; k++) out[k] = NAN;
+        for (int y = 0; y < s->h; y++)
+            for (int x = 0; x < s->w; x++) {
+                double J[4], d[2];
+                if (node_jacobian(m, s, x, y, J) || oracle_deformation(J, s->G, d)) continue;
+                long cell = (long)wrapi(s->y0 + y, c->ny) * c->nx + wrapi(s->x0 + x, c->nx);
+                out[cell] = field == 14 ? d[0] : d[1];
+            }
+        return 0;
+    }
     if (field >= 10 && field <= 13) {
         if (solid < 0 || solid >= m->ns) return seterr(m, "bad solid id");
         const osolid_t *s = &m->s[solid];
@@ -835,27 +881,36 @@ int oracle_read_field(void *h, int field, int solid, double *out) {
 
 /* Per-solid statistics at the current time: lambda = 1 - H(phi) over domain
  * nodes; out[0..7] = sum lambda, centroid x, centroid y (unwrapped frame),
- * sum lambda rho, sum lambda rho u, sum lambda rho v, window x0, window y0. */
+ * sum lambda rho, sum lambda rho u, sum lambda rho v, and over the solid nodes
+ * (phi < 0) the maximum and the lambda-weighted mean of |det F - 1|. */
 int oracle_solid_stats(void *h, int solid, double *out) {
     osim_t *m = h;
     const ocfg_t *c = &m->c;
     if (m->step < 0 && oracle_init(h)) return -1;
     if (solid < 0 || solid >= m->ns) return seterr(m, "bad solid id");
     const osolid_t *s = &m->s[solid];
-    double L = 0, Lx = 0, Ly = 0, Lr = 0, Lu = 0, Lv = 0;
+    double L = 0, Lx = 0, Ly = 0, Lr = 0, Lu = 0, Lv = 0, Dmax = 0, Dsum = 0, Dw = 0;
     for (int y = 0; y < s->h; y++)
         for (int x = 0; x < s->w; x++) {
             int k = y * s->w + x, gx = s->x0 + x, gy = s->y0 + y;
             if (s->lab[k] < 0 || !in_domain(c, gx, gy)) continue;
+            if (!(s->phi[k] < c->eps)) continue;
             long cell = (long)wrapi(gy, c->ny) * c->nx + wrapi(gx, c->nx);
             double lam = 1.0 - oracle_heaviside(s->phi[k], c->eps);
             L += lam; Lx += lam * gx; Ly += lam * gy;
             Lr += lam * m->rho[cell];
             Lu += lam * m->rho[cell] * m->ux[cell];
             Lv += lam * m->rho[cell] * m->uy[cell];
+            double J[4], d[2];
+            if (node_jacobian(m, s, x, y, J) == 0 && oracle_deformation(J, s->G, d) == 0) {
+                double a = fabs(d[0]);
+                if (a > Dmax) Dmax = a;
+                Dsum += lam * a;
+                Dw += lam;
+            }
         }
     out[0] = L; out[1] = Lx / L; out[2] = Ly / L; out[3] = Lr; out[4] = Lu; out[5] = Lv;
-    out[6] = s->x0; out[7] = s->y0;
+    out[6] = Dmax; out[7] = Dw > 0 ? Dsum / Dw : 0.0;
     return 0;
 }
 

@@ -26,7 +26,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NUMERIC", -4: "ERR_OV
           -5: "ERR_EXTRAP", -6: "ERR_TIMEOUT", -7: "ERR_PARAM_RANGE", -8: "ERR_STATE"}
 PRECISION = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "Fx": 3, "Fy": 4, "drho": 5,
-          "xi_x": 10, "xi_y": 11, "phi": 12}
+          "xi_x": 10, "xi_y": 11, "phi": 12, "detF_dev": 14, "von_mises": 15}
 EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_init", "lbrmt_step",
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",

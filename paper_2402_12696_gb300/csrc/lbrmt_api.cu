@@ -521,7 +521,7 @@ extern "C" lbrmt_status lbrmt_step_timed(lbrmt_sim *s, int nsteps, float *ms_out
     return check_flags(s);
 }
 
-static bool field_ok(int f) { return (f >= 0 && f <= 5) || (f >= 10 && f <= 12) || (f >= 20 && f < 29); }
+static bool field_ok(int f) { return (f >= 0 && f <= 5) || (f >= 10 && f <= 12) || f == 14 || f == 15 || (f >= 20 && f < 29); }
 
 extern "C" lbrmt_status lbrmt_read_fields(lbrmt_sim *s, int sim_index, int field, int solid_id, double *dev_out) {
     if (!s || !dev_out || sim_index != 0 || !field_ok(field)) return LBRMT_ERR_ARG;
@@ -531,7 +531,7 @@ extern "C" lbrmt_status lbrmt_read_fields(lbrmt_sim *s, int sim_index, int field
     }
     const int cur = (int)(s->steps & 1);
     const int lastreg = 1 - cur;  // registry of the step (or initialisation) that wrote the state
-    if (field >= 10 && field <= 12) {
+    if (field >= 10 && field <= 15) {
         if (solid_id < 0 || solid_id >= (int)s->solids.size()) return fail(s, LBRMT_ERR_ARG, "bad solid id");
         cudaError_t e = cudaMemsetAsync(dev_out, 0xFF, (size_t)s->sp.P * 8, s->stream);  // NaN
         if (e != cudaSuccess) return cuda_fail(s, e, "clear field");

@@ -296,7 +296,7 @@ struct Engine {
     static cudaError_t field(const SimParams &sp, const DevState &d, int cur, int lastreg, int kind, int solid,
                              double *out, cudaStream_t st) {
         dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
-        if (kind >= 10 && kind <= 12) {
+        if (kind >= 10 && kind <= 15 && kind != 13) {
             solid_field_kernel<R><<<64, 256, 0, st>>>(sp, (const R *)d.xi[cur], d.frame[cur], d.solids, solid,
                                                       kind - 10, out);
             return cudaGetLastError();

@@ -1318,7 +1318,35 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
     out[c] = v;
 }
 
-// One solid's reference map / level set onto the grid (NaN where not in its band).
+// Deformation measures of solid node (lx, ly) from central differences of xi
+// over its 4-neighbours, J = d xi / dx = I + A: det F - 1 with F = J^-1 (the
+// volumetric deviation of Sec. 4.1), and the von Mises stress of the
+// neo-Hookean stress of Eq. 3_3_solid_stress in plane strain (the out-of-plane
+// deviatoric component is -(tau_xx + tau_yy)).  False where a neighbour is
+// missing or J is singular.
+template <class R>
+__device__ __forceinline__ bool node_deformation(const R *X, const R *Y, int T, int lx, int ly, const Frame &fr, R G,
+                                                 R &ddet, R &vm) {
+    if (!(lx > fr.bx0 && lx < fr.bx1 && ly > fr.by0 && ly < fr.by1)) return false;
+    const int k = ly * T + lx;
+    const R Xe = X[k + 1], Xw = X[k - 1], Xn = X[k + T], Xs = X[k - T];
+    const R Ye = Y[k + 1], Yw = Y[k - 1], Yn = Y[k + T], Ys = Y[k - T];
+    if (!(Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs)) return false;
+    // eta = xi - position: d xi / dx = I + d eta / dx
+    const R Axx = R(0.5) * (Xe - Xw), Axy = R(0.5) * (Xn - Xs), Ayx = R(0.5) * (Ye - Yw), Ayy = R(0.5) * (Yn - Ys);
+    const R dl = (Axx + Ayy) + (Axx * Ayy - Axy * Ayx);  // det J - 1
+    if (R(1) + dl == R(0)) return false;
+    ddet = -dl / (R(1) + dl);
+    R txx, txy, tyy;
+    stress_from_grad<R>(Axx, Axy, Ayx, Ayy, G, txx, txy, tyy);
+    const R tzz = -(txx + tyy);
+    vm = rsqrt_<R>(R(1.5) * (txx * txx + tyy * tyy + tzz * tzz + R(2) * txy * txy));
+    return true;
+}
+
+// One solid's field onto the grid: kind 0, 1 the reference map, 2 the level
+// set (on the solid and its band), 4 det F - 1 and 5 the von Mises stress (on
+// the solid nodes, phi < 0); NaN elsewhere.
 template <class R>
 __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frames, const SolidDesc *solids, int s,
                                    int kind, double *out) {
@@ -1338,7 +1366,14 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
         // xi = eta + l + off + X_c
         if (kind == 0) v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
         else if (kind == 1) v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
-        else v = (double)phi_eta(X, Y, lx, ly, fr, rq);
+        else if (kind == 2) v = (double)phi_eta(X, Y, lx, ly, fr, rq);
+        else {
+            if (!(phi_eta(X, Y, lx, ly, fr, rq) < -R(PHI_TIE))) continue;
+            R ddet, vm;
+            if (!node_deformation<R>(xi + sd.off, xi + sd.off + T * T, T, lx, ly, fr, pick<R>(sd.G, sd.G_f), ddet, vm))
+                continue;
+            v = kind == 4 ? (double)ddet : (double)vm;
+        }
         out[c] = v;
     }
 }
@@ -1347,7 +1382,8 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
 template <class R, class S>
 __global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, const int *reg, const R *pool,
                                    const R *xi, const Frame *frames, const SolidDesc *solids, double *out) {
-    __shared__ double red[32 * 6];
+    __shared__ double red[32 * 8];
+    __shared__ unsigned long long dmax;
     const int s = blockIdx.x;
     const SolidDesc sd = solids[s];
     const Frame fr = frames[s];
@@ -1355,7 +1391,10 @@ __global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, con
     const Rsq<R> rq(sd);
     const int T = sd.T;
     const R eps = pick<R>(sp.eps, sp.eps_f);
-    double st[6] = {0, 0, 0, 0, 0, 0};
+    double st[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // ..., sum lambda |det F - 1|, sum lambda over them
+    double mx = 0.0;
+    if (threadIdx.x == 0) dmax = 0ull;
+    __syncthreads();
     for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
         const int lx = t % T, ly = t / T;
         const int gx = o.x + lx, gy = o.y + ly;
@@ -1369,12 +1408,22 @@ __global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, con
         const double lam = 1.0 - (double)heaviside<R>(phi, eps);
         st[0] += lam; st[1] += lam * gx; st[2] += lam * gy;
         st[3] += lam * (double)rho; st[4] += lam * (double)rho * (double)u; st[5] += lam * (double)rho * (double)v;
+        R ddet, vm;
+        if (phi < -R(PHI_TIE) &&
+            node_deformation<R>(xi + sd.off, xi + sd.off + T * T, T, lx, ly, fr, pick<R>(sd.G, sd.G_f), ddet, vm)) {
+            const double a = fabs((double)ddet);
+            st[6] += lam * a;
+            st[7] += lam;
+            mx = fmax(mx, a);
+        }
     }
-    block_sum<6>(st, red);
+    atomicMax(&dmax, (unsigned long long)__double_as_longlong(mx));  // non-negative: bits order as values
+    block_sum<8>(st, red);
     if (threadIdx.x == 0) {
         double *q = out + 8 * s;
         q[0] = st[0]; q[1] = st[1] / st[0]; q[2] = st[2] / st[0]; q[3] = st[3]; q[4] = st[4]; q[5] = st[5];
-        q[6] = 0; q[7] = 0;
+        q[6] = __longlong_as_double((long long)dmax);
+        q[7] = st[7] > 0.0 ? st[6] / st[7] : 0.0;
     }
 }
 

@@ -209,3 +209,26 @@ def test_tma_and_direct_loads_bit_identical(prec):
         sim.close()
     for a, b in zip(*outs):
         assert np.array_equal(a, b, equal_nan=True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_deformation_fields_and_stats(prec):
+    # det F - 1, von Mises stress and the det F statistics against the oracle
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.contact_pair(gap=0.8, nx=96, ny=64)
+    sim = pkg.Simulation(sc, precision=prec)
+    ref = oracle.Oracle(sc)
+    sim.step(60)
+    ref.step(60)
+    tol = 1e-9 if prec == "fp64" else 2e-4
+    for s in range(len(sc["solids"])):
+        for name in ("detF_dev", "von_mises"):
+            a, b = sim.field_host(name, s), ref.field(name, s)
+            assert np.array_equal(np.isfinite(a), np.isfinite(b)), name
+            m = np.isfinite(b)
+            scale = max(np.abs(b[m]).max(), 1e-6 if name == "detF_dev" else 1e-6 * sc["solids"][s]["G"])
+            assert np.abs(a[m] - b[m]).max() <= tol * scale, (name, np.abs(a[m] - b[m]).max(), scale)
+        st, so = sim.solid_stats()[s], ref.solid_stats(s)
+        assert abs(st[6] - so[6]) <= tol * max(so[6], 1e-6) and abs(st[7] - so[7]) <= tol * max(so[7], 1e-6)
+    sim.close()
+    ref.close()

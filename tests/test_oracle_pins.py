@@ -472,3 +472,46 @@ def test_body_force_field_momentum_gain():
     gy = (prev[1] / (2 * tau) + (1 - 1 / (2 * tau)) * cur[1]).sum()
     assert abs((CX[:, None, None] * f1).sum() - px - gx) < 1e-11
     assert abs((CY[:, None, None] * f1).sum() - py - gy) < 1e-11
+
+
+def test_deformation_closed_forms():
+    # det F - 1 and the von Mises stress of tau = G (F F^T - (tr(F F^T) + 1)/3 I)
+    # in plane strain (tau_zz = G (1 - (tr + 1)/3)), for Jacobians J = d xi/dx
+    G = 0.7
+    assert oracle.deformation(np.eye(2), G) == (0.0, 0.0)
+    for th in (0.3, -1.1, 2.5):  # rigid rotation: F = R^T, F F^T = I
+        J = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        d, vm = oracle.deformation(J, G)
+        assert abs(d) < 1e-15 and vm < 1e-15
+    for a in (0.8, 1.25, 2.0):  # F = diag(a, 1/a): isochoric stretch
+        J = np.diag([1 / a, a])
+        d, vm = oracle.deformation(J, G)
+        tr = (a * a + 1 / (a * a) + 1) / 3
+        t = np.array([a * a - tr, 1 / (a * a) - tr, 1 - tr]) * G
+        assert abs(d) < 1e-15
+        assert abs(vm - np.sqrt(1.5 * (t ** 2).sum())) < 1e-14
+    for s in (0.9, 1.1):  # pure dilation: F = s I, deviatoric stress from the z direction only
+        d, vm = oracle.deformation(np.eye(2) / s, G)
+        assert abs(d - (s * s - 1)) < 1e-14
+        tr = (2 * s * s + 1) / 3
+        t = np.array([s * s - tr, s * s - tr, 1 - tr]) * G
+        assert abs(vm - np.sqrt(1.5 * (t ** 2).sum())) < 1e-14
+    g = 0.4  # simple shear F = [[1, g], [0, 1]]: B = [[1 + g^2, g], [g, 1]],
+    # tau = G (2g^2/3, -g^2/3, -g^2/3; g), von Mises = G g sqrt(g^2 + 3)
+    J = np.linalg.inv(np.array([[1.0, g], [0.0, 1.0]]))
+    d, vm = oracle.deformation(J, G)
+    assert abs(d) < 1e-15
+    assert abs(vm - G * g * np.sqrt(g * g + 3)) < 1e-14
+
+
+def test_initial_solid_is_undeformed():
+    # xi = x at initialisation: J = I on every solid node, det F = 1, no stress
+    sc = scenarios.settling_small(0)
+    o = oracle.Oracle(sc)
+    for s in range(len(sc["solids"])):
+        d, vm = o.field("detF_dev", s), o.field("von_mises", s)
+        m = np.isfinite(d)
+        assert m.sum() > 100
+        assert np.abs(d[m]).max() < 1e-13 and np.abs(vm[m]).max() < 1e-14
+        st = o.solid_stats(s)
+        assert st[6] < 1e-13 and st[7] < 1e-13
