@@ -213,6 +213,37 @@ def bench_adjoint(args, dev):
     return out
 
 
+def bench_shapes(args, dev):
+    """The 506-ellipse mixing workload (800x450, walls, tau 1, G 1, semi-axes
+    8 x 4 lying and standing, heavier 1.25 and lighter 0.83), FP32: MLUPS of
+    graph-replayed steps timed with CUDA events."""
+    import torch
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.mixing_ellipses(0)
+    stream = torch.cuda.Stream(dev)
+    sim = pkg.Simulation(sc, precision="fp32", device=str(dev), stream=stream)
+    sim.init()
+    sim.step(args.warmup)
+    sim.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    sim.step(args.shapes_steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    sim.sync()
+    ms = ev0.elapsed_time(ev1)
+    kms = sim.step_timed(10)
+    st = sim.solid_stats()
+    out = {"workload": "mixing of 506 ellipses, 800x450 walls, semi-axes 8x4, FP32 (mixing_ellipses seed 0)",
+           "value": sc["nx"] * sc["ny"] * args.shapes_steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
+           "steps": args.shapes_steps, "ms_per_step": ms / args.shapes_steps,
+           "kernel_ms": {"rmt_solid_kernel": kms[0], "force_kernel": kms[1], "lb_step_kernel": kms[2]},
+           "max_detF_dev": float(st[:, 6].max())}
+    sim.close()
+    return out
+
+
 def bench_lbrmt(args):
     import torch
     import paper_2402_12696_gb300 as pkg
@@ -308,6 +339,7 @@ def bench_lbrmt(args):
 
     batched = bench_batch(args, dev) if args.batch_steps > 0 and rank == 0 else None
     adjoint = bench_adjoint(args, dev) if args.adjoint_steps > 0 and rank == 0 else None
+    shapes = bench_shapes(args, dev) if args.shapes_steps > 0 and rank == 0 else None
 
     if rank != 0:
         if ws > 1:
@@ -368,6 +400,7 @@ def bench_lbrmt(args):
         "cpu_baseline": cpu,
         "batched": batched,
         "adjoint": adjoint,
+        "shapes": shapes,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -394,6 +427,8 @@ def main():
                     help="registry / LB tile width (height 256 / tile_x); 0: autotuned")
     ap.add_argument("--lb-loads", default="tma", choices=["tma", "direct"],
                     help="LB kernel loads when the tile shape is fixed: tensor-memory staging or direct")
+    ap.add_argument("--shapes-steps", type=int, default=200,
+                    help="timed steps of the 506-ellipse workload (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=3000,
                     help="steps of the adjoint-cost measurement (0: skip)")
     args = ap.parse_args()

@@ -54,7 +54,7 @@ typedef enum {
 enum { LBRMT_PERIODIC = 0, LBRMT_WALL = 1 };
 enum { LBRMT_FP32 = 0, LBRMT_FP64 = 1, LBRMT_FP16_STORE = 2, LBRMT_BF16_STORE = 3 };
 enum { LBRMT_FORCE_NONE = 0, LBRMT_FORCE_CONST = 1, LBRMT_FORCE_SINE_X = 2, LBRMT_FORCE_FIELD = 3 };
-enum { LBRMT_SHAPE_DISK = 0 };
+enum { LBRMT_SHAPE_DISK = 0, LBRMT_SHAPE_ELLIPSE = 1, LBRMT_SHAPE_RECT = 2 };
 
 /* Field ids for lbrmt_read_fields.  RHO/UX/UY are the moments of the current
  * populations (Sec. 3.4); FX/FY/DRHO are the force density F of Eq. 2_4_F_divs
@@ -117,6 +117,16 @@ lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream, lbrmt_sim 
  * id (0, 1, ...) in *solid_id_out (may be NULL). */
 lbrmt_status lbrmt_add_solid(lbrmt_sim *sim, int shape, double cx, double cy, double radius,
                              double rho_s, double G, int *solid_id_out);
+
+/* Add a solid of any shape: LBRMT_SHAPE_DISK (radius a; b ignored),
+ * LBRMT_SHAPE_ELLIPSE (semi-axes a along x, b along y) or LBRMT_SHAPE_RECT
+ * (half-sides a, b), axis-aligned, centred at (cx, cy); its level set phi_0 is
+ * the signed distance to the boundary (negative inside; Sec. 3 uses phi < 0
+ * for the solid).  a, b >= 1; G <= rho_s (the shear wave speed sqrt(G/rho_s)
+ * within one node per step, Appendix A; else LBRMT_ERR_PARAM_RANGE).  The
+ * adjoint supports disks only. */
+lbrmt_status lbrmt_add_solid_shape(lbrmt_sim *sim, int shape, double cx, double cy, double a, double b,
+                                   double rho_s, double G, int *solid_id_out);
 
 /* Body force field f(x) of Eq. 2_4_F_divs for force_kind LBRMT_FORCE_FIELD:
  * dev_xy is a device array of 2*nx*ny doubles (x components, then y
@@ -277,7 +287,10 @@ typedef struct lbrmt_batch lbrmt_batch;
  * The batch owns its members. */
 lbrmt_status lbrmt_create_batch(const lbrmt_config *cfgs, int nsim, void *cuda_stream, lbrmt_batch **out);
 
-/* Add a solid to member sim_index (before lbrmt_batch_init); as lbrmt_add_solid. */
+/* Add a solid to member sim_index (before lbrmt_batch_init); as
+ * lbrmt_add_solid_shape / lbrmt_add_solid. */
+lbrmt_status lbrmt_batch_add_solid_shape(lbrmt_batch *batch, int sim_index, int shape, double cx, double cy,
+                                         double a, double b, double rho_s, double G, int *solid_id_out);
 lbrmt_status lbrmt_batch_add_solid(lbrmt_batch *batch, int sim_index, int shape, double cx, double cy,
                                    double radius, double rho_s, double G, int *solid_id_out);
 

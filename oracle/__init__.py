@@ -50,6 +50,9 @@ def lib():
         L.oracle_add_solid.argtypes = [p, d, d, d, d, d]
         L.oracle_set_body_force.argtypes = [p, dp]
         L.oracle_deformation.argtypes = [dp, d, dp]
+        L.oracle_add_solid_shape.argtypes = [p, i, d, d, d, d, d, d]
+        L.oracle_phi0.argtypes = [i, d, d, d, d]
+        L.oracle_phi0.restype = d
         L.oracle_init.argtypes = [p]
         L.oracle_step.argtypes = [p, i]
         L.oracle_read_field.argtypes = [p, i, i, dp]
@@ -76,6 +79,15 @@ def lib():
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+SHAPES = {"disk": 0, "ellipse": 1, "rect": 2}
+
+
+def phi0(shape, a, b, qx, qy):
+    """Signed distance of (qx, qy) (relative to the centre) to an axis-aligned
+    disk (radius a), ellipse (semi-axes a, b) or rectangle (half-sides a, b)."""
+    return lib().oracle_phi0(SHAPES[shape], float(a), float(b), float(qx), float(qy))
 
 
 def deformation(J, G):
@@ -152,7 +164,9 @@ class Oracle:
         if not self.h:
             raise OracleError("oracle_create failed (out of memory?)")
         for s in sc["solids"]:
-            if L.oracle_add_solid(self.h, s["x"], s["y"], s["r"], s["rho_s"], s["G"]) < 0:
+            shape = SHAPES[s.get("shape", "disk")]
+            a, b = (s["r"], s["r"]) if shape == 0 else (s["a"], s["b"])
+            if L.oracle_add_solid_shape(self.h, shape, s["x"], s["y"], a, b, s["rho_s"], s["G"]) < 0:
                 self._raise()
         if sc["force_kind"] == 3:
             bf = np.ascontiguousarray(sc["body_field"], dtype=np.float64).reshape(2, self.ny, self.nx)

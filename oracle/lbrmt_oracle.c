@@ -78,7 +78,9 @@ typedef struct {
 } ocfg_t;
 
 typedef struct {
-    double xc, yc, R, rho_s, G;
+    double xc, yc, R, rho_s, G;  /* R: radius of the disk, circumscribed radius of other shapes */
+    int shape;                   /* 0 disk, 1 axis-aligned ellipse, 2 axis-aligned rectangle */
+    double a, b;                 /* semi-axes / half-sides along x and y */
     int x0, y0, w, h;  /* window in unwrapped coordinates */
     double *X, *Y, *phi;
     signed char *lab;  /* -1 outside S u band, 0 advected solid set, l = layer */
@@ -278,8 +280,58 @@ int oracle_extrap_target(int w, int h, const signed char *lab, const double *X,
 
 static int wrapi(int g, int n) { int r = g % n; return r < 0 ? r + n : r; }
 
+/* Distance from (y0, y1), y0, y1 >= 0, to the ellipse (x/e0)^2 + (y/e1)^2 = 1
+ * with e0 >= e1 > 0.  The closest point is x_i = e_i^2 y_i / (t + e_i^2) for
+ * the root t of sum_i (e_i y_i / (t + e_i^2))^2 = 1; in s = t / e1^2 that root
+ * is bracketed and found by bisection to full precision (Eberly's method for
+ * the distance from a point to an ellipse). */
+static double ellipse_dist_q1(double e0, double e1, double y0, double y1) {
+    if (y1 > 0) {
+        if (y0 > 0) {
+            double z0 = y0 / e0, z1 = y1 / e1, g = z0 * z0 + z1 * z1 - 1.0;
+            if (g == 0.0) return 0.0;
+            double r0 = (e0 / e1) * (e0 / e1), n0 = r0 * z0;
+            double s0 = z1 - 1.0, s1 = g < 0 ? 0.0 : hypot(n0, z1) - 1.0, sm = 0.0;
+            for (int it = 0; it < 2000; it++) {
+                sm = 0.5 * (s0 + s1);
+                if (sm == s0 || sm == s1) break;
+                double ra = n0 / (sm + r0), rb = z1 / (sm + 1.0), f = ra * ra + rb * rb - 1.0;
+                if (f > 0) s0 = sm;
+                else if (f < 0) s1 = sm;
+                else break;
+            }
+            double x0 = r0 * y0 / (sm + r0), x1 = y1 / (sm + 1.0);
+            return hypot(x0 - y0, x1 - y1);
+        }
+        return fabs(y1 - e1);
+    }
+    double numer0 = e0 * y0, denom0 = e0 * e0 - e1 * e1;
+    if (numer0 < denom0) {
+        double xde0 = numer0 / denom0, x0 = e0 * xde0, x1 = e1 * sqrt(1.0 - xde0 * xde0);
+        return hypot(x0 - y0, x1);
+    }
+    return fabs(y0 - e0);
+}
+
+/* Signed distance (negative inside) of (qx, qy) relative to the centre to an
+ * axis-aligned shape: 0 disk of radius a, 1 ellipse with semi-axes a (x) and
+ * b (y), 2 rectangle with half-sides a and b. */
+double oracle_phi0(int shape, double a, double b, double qx, double qy) {
+    if (shape == 1) {
+        double y0 = fabs(qx), y1 = fabs(qy), e0 = a, e1 = b;
+        if (e0 < e1) { double t = e0; e0 = e1; e1 = t; t = y0; y0 = y1; y1 = t; }
+        double d = ellipse_dist_q1(e0, e1, y0, y1);
+        return (y0 / e0) * (y0 / e0) + (y1 / e1) * (y1 / e1) < 1.0 ? -d : d;
+    }
+    if (shape == 2) {
+        double dx = fabs(qx) - a, dy = fabs(qy) - b;
+        return hypot(fmax(dx, 0.0), fmax(dy, 0.0)) + fmin(fmax(dx, dy), 0.0);
+    }
+    return hypot(qx, qy) - a;
+}
+
 static double phi0(const osolid_t *s, double X, double Y) {
-    return hypot(X - s->xc, Y - s->yc) - s->R;
+    return oracle_phi0(s->shape, s->a, s->b, X - s->xc, Y - s->yc);
 }
 
 static int seterr(osim_t *m, const char *msg) {
@@ -756,7 +808,22 @@ int oracle_add_solid(void *h, double xc, double yc, double R, double rho_s, doub
     osolid_t *s = &m->s[m->ns];
     memset(s, 0, sizeof *s);
     s->xc = xc; s->yc = yc; s->R = R; s->rho_s = rho_s; s->G = G;
+    s->shape = 0; s->a = R; s->b = R;
     return m->ns++;
+}
+
+/* A solid of shape 0 (disk, radius a), 1 (ellipse, semi-axes a, b) or 2
+ * (rectangle, half-sides a, b), axis-aligned, centred at (xc, yc). */
+int oracle_add_solid_shape(void *h, int shape, double xc, double yc, double a, double b, double rho_s, double G) {
+    if (shape < 0 || shape > 2 || !(a > 0) || !(b > 0)) return seterr((osim_t *)h, "bad shape");
+    double R = shape == 0 ? a : shape == 1 ? fmax(a, b) : hypot(a, b);
+    int id = oracle_add_solid(h, xc, yc, R, rho_s, G);
+    if (id < 0) return id;
+    osim_t *m = h;
+    m->s[id].shape = shape;
+    m->s[id].a = shape == 0 ? a : a;
+    m->s[id].b = shape == 0 ? a : b;
+    return id;
 }
 
 /* Algorithm 1, initialisation: xi_0 = x on solid + band, phi = phi_0(xi_0),

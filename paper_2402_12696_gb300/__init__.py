@@ -27,7 +27,9 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NUMERIC", -4: "ERR_OV
 PRECISION = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "Fx": 3, "Fy": 4, "drho": 5,
           "xi_x": 10, "xi_y": 11, "phi": 12, "detF_dev": 14, "von_mises": 15}
-EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_init", "lbrmt_step",
+SHAPES = {"disk": 0, "ellipse": 1, "rect": 2}
+EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add_solid_shape",
+           "lbrmt_batch_add_solid_shape", "lbrmt_init", "lbrmt_step",
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
@@ -76,6 +78,8 @@ def load():
     L.lbrmt_default_config.restype = None
     L.lbrmt_create.argtypes = [cfgp, p, C.POINTER(p)]
     L.lbrmt_add_solid.argtypes = [p, i, d, d, d, d, d, C.POINTER(i)]
+    L.lbrmt_add_solid_shape.argtypes = [p, i, d, d, d, d, d, d, C.POINTER(i)]
+    L.lbrmt_batch_add_solid_shape.argtypes = [p, i, i, d, d, d, d, d, d, C.POINTER(i)]
     L.lbrmt_init.argtypes = [p]
     L.lbrmt_step.argtypes = [p, i]
     L.lbrmt_read_fields.argtypes = [p, i, i, i, p]
@@ -155,6 +159,18 @@ def lbrmt_add_solid(h, shape, cx, cy, radius, rho_s, G):
     sid = C.c_int()
     _check(h, load().lbrmt_add_solid(h, shape, cx, cy, radius, rho_s, G, C.byref(sid)))
     return sid.value
+
+
+def lbrmt_add_solid_shape(h, shape, cx, cy, a, b, rho_s, G):
+    sid = C.c_int()
+    _check(h, load().lbrmt_add_solid_shape(h, shape, cx, cy, a, b, rho_s, G, C.byref(sid)))
+    return sid.value
+
+
+def _solid_geometry(s):
+    """(shape id, a, b) of a scenario solid dict (disks: a = b = r)."""
+    shape = SHAPES[s.get("shape", "disk")]
+    return (shape, s["r"], s["r"]) if shape == 0 else (shape, s["a"], s["b"])
 
 
 def lbrmt_init(h):
@@ -246,6 +262,12 @@ def lbrmt_create_batch(cfgs, stream_ptr):
 def lbrmt_batch_add_solid(b, sim_index, shape, cx, cy, radius, rho_s, G):
     sid = C.c_int()
     _bcheck(b, load().lbrmt_batch_add_solid(b, sim_index, shape, cx, cy, radius, rho_s, G, C.byref(sid)))
+    return sid.value
+
+
+def lbrmt_batch_add_solid_shape(b, sim_index, shape, cx, cy, a, bb, rho_s, G):
+    sid = C.c_int()
+    _bcheck(b, load().lbrmt_batch_add_solid_shape(b, sim_index, shape, cx, cy, a, bb, rho_s, G, C.byref(sid)))
     return sid.value
 
 
@@ -354,7 +376,8 @@ class Simulation:
             load().lbrmt_set_use_graphs(self.h, int(bool(use_graphs)))
             load().lbrmt_set_use_tma(self.h, int(bool(use_tma)))
             for s in sc["solids"]:
-                lbrmt_add_solid(self.h, 0, s["x"], s["y"], s["r"], s["rho_s"], s["G"])
+                shape, a, b = _solid_geometry(s)
+                lbrmt_add_solid_shape(self.h, shape, s["x"], s["y"], a, b, s["rho_s"], s["G"])
             if sc["force_kind"] == 3:
                 self.set_body_force_field(sc["body_field"])
 
@@ -542,7 +565,8 @@ class Batch:
             self.b = lbrmt_create_batch(cfgs, self.stream.cuda_stream)
             for k, sc in enumerate(self.scs):
                 for s in sc["solids"]:
-                    lbrmt_batch_add_solid(self.b, k, 0, s["x"], s["y"], s["r"], s["rho_s"], s["G"])
+                    shape, a, bb = _solid_geometry(s)
+                    lbrmt_batch_add_solid_shape(self.b, k, shape, s["x"], s["y"], a, bb, s["rho_s"], s["G"])
             lbrmt_batch_init(self.b, autotune_steps)
         self.members = [_Member(self, k) for k in range(len(self.scs))]
 

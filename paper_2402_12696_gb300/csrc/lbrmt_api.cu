@@ -174,23 +174,33 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     return LBRMT_OK;
 }
 
-extern "C" lbrmt_status lbrmt_add_solid(lbrmt_sim *s, int shape, double cx, double cy, double radius,
-                                        double rho_s, double G, int *id_out) {
+extern "C" lbrmt_status lbrmt_add_solid_shape(lbrmt_sim *s, int shape, double cx, double cy, double a, double b,
+                                              double rho_s, double G, int *id_out) {
     if (!s) return LBRMT_ERR_ARG;
     if (s->inited) return fail(s, LBRMT_ERR_STATE, "solids must be added before the first step");
-    if (shape != LBRMT_SHAPE_DISK) return fail(s, LBRMT_ERR_ARG, "only disks are supported");
-    if (!(radius >= 1.0) || !(rho_s > 0) || !(G >= 0) || !std::isfinite(cx) || !std::isfinite(cy))
+    if (shape < LBRMT_SHAPE_DISK || shape > LBRMT_SHAPE_RECT) return fail(s, LBRMT_ERR_ARG, "unknown shape");
+    if (shape == LBRMT_SHAPE_DISK) b = a;
+    if (!(a >= 1.0) || !(b >= 1.0) || !(rho_s > 0) || !(G >= 0) || !std::isfinite(cx) || !std::isfinite(cy))
         return fail(s, LBRMT_ERR_ARG, "bad solid parameters");
+    // Appendix A: the solid's shear wave speed sqrt(G / rho_s) must not exceed one node per step
+    if (G > rho_s) return fail(s, LBRMT_ERR_PARAM_RANGE, "shear wave speed sqrt(G/rho_s) above the lattice speed");
+    const double radius = shape == LBRMT_SHAPE_DISK ? a : shape == LBRMT_SHAPE_ELLIPSE ? std::max(a, b) : std::hypot(a, b);
     const int margin = 4 + (int)std::ceil(radius / 4.0);
     int T = 2 * (int)std::ceil(radius) + 2 * (s->cfg.n_layers + margin) + 1;
     T = (T + 7) & ~7;
     if (T > TILE_SIDE_MAX) return fail(s, LBRMT_ERR_ARG, "solid too large for a tile");
     if ((!s->cfg.bc_x && T >= s->cfg.nx) || (!s->cfg.bc_y && T >= s->cfg.ny))
         return fail(s, LBRMT_ERR_ARG, "solid tile wider than the periodic domain");
-    SolidHost h{cx, cy, radius, rho_s, G, T, 0};
+    SolidHost h{cx, cy, radius, rho_s, G, shape, a, b, T, 0};
     s->solids.push_back(h);
     if (id_out) *id_out = (int)s->solids.size() - 1;
     return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_add_solid(lbrmt_sim *s, int shape, double cx, double cy, double radius,
+                                        double rho_s, double G, int *id_out) {
+    if (s && shape != LBRMT_SHAPE_DISK) return fail(s, LBRMT_ERR_ARG, "lbrmt_add_solid adds disks; use lbrmt_add_solid_shape");
+    return lbrmt_add_solid_shape(s, LBRMT_SHAPE_DISK, cx, cy, radius, radius, rho_s, G, id_out);
 }
 
 static lbrmt_status check_flags(lbrmt_sim *s) {
@@ -235,6 +245,7 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         org[k].offy = (float)(std::rint(((double)org[k].oy - h.yc) * 16384.0) / 16384.0);
         org[k].bx0 = org[k].by0 = 1; org[k].bx1 = org[k].by1 = 0;  // empty until initialised
         sd[k].xc = h.xc; sd[k].yc = h.yc; sd[k].R = h.R; sd[k].rho_s = h.rho_s; sd[k].G = h.G;
+        sd[k].shape = h.shape; sd[k].a = h.a; sd[k].b = h.b;
         sd[k].drho = h.rho_s - s->cfg.rho_f;
         sd[k].accel = -(1.0 - s->cfg.rho_f / h.rho_s) * s->cfg.gravity;
         const double r2 = h.R * h.R;
@@ -290,7 +301,7 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     long long total = 0;
     for (auto &h : s->solids) {
         h.off = total;
-        total += 2ll * h.T * h.T;
+        total += 3ll * h.T * h.T;  // eta_x, eta_y, phi planes
     }
     s->xi_total = total;
     const size_t rs = s->eng->real_size;

@@ -34,7 +34,7 @@ constexpr int TILE_CHOICES[4] = {16, 32, 64, 128};
 
 struct SolidSpec {
     int shape;
-    double cx, cy, r, rho_s, G;
+    double cx, cy, a, b, rho_s, G;
 };
 
 struct Member {
@@ -114,7 +114,7 @@ static lbrmt_status make_member(lbrmt_batch *b, int k) {
     lbrmt_status st = lbrmt_create(&mb.cfg, b->stream, &mb.sim);
     if (st != LBRMT_OK) return bfail(b, st, "member " + std::to_string(k) + ": create");
     for (const SolidSpec &s : mb.solids) {
-        st = lbrmt_add_solid(mb.sim, s.shape, s.cx, s.cy, s.r, s.rho_s, s.G, nullptr);
+        st = lbrmt_add_solid_shape(mb.sim, s.shape, s.cx, s.cy, s.a, s.b, s.rho_s, s.G, nullptr);
         if (st != LBRMT_OK) return member_fail(b, k, st);
     }
     st = lbrmt_init(mb.sim);
@@ -314,15 +314,21 @@ extern "C" lbrmt_status lbrmt_create_batch(const lbrmt_config *cfgs, int nsim, v
     return LBRMT_OK;
 }
 
-extern "C" lbrmt_status lbrmt_batch_add_solid(lbrmt_batch *b, int sim_index, int shape, double cx, double cy,
-                                              double radius, double rho_s, double G, int *solid_id_out) {
+extern "C" lbrmt_status lbrmt_batch_add_solid_shape(lbrmt_batch *b, int sim_index, int shape, double cx, double cy,
+                                                    double a, double bb, double rho_s, double G, int *solid_id_out) {
     if (!b || sim_index < 0 || sim_index >= (int)b->m.size()) return LBRMT_ERR_ARG;
     if (b->inited) return bfail(b, LBRMT_ERR_STATE, "solids must be added before lbrmt_batch_init");
     Member &mb = b->m[sim_index];
-    lbrmt_status st = lbrmt_add_solid(mb.sim, shape, cx, cy, radius, rho_s, G, solid_id_out);
+    lbrmt_status st = lbrmt_add_solid_shape(mb.sim, shape, cx, cy, a, bb, rho_s, G, solid_id_out);
     if (st != LBRMT_OK) return member_fail(b, sim_index, st);
-    mb.solids.push_back(SolidSpec{shape, cx, cy, radius, rho_s, G});
+    mb.solids.push_back(SolidSpec{shape, cx, cy, a, shape == LBRMT_SHAPE_DISK ? a : bb, rho_s, G});
     return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_batch_add_solid(lbrmt_batch *b, int sim_index, int shape, double cx, double cy,
+                                              double radius, double rho_s, double G, int *solid_id_out) {
+    if (b && shape != LBRMT_SHAPE_DISK) return bfail(b, LBRMT_ERR_ARG, "lbrmt_batch_add_solid adds disks");
+    return lbrmt_batch_add_solid_shape(b, sim_index, LBRMT_SHAPE_DISK, cx, cy, radius, radius, rho_s, G, solid_id_out);
 }
 
 extern "C" lbrmt_status lbrmt_batch_init(lbrmt_batch *b, int autotune_steps) {

@@ -68,7 +68,9 @@ template <> __device__ __forceinline__ float pick<float>(double, float f) { retu
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 struct SolidDesc {
-    double xc, yc, R, rho_s, G;
+    double xc, yc, R, rho_s, G;  // R: disk radius (circumscribed radius of other shapes)
+    int shape;                   // 0 disk, 1 axis-aligned ellipse, 2 axis-aligned rectangle
+    double a, b;                 // semi-axes / half-sides along x and y
     double r2lo, drho, accel;   // R^2 - (double)(float)R^2, rho_s - rho_f, -(1 - rho_f/rho_s) g
     float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f;
     int T;
@@ -447,13 +449,70 @@ template <> __device__ __forceinline__ double fma_rn<double>(double a, double b,
 template <class R>
 struct Rsq {
     R hi, lo, rad;
+    int shape;
+    double a, b;
     __device__ __forceinline__ Rsq() {}
     __device__ __forceinline__ explicit Rsq(const SolidDesc &sd) {
         hi = pick<R>(sd.R * sd.R, sd.r2hi_f);
         lo = pick<R>(0.0, sd.r2lo_f);
         rad = pick<R>(sd.R, sd.R_f);
+        shape = sd.shape;
+        a = sd.a;
+        b = sd.b;
     }
 };
+
+// Distance from (y0, y1) >= 0 to the ellipse (x/e0)^2 + (y/e1)^2 = 1, e0 >= e1:
+// the closest point is e_i^2 y_i / (t + e_i^2) for the root t of
+// sum (e_i y_i / (t + e_i^2))^2 = 1 (Eberly's characterisation).  In s = t / e1^2
+// the function is decreasing and convex on the bracket [z1 - 1, s1], so Newton
+// steps from the bracket's left end (where it is >= 0) rise monotonically to the
+// root; they stop when they no longer move or leave the bracket.
+__device__ inline double ellipse_distance_q1(double e0, double e1, double y0, double y1) {
+    if (y1 > 0.0) {
+        if (y0 > 0.0) {
+            const double z0 = y0 / e0, z1 = y1 / e1, g = z0 * z0 + z1 * z1 - 1.0;
+            if (g == 0.0) return 0.0;
+            const double r0 = (e0 / e1) * (e0 / e1), n0 = r0 * z0;
+            const double hi = g < 0.0 ? 0.0 : hypot(n0, z1) - 1.0;
+            double s = z1 - 1.0;
+            for (int it = 0; it < 100; it++) {
+                const double ia = 1.0 / (s + r0), ib = 1.0 / (s + 1.0);
+                const double ra = n0 * ia, rb = z1 * ib, f = ra * ra + rb * rb - 1.0;
+                if (!(f > 0.0)) break;
+                const double df = -2.0 * (ra * ra * ia + rb * rb * ib);
+                const double sn = s - f / df;
+                if (!(sn > s) || sn > hi) break;
+                s = sn;
+            }
+            return hypot(r0 * y0 / (s + r0) - y0, y1 / (s + 1.0) - y1);
+        }
+        return fabs(y1 - e1);
+    }
+    const double num = e0 * y0, den = e0 * e0 - e1 * e1;
+    if (num < den) {
+        const double x = num / den;
+        return hypot(e0 * x - y0, e1 * sqrt(1.0 - x * x));
+    }
+    return fabs(y0 - e0);
+}
+
+// Signed distance (negative inside) of q (relative to the centre) to the
+// axis-aligned ellipse (shape 1, semi-axes a, b) or rectangle (shape 2,
+// half-sides a, b), in double precision.
+__device__ inline double shape_sdf(int shape, double a, double b, double qx, double qy) {
+    if (shape == 2) {
+        const double dx = fabs(qx) - a, dy = fabs(qy) - b;
+        return hypot(fmax(dx, 0.0), fmax(dy, 0.0)) + fmin(fmax(dx, dy), 0.0);
+    }
+    double y0 = fabs(qx), y1 = fabs(qy), e0 = a, e1 = b;
+    if (e0 < e1) {
+        double t = e0; e0 = e1; e1 = t;
+        t = y0; y0 = y1; y1 = t;
+    }
+    const double d = ellipse_distance_q1(e0, e1, y0, y1);
+    return (y0 / e0) * (y0 / e0) + (y1 / e1) * (y1 / e1) < 1.0 ? -d : d;
+}
 
 // Level set phi_0 of a disk at a tile node: with p = l + off (exact) and eta,
 // phi = |p + eta| - R = (|p|^2 - R^2 + 2 p.eta + |eta|^2) / (|p + eta| + R),
@@ -461,6 +520,10 @@ struct Rsq {
 // phi keeps its relative precision near the interface.
 template <class R>
 __device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const Frame &fr, const Rsq<R> &q) {
+    if (q.shape != 0) {  // ellipses and rectangles: q = eta + l + off, exact in double
+        const double X = ((double)lx + (double)fr.offx) + (double)ex, Y = ((double)ly + (double)fr.offy) + (double)ey;
+        return R(shape_sdf(q.shape, q.a, q.b, X, Y));
+    }
     const R px = add_rn<R>(R(lx), R(fr.offx)), py = add_rn<R>(R(ly), R(fr.offy));  // exact
     const R a = mul_rn<R>(px, px), ea = fma_rn<R>(px, px, -a);
     const R b = mul_rn<R>(py, py), eb = fma_rn<R>(py, py, -b);
@@ -554,8 +617,10 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     const Rsq<R> rq(sd);
     R *Xo = a.xi_out + sd.off;
     R *Yo = Xo + TT;
+    R *Po = Yo + TT;  // phi^{n+1} of the tile nodes (third plane), written by the relabel
     const R *Xi = a.init ? nullptr : a.xi_in + sd.off;
     const R *Yi = a.init ? nullptr : Xi + TT;
+    const R *Pi = a.init ? nullptr : Yi + TT;  // phi^n, stored by the previous step's relabel
     const R eps = pick<R>(sp.eps, sp.eps_f);
     if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
     if (threadIdx.x < 2) nlist[threadIdx.x] = 0;
@@ -589,7 +654,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
             const int k = iy * T + ix;
             const R ex = Xi[k], ey = Yi[k];
             if (!(ex == ex)) continue;
-            const R phi = phi_eta(ex, ey, ix, iy, fi, rq);
+            const R phi = Pi[k];
             if (!(phi < eps) || !domain_cell(sp, gx, gy)) continue;
             if (lx < 0 || ly < 0 || lx >= T || ly >= T) { atomicOr(a.err, ERR_TILE_OVERFLOW); continue; }
             R rho, u, v;
@@ -713,8 +778,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                     const int k0 = iy * T + ix;
                     const R Xe = Xi[k0 + 1], Xw = Xi[k0 - 1], Xn = Xi[k0 + T], Xs = Xi[k0 - T];
                     if (Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs) {
-                        const R pe = phi_eta(Xe, Yi[k0 + 1], ix + 1, iy, fi, rq), pw = phi_eta(Xw, Yi[k0 - 1], ix - 1, iy, fi, rq);
-                        const R pn = phi_eta(Xn, Yi[k0 + T], ix, iy + 1, fi, rq), ps = phi_eta(Xs, Yi[k0 - T], ix, iy - 1, fi, rq);
+                        const R pe = Pi[k0 + 1], pw = Pi[k0 - 1], pn = Pi[k0 + T], ps = Pi[k0 - T];
                         const R gxp = (pe - pw) / R(2), gyp = (pn - ps) / R(2);
                         const R nn = rsqrt_<R>(gxp * gxp + gyp * gyp);
                         if (nn > R(0)) { use_n = true; nhx = gxp / nn; nhy = gyp / nn; }
@@ -739,12 +803,15 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
             const int lx = x0 + wk.c, ly = y0 + wk.r, t = ly * T + lx;
             if (lab[t] >= 0) {
                 bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
-                if (phi_eta(Xo[t], Yo[t], lx, ly, fo, rq) < eps) {
+                const R phi = phi_eta(Xo[t], Yo[t], lx, ly, fo, rq);
+                Po[t] = phi;
+                if (phi < eps) {
                     bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
                 }
             } else {
                 Xo[t] = nanv<R>();
                 Yo[t] = nanv<R>();
+                Po[t] = nanv<R>();
             }
         }
     }
@@ -937,7 +1004,7 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 const R *Xs = a.xi + soff[ks];
                 X = Xs[ly * T + lx];
                 Y = Xs[T * T + ly * T + lx];
-                if (X == X) P = phi_eta(X, Y, lx, ly, fr, srq[ks]);
+                if (X == X) P = Xs[2 * T * T + ly * T + lx];  // the stored phi
             }
             sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
         }
@@ -1366,9 +1433,9 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
         // xi = eta + l + off + X_c
         if (kind == 0) v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
         else if (kind == 1) v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
-        else if (kind == 2) v = (double)phi_eta(X, Y, lx, ly, fr, rq);
+        else if (kind == 2) v = (double)xi[sd.off + 2 * T * T + t];
         else {
-            if (!(phi_eta(X, Y, lx, ly, fr, rq) < -R(PHI_TIE))) continue;
+            if (!(xi[sd.off + 2 * T * T + t] < -R(PHI_TIE))) continue;
             R ddet, vm;
             if (!node_deformation<R>(xi + sd.off, xi + sd.off + T * T, T, lx, ly, fr, pick<R>(sd.G, sd.G_f), ddet, vm))
                 continue;
@@ -1399,9 +1466,9 @@ __global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, con
         const int lx = t % T, ly = t / T;
         const int gx = o.x + lx, gy = o.y + ly;
         if (!in_box(fr, lx, ly)) continue;
-        const R X = xi[sd.off + t], Y = xi[sd.off + T * T + t];
+        const R X = xi[sd.off + t];
         if (!(X == X) || !domain_cell(sp, gx, gy)) continue;
-        const R phi = phi_eta(X, Y, lx, ly, fr, rq);
+        const R phi = xi[sd.off + 2 * T * T + t];
         if (!(phi < eps)) continue;
         R rho, u, v;
         node_moments<R, S>(sp, f, carry, reg, pool, wrapi(gx, sp.nx), wrapi(gy, sp.ny), rho, u, v);

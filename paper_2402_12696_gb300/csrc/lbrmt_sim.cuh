@@ -8,7 +8,9 @@
 #include "lbrmt_engine.cuh"
 
 struct SolidHost {
-    double xc, yc, R, rho_s, G;
+    double xc, yc, R, rho_s, G;  // R: disk radius, circumscribed radius of other shapes
+    int shape;
+    double a, b;
     int T;
     long long off;
 };

@@ -208,3 +208,75 @@ ALL = {
     "mixing_4096": mixing_4096,
     "adjoint_ldc_256": adjoint_ldc_256,
 }
+
+
+def _shape_radius(s):
+    """Circumscribed radius of a solid dict."""
+    shape = s.get("shape", "disk")
+    if shape == "disk":
+        return s["r"]
+    return max(s["a"], s["b"]) if shape == "ellipse" else math.hypot(s["a"], s["b"])
+
+
+def place_shapes(rng, sc, specs, rho_lo, rho_hi, g_lo, g_hi, max_tries=400):
+    """Rejection-sample non-overlapping solids of the given shapes (dicts with
+    'shape' and 'a', 'b' or 'r'), using their circumscribed radii for the
+    surface gap >= 2 eps + 1 and the wall gap >= eps + 2."""
+    nx, ny = sc["nx"], sc["ny"]
+    px, py = sc["wall_x"] == 0, sc["wall_y"] == 0
+    gap, wall_gap = 2 * EPS + 1, EPS + 2
+    placed = sc["solids"]
+    for spec in specs:
+        r = _shape_radius(spec)
+        rho_s = float(rng.uniform(rho_lo, rho_hi))
+        G = float(rng.uniform(g_lo, g_hi))
+        for _t in range(max_tries):
+            lo_x, hi_x = (0.0, float(nx)) if px else (r + wall_gap - 0.5, nx - 0.5 - r - wall_gap)
+            lo_y, hi_y = (0.0, float(ny)) if py else (r + wall_gap - 0.5, ny - 0.5 - r - wall_gap)
+            if hi_x <= lo_x or hi_y <= lo_y:
+                break
+            x, y = float(rng.uniform(lo_x, hi_x)), float(rng.uniform(lo_y, hi_y))
+            if all(math.hypot(_min_image(x - s["x"], nx, px), _min_image(y - s["y"], ny, py))
+                   >= r + _shape_radius(s) + gap for s in placed):
+                placed.append(dict(spec, x=x, y=y, r=r, rho_s=rho_s, G=G))
+                break
+    return sc
+
+
+def shapes_small(seed=0, nx=128, ny=96, gravity=2e-4):
+    """128x96 box, periodic x, walls y, tau 0.7, gravity: a horizontal and a
+    vertical ellipse, a square, a rectangle and a disk, rho_s~U[1.1,1.6],
+    G~U[0.005,0.02]."""
+    rng = np.random.default_rng(3000 + seed)
+    sc = _base(nx, ny, 0, 1, 0.7, gravity=gravity, name=f"shapes_small_s{seed}")
+    specs = [{"shape": "ellipse", "a": 11.0, "b": 6.0}, {"shape": "ellipse", "a": 5.0, "b": 10.0},
+             {"shape": "rect", "a": 6.0, "b": 6.0}, {"shape": "rect", "a": 9.0, "b": 5.0},
+             {"shape": "disk", "r": 7.0}]
+    return place_shapes(rng, sc, specs, 1.1, 1.6, 0.005, 0.02)
+
+
+def mixing_ellipses(seed=0, nx=800, ny=450, a=8.0, b=4.0, gravity=2e-5, G=0.05):
+    """Mixing of 506 ellipses (Sec. 4, the 800x450 case): walls on all sides,
+    tau 1, 242 heavier (rho_s 1.25) and 264 lighter (rho_s 0.83) ellipses with
+    semi-axes a x b, lying and standing alternately on a 23 x 22 lattice (each
+    jittered by up to half a node).  The paper gives neither the ellipse size
+    nor gravity, and its G = 1 is in physical units (in lattice units it would
+    break the shear-wave limit G <= rho_s of its Appendix A): a = 8, b = 4,
+    g = 2e-5 and G = 0.05 (shear wave speed 0.2-0.25 nodes per step) are chosen."""
+    rng = np.random.default_rng(4000 + seed)
+    sc = _base(nx, ny, 1, 1, 1.0, gravity=gravity, name=f"mixing_ellipses_s{seed}")
+    heavy = np.zeros(506, dtype=bool)
+    heavy[rng.choice(506, 242, replace=False)] = True
+    m = 11.5
+    xs = m + np.arange(23) * (nx - 1 - 2 * m) / 22.0
+    ys = m + np.arange(22) * (ny - 1 - 2 * m) / 21.0
+    k = 0
+    for iy, y in enumerate(ys):
+        for ix, x in enumerate(xs):
+            lying = (ix + iy) % 2 == 0
+            sc["solids"].append({"shape": "ellipse", "a": a if lying else b, "b": b if lying else a,
+                                 "r": max(a, b), "x": float(x + rng.uniform(-0.5, 0.5)),
+                                 "y": float(y + rng.uniform(-0.5, 0.5)),
+                                 "rho_s": 1.25 if heavy[k] else 0.83, "G": float(G)})
+            k += 1
+    return sc

@@ -87,6 +87,7 @@ CASES = {
     "mixing_small_1": lambda: scenarios.mixing_small(1),
     "contact_pair": lambda: scenarios.contact_pair(gap=0.8, nx=96, ny=64),
     "ldc_body_field_64": lambda: scenarios.adjoint_ldc(64, r=12, body=scenarios.smooth_body_field(0, 64, amp=1e-4)),
+    "shapes_small_0": lambda: scenarios.shapes_small(0),
 }
 
 

@@ -515,3 +515,76 @@ def test_initial_solid_is_undeformed():
         assert np.abs(d[m]).max() < 1e-13 and np.abs(vm[m]).max() < 1e-14
         st = o.solid_stats(s)
         assert st[6] < 1e-13 and st[7] < 1e-13
+
+
+def _boundary_points(shape, a, b, n=400000):
+    t = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    if shape == "ellipse":
+        return np.stack([a * np.cos(t), b * np.sin(t)], 1)
+    # rectangle perimeter, uniformly
+    per = 4 * (a + b)
+    s = np.linspace(0, per, n, endpoint=False)
+    pts = np.empty((n, 2))
+    for k, v in enumerate(s):
+        if v < 2 * a:
+            pts[k] = (-a + v, -b)
+        elif v < 2 * a + 2 * b:
+            pts[k] = (a, -b + (v - 2 * a))
+        elif v < 4 * a + 2 * b:
+            pts[k] = (a - (v - 2 * a - 2 * b), b)
+        else:
+            pts[k] = (-a, b - (v - 4 * a - 2 * b))
+    corners = np.array([[-a, -b], [a, -b], [a, b], [-a, b]])  # the nearest point may be a corner
+    return np.concatenate([pts, corners])
+
+
+@pytest.mark.parametrize("shape,a,b", [("ellipse", 11.0, 6.0), ("ellipse", 4.0, 9.5), ("rect", 9.0, 5.0),
+                                       ("rect", 6.0, 6.0)])
+def test_shape_signed_distance_brute_force(shape, a, b):
+    # phi_0 is the signed distance to the boundary (negative inside): checked
+    # against the nearest of 4e5 boundary samples (spacing < 2e-4, so the
+    # sampled distance is within ~1e-8 of the exact one away from the samples)
+    rng = np.random.default_rng(7)
+    pts = _boundary_points(shape, a, b)
+    q = rng.uniform(-1.6 * max(a, b), 1.6 * max(a, b), size=(60, 2))
+    for qx, qy in q:
+        d = np.sqrt(((pts - (qx, qy)) ** 2).sum(1)).min()
+        inside = ((qx / a) ** 2 + (qy / b) ** 2 < 1) if shape == "ellipse" else (abs(qx) < a and abs(qy) < b)
+        ref = -d if inside else d
+        assert abs(oracle.phi0(shape, a, b, qx, qy) - ref) < 1e-6, (qx, qy)
+
+
+def test_shape_signed_distance_special_cases():
+    # an ellipse with equal semi-axes is the disk; points on the axes and at corners
+    for qx, qy in [(0.3, -2.0), (7.5, 1.0), (-12.0, 3.0), (0.0, 0.0)]:
+        assert abs(oracle.phi0("ellipse", 6, 6, qx, qy) - (np.hypot(qx, qy) - 6)) < 1e-12
+        assert abs(oracle.phi0("disk", 6, 6, qx, qy) - (np.hypot(qx, qy) - 6)) < 1e-15
+    assert oracle.phi0("ellipse", 10, 5, 0, 0) == -5.0
+    assert abs(oracle.phi0("ellipse", 10, 5, 12, 0) - 2.0) < 1e-15
+    assert abs(oracle.phi0("ellipse", 10, 5, 0, -7) - 2.0) < 1e-15
+    assert abs(oracle.phi0("rect", 4, 2, 5, 3) - np.sqrt(2)) < 1e-15  # off a corner
+    assert oracle.phi0("rect", 4, 2, 1, 0.5) == -1.5                  # inside: distance to the nearer side
+    assert oracle.phi0("rect", 4, 2, 6, 0) == 2.0
+
+
+def test_shapes_initial_area_and_rest():
+    # the initial solid set of each shape covers its area (to the perimeter's
+    # order), and rest stays an exact fixed point with non-circular solids
+    sc = scenarios.shapes_small(0, gravity=0.0)
+    o = oracle.Oracle(sc)
+    for k, s in enumerate(sc["solids"]):
+        lab = o.field("label", k)
+        n = int((lab == 0).sum())
+        shape = s.get("shape", "disk")
+        area = {"disk": np.pi * s["r"] ** 2, "ellipse": np.pi * s.get("a", 0) * s.get("b", 0),
+                "rect": 4 * s.get("a", 0) * s.get("b", 0)}[shape]
+        per = 2 * np.pi * _shape_r(s) if shape != "rect" else 4 * (s["a"] + s["b"])
+        assert abs(n - area) < per, (shape, n, area)
+    f0 = o.populations()
+    o.step(25)
+    assert np.abs(o.populations() - f0).max() < 1e-12
+    assert np.abs(o.field("ux")).max() < 1e-13 and np.abs(o.field("uy")).max() < 1e-13
+
+
+def _shape_r(s):
+    return s["r"] if s.get("shape", "disk") == "disk" else max(s["a"], s["b"])
