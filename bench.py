@@ -244,6 +244,46 @@ def bench_shapes(args, dev):
     return out
 
 
+def study_convergence(args):
+    """Volume conservation under grid refinement (Sec. 4.1): the cavity with a
+    disk at L = 80, 160, 320, 640 run to the same physical time; max and
+    lambda-weighted mean of |det F - 1| over the solid at the end, and the
+    observed convergence rates between successive L (the paper reports 9.2 %
+    at L = 80, 0.3 % at L = 640 and a rate of about 1.4)."""
+    import torch
+    import paper_2402_12696_gb300 as pkg
+    dev = torch.device("cuda:0")
+    rows = []
+    for L in [int(v) for v in args.study_levels.split(",")]:
+        sc = scenarios.ldc_convergence(L)
+        steps = sc["steps"] if args.study_steps_scale == 1.0 else int(sc["steps"] * args.study_steps_scale)
+        sim = pkg.Simulation(sc, precision=args.precision, device="cuda:0")
+        sim.init()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        done = 0
+        while done < steps:
+            n = min(20000, steps - done)
+            sim.step(n)
+            done += n
+        sim.sync()
+        dt = time.perf_counter() - t0
+        st = sim.solid_stats()[0]
+        rows.append({"L": L, "steps": steps, "lid_u": sc["lid_u"], "G": sc["solids"][0]["G"],
+                     "max_detF_dev": float(st[6]), "mean_detF_dev": float(st[7]),
+                     "centroid": [float(st[1]) / L, float(st[2]) / L], "wall_s": dt,
+                     "mlups": L * L * steps / dt / 1e6})
+        sim.close()
+    for a, b in zip(rows, rows[1:]):
+        for k in ("max_detF_dev", "mean_detF_dev"):
+            if a[k] > 0 and b[k] > 0:
+                b["rate_" + k] = float(np.log(a[k] / b[k]) / np.log(b["L"] / a["L"]))
+    print(json.dumps({"study": "convergence", "workload": "cavity with a disk r = 0.2L at (0.6L, 0.5L), Re 100, "
+                      "tau 0.8, G = 0.1 rho U^2, T = 2000 (L/80)^2 (before the disk nears a wall)",
+                      "precision": args.precision, "rows": rows}),
+          flush=True)
+
+
 def bench_lbrmt(args):
     import torch
     import paper_2402_12696_gb300 as pkg
@@ -427,11 +467,18 @@ def main():
                     help="registry / LB tile width (height 256 / tile_x); 0: autotuned")
     ap.add_argument("--lb-loads", default="tma", choices=["tma", "direct"],
                     help="LB kernel loads when the tile shape is fixed: tensor-memory staging or direct")
+    ap.add_argument("--study", default="", choices=["", "convergence"],
+                    help="run a study instead of the benchmark (prints its own JSON line)")
+    ap.add_argument("--study-levels", default="80,160,320,640")
+    ap.add_argument("--study-steps-scale", type=float, default=1.0)
     ap.add_argument("--shapes-steps", type=int, default=200,
                     help="timed steps of the 506-ellipse workload (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=3000,
                     help="steps of the adjoint-cost measurement (0: skip)")
     args = ap.parse_args()
+    if args.study == "convergence":
+        study_convergence(args)
+        return
     if args.impl == "reference":
         bench_reference(args)
     else:

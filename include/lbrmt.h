@@ -96,6 +96,9 @@ typedef struct {
     int rmax;                   /* largest extrapolation window half-width (>= 2) */
     int tile_x;                 /* registry / LB tile width: 16, 32, 64 or 128 nodes (height 256 /
                                    tile_x); 0 selects 32.  Results do not depend on it. */
+    double deform_margin;       /* room a solid's tile leaves for deformation beyond its band, as a
+                                   fraction of its (circumscribed) radius (default 0.25; a band that
+                                   reaches the tile edge raises LBRMT_ERR_OVERFLOW) */
     lbrmt_alloc_fn alloc;       /* optional device allocator */
     lbrmt_free_fn free;
     void *alloc_ctx;

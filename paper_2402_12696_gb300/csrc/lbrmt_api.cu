@@ -69,6 +69,7 @@ extern "C" void lbrmt_default_config(lbrmt_config *c) {
     c->max_solids_per_tile = KMAX;
     c->rmax = 11;
     c->tile_x = 32;
+    c->deform_margin = 0.25;
 }
 
 extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream, lbrmt_sim **out) {
@@ -83,6 +84,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (c.lid_u != 0.0 && c.bc_y != LBRMT_WALL) return LBRMT_ERR_ARG;
     if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > LBRMT_FORCE_FIELD) return LBRMT_ERR_ARG;
     if (c.precision < LBRMT_FP32 || c.precision > LBRMT_BF16_STORE) return LBRMT_ERR_ARG;
+    if (!(c.deform_margin >= 0.0) || c.deform_margin > 4.0) return LBRMT_ERR_ARG;
     const int tx = c.tile_x == 0 ? 32 : c.tile_x;
     if (tx != 16 && tx != 32 && tx != 64 && tx != 128) return LBRMT_ERR_ARG;
 
@@ -185,7 +187,7 @@ extern "C" lbrmt_status lbrmt_add_solid_shape(lbrmt_sim *s, int shape, double cx
     // Appendix A: the solid's shear wave speed sqrt(G / rho_s) must not exceed one node per step
     if (G > rho_s) return fail(s, LBRMT_ERR_PARAM_RANGE, "shear wave speed sqrt(G/rho_s) above the lattice speed");
     const double radius = shape == LBRMT_SHAPE_DISK ? a : shape == LBRMT_SHAPE_ELLIPSE ? std::max(a, b) : std::hypot(a, b);
-    const int margin = 4 + (int)std::ceil(radius / 4.0);
+    const int margin = 4 + (int)std::ceil(radius * s->cfg.deform_margin);
     int T = 2 * (int)std::ceil(radius) + 2 * (s->cfg.n_layers + margin) + 1;
     T = (T + 7) & ~7;
     if (T > TILE_SIDE_MAX) return fail(s, LBRMT_ERR_ARG, "solid too large for a tile");

@@ -15,6 +15,7 @@ struct LaunchInfo {
     int force_blocks;    // persistent grid of K3
     int rmt_smem;        // dynamic shared memory of K2
     int force_smem;      // dynamic shared memory of K3
+    bool rmt_big = false; // K2 with 1024-thread CTAs (few solids, FP32 arithmetic)
     bool tma = false;    // tensor maps of the populations and half-force are valid
     bool use_tma = true; // K1 with TMA staging (else the direct-load kernel)
     int lb_blocks = 0, lb_smem = 0;
@@ -136,6 +137,14 @@ struct Engine {
         cudaError_t e = cudaFuncSetAttribute(rmt_solid_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              RMT_SMEM_MAX);
         if (e != cudaSuccess) return e;
+        int nsm0 = 0, dev0 = 0;
+        cudaGetDevice(&dev0);
+        cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0);
+        li->rmt_big = sizeof(R) == 4 && sp.nsolids > 0 && 2 * sp.nsolids <= nsm0;
+        if (li->rmt_big) {
+            e = cudaFuncSetAttribute(rmt_solid_kernel_big<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX);
+            if (e != cudaSuccess) return e;
+        }
         e = cudaFuncSetAttribute(force_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  force_smem_max() * (int)sizeof(R));
         if (e != cudaSuccess) return e;
@@ -263,9 +272,14 @@ struct Engine {
         return cudaGetLastError();
     }
 
+    static void launch_rmt(const SimParams &sp, const LaunchInfo &li, const RmtArgs<R, S> &a, cudaStream_t st) {
+        if (li.rmt_big) rmt_solid_kernel_big<R, S><<<sp.nsolids, RMT_THREADS_BIG, li.rmt_smem, st>>>(sp, a);
+        else rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, a);
+    }
+
     static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
         if (sp.nsolids > 0) {
-            rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, 0, 1));
+            launch_rmt(sp, li, rmt_args(d, 0, 1), st);
             force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 1));
         }
         dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
@@ -278,7 +292,7 @@ struct Engine {
                             cudaStream_t st, cudaEvent_t *ev, void *tape) {
         const int p = parity, q = 1 - parity;
         if (ev) cudaEventRecord(ev[0], st);
-        if (sp.nsolids > 0) rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, rmt_args(d, p, 0));
+        if (sp.nsolids > 0) launch_rmt(sp, li, rmt_args(d, p, 0), st);
         if (ev) cudaEventRecord(ev[1], st);
         if (sp.nsolids > 0) force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, q, p));
         if (ev) cudaEventRecord(ev[2], st);

@@ -35,7 +35,7 @@ constexpr int RMT_THREADS = 256;
 #define RMT_MIN_BLOCKS 4
 #endif
 constexpr int LIST_CAP = 2048;              // per-layer target list in shared memory
-constexpr int TILE_SIDE_MAX = 240;          // largest solid tile side
+constexpr int TILE_SIDE_MAX = 448;          // largest solid tile side (byte labels + lists in shared memory)
 constexpr int RMT_SMEM_MAX = ((TILE_SIDE_MAX * TILE_SIDE_MAX + 15) & ~15) + 8 * LIST_CAP;
 constexpr int POOL_STRIDE = 3 * TILE_N;     // per tile: Fx, Fy, drho planes
 // Tie rules shared with the method's definition: a node with |phi| <= PHI_TIE
@@ -878,6 +878,15 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
 
 template <class R, class S>
 __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2) rmt_solid_kernel(SimParams sp, RmtArgs<R, S> a) {
+    rmt_solid<R, S>(sp, a, a.order ? a.order[blockIdx.x] : (int)blockIdx.x);
+}
+
+// The same with 1024-thread CTAs, for simulations with fewer solids than SMs:
+// each solid's layer chain then runs on four times the threads.  Same register
+// budget as the 256-thread kernel (64), hence the same instructions per node.
+constexpr int RMT_THREADS_BIG = 1024;
+template <class R, class S>
+__global__ void __launch_bounds__(RMT_THREADS_BIG, 1) rmt_solid_kernel_big(SimParams sp, RmtArgs<R, S> a) {
     rmt_solid<R, S>(sp, a, a.order ? a.order[blockIdx.x] : (int)blockIdx.x);
 }
 

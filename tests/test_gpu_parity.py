@@ -233,3 +233,22 @@ def test_deformation_fields_and_stats(prec):
         assert abs(st[6] - so[6]) <= tol * max(so[6], 1e-6) and abs(st[7] - so[7]) <= tol * max(so[7], 1e-6)
     sim.close()
     ref.close()
+
+
+def test_convergence_study_case_matches_oracle():
+    # the L = 80 case of the grid-convergence study, its full 2000 steps in
+    # FP64: fields and the det F statistics the study reports
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.ldc_convergence(80)
+    sim = pkg.Simulation(sc, precision="fp64")
+    ref = oracle.Oracle(sc)
+    sim.step(sc["steps"])
+    ref.step(sc["steps"])
+    r = compare(sim, ref, sc)
+    for k in ("rho", "u", "xi", "F"):
+        assert r[k] < 1e-8, (k, r)
+    st, so = sim.solid_stats()[0], ref.solid_stats(0)
+    assert abs(st[6] - so[6]) < 1e-8 * so[6] and abs(st[7] - so[7]) < 1e-8 * so[7], (st, so)
+    assert abs(st[1] - so[1]) < 1e-9 * 80 and abs(st[2] - so[2]) < 1e-9 * 80
+    sim.close()
+    ref.close()
