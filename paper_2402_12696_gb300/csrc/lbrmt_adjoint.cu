@@ -207,6 +207,11 @@ static lbrmt_status backward_impl(lbrmt_sim *s, const double *dLdc, double *dLdG
     const int fblocks = nsm * std::max(per, 1);
     const int rsm = ((s->li.tmax * s->li.tmax + 15) & ~15);
     ok(cudaFuncSetAttribute(rmt_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX));
+    // the forward's choice: 1024-thread CTAs for FP32 arithmetic and few solids
+    constexpr bool can_big = sizeof(R) == 4;
+    const bool big = can_big && s->li.rmt_big;
+    if constexpr (can_big)
+        if (big) ok(cudaFuncSetAttribute(rmt_adjoint_kernel_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX));
     const int lblocks = (int)std::min<long long>((P + 255) / 256, (long long)nsm * 8);
     if (e != cudaSuccess) return lbrmt_internal_fail(s, LBRMT_ERR_CUDA, std::string("adjoint setup: ") + cudaGetErrorString(e));
 
@@ -281,7 +286,13 @@ static lbrmt_status backward_impl(lbrmt_sim *s, const double *dLdc, double *dLdG
                 ra.fb = fb[p];
                 ra.cb = cb[p];
                 ra.solids = d.solids;
-                rmt_adjoint_kernel<R><<<S, RMT_THREADS, rsm, st>>>(sp, ra);
+                bool launched = false;
+                if constexpr (can_big)
+                    if (big) {
+                        rmt_adjoint_kernel_big<R><<<S, RMT_THREADS_BIG, rsm, st>>>(sp, ra);
+                        launched = true;
+                    }
+                if (!launched) rmt_adjoint_kernel<R><<<S, RMT_THREADS, rsm, st>>>(sp, ra);
                 ok(cudaMemsetAsync(xib[q], 0, xib_bytes, st));
             }
             ok(cudaGetLastError());

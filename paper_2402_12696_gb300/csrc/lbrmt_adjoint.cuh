@@ -585,7 +585,21 @@ __device__ void extrapolate_adjoint(const SimParams &sp, const signed char *lab,
 }
 
 template <class R>
+__device__ void rmt_adjoint_solid(const SimParams &sp, const RmtAdjArgs<R> &a);
+
+template <class R>
 __global__ void __launch_bounds__(RMT_THREADS) rmt_adjoint_kernel(SimParams sp, RmtAdjArgs<R> a) {
+    rmt_adjoint_solid<R>(sp, a);
+}
+
+// 1024-thread CTAs for FP32 simulations with few solids (as the forward kernel).
+template <class R>
+__global__ void __launch_bounds__(RMT_THREADS_BIG, 1) rmt_adjoint_kernel_big(SimParams sp, RmtAdjArgs<R> a) {
+    rmt_adjoint_solid<R>(sp, a);
+}
+
+template <class R>
+__device__ void rmt_adjoint_solid(const SimParams &sp, const RmtAdjArgs<R> &a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int bb[4];
     const int s = blockIdx.x;
