@@ -101,10 +101,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     SimParams &sp = s->sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.nx = c.nx; sp.ny = c.ny; sp.wall_x = c.bc_x; sp.wall_y = c.bc_y;
-    sp.tx = tx; sp.ty = TILE_N / tx;
-    sp.lx = __builtin_ctz((unsigned)sp.tx); sp.ly = __builtin_ctz((unsigned)sp.ty);
-    sp.ntx = (c.nx + sp.tx - 1) / sp.tx;
-    sp.nty = (c.ny + sp.ty - 1) / sp.ty;
+    set_tile_params(sp, tx);
     sp.P = (long long)c.nx * c.ny;
     sp.tau = c.tau; sp.rho_f = c.rho_f; sp.lid_u = c.lid_u; sp.eps = c.eps; sp.eta = c.eta;
     sp.gravity = c.gravity; sp.force_kind = c.force_kind; sp.fa0 = c.force_a[0]; sp.fa1 = c.force_a[1];
@@ -115,10 +112,15 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
 
     // registry and pool sized for the largest tile count over the tile shapes, so
     // the shape can change later (lbrmt_set_tile_x) without reallocation
-    size_t ntiles = 0;
-    for (int w = 16; w <= 128; w *= 2)
-        ntiles = std::max(ntiles, (size_t)((c.nx + w - 1) / w) * (size_t)((c.ny + TILE_N / w - 1) / (TILE_N / w)));
+    size_t ntiles = 0, nparts = 0;
+    for (int w = 16; w <= 128; w *= 2) {
+        SimParams t = sp;
+        set_tile_params(t, w);
+        ntiles = std::max(ntiles, (size_t)t.ntx * (size_t)t.nty);
+        nparts = std::max(nparts, (size_t)lb_mass_parts(t));
+    }
     s->ntiles_cap = (long long)ntiles;
+    s->mass_parts_cap = (long long)nparts;
     const size_t P = (size_t)sp.P;
     const size_t rs = s->eng->real_size, ss = s->eng->store_size;
     DevState &d = s->d;
@@ -135,7 +137,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     ok = ok && (d.carry = dalloc(s, 2 * P * ss));
     ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
     if (c.force_kind == LBRMT_FORCE_FIELD) ok = ok && (d.bfield = dalloc(s, 2 * P * rs));
-    ok = ok && (d.mass_partials = (double *)dalloc(s, ntiles * (TILE_N / 32) * 8));
+    ok = ok && (d.mass_partials = (double *)dalloc(s, nparts * 8));
     ok = ok && (d.err = (unsigned *)dalloc(s, 16));
     ok = ok && (s->scratch = (double *)dalloc(s, 64));
     if (!ok) {
@@ -152,7 +154,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, st);
     if (e == cudaSuccess && d.bfield) e = cudaMemsetAsync(d.bfield, 0, 2 * P * rs, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, ntiles * (TILE_N / 32) * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, nparts * 8, st);
     // body force per row (x component), Sec. 4 forcing on all phases
     std::vector<double> fb(c.ny, 0.0);
     for (int j = 0; j < c.ny; j++) {
@@ -282,6 +284,8 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[k], 0, 16, s->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.carry, 0, 2 * (size_t)s->sp.P * s->eng->store_size, s->stream);
+    // the slots a tile shape's K1 does not write must hold zero (a previous shape may have written them)
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, (size_t)s->mass_parts_cap * 8, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "clear registry");
     e = s->eng->init(s->sp, d, s->li, s->stream);
@@ -338,10 +342,7 @@ extern "C" lbrmt_status lbrmt_reset(lbrmt_sim *s) {
 static void set_tile_shape(lbrmt_sim *s, int tx) {
     SimParams &sp = s->sp;
     s->cfg.tile_x = tx;
-    sp.tx = tx; sp.ty = TILE_N / tx;
-    sp.lx = __builtin_ctz((unsigned)sp.tx); sp.ly = __builtin_ctz((unsigned)sp.ty);
-    sp.ntx = (s->cfg.nx + sp.tx - 1) / sp.tx;
-    sp.nty = (s->cfg.ny + sp.ty - 1) / sp.ty;
+    set_tile_params(sp, tx);
 }
 
 extern "C" lbrmt_status lbrmt_set_tile_x(lbrmt_sim *s, int tile_x) {
@@ -603,7 +604,7 @@ extern "C" lbrmt_status lbrmt_solid_stats(lbrmt_sim *s, int sim_index, double *h
 extern "C" lbrmt_status lbrmt_total_mass(lbrmt_sim *s, int sim_index, double *host_out) {
     if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
     if (s->steps == 0) return fail(s, LBRMT_ERR_STATE, "total mass is recorded by the first step");
-    const int n = s->sp.ntx * s->sp.nty * (TILE_N / 32);
+    const int n = (int)lb_mass_parts(s->sp);
     mass_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d.mass_partials, n, s->sp.rho_f * (double)s->sp.P, s->scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "mass kernel");

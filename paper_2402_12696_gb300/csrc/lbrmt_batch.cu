@@ -140,9 +140,9 @@ static lbrmt_status build_lists(lbrmt_batch *b) {
             rmt_T.push_back(s->solids[q].T);
             tmax = std::max(tmax, s->solids[q].T);
         }
-        if (s->sp.ntx >= 65536 || s->sp.nty >= 32768) return bfail(b, LBRMT_ERR_ARG, "member grid too large for a batch");
-        for (int by = 0; by < s->sp.nty; by++)
-            for (int bx = 0; bx < s->sp.ntx; bx++) lb.push_back(make_int2(k, (by << 16) | bx));
+        if (s->sp.nrx >= 65536 || s->sp.nty >= 32768) return bfail(b, LBRMT_ERR_ARG, "member grid too large for a batch");
+        for (int ry = 0; ry < s->sp.nty; ry++)
+            for (int rx = 0; rx < s->sp.nrx; rx++) lb.push_back(make_int2(k, (ry << 16) | rx));
         fs_elems = std::max(fs_elems, force_smem_elems(s->sp.tx, s->sp.ty));
     }
     // largest solid tiles first: the persistent K2 grid then ends with the short items

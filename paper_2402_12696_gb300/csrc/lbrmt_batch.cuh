@@ -82,29 +82,14 @@ __global__ void __launch_bounds__(TILE_N) force_batch_kernel(const BatchSimDesc<
     }
 }
 
-// K1 over every tile of every simulation: item = (simulation, by << 16 | bx).
-// Each CTA takes one contiguous run of the simulation-major list.
+// K1 over every region of every simulation: one CTA per item (simulation,
+// ry << 16 | rx) of the simulation-major list.
 template <class R, class S>
-__global__ void __launch_bounds__(TILE_N) lb_batch_kernel(const BatchSimDesc<R, S> *sims, const int2 *items, int nitems,
-                                                          int parity) {
-    __shared__ SimParams sp;
-    __shared__ LbArgs<R, S> la;
-    const int per = (nitems + gridDim.x - 1) / gridDim.x;
-    const int k0 = blockIdx.x * per, k1 = min(nitems, k0 + per);
-    int cur = -1;
-    for (int k = k0; k < k1; k++) {
-        const int2 w = items[k];
-        if (w.x != cur) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                sp = sims[w.x].sp;
-                la = sims[w.x].lb[parity];
-            }
-            __syncthreads();
-            cur = w.x;
-        }
-        lb_tile<R, S, false>(sp, la, w.y & 0xffff, w.y >> 16, nullptr);
-    }
+__global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S> - 1) lb_batch_kernel(const BatchSimDesc<R, S> *sims,
+                                                                             const int2 *items, int parity) {
+    const int2 w = items[blockIdx.x];
+    const BatchSimDesc<R, S> *d = sims + w.x;  // uniform, L1-resident reads
+    lb_region<R, S>(d->sp, d->lb[parity], w.y & 0xffff, w.y >> 16);
 }
 
 }  // namespace lbrmt

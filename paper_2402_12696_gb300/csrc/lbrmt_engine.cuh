@@ -49,7 +49,6 @@ template <> inline CUtensorMapDataType tma_dtype<__nv_bfloat16>() { return CU_TE
 struct BatchLaunch {
     int rmt_blocks, rmt_smem;      // K2: persistent grid, dynamic shared memory (largest solid tile)
     int force_blocks, force_smem;  // K3 (widest tile shape)
-    int lb_blocks;                 // K1
 };
 
 struct EngineOps {
@@ -253,9 +252,6 @@ struct Engine {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_batch_kernel<R, S>, TILE_N, bl->force_smem);
         if (e != cudaSuccess) return e;
         bl->force_blocks = nsm * std::max(per, 1);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lb_batch_kernel<R, S>, TILE_N, 0);
-        if (e != cudaSuccess) return e;
-        bl->lb_blocks = nsm * std::max(per, 1);
         return cudaSuccess;
     }
 
@@ -267,7 +263,7 @@ struct Engine {
         if (ev) cudaEventRecord(ev[1], st);
         if (n_rmt > 0) force_batch_kernel<R, S><<<bl.force_blocks, TILE_N, bl.force_smem, st>>>(ds, nsim, parity);
         if (ev) cudaEventRecord(ev[2], st);
-        lb_batch_kernel<R, S><<<bl.lb_blocks, TILE_N, 0, st>>>(ds, lb_items, n_lb, parity);
+        if (n_lb > 0) lb_batch_kernel<R, S><<<n_lb, TILE_N, 0, st>>>(ds, lb_items, parity);
         if (ev) cudaEventRecord(ev[3], st);
         return cudaGetLastError();
     }
@@ -296,7 +292,7 @@ struct Engine {
         if (ev) cudaEventRecord(ev[1], st);
         if (sp.nsolids > 0) force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, q, p));
         if (ev) cudaEventRecord(ev[2], st);
-        dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
+        dim3 grid(sp.nrx, sp.nty), blk(TILE_N);
         LbArgs<R, S> la = lb_args(d, p);
         la.tape = static_cast<R *>(tape);
         if (li.tma && li.use_tma)

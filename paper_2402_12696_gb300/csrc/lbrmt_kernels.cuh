@@ -53,6 +53,7 @@ struct SimParams {
     int nx, ny, wall_x, wall_y;
     int ntx, nty;
     int tx, ty, lx, ly;  // registry tile shape and log2 of each side
+    int rk, lk, nrx;     // K1 region: rk = 2^lk registry tiles side by side, nrx regions per row
     long long P;  // plane size nx*ny
     double tau, rho_f, lid_u, eps, eta, gravity;
     int force_kind;
@@ -62,6 +63,31 @@ struct SimParams {
     float omega_f, kf_f, rho_f_f, lid_u_f, eps_f, eta_f, fy_f;
     double omega, kf, fy;  // 1/tau, 1 - 1/(2 tau), constant y body force
 };
+
+// K1 walks regions LB_REGION_W nodes wide (rk registry tiles when tile_x is
+// narrower): the push stores of a warp then cover long rows, which keeps the
+// partial 32-byte sectors at the row ends a small share of the written bytes.
+constexpr int LB_REGION_W = 64;
+// K1 CTAs per SM the register allocation must allow: memory-latency bound, so
+// occupancy buys bandwidth (FP32: 40 registers, 6 CTAs of 256; 16-bit storage
+// needs 48 for its conversions, FP64 arithmetic 80)
+template <class R, class S> constexpr int LB_MIN_BLOCKS = sizeof(R) == 8 ? 3 : (sizeof(S) == 2 ? 5 : 6);
+
+__host__ __device__ inline void set_tile_params(SimParams &sp, int tx) {
+    sp.tx = tx; sp.ty = TILE_N / tx;
+    sp.lx = 0; while ((1 << sp.lx) < sp.tx) sp.lx++;
+    sp.ly = 0; while ((1 << sp.ly) < sp.ty) sp.ly++;
+    sp.ntx = (sp.nx + sp.tx - 1) / sp.tx;
+    sp.nty = (sp.ny + sp.ty - 1) / sp.ty;
+    sp.rk = tx < LB_REGION_W ? LB_REGION_W / tx : 1;
+    sp.lk = 0; while ((1 << sp.lk) < sp.rk) sp.lk++;
+    sp.nrx = (sp.ntx + sp.rk - 1) / sp.rk;
+}
+
+// FP64 mass partials of K1: one per warp and region pass (rk passes per region)
+__host__ __device__ inline long long lb_mass_parts(const SimParams &sp) {
+    return (long long)sp.nrx * sp.nty * sp.rk * (TILE_N / 32);
+}
 
 template <class R> __device__ __forceinline__ R pick(double d, float f);
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
@@ -1133,117 +1159,136 @@ struct LbArgs {
     unsigned *err;
 };
 
-// One registry tile (bx, by) of K1, one thread per node.  STAGED: the tile's
-// populations and half-force were staged in shared memory (9 + 2 planes of
-// TILE_N values, node lt at offset lt), else they are read from global memory.
+// One node (i, j) of K1: moments, SFC equilibrium, Guo forcing, BGK collision,
+// walls and push streaming.  tile / lt: the node's registry tile and its index
+// there (the pool's layout); interior: every push target of the caller's block
+// lies inside the domain.  STAGED: the node's populations and half-force were
+// staged in shared memory (9 + 2 planes of TILE_N values, node lt at offset lt).
+// Returns rho - rho_f.
+template <class R, class S, bool STAGED>
+__device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a, const int i, const int j,
+                                     const int tile, const int lt, const bool interior, const S *stage) {
+    const int nx = sp.nx, ny = sp.ny, P = (int)sp.P;  // 9 P < 2^31 is checked at creation
+    const int c = j * nx + i;
+    const int prev_count = a.clr_count[tile];  // cleared by the caller after every node read it
+    R f[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
+        f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.f_in + q * P + c);
+    const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
+    const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const R dr = dro + ds;  // rho - rho_f
+    const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
+    const R inv = rcp_rn<R>(rho);
+    const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt) : ldC<S, R>(a.carry + c);
+    const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt) : ldC<S, R>(a.carry + P + c);
+    const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
+    R Fx, Fy, drt = R(0);
+    if (sp.force_kind == 3) {
+        Fx = a.bfield[c];
+        Fy = a.bfield[P + c];
+    } else {
+        Fx = a.fbody[j];
+        Fy = pick<R>(sp.fy, sp.fy_f);
+    }
+    if (a.reg_count[tile] > 0) {
+        const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
+        Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
+    }
+    if (!(rho == rho) || !(ux == ux) || !(uy == uy)) atomicOr(a.err, ERR_NAN);
+    const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
+    const R u2 = ux * ux + uy * uy;
+    const R uF = ux * Fx + uy * Fy;
+    const R dd = dro - drt;      // change of the rest base over the step (small)
+    const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
+    f[0] += dd;                  // rest population relative to this step's Delta rho
+    // Collision f^ = f - omega (f - f^eq) + (1 - omega/2) F_i (Eq. 2_2_bgk_force) with
+    // f^eq of Eq. 2_3_feq_sfc in the stored form (minus w rho_f, minus Delta rho for
+    // q = 0) and the Guo term of Eq. 2_2_Fi times rho.  Opposite directions share the
+    // even parts (in c) of f^eq and F_i and differ in the sign of the odd parts.
+    const R om1 = R(1) - omega;
+    const R r15u2 = R(1.5) * u2, r3uF = R(3) * uF;
+    R fh[9];
+    {
+        const R w = R(4) / R(9), rw = rho * w;
+        fh[0] = om1 * f[0] + omega * (w * ddr - rw * r15u2) - kf * rw * r3uF;
+    }
+#pragma unroll
+    for (int pr = 0; pr < 4; pr++) {
+        const int q = pr + 1 + (pr >= 2 ? 2 : 0);  // 1, 2, 5, 6; partners 3, 4, 7, 8
+        const int qo = oppq(q);
+        const R w = wq<R>(q), rw = rho * w;
+        const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
+        const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
+        const R even = omega * (w * ddr + rw * (R(4.5) * cu * cu - r15u2)) + kf * rw * (R(9) * cu * cF - r3uF);
+        const R odd = R(3) * rw * (omega * cu + kf * cF);
+        fh[q] = om1 * f[q] + even + odd;
+        fh[qo] = om1 * f[qo] + even - odd;
+    }
+    if (a.tape) {
+        a.tape[c] = rho; a.tape[P + c] = ux; a.tape[2 * P + c] = uy;
+        a.tape[3 * P + c] = Fx; a.tape[4 * P + c] = Fy;
+    }
+    stC<S, R>(a.carry + c, R(0.5) * rho * Fx);
+    stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy);
+    if constexpr (is16<S>()) {
+        bool ov = false;
+#pragma unroll
+        for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q]);
+        if (ov) atomicOr(a.err, ERR_OVERFLOW16);
+    }
+    stS<S, R>(a.f_out + c, fh[0]);
+    if (interior) {
+#pragma unroll
+        for (int q = 1; q < 9; q++) stS<S, R>(a.f_out + q * P + c + cyq(q) * nx + cxq(q), fh[q]);
+    } else {
+#pragma unroll
+        for (int q = 1; q < 9; q++) {
+            int di = i + cxq(q), dj = j + cyq(q);
+            const bool ox = di < 0 || di >= nx, oy = dj < 0 || dj >= ny;
+            if ((ox && sp.wall_x) || (oy && sp.wall_y)) {
+                // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
+                const R uw = (oy && sp.wall_y && dj >= ny) ? pick<R>(sp.lid_u, sp.lid_u_f) : R(0);
+                const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
+                stS<S, R>(a.f_out + oppq(q) * P + c, val);
+            } else {
+                if (ox) di = di < 0 ? di + nx : di - nx;
+                if (oy) dj = dj < 0 ? dj + ny : dj - ny;
+                stS<S, R>(a.f_out + q * P + dj * nx + di, fh[q]);
+            }
+        }
+    }
+    return dr;
+}
+
+// FP64 partial of the warp's rho - rho_f sums (one slot per warp and pass).
+__device__ __forceinline__ void lb_mass_partial(double *slot, float dm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
+    if ((threadIdx.x & 31) == 0) *slot = (double)dm;
+}
+__device__ __forceinline__ void lb_mass_partial(double *slot, double dm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
+    if ((threadIdx.x & 31) == 0) *slot = dm;
+}
+
+// One registry tile (bx, by) of K1, one thread per node (the staged form: the
+// tile's planes are in shared memory).  Its mass partials use the slots of the
+// region layout (pass = the tile's place in its region).
 template <class R, class S, bool STAGED>
 __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> &a, const int bx, const int by,
                                         const S *stage) {
     const int lt = threadIdx.x;
     const int i = bx * sp.tx + (lt & (sp.tx - 1)), j = by * sp.ty + (lt >> sp.lx);
     const int tile = by * sp.ntx + bx;
-    const int nx = sp.nx, ny = sp.ny, P = (int)sp.P;  // 9 P < 2^31 is checked at creation
-    const int prev_count = a.clr_count[tile];  // cleared below, after every thread has read it
-    // every push target of this tile lies inside the domain
-    const bool interior = bx > 0 && (bx + 1) * sp.tx < nx && by > 0 && (by + 1) * sp.ty < ny;
+    const bool interior = bx > 0 && (bx + 1) * sp.tx < sp.nx && by > 0 && (by + 1) * sp.ty < sp.ny;
     R dm = R(0);
-    if (i < nx && j < ny) {
-        const int c = j * nx + i;
-        R f[9];
-#pragma unroll
-        for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
-            f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.f_in + q * P + c);
-        const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
-        const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const R dr = dro + ds;  // rho - rho_f
-        const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-        const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
-        const R inv = rcp_rn<R>(rho);
-        const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt) : ldC<S, R>(a.carry + c);
-        const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt) : ldC<S, R>(a.carry + P + c);
-        const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
-        R Fx, Fy, drt = R(0);
-        if (sp.force_kind == 3) {
-            Fx = a.bfield[c];
-            Fy = a.bfield[P + c];
-        } else {
-            Fx = a.fbody[j];
-            Fy = pick<R>(sp.fy, sp.fy_f);
-        }
-        if (a.reg_count[tile] > 0) {
-            const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
-            Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
-        }
-        if (!(rho == rho) || !(ux == ux) || !(uy == uy)) atomicOr(a.err, ERR_NAN);
-        const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
-        const R u2 = ux * ux + uy * uy;
-        const R uF = ux * Fx + uy * Fy;
-        const R dd = dro - drt;      // change of the rest base over the step (small)
-        const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
-        f[0] += dd;                  // rest population relative to this step's Delta rho
-        // Collision f^ = f - omega (f - f^eq) + (1 - omega/2) F_i (Eq. 2_2_bgk_force) with
-        // f^eq of Eq. 2_3_feq_sfc in the stored form (minus w rho_f, minus Delta rho for
-        // q = 0) and the Guo term of Eq. 2_2_Fi times rho.  Opposite directions share the
-        // even parts (in c) of f^eq and F_i and differ in the sign of the odd parts.
-        const R om1 = R(1) - omega;
-        const R r15u2 = R(1.5) * u2, r3uF = R(3) * uF;
-        R fh[9];
-        {
-            const R w = R(4) / R(9), rw = rho * w;
-            fh[0] = om1 * f[0] + omega * (w * ddr - rw * r15u2) - kf * rw * r3uF;
-        }
-#pragma unroll
-        for (int pr = 0; pr < 4; pr++) {
-            const int q = pr + 1 + (pr >= 2 ? 2 : 0);  // 1, 2, 5, 6; partners 3, 4, 7, 8
-            const int qo = oppq(q);
-            const R w = wq<R>(q), rw = rho * w;
-            const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
-            const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
-            const R even = omega * (w * ddr + rw * (R(4.5) * cu * cu - r15u2)) + kf * rw * (R(9) * cu * cF - r3uF);
-            const R odd = R(3) * rw * (omega * cu + kf * cF);
-            fh[q] = om1 * f[q] + even + odd;
-            fh[qo] = om1 * f[qo] + even - odd;
-        }
-        if (a.tape) {
-            a.tape[c] = rho; a.tape[P + c] = ux; a.tape[2 * P + c] = uy;
-            a.tape[3 * P + c] = Fx; a.tape[4 * P + c] = Fy;
-        }
-        stC<S, R>(a.carry + c, R(0.5) * rho * Fx);
-        stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy);
-        if constexpr (is16<S>()) {
-            bool ov = false;
-#pragma unroll
-            for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q]);
-            if (ov) atomicOr(a.err, ERR_OVERFLOW16);
-        }
-        stS<S, R>(a.f_out + c, fh[0]);
-        if (interior) {
-#pragma unroll
-            for (int q = 1; q < 9; q++) stS<S, R>(a.f_out + q * P + c + cyq(q) * nx + cxq(q), fh[q]);
-        } else {
-#pragma unroll
-            for (int q = 1; q < 9; q++) {
-                int di = i + cxq(q), dj = j + cyq(q);
-                const bool ox = di < 0 || di >= nx, oy = dj < 0 || dj >= ny;
-                if ((ox && sp.wall_x) || (oy && sp.wall_y)) {
-                    // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
-                    const R uw = (oy && sp.wall_y && dj >= ny) ? pick<R>(sp.lid_u, sp.lid_u_f) : R(0);
-                    const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
-                    stS<S, R>(a.f_out + oppq(q) * P + c, val);
-                } else {
-                    if (ox) di = di < 0 ? di + nx : di - nx;
-                    if (oy) dj = dj < 0 ? dj + ny : dj - ny;
-                    stS<S, R>(a.f_out + q * P + dj * nx + di, fh[q]);
-                }
-            }
-        }
-        dm = dr;
-    }
-    // total mass: rho - rho_f summed over the warp, then FP64 per warp
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
-    if ((lt & 31) == 0) a.mass_partials[(long long)tile * (TILE_N / 32) + (lt >> 5)] = (double)dm;
+    if (i < sp.nx && j < sp.ny) dm = lb_node<R, S, STAGED>(sp, a, i, j, tile, lt, interior, stage);
+    const long long slot = ((((long long)by * sp.nrx + (bx >> sp.lk)) << sp.lk) + (bx & (sp.rk - 1))) * (TILE_N / 32);
+    lb_mass_partial(a.mass_partials + slot + (lt >> 5), dm);
     __syncthreads();
     if (lt == 0) {
         a.clr_count[tile] = 0;
@@ -1251,9 +1296,38 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
     }
 }
 
+// One region (rx, ry) of K1: rk registry tiles side by side (LB_REGION_W x ty
+// nodes, or one tile when tile_x >= LB_REGION_W), walked in rk passes of TILE_N
+// nodes, each pass a band of whole rows.
 template <class R, class S>
-__global__ void __launch_bounds__(TILE_N) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
-    lb_tile<R, S, false>(sp, a, blockIdx.x, blockIdx.y, nullptr);
+__device__ __forceinline__ void lb_region(const SimParams &sp, const LbArgs<R, S> &a, const int rx, const int ry) {
+    const int lt = threadIdx.x;
+    const int lw = sp.lx + sp.lk, W = 1 << lw;
+    const int x0 = rx << lw, y0 = ry * sp.ty;
+    const bool interior = x0 > 0 && x0 + W < sp.nx && y0 > 0 && y0 + sp.ty < sp.ny;
+    double *part = a.mass_partials + (((long long)ry * sp.nrx + rx) << sp.lk) * (TILE_N / 32);
+    for (int p = 0; p < sp.rk; p++) {
+        const int n = p * TILE_N + lt;
+        const int xl = n & (W - 1), yl = n >> lw;
+        const int i = x0 + xl, j = y0 + yl;
+        R dm = R(0);
+        if (i < sp.nx && j < sp.ny) {
+            const int tile = ry * sp.ntx + (rx << sp.lk) + (xl >> sp.lx);
+            dm = lb_node<R, S, false>(sp, a, i, j, tile, (yl << sp.lx) + (xl & (sp.tx - 1)), interior, nullptr);
+        }
+        lb_mass_partial(part + p * (TILE_N / 32) + (lt >> 5), dm);
+    }
+    __syncthreads();  // every node of the region's tiles has read the previous registry
+    if (lt < sp.rk) {
+        const int bx = (rx << sp.lk) + lt;
+        if (bx < sp.ntx) a.clr_count[ry * sp.ntx + bx] = 0;
+    }
+    if (lt == 0 && rx == 0 && ry == 0) *a.clr_nactive = 0;
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
+    lb_region<R, S>(sp, a, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1296,7 +1370,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 }
 
 template <class R, class S>
-__global__ void __launch_bounds__(TILE_N) lb_tma_kernel(SimParams sp, LbArgs<R, S> a,
+__global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_tma_kernel(SimParams sp, LbArgs<R, S> a,
                                                         const __grid_constant__ CUtensorMap tm_f,
                                                         const __grid_constant__ CUtensorMap tm_c, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem[];
