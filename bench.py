@@ -68,7 +68,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-i", str(self.gpu), "-lms", "200"],
+                                       "-i", str(self.gpu), "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -403,7 +403,9 @@ def bench_lbrmt(args):
             import hashlib
             rec = json.load(open(tfile))
             src = os.path.join(ROOT, "paper_2402_12696_gb300", "csrc", "lbrmt_kernels.cuh")
-            if hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] == rec.get("kernel_source_sha1"):
+            same_src = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] == rec.get("kernel_source_sha1")
+            same_cfg = rec.get("tile_x") == tile_used and rec.get("lb_loads") == ("tma" if tma_used else "direct")
+            if same_src and same_cfg:
                 traffic = rec.get("bytes_per_launch")
         except Exception:
             traffic = None
@@ -451,7 +453,7 @@ def bench_lbrmt(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="lbrmt", choices=["lbrmt", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
