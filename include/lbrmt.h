@@ -223,8 +223,9 @@ long long lbrmt_steps_done(const lbrmt_sim *sim);
 int lbrmt_num_solids(const lbrmt_sim *sim);
 long long lbrmt_last_launch_count(const lbrmt_sim *sim);
 
-/* Advance nsteps >= 1 steps with direct launches and a CUDA event around
- * every kernel (on the simulation's stream), then wait.  ms_out[k] receives
+/* Advance nsteps >= 1 steps with direct launches of the sequential schedule
+ * (lbrmt_set_overlap) and a CUDA event around every kernel (on the
+ * simulation's stream), then wait.  ms_out[k] receives
  * the mean duration in milliseconds of kernel k of a step: 0 = reference-map
  * kernel (advect, extrapolate, relabel), 1 = stress/force kernel, 2 = fused
  * lattice Boltzmann kernel (host array of 3 floats; 0 where not launched). */
@@ -239,6 +240,21 @@ lbrmt_status lbrmt_set_use_graphs(lbrmt_sim *sim, int enable);
  * multiple of 16 bytes; lbrmt_uses_tma tells whether it is in use. */
 lbrmt_status lbrmt_set_use_tma(lbrmt_sim *sim, int enable);
 int lbrmt_uses_tma(const lbrmt_sim *sim);
+
+/* Overlapped step (1, default) or sequential step (0).  Overlapped: each step
+ * first classifies the lattice Boltzmann kernel's regions (64 nodes wide) from
+ * the previous step's tile registry; the regions whose tiles and neighbour tiles
+ * hold no solid (interfaces move less than one node per step, Appendix A) are
+ * advanced on an internal lowest-priority stream concurrently with the
+ * reference-map and stress kernels, which the simulation's stream runs at the
+ * highest priority; the step ends when both are done (the caller's stream then
+ * waits for the internal one).  The results are the same bit for bit.  A solid
+ * found in a region that a step treated as free raises LBRMT_ERR_NUMERIC at the
+ * next error check.  Not used with tensor-memory loads (lbrmt_set_use_tma) or
+ * without solids; lbrmt_step_timed always takes the sequential schedule.
+ * lbrmt_uses_overlap tells whether steps overlap (after initialisation). */
+lbrmt_status lbrmt_set_overlap(lbrmt_sim *sim, int enable);
+int lbrmt_uses_overlap(const lbrmt_sim *sim);
 
 /* Text of the last error on this handle ("" if none). */
 const char *lbrmt_last_error(const lbrmt_sim *sim);

@@ -33,7 +33,7 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
-           "lbrmt_uses_tma",
+           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
            "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward", "lbrmt_set_tile_x", "lbrmt_tile_x",
            "lbrmt_autotune_tile",
@@ -99,6 +99,8 @@ def load():
     L.lbrmt_set_use_graphs.argtypes = [p, i]
     L.lbrmt_set_use_tma.argtypes = [p, i]
     L.lbrmt_uses_tma.argtypes = [p]
+    L.lbrmt_set_overlap.argtypes = [p, i]
+    L.lbrmt_uses_overlap.argtypes = [p]
     L.lbrmt_last_error.argtypes = [p]
     L.lbrmt_last_error.restype = C.c_char_p
     L.lbrmt_destroy.argtypes = [p]
@@ -359,7 +361,7 @@ class Simulation:
     """One LBRMT simulation on a CUDA device, built from a scenario dict."""
 
     def __init__(self, sc, precision="fp32", device="cuda:0", stream=None, use_graphs=True,
-                 max_solids_per_tile=8, rmax=11, tile_x=32, use_tma=True):
+                 max_solids_per_tile=8, rmax=11, tile_x=32, use_tma=True, overlap=True):
         import torch
         self.torch = torch
         self.sc = sc
@@ -376,6 +378,7 @@ class Simulation:
             self.h = lbrmt_create(cfg, self.stream.cuda_stream)
             load().lbrmt_set_use_graphs(self.h, int(bool(use_graphs)))
             load().lbrmt_set_use_tma(self.h, int(bool(use_tma)))
+            _check(self.h, load().lbrmt_set_overlap(self.h, int(bool(overlap))))
             for s in sc["solids"]:
                 shape, a, b = _solid_geometry(s)
                 lbrmt_add_solid_shape(self.h, shape, s["x"], s["y"], a, b, s["rho_s"], s["G"])
@@ -444,6 +447,14 @@ class Simulation:
     @property
     def uses_tma(self):
         return bool(load().lbrmt_uses_tma(self.h))
+
+    def set_overlap(self, enable):
+        """Overlapped (True) or sequential (False) step schedule (lbrmt_set_overlap)."""
+        _check(self.h, load().lbrmt_set_overlap(self.h, int(bool(enable))))
+
+    @property
+    def uses_overlap(self):
+        return bool(load().lbrmt_uses_overlap(self.h))
 
     @property
     def last_launch_count(self):

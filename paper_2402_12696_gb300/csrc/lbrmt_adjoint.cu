@@ -61,6 +61,7 @@ static void collect_state(lbrmt_sim *s, AdjointStore &A) {
         A.bufs.push_back({d.reg_active[k], ntiles * 4});
         A.bufs.push_back({d.reg_nactive[k], 16});
         A.bufs.push_back({d.pool[k], ntiles * POOL_STRIDE * rs});
+        A.bufs.push_back({d.busy[k], (size_t)s->sp.nrx * s->sp.nty});
     }
     A.bufs.push_back({d.carry, 2 * P * ss});
     A.bufs.push_back({d.stats_step, S * 64});

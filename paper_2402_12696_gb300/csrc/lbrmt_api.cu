@@ -32,6 +32,15 @@ __global__ void mass_reduce_kernel(const double *partials, int n, double base, d
 }
 }  // namespace lbrmt
 
+static void release_streams(lbrmt_sim *s) {
+    if (s->li.fork) cudaEventDestroy(s->li.fork);
+    if (s->li.join) cudaEventDestroy(s->li.join);
+    if (s->li.flags) cudaEventDestroy(s->li.flags);
+    if (s->li.side) cudaStreamDestroy(s->li.side);
+    s->li.fork = s->li.join = s->li.flags = nullptr;
+    s->li.side = nullptr;
+}
+
 static lbrmt_status fail(lbrmt_sim *s, lbrmt_status st, const std::string &msg) {
     if (s) s->err = msg;
     return st;
@@ -112,15 +121,17 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
 
     // registry and pool sized for the largest tile count over the tile shapes, so
     // the shape can change later (lbrmt_set_tile_x) without reallocation
-    size_t ntiles = 0, nparts = 0;
+    size_t ntiles = 0, nparts = 0, nregions = 0;
     for (int w = 16; w <= 128; w *= 2) {
         SimParams t = sp;
         set_tile_params(t, w);
         ntiles = std::max(ntiles, (size_t)t.ntx * (size_t)t.nty);
         nparts = std::max(nparts, (size_t)lb_mass_parts(t));
+        nregions = std::max(nregions, (size_t)t.nrx * (size_t)t.nty);
     }
     s->ntiles_cap = (long long)ntiles;
     s->mass_parts_cap = (long long)nparts;
+    s->nregions_cap = (long long)nregions;
     const size_t P = (size_t)sp.P;
     const size_t rs = s->eng->real_size, ss = s->eng->store_size;
     DevState &d = s->d;
@@ -133,6 +144,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         ok = ok && (d.reg_active[k] = (int *)dalloc(s, ntiles * 4));
         ok = ok && (d.reg_nactive[k] = (int *)dalloc(s, 16));
         ok = ok && (d.pool[k] = dalloc(s, ntiles * POOL_STRIDE * rs));
+        ok = ok && (d.busy[k] = (unsigned char *)dalloc(s, nregions));
     }
     ok = ok && (d.carry = dalloc(s, 2 * P * ss));
     ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
@@ -140,7 +152,18 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     ok = ok && (d.mass_partials = (double *)dalloc(s, nparts * 8));
     ok = ok && (d.err = (unsigned *)dalloc(s, 16));
     ok = ok && (s->scratch = (double *)dalloc(s, 64));
+    // side stream (lowest priority) and fork / join events of the overlapped step
+    if (ok) {
+        int least = 0, greatest = 0;
+        ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&s->li.side, cudaStreamNonBlocking, least) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->li.fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->li.join, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->li.flags, cudaEventDisableTiming) == cudaSuccess;
+        s->li.prio_hi = greatest;
+    }
     if (!ok) {
+        release_streams(s);
         dfree_all(s);
         delete s;
         return LBRMT_ERR_CUDA;
@@ -224,6 +247,8 @@ static lbrmt_status check_flags(lbrmt_sim *s) {
     if (f & ERR_OVERFLOW16) return fail(s, LBRMT_ERR_OVERFLOW, "a population exceeded the 16-bit storage range");
     if (f & ERR_TIMEOUT) return fail(s, LBRMT_ERR_TIMEOUT, "a bounded wait on a tensor copy gave up");
     if (f & ERR_ALIGN) return fail(s, LBRMT_ERR_CUDA, "misaligned shared-memory stage (tensor copies skipped)");
+    if (f & ERR_FREE_REGION)
+        return fail(s, LBRMT_ERR_NUMERIC, "an interface moved more than one node in a step (a region stepped as solid-free held a solid)");
     return fail(s, LBRMT_ERR_NUMERIC, "device error flag");
 }
 
@@ -286,6 +311,8 @@ static lbrmt_status run_init(lbrmt_sim *s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(d.carry, 0, 2 * (size_t)s->sp.P * s->eng->store_size, s->stream);
     // the slots a tile shape's K1 does not write must hold zero (a previous shape may have written them)
     if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, (size_t)s->mass_parts_cap * 8, s->stream);
+    // every region counts as busy for the first step's check of the previous classification
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemsetAsync(d.busy[k], 1, (size_t)s->nregions_cap, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 16, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "clear registry");
     e = s->eng->init(s->sp, d, s->li, s->stream);
@@ -438,7 +465,7 @@ static lbrmt_status direct_step(lbrmt_sim *s) {
     cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, nullptr, nullptr);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->steps++;
-    s->last_launches += s->sp.nsolids > 0 ? 3 : 1;
+    s->last_launches += step_launches(s->sp, s->li);
     return LBRMT_OK;
 }
 
@@ -455,7 +482,8 @@ static lbrmt_status build_graph(lbrmt_sim *s) {
         if (g) cudaGraphDestroy(g);
         return cuda_fail(s, e, "capture");
     }
-    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    // per-node priorities: the overlapped step runs K2, K3 and the busy K1 ahead of the free K1
+    e = cudaGraphInstantiate(&s->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         s->gexec = nullptr;
@@ -488,7 +516,7 @@ extern "C" lbrmt_status lbrmt_step(lbrmt_sim *s, int nsteps) {
             cudaError_t e = cudaGraphLaunch(s->gexec, s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
             s->steps += 2;
-            s->last_launches += s->sp.nsolids > 0 ? 6 : 2;
+            s->last_launches += 2 * step_launches(s->sp, s->li);
             left -= 2;
         }
     }
@@ -516,7 +544,7 @@ extern "C" lbrmt_status lbrmt_step_timed(lbrmt_sim *s, int nsteps, float *ms_out
         cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, &ev[4 * (size_t)n], nullptr);
         if (e != cudaSuccess) { status = cuda_fail(s, e, "timed step"); break; }
         s->steps++;
-        s->last_launches += s->sp.nsolids > 0 ? 3 : 1;
+        s->last_launches += step_launches(s->sp, s->li, true);
     }
     double acc[3] = {0, 0, 0};
     if (status == LBRMT_OK) {
@@ -656,11 +684,27 @@ extern "C" int lbrmt_uses_tma(const lbrmt_sim *s) { return s && s->inited && s->
 
 extern "C" const char *lbrmt_last_error(const lbrmt_sim *s) { return s ? s->err.c_str() : "null handle"; }
 
+extern "C" lbrmt_status lbrmt_set_overlap(lbrmt_sim *s, int enable) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    s->li.split = enable != 0;
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return LBRMT_OK;
+}
+
+extern "C" int lbrmt_uses_overlap(const lbrmt_sim *s) { return s && s->inited && step_overlaps(s->sp, s->li) ? 1 : 0; }
+
 extern "C" void lbrmt_destroy(lbrmt_sim *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
+    if (s->li.side) cudaStreamSynchronize(s->li.side);
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    release_streams(s);
     if (s->adj) lbrmt_internal_adjoint_free(s);
     dfree_all(s);
     delete s;

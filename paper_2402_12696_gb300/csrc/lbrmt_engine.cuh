@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "lbrmt_batch.cuh"
 #include "lbrmt_kernels.cuh"
@@ -20,7 +21,43 @@ struct LaunchInfo {
     bool use_tma = true; // K1 with TMA staging (else the direct-load kernel)
     int lb_blocks = 0, lb_smem = 0;
     CUtensorMap tm_f[2], tm_c;
+    // Overlapped step: K1 of the regions without solid forcing runs on a side
+    // stream of the lowest priority, concurrently with K2, K3 and K1 of the other
+    // regions, which are launched with the highest priority.  The stream and the
+    // fork / join events are owned by the simulation.
+    bool split = true;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, flags = nullptr;
+    int prio_hi = 0;
 };
+
+// Does a step run the overlapped schedule (K1 split into busy and free regions)?
+inline bool step_overlaps(const SimParams &sp, const LaunchInfo &li) {
+    return li.split && li.side && sp.nsolids > 0 && !(li.tma && li.use_tma);
+}
+
+// Kernel launches of one step (timed: the sequential schedule of lbrmt_step_timed).
+inline int step_launches(const SimParams &sp, const LaunchInfo &li, bool timed = false) {
+    if (sp.nsolids == 0) return 1;
+    return step_overlaps(sp, li) && !timed ? 5 : 4;  // classification, K2, K3, K1 (busy and free regions)
+}
+
+// Launch with a scheduling priority (a launch attribute, kept by stream capture).
+template <class... P, class... A>
+inline cudaError_t launch_prio(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int prio,
+                               A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -268,9 +305,11 @@ struct Engine {
         return cudaGetLastError();
     }
 
-    static void launch_rmt(const SimParams &sp, const LaunchInfo &li, const RmtArgs<R, S> &a, cudaStream_t st) {
-        if (li.rmt_big) rmt_solid_kernel_big<R, S><<<sp.nsolids, RMT_THREADS_BIG, li.rmt_smem, st>>>(sp, a);
-        else rmt_solid_kernel<R, S><<<sp.nsolids, RMT_THREADS, li.rmt_smem, st>>>(sp, a);
+    static void launch_rmt(const SimParams &sp, const LaunchInfo &li, const RmtArgs<R, S> &a, cudaStream_t st,
+                           int prio = 0) {
+        if (li.rmt_big)
+            launch_prio(rmt_solid_kernel_big<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS_BIG), li.rmt_smem, st, prio, sp, a);
+        else launch_prio(rmt_solid_kernel<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS), li.rmt_smem, st, prio, sp, a);
     }
 
     static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
@@ -283,23 +322,44 @@ struct Engine {
         return cudaGetLastError();
     }
 
-    // ev (optional): four events recorded before K2, before K3, before K1 and after K1.
+    // ev (optional): four events recorded before K2, before K3, before K1 and after
+    // K1; the step then takes the sequential schedule (one K1 over every region,
+    // on st after K3), so each kernel is timed alone.
     static cudaError_t step(const SimParams &sp, const DevState &d, const LaunchInfo &li, int parity,
                             cudaStream_t st, cudaEvent_t *ev, void *tape) {
         const int p = parity, q = 1 - parity;
-        if (ev) cudaEventRecord(ev[0], st);
-        if (sp.nsolids > 0) launch_rmt(sp, li, rmt_args(d, p, 0), st);
-        if (ev) cudaEventRecord(ev[1], st);
-        if (sp.nsolids > 0) force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, q, p));
-        if (ev) cudaEventRecord(ev[2], st);
-        dim3 grid(sp.nrx, sp.nty), blk(TILE_N);
+        const bool overlap = step_overlaps(sp, li) && !ev;
+        const int prio = overlap ? li.prio_hi : 0;
+        const dim3 grid(sp.nrx, sp.nty), blk(TILE_N);
         LbArgs<R, S> la = lb_args(d, p);
         la.tape = static_cast<R *>(tape);
+        const int nreg = sp.nrx * sp.nty;
+        if (overlap) {  // fork: classification and K1 of the free regions on the side stream
+            cudaEventRecord(li.fork, st);
+            cudaStreamWaitEvent(li.side, li.fork, 0);
+            lb_busy_kernel<<<(nreg + 255) / 256, 256, 0, li.side>>>(sp, d.reg_count[q], d.busy[q], d.busy[p], d.err);
+            cudaEventRecord(li.flags, li.side);
+            lb_step_kernel<R, S, 2><<<grid, blk, 0, li.side>>>(sp, la, d.busy[p]);
+            cudaEventRecord(li.join, li.side);
+        } else if (sp.nsolids > 0) {
+            lb_busy_kernel<<<(nreg + 255) / 256, 256, 0, st>>>(sp, d.reg_count[q], d.busy[q], d.busy[p], d.err);
+        }
+        if (ev) cudaEventRecord(ev[0], st);
+        if (sp.nsolids > 0) launch_rmt(sp, li, rmt_args(d, p, 0), st, prio);
+        if (ev) cudaEventRecord(ev[1], st);
+        if (sp.nsolids > 0)
+            launch_prio(force_kernel<R>, dim3(li.force_blocks), dim3(TILE_N), li.force_smem, st, prio, sp,
+                        force_args(d, q, p));
+        if (ev) cudaEventRecord(ev[2], st);
         if (li.tma && li.use_tma)
             lb_tma_kernel<R, S><<<li.lb_blocks, TILE_N, li.lb_smem, st>>>(sp, la, li.tm_f[p], li.tm_c, sp.ntx * sp.nty);
-        else
-            lb_step_kernel<R, S><<<grid, blk, 0, st>>>(sp, la);
+        else if (overlap) {
+            cudaStreamWaitEvent(st, li.flags, 0);  // the classification is done
+            launch_prio(lb_step_kernel<R, S, 1>, grid, blk, 0, st, prio, sp, la, (const unsigned char *)d.busy[p]);
+        } else
+            lb_step_kernel<R, S, 0><<<grid, blk, 0, st>>>(sp, la, nullptr);
         if (ev) cudaEventRecord(ev[3], st);
+        if (overlap) cudaStreamWaitEvent(st, li.join, 0);  // join
         return cudaGetLastError();
     }
 

@@ -45,7 +45,8 @@ constexpr double COS_TIE = 1e-9;
 
 enum ErrBits : unsigned {
     ERR_NAN = 1u, ERR_TILE_OVERFLOW = 2u, ERR_SLOT_OVERFLOW = 4u, ERR_EXTRAP = 8u,
-    ERR_SINGULAR = 16u, ERR_STENCIL = 32u, ERR_OVERFLOW16 = 64u, ERR_TIMEOUT = 128u, ERR_ALIGN = 256u
+    ERR_SINGULAR = 16u, ERR_STENCIL = 32u, ERR_OVERFLOW16 = 64u, ERR_TIMEOUT = 128u, ERR_ALIGN = 256u,
+    ERR_FREE_REGION = 512u
 };
 
 // Scalar parameters, passed by value.
@@ -132,6 +133,7 @@ struct DevState {
     void *pool[2];         // per tile: Fx_pool, Fy_pool, drho (TILE_N each)
     void *bfield;          // force_kind 3: body force field, x plane then y plane (nx*ny each)
     int *order;            // solids by decreasing tile side (launch order of the solid kernel)
+    unsigned char *busy[2]; // per K1 region, by step parity: 1 if it may hold solid forcing this step
     void *fbody;           // per row: body-force x component
     double *mass_partials; // per LB block
     double *stats_step;    // S x 8, stats of the state at the start of the last step
@@ -1165,12 +1167,14 @@ struct LbArgs {
 // lies inside the domain.  STAGED: the node's populations and half-force were
 // staged in shared memory (9 + 2 planes of TILE_N values, node lt at offset lt).
 // Returns rho - rho_f.
-template <class R, class S, bool STAGED>
+// REG false: the node's tile is registered in neither this step's nor the
+// previous step's registry (a free region), so neither is read.
+template <class R, class S, bool STAGED, bool REG = true>
 __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a, const int i, const int j,
                                      const int tile, const int lt, const bool interior, const S *stage) {
     const int nx = sp.nx, ny = sp.ny, P = (int)sp.P;  // 9 P < 2^31 is checked at creation
     const int c = j * nx + i;
-    const int prev_count = a.clr_count[tile];  // cleared by the caller after every node read it
+    const int prev_count = REG ? a.clr_count[tile] : 0;  // cleared by the caller after every node read it
     R f[9];
 #pragma unroll
     for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
@@ -1193,7 +1197,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
         Fx = a.fbody[j];
         Fy = pick<R>(sp.fy, sp.fy_f);
     }
-    if (a.reg_count[tile] > 0) {
+    if (REG && a.reg_count[tile] > 0) {
         const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
         Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
     }
@@ -1299,7 +1303,9 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
 // One region (rx, ry) of K1: rk registry tiles side by side (LB_REGION_W x ty
 // nodes, or one tile when tile_x >= LB_REGION_W), walked in rk passes of TILE_N
 // nodes, each pass a band of whole rows.
-template <class R, class S>
+// REG false: a free region (no registry reads; its registry tiles are empty,
+// so there is nothing to clear).
+template <class R, class S, bool REG = true>
 __device__ __forceinline__ void lb_region(const SimParams &sp, const LbArgs<R, S> &a, const int rx, const int ry) {
     const int lt = threadIdx.x;
     const int lw = sp.lx + sp.lk, W = 1 << lw;
@@ -1313,21 +1319,67 @@ __device__ __forceinline__ void lb_region(const SimParams &sp, const LbArgs<R, S
         R dm = R(0);
         if (i < sp.nx && j < sp.ny) {
             const int tile = ry * sp.ntx + (rx << sp.lk) + (xl >> sp.lx);
-            dm = lb_node<R, S, false>(sp, a, i, j, tile, (yl << sp.lx) + (xl & (sp.tx - 1)), interior, nullptr);
+            dm = lb_node<R, S, false, REG>(sp, a, i, j, tile, (yl << sp.lx) + (xl & (sp.tx - 1)), interior, nullptr);
         }
         lb_mass_partial(part + p * (TILE_N / 32) + (lt >> 5), dm);
     }
-    __syncthreads();  // every node of the region's tiles has read the previous registry
-    if (lt < sp.rk) {
-        const int bx = (rx << sp.lk) + lt;
-        if (bx < sp.ntx) a.clr_count[ry * sp.ntx + bx] = 0;
+    if (REG) {
+        __syncthreads();  // every node of the region's tiles has read the previous registry
+        if (lt < sp.rk) {
+            const int bx = (rx << sp.lk) + lt;
+            if (bx < sp.ntx) a.clr_count[ry * sp.ntx + bx] = 0;
+        }
     }
     if (lt == 0 && rx == 0 && ry == 0) *a.clr_nactive = 0;
 }
 
-template <class R, class S>
-__global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_step_kernel(SimParams sp, LbArgs<R, S> a) {
-    lb_region<R, S>(sp, a, blockIdx.x, blockIdx.y);
+// K1 over the regions of one kind.  MODE 0: every region; 1: the busy regions
+// (busy[r] != 0); 2: the free regions, without registry reads.  The split lets
+// the free regions run concurrently with K2 and K3 (overlapped step).
+template <class R, class S, int MODE>
+__global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_step_kernel(SimParams sp, LbArgs<R, S> a,
+                                                                           const unsigned char *busy) {
+    if (MODE != 0) {
+        const bool b = busy[blockIdx.y * sp.nrx + blockIdx.x] != 0;
+        if (b != (MODE == 1)) return;  // uniform over the CTA, before any barrier
+    }
+    lb_region<R, S, MODE != 2>(sp, a, blockIdx.x, blockIdx.y);
+}
+
+// Classification of the K1 regions for the overlapped step n: a region is busy
+// when one of its registry tiles or of their 8 neighbour tiles is registered in
+// registry n - 1.  A registry covers the tiles that the box of the blur zone,
+// grown by one node, touches; interfaces move less than one node per step, so
+// registry n lies inside the busy regions and a free region needs neither
+// registry.  The previous classification is checked on the fly: a tile of a
+// region that step n - 1 treated as free must not be in registry n - 1.
+static __global__ void lb_busy_kernel(SimParams sp, const int *reg_prev, const unsigned char *busy_prev, unsigned char *busy,
+                               unsigned *err) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= sp.nrx * sp.nty) return;
+    const int rx = r % sp.nrx, ry = r / sp.nrx;
+    const int b0 = rx << sp.lk, b1 = min(b0 + sp.rk, sp.ntx) - 1;  // the region's tile columns
+    bool any = false, own = false;
+    for (int dy = -1; dy <= 1; dy++) {
+        int by = ry + dy;
+        if (by < 0 || by >= sp.nty) {
+            if (sp.wall_y) continue;
+            by = by < 0 ? by + sp.nty : by - sp.nty;
+        }
+        for (int bx = b0 - 1; bx <= b1 + 1; bx++) {
+            int tx = bx;
+            if (tx < 0 || tx >= sp.ntx) {
+                if (sp.wall_x) continue;
+                tx = tx < 0 ? tx + sp.ntx : tx - sp.ntx;
+            }
+            if (reg_prev[by * sp.ntx + tx] > 0) {
+                any = true;
+                if (dy == 0 && bx >= b0 && bx <= b1) own = true;
+            }
+        }
+    }
+    if (own && !busy_prev[r]) atomicOr(err, ERR_FREE_REGION);
+    busy[r] = any ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -29,6 +29,7 @@ struct lbrmt_sim {
     long long xi_total = 0;         // reals in one xi buffer (all solid tiles)
     long long ntiles_cap = 0;       // registry / pool capacity in tiles (largest over the tile shapes)
     long long mass_parts_cap = 0;  // K1 mass partial slots allocated (max over tile shapes)
+    long long nregions_cap = 0;    // K1 regions (busy flags) allocated (max over tile shapes)
     bool inited = false;
     long long steps = 0;
     bool use_graphs = true;

@@ -243,6 +243,15 @@ def place_shapes(rng, sc, specs, rho_lo, rho_hi, g_lo, g_hi, max_tries=400):
     return sc
 
 
+def heavy_disk_drift(n=96, r=12.0, tau=0.6, G=0.02, rho_s=1.5, accel=-1e-5):
+    """A single disk in an n x n periodic box, everything driven by one uniform
+    acceleration (force on all phases): the stiffest, heaviest disk of the
+    4096^2 mixing workload at its tau, in the near-uniform part of its forcing."""
+    sc = _base(n, n, 0, 0, tau, force_kind=1, force_a=(accel, 0.0), name=f"heavy_disk_drift_{n}")
+    sc["solids"].append({"x": n / 2 + 0.3, "y": n / 2 + 0.17, "r": float(r), "rho_s": float(rho_s), "G": float(G)})
+    return sc
+
+
 def shapes_small(seed=0, nx=128, ny=96, gravity=2e-4):
     """128x96 box, periodic x, walls y, tau 0.7, gravity: a horizontal and a
     vertical ellipse, a square, a rectangle and a disk, rho_s~U[1.1,1.6],
