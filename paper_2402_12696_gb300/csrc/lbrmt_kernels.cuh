@@ -245,6 +245,19 @@ __device__ __forceinline__ R rest_base(const SimParams &sp, const int *reg, cons
 
 // Moments of node (i, j): rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
 // reg/pool: registry and force pool of the step that wrote the populations.
+// rho and v from the stored populations fq, the rest base dro and the carry (cx, cy).
+template <class R>
+__device__ __forceinline__ void moments_from(const SimParams &sp, const R (&fq)[9], R dro, R cx, R cy, R &rho, R &u,
+                                             R &v) {
+    R dr = dro + (((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8]);
+    R jx = (fq[1] - fq[3]) + (fq[5] - fq[6]) + (fq[8] - fq[7]);
+    R jy = (fq[2] - fq[4]) + (fq[5] - fq[7]) + (fq[6] - fq[8]);
+    rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
+    R inv = rcp_rn<R>(rho);  // as the LB kernel
+    u = (jx + cx) * inv;
+    v = (jy + cy) * inv;
+}
+
 template <class R, class S>
 __device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const S *carry, const int *reg,
                                              const R *pool, int i, int j, R &rho, R &u, R &v) {
@@ -252,14 +265,8 @@ __device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, co
     R fq[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) fq[q] = ldS<S, R>(f + q * sp.P + c);
-    R dr = rest_base<R>(sp, reg, pool, i, j) +
-           (((fq[0] + fq[1]) + (fq[2] + fq[3])) + ((fq[4] + fq[5]) + (fq[6] + fq[7])) + fq[8]);
-    R jx = (fq[1] - fq[3]) + (fq[5] - fq[6]) + (fq[8] - fq[7]);
-    R jy = (fq[2] - fq[4]) + (fq[5] - fq[7]) + (fq[6] - fq[8]);
-    rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
-    R inv = rcp_rn<R>(rho);  // as the LB kernel
-    u = (jx + ldC<S, R>(carry + c)) * inv;
-    v = (jy + ldC<S, R>(carry + sp.P + c)) * inv;
+    moments_from<R>(sp, fq, rest_base<R>(sp, reg, pool, i, j), ldC<S, R>(carry + c), ldC<S, R>(carry + sp.P + c), rho,
+                    u, v);
 }
 
 // Block-wide sum of NV doubles (blockDim.x multiple of 32, <= 1024).
@@ -402,6 +409,55 @@ __device__ __forceinline__ void lsq_window5(Lsq<R> &A, const signed char *lab, c
         }
 }
 
+// The 5x5 window without directional weights (layers beyond the second): the
+// weights 2^{-(|dx|+|dy|)} then depend only on which of the 24 nodes are valid,
+// so the sums of M and of the collinearity test follow from each row's 5-bit
+// validity mask by bit counts.  Every term is a multiple of 1/16, so these sums
+// are exact, as the running sums of lsq_window5 are; only the right-hand sides
+// read the nodes' values, accumulated in the same node order.
+template <class R>
+__device__ __forceinline__ void lsq_window5_mask(Lsq<R> &A, const signed char *lab, const R *X, const R *Y, int t,
+                                                 int T, int l) {
+    int n = 0, sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+    int a16 = 0, b16 = 0, c16 = 0, d16 = 0, e16 = 0, f16 = 0;  // 16 x the entries of M
+    unsigned rows = 0;                                         // 5 bits per row, dx = -2..2
+#pragma unroll
+    for (int dy = -2; dy <= 2; dy++) {
+        unsigned r = 0;
+#pragma unroll
+        for (int dx = -2; dx <= 2; dx++) {
+            if (dx == 0 && dy == 0) continue;  // the target itself (layer l) never counts
+            const int L = lab[t + dy * T + dx];
+            r |= ((unsigned)L < (unsigned)l ? 1u : 0u) << (dx + 2);
+        }
+        rows |= r << (5 * (dy + 2));
+        const int c0 = (r >> 2) & 1, p1 = __popc(r & 0x0au), p2 = __popc(r & 0x11u);
+        const int d1 = (int)((r >> 3) & 1) - (int)((r >> 1) & 1), d2 = (int)((r >> 4) & 1) - (int)(r & 1);
+        const int nr = c0 + p1 + p2, sxr = d1 + 2 * d2;
+        // row sums of 4 2^{-|dx|} dx^k (k = 0, 1, 2), row weight 4 2^{-|dy|}
+        const int s0 = 4 * c0 + 2 * p1 + p2, s1 = 2 * d1 + 2 * d2, s2 = 2 * p1 + 4 * p2;
+        const int g = dy == 0 ? 4 : (dy == 1 || dy == -1 ? 2 : 1);
+        n += nr; sx += sxr; sxx += p1 + 4 * p2; sy += dy * nr; syy += dy * dy * nr; sxy += dy * sxr;
+        f16 += g * s0; c16 += g * s1; a16 += g * s2; e16 += g * dy * s0; d16 += g * dy * dy * s0; b16 += g * dy * s1;
+    }
+    A.nvalid += n; A.n += n; A.sx += sx; A.sy += sy; A.sxx += sxx; A.syy += syy; A.sxy += sxy;
+    const R q = R(0.0625);
+    A.a += R(a16) * q; A.b += R(b16) * q; A.c += R(c16) * q; A.d += R(d16) * q; A.e += R(e16) * q; A.fw += R(f16) * q;
+#pragma unroll
+    for (int dy = -2; dy <= 2; dy++)
+#pragma unroll
+        for (int dx = -2; dx <= 2; dx++) {
+            if (dx == 0 && dy == 0) continue;
+            if (!((rows >> (5 * (dy + 2) + dx + 2)) & 1u)) continue;
+            const int k = t + dy * T + dx;
+            const R Xv = X[k] - A.xref, Yv = Y[k] - A.yref;
+            const R w = pow2neg<R>((dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy));
+            const R wx = w * R(dx), wy = w * R(dy);
+            A.bx0 += wx * Xv; A.bx1 += wy * Xv; A.bx2 += w * Xv;
+            A.by0 += wx * Yv; A.by1 += wy * Yv; A.by2 += w * Yv;
+        }
+}
+
 // Weighted least-squares fit of one target (Sec. 3.2, steps (i)-(iii)).  The
 // weights do not depend on the window size, so growing r from r-1 only adds
 // the ring |dx| = r or |dy| = r to the sums of the smaller window.  The fit is
@@ -426,7 +482,7 @@ __device__ void extrapolate_target(const SimParams &sp, const signed char *lab, 
     }
     if (tx >= 2 && ty >= 2 && tx < T - 2 && ty < T - 2) {
         if (use_n) lsq_window5<R, true>(A, lab, X, Y, t, T, l, nhx, nhy);
-        else lsq_window5<R, false>(A, lab, X, Y, t, T, l, nhx, nhy);
+        else lsq_window5_mask<R>(A, lab, X, Y, t, T, l);
     } else {
         for (int dy = -2; dy <= 2; dy++)
             for (int dx = -2; dx <= 2; dx++)
@@ -623,6 +679,75 @@ struct BoxWalk {
     __device__ __forceinline__ void next() { c += dc; r += dr; if (c >= w) { c -= w; r++; } }
 };
 
+// One node of pass 0 (advection): its stored state and the LB state at it,
+// gathered with independent loads (the rest base is loaded whatever the
+// registry count and selected after).
+template <class R>
+struct P0Node {
+    int ix, iy, cnt;
+    R ex, ey, phi, cx, cy, pv;
+    R f[9];
+};
+
+template <class R, class S>
+__device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, S> &a, const R *Xi, const R *Yi,
+                                          const R *Pi, int T, int2 oo, int shx, int shy, int entry, P0Node<R> &nd) {
+    nd.ix = entry & 0xffff;
+    nd.iy = entry >> 16;
+    const int k = nd.iy * T + nd.ix;
+    const int i = wrapi(oo.x + nd.ix - shx, sp.nx), j = wrapi(oo.y + nd.iy - shy, sp.ny);
+    const long long c = (long long)j * sp.nx + i;
+    const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    nd.ex = Xi[k];
+    nd.ey = Yi[k];
+    nd.phi = Pi[k];
+#pragma unroll
+    for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(a.f + q * sp.P + c);
+    nd.cx = ldC<S, R>(a.carry + c);
+    nd.cy = ldC<S, R>(a.carry + sp.P + c);
+    nd.cnt = a.reg_prev[tile];
+    nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
+}
+
+// The rest of pass 0 for a gathered node of the blur zone or the solid:
+// statistics, and for a solid node the upwind advection (Eqs. 3_1_refmap_adv,
+// 3_1_eno) into the output tile.
+template <class R, class S>
+__device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, S> &a, const P0Node<R> &nd,
+                                          const R *Xi, const R *Yi, R *Xo, R *Yo, signed char *lab, int T,
+                                          const Frame &fi, int shx, int shy, R ddx, R ddy, R eps, R (&stl)[6],
+                                          int (&sb)[4]) {
+    const int ix = nd.ix, iy = nd.iy, lx = ix - shx, ly = iy - shy;
+    R rho, u, v;
+    moments_from<R>(sp, nd.f, nd.cnt > 0 ? nd.pv : R(0), nd.cx, nd.cy, rho, u, v);
+    const R lam = R(1) - heaviside<R>(nd.phi, eps);
+    stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
+    stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
+    if (!(nd.phi < -R(PHI_TIE))) return;
+    const int sx = (u >= R(0)) ? -1 : 1, sy = (v >= R(0)) ? -1 : 1;
+    const int x2 = ix + 2 * sx, y2 = iy + 2 * sy;
+    if (x2 < fi.bx0 || x2 > fi.bx1 || y2 < fi.by0 || y2 > fi.by1) {
+        atomicOr(a.err, ERR_STENCIL);
+        return;
+    }
+    const int k = iy * T + ix;
+    const int k1 = k + sx, k2 = k + 2 * sx, k3 = k + sy * T, k4 = k + 2 * sy * T;
+    const R X1 = Xi[k1], X2 = Xi[k2], X3 = Xi[k3], X4 = Xi[k4];
+    const R Y1 = Yi[k1], Y2 = Yi[k2], Y3 = Yi[k3], Y4 = Yi[k4];
+    if (!(X1 == X1 && X2 == X2 && X3 == X3 && X4 == X4)) atomicOr(a.err, ERR_STENCIL);
+    // one-sided second-order differences of eta; xi = eta + position adds (1,0)/(0,1)
+    const R ex = nd.ex, ey = nd.ey;
+    const R hx = R(-sx) * R(0.5), hy = R(-sy) * R(0.5);
+    const R dXdx = hx * (R(3) * ex - R(4) * X1 + X2), dYdx = hx * (R(3) * ey - R(4) * Y1 + Y2);
+    const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
+    // xi = eta + x - d: the node's own motion enters as -(u - dd)
+    const int t = ly * T + lx;
+    Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
+    Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
+    lab[t] = 0;
+    sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
+}
+
 template <class R, class S>
 __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int s) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -660,58 +785,74 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
 
     // Pass 0: the advected set S = {domain nodes with phi^n < 0}, Eqs. 3_1_refmap_adv / 3_1_eno,
     // over the input tile's box (the whole tile at initialisation).
-    {
-        const int ib0 = a.init ? 0 : fi.bx0, ib1 = a.init ? T - 1 : fi.bx1;
-        const int jb0 = a.init ? 0 : fi.by0, jb1 = a.init ? T - 1 : fi.by1;
-        const int bw = ib1 - ib0 + 1, bn = (ib1 >= ib0 && jb1 >= jb0) ? bw * (jb1 - jb0 + 1) : 0;
+    const int ib0 = a.init ? 0 : fi.bx0, ib1 = a.init ? T - 1 : fi.bx1;
+    const int jb0 = a.init ? 0 : fi.by0, jb1 = a.init ? T - 1 : fi.by1;
+    const int bw = ib1 - ib0 + 1, bn = (ib1 >= ib0 && jb1 >= jb0) ? bw * (jb1 - jb0 + 1) : 0;
+    if (a.init) {
         BoxWalk wk(bw);
         for (int kk = threadIdx.x; kk < bn; kk += blockDim.x, wk.next()) {
             const int ix = ib0 + wk.c, iy = jb0 + wk.r;  // input-tile coordinates
             const int lx = ix - shx, ly = iy - shy;      // output-tile coordinates
             const int gx = oo.x + lx, gy = oo.y + ly;
-            if (a.init) {
-                // xi = x: eta = d of the initial frame
-                const R e0x = R(frame_d(fo, sd.xc, true)), e0y = R(frame_d(fo, sd.yc, false));
-                if (domain_cell(sp, gx, gy) && phi_eta(e0x, e0y, lx, ly, fo, rq) < -R(PHI_TIE)) {
-                    const int t = ly * T + lx;
-                    Xo[t] = e0x; Yo[t] = e0y; lab[t] = 0;
-                    sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
+            // xi = x: eta = d of the initial frame
+            const R e0x = R(frame_d(fo, sd.xc, true)), e0y = R(frame_d(fo, sd.yc, false));
+            if (domain_cell(sp, gx, gy) && phi_eta(e0x, e0y, lx, ly, fo, rq) < -R(PHI_TIE)) {
+                const int t = ly * T + lx;
+                Xo[t] = e0x; Yo[t] = e0y; lab[t] = 0;
+                sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
+            }
+        }
+    } else {
+        // (a) each warp lists, in box order, the nodes of its share of the box
+        // (items threadIdx.x + m blockDim.x) that lie in the blur zone or the
+        // solid, in its own segment of the (not yet used) layer lists; (b) it
+        // then advances them two per lane at a time, every load of both nodes
+        // issued before the arithmetic.  A warp whose segment overflows walks
+        // its share node by node instead.
+        const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
+        const int seg_cap = (2 * LIST_CAP) / nw;
+        int *seg = lists + warp * seg_cap;
+        int nseg = 0;
+        BoxWalk wk(bw);
+        for (int base = 0; base < bn; base += blockDim.x, wk.next()) {
+            const int kk = base + threadIdx.x;
+            bool hit = false;
+            int entry = 0;
+            if (kk < bn) {
+                const int ix = ib0 + wk.c, iy = jb0 + wk.r;
+                const int lx = ix - shx, ly = iy - shy;
+                const R phi = Pi[iy * T + ix];
+                if (phi < eps && domain_cell(sp, oo.x + lx, oo.y + ly)) {
+                    if (lx < 0 || ly < 0 || lx >= T || ly >= T) atomicOr(a.err, ERR_TILE_OVERFLOW);
+                    else { hit = true; entry = ix | (iy << 16); }
                 }
-                continue;
             }
-            const int k = iy * T + ix;
-            const R ex = Xi[k], ey = Yi[k];
-            if (!(ex == ex)) continue;
-            const R phi = Pi[k];
-            if (!(phi < eps) || !domain_cell(sp, gx, gy)) continue;
-            if (lx < 0 || ly < 0 || lx >= T || ly >= T) { atomicOr(a.err, ERR_TILE_OVERFLOW); continue; }
-            R rho, u, v;
-            node_moments<R, S>(sp, a.f, a.carry, a.reg_prev, a.pool_prev, wrapi(gx, sp.nx), wrapi(gy, sp.ny),
-                               rho, u, v);
-            const R lam = R(1) - heaviside<R>(phi, eps);
-            stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
-            stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
-            if (!(phi < -R(PHI_TIE))) continue;
-            const int sx = (u >= R(0)) ? -1 : 1, sy = (v >= R(0)) ? -1 : 1;
-            const int x2 = ix + 2 * sx, y2 = iy + 2 * sy;
-            if (x2 < fi.bx0 || x2 > fi.bx1 || y2 < fi.by0 || y2 > fi.by1) {
-                atomicOr(a.err, ERR_STENCIL);
-                continue;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            const int pos = nseg + __popc(m & ((1u << lane) - 1u));
+            if (hit && pos < seg_cap) seg[pos] = entry;
+            nseg += __popc(m);
+        }
+        __syncwarp();
+        if (nseg <= seg_cap) {
+            for (int e = lane; e < nseg; e += 64) {
+                const bool two = e + 32 < nseg;
+                P0Node<R> n1, n2;
+                p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[e], n1);
+                p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[two ? e + 32 : e], n2);
+                p0_finish<R, S>(sp, a, n1, Xi, Yi, Xo, Yo, lab, T, fi, shx, shy, ddx, ddy, eps, stl, sb);
+                if (two) p0_finish<R, S>(sp, a, n2, Xi, Yi, Xo, Yo, lab, T, fi, shx, shy, ddx, ddy, eps, stl, sb);
             }
-            const int k1 = k + sx, k2 = k + 2 * sx, k3 = k + sy * T, k4 = k + 2 * sy * T;
-            const R X1 = Xi[k1], X2 = Xi[k2], X3 = Xi[k3], X4 = Xi[k4];
-            const R Y1 = Yi[k1], Y2 = Yi[k2], Y3 = Yi[k3], Y4 = Yi[k4];
-            if (!(X1 == X1 && X2 == X2 && X3 == X3 && X4 == X4)) atomicOr(a.err, ERR_STENCIL);
-            // one-sided second-order differences of eta; xi = eta + position adds (1,0)/(0,1)
-            const R hx = R(-sx) * R(0.5), hy = R(-sy) * R(0.5);
-            const R dXdx = hx * (R(3) * ex - R(4) * X1 + X2), dYdx = hx * (R(3) * ey - R(4) * Y1 + Y2);
-            const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
-            // xi = eta + x - d: the node's own motion enters as -(u - dd)
-            const int t = ly * T + lx;
-            Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
-            Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
-            lab[t] = 0;
-            sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
+        } else {
+            BoxWalk wk2(bw);
+            for (int kk = threadIdx.x; kk < bn; kk += blockDim.x, wk2.next()) {
+                const int ix = ib0 + wk2.c, iy = jb0 + wk2.r;
+                const int lx = ix - shx, ly = iy - shy;
+                if (!(Pi[iy * T + ix] < eps) || !domain_cell(sp, oo.x + lx, oo.y + ly)) continue;
+                if (lx < 0 || ly < 0 || lx >= T || ly >= T) continue;  // flagged in (a)
+                P0Node<R> nd;
+                p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, ix | (iy << 16), nd);
+                p0_finish<R, S>(sp, a, nd, Xi, Yi, Xo, Yo, lab, T, fi, shx, shy, ddx, ddy, eps, stl, sb);
+            }
         }
     }
     for (int k = 0; k < 4; k++) warp_minmax(sb[k], (k & 1) == 0);
