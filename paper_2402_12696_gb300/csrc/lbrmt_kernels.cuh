@@ -657,19 +657,6 @@ __device__ __forceinline__ int tile_ranges(int lo, int hi, int n, int wall, int 
     return 2;
 }
 
-// Claim a free label byte (-1 -> l) with a CAS on the 32-bit word holding it.
-__device__ __forceinline__ bool claim_label(signed char *lab, int q, int l) {
-    unsigned *w = reinterpret_cast<unsigned *>(lab + (q & ~3));
-    const int sh = (q & 3) * 8;
-    unsigned old = *reinterpret_cast<volatile unsigned *>(w), assumed;
-    do {
-        assumed = old;
-        if (((assumed >> sh) & 0xffu) != 0xffu) return false;
-        old = atomicCAS(w, assumed, (assumed & ~(0xffu << sh)) | ((unsigned)l << sh));
-    } while (old != assumed);
-    return true;
-}
-
 // Row-major walk of a w-wide box by a CTA: (c, r) of item k, advanced by blockDim.x items at a time.
 struct BoxWalk {
     int c, r, dc, dr, w;
@@ -751,7 +738,8 @@ __device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, 
 template <class R, class S>
 __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int s) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int nlist[2];  // list lengths of alternate layers
+    __shared__ int lcnt[24];  // per layer: node count, then the next free list slot
+    __shared__ int loff[24];  // per layer: first list slot (layer l at loff[l] .. loff[l + 1])
     __shared__ int bb[12];    // S bbox (0-3), band bbox (4-7), blur-zone bbox (8-11)
     __shared__ double red[32 * 6];
     __syncthreads();  // the shared state of a previous solid is no longer read
@@ -776,7 +764,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     const R *Pi = a.init ? nullptr : Yi + TT;  // phi^n, stored by the previous step's relabel
     const R eps = pick<R>(sp.eps, sp.eps_f);
     if (threadIdx.x < 12) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
-    if (threadIdx.x < 2) nlist[threadIdx.x] = 0;
+    if (threadIdx.x < 24) lcnt[threadIdx.x] = 0;
     for (int k = threadIdx.x; k < (TT + 15) >> 4; k += blockDim.x)
         reinterpret_cast<int4 *>(lab)[k] = make_int4(-1, -1, -1, -1);
     R stl[6] = {0, 0, 0, 0, 0, 0};  // sum lambda, lambda lx, lambda ly, lambda rho, lambda rho u, lambda rho v
@@ -861,74 +849,91 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     }
     __syncthreads();
 
-    // Layers 1..n_layers by 4-neighbour dilation; extrapolate each layer (Sec. 3.2).
-    // Layer 1 comes from a scan of the solid bbox grown by one; layer l > 1 from
-    // the free 4-neighbours of the layer l-1 list (claimed with a CAS).  Nodes
-    // beyond the pad of a no-slip side are never labelled.
+    // Layers 1..n_layers by 4-neighbour dilation of S (Sec. 3.2; 11 layers, Sec. 4),
+    // within the allowed cells (nodes beyond the pad of a no-slip side never
+    // count).  The allowed cells of a tile form a rectangle, where the number of
+    // 4-neighbour dilation steps from S is the L1 distance to S: the labels come
+    // from a separable L1 distance transform in place on the label bytes (a
+    // sweep per row, then one per column, capped at n_layers + 1), and a
+    // counting pass lists the nodes of every layer.  The layers are then fitted
+    // one after another (Sec. 3.2), each from S and the layers before it.
     const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
     if (sx0 > sx1) {
         if (threadIdx.x == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);  // the solid vanished
     }
-    bool prev_full = true;  // previous list complete (no overflow)
-    int nl_prev = 0;        // size of the previous layer's list (same value in every thread)
-    for (int l = 1; l <= sp.n_layers && sx0 <= sx1; l++) {
-        int *cur = lists + (l & 1) * LIST_CAP;
-        const int *prv = lists + ((l + 1) & 1) * LIST_CAP;
-        const int nprev = min(nl_prev, LIST_CAP);
-        int *cnt = &nlist[l & 1];  // zero: reset after the layer two back was read
-        __syncthreads();
-        if (l == 1 || !prev_full) {
-            const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
-            const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
-            const int nround = (n + 31) & ~31;
-            BoxWalk wk(w);
-            for (int k = threadIdx.x; k < nround; k += blockDim.x, wk.next()) {
-                bool hit = false;
-                const int lx = x0 + wk.c, ly = y0 + wk.r;
-                const int t = ly * T + lx;
-                if (k < n && lab[t] == -1 && allowed_cell(sp, oo.x + lx, oo.y + ly))
-                    hit = (lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
-                          (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1);
-                const unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    int base = 0;
-                    if (lane == leader) base = atomicAdd(cnt, __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (hit) {
-                        lab[t] = (signed char)l;
-                        const int idx = base + __popc(m & ((1u << lane) - 1u));
-                        if (idx < LIST_CAP) cur[idx] = lx | (ly << 16);
-                    }
-                }
+    const int NL = sp.n_layers;
+    bool listed = false;  // every layer's nodes are in the lists (else each layer scans the tile)
+    if (sx0 <= sx1) {
+        const int x0 = max(sx0 - NL, 0), x1 = min(sx1 + NL, T - 1), y0 = max(sy0 - NL, 0), y1 = min(sy1 + NL, T - 1);
+        const int cap = NL + 1;
+        for (int y = y0 + (int)threadIdx.x; y <= y1; y += blockDim.x) {
+            signed char *row = lab + y * T;
+            int last = -(1 << 20);
+            for (int x = x0; x <= x1; x++) {
+                if (row[x] == 0) last = x;
+                else row[x] = (signed char)min(x - last, cap);
             }
-        } else {
-            for (int k = threadIdx.x; k < 4 * nprev; k += blockDim.x) {
-                const int p = prv[k >> 2], dir = k & 3;
-                int lx = p & 0xffff, ly = p >> 16;
-                if (dir == 0) lx--;
-                else if (dir == 1) lx++;
-                else if (dir == 2) ly--;
-                else ly++;
-                if (lx < 0 || ly < 0 || lx >= T || ly >= T) continue;
-                const int q = ly * T + lx;
-                if (lab[q] == -1 && allowed_cell(sp, oo.x + lx, oo.y + ly) && claim_label(lab, q, l)) {
-                    const int idx = atomicAdd(cnt, 1);
-                    if (idx < LIST_CAP) cur[idx] = lx | (ly << 16);
-                }
+            last = 1 << 20;
+            for (int x = x1; x >= x0; x--) {
+                if (row[x] == 0) last = x;
+                else row[x] = (signed char)min((int)row[x], min(last - x, cap));
             }
         }
         __syncthreads();
-        const int nl = *cnt;
-        if (threadIdx.x == 0) nlist[(l + 1) & 1] = 0;  // every thread read it before this layer's first barrier
-        nl_prev = nl;
-        prev_full = nl <= LIST_CAP;
-        const int nitems = prev_full ? nl : TT;
+        for (int x = x0 + (int)threadIdx.x; x <= x1; x += blockDim.x) {
+            int d = cap;
+            for (int y = y0; y <= y1; y++) {
+                signed char *q = lab + y * T + x;
+                d = min((int)*q, d + 1);
+                *q = (signed char)d;
+            }
+            d = cap;
+            for (int y = y1; y >= y0; y--) {
+                signed char *q = lab + y * T + x;
+                d = min((int)*q, d + 1);
+                *q = (signed char)d;
+            }
+        }
+        __syncthreads();
+        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+        {
+            BoxWalk wk(w);
+            for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
+                const int lx = x0 + wk.c, ly = y0 + wk.r, t = ly * T + lx;
+                const int d = lab[t];
+                if (d < 1) continue;
+                if (d <= NL && allowed_cell(sp, oo.x + lx, oo.y + ly)) atomicAdd(&lcnt[d], 1);
+                else lab[t] = -1;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            loff[1] = 0;
+            for (int l = 1; l <= NL; l++) {
+                loff[l + 1] = loff[l] + lcnt[l];
+                lcnt[l] = loff[l];
+            }
+        }
+        __syncthreads();
+        listed = loff[NL + 1] <= 2 * LIST_CAP;
+        if (listed) {
+            BoxWalk wk(w);
+            for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
+                const int lx = x0 + wk.c, ly = y0 + wk.r;
+                const int d = lab[ly * T + lx];
+                if (d >= 1) lists[atomicAdd(&lcnt[d], 1)] = lx | (ly << 16);
+            }
+        }
+        __syncthreads();
+    }
+    for (int l = 1; l <= NL && sx0 <= sx1; l++) {
+        const int nitems = listed ? loff[l + 1] - loff[l] : TT;
         for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
             int lx, ly;
-            if (prev_full) {
-                lx = cur[k] & 0xffff; ly = cur[k] >> 16;
-            } else {  // overflowed list: scan the tile
+            if (listed) {
+                const int e = lists[loff[l] + k];
+                lx = e & 0xffff; ly = e >> 16;
+            } else {  // too many band nodes for the lists: scan the tile
                 lx = k % T; ly = k / T;
                 if (lab[k] != l) continue;
             }
@@ -956,8 +961,8 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
             }
             extrapolate_target<R>(sp, lab, Xo, Yo, T, lx, ly, l, use_n, nhx, nhy, a.err);
         }
+        __syncthreads();
     }
-    __syncthreads();
 
     // Relabel phi^{n+1} = phi_0(xi^{n+1}) over the box that can hold band nodes
     // (layer l lies within l of the solid bbox); band and blur-zone bboxes;
