@@ -1150,46 +1150,51 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
     {
         const int tx = tile % sp.ntx, ty = tile / sp.ntx;
         const int i0 = tx * TX, j0 = ty * sp.ty;
-        if (threadIdx.x == 0) {
-            int n = min(a.reg_count[tile], sp.kmax);
-            for (int k = 0; k < n; k++) ids[k] = a.reg_solids[tile * KMAX + k];
-            for (int k = 1; k < n; k++) {  // sort by id: fixed summation order
-                int v = ids[k], m = k - 1;
-                while (m >= 0 && ids[m] > v) { ids[m + 1] = ids[m]; m--; }
-                ids[m + 1] = v;
+        // The tile's solids and their descriptors, read by the first warp in
+        // parallel; slot = rank of the id (ids are distinct): a fixed summation order.
+        if (threadIdx.x < 32) {
+            const int n = min(a.reg_count[tile], sp.kmax);
+            const int k = threadIdx.x;
+            const int id = k < n ? a.reg_solids[tile * KMAX + k] : 0x7fffffff;
+            int rank = 0;
+#pragma unroll
+            for (int m = 0; m < KMAX; m++) rank += __shfl_sync(0xffffffffu, id, m) < id ? 1 : 0;
+            if (k < n) {
+                const SolidDesc &sd = a.solids[id];
+                ids[rank] = id;
+                sfr[rank] = a.frame[id];
+                sG[rank] = pick<R>(sd.G, sd.G_f);
+                sD[rank] = pick<R>(sd.drho, sd.drho_f);
+                sA[rank] = pick<R>(sd.accel, sd.accel_f);
+                srq[rank] = Rsq<R>(sd);
+                sT[rank] = sd.T;
+                soff[rank] = sd.off;
             }
-            fs.nk = n;
-        }
-        __syncthreads();
-        if (threadIdx.x < fs.nk) {
-            const SolidDesc &sd = a.solids[ids[threadIdx.x]];
-            sfr[threadIdx.x] = a.frame[ids[threadIdx.x]];
-            sG[threadIdx.x] = pick<R>(sd.G, sd.G_f);
-            sD[threadIdx.x] = pick<R>(sd.drho, sd.drho_f);
-            sA[threadIdx.x] = pick<R>(sd.accel, sd.accel_f);
-            srq[threadIdx.x] = Rsq<R>(sd);
-            sT[threadIdx.x] = sd.T;
-            soff[threadIdx.x] = sd.off;
+            if (k == 0) fs.nk = n;
         }
         __syncthreads();
         const int n = fs.nk;
         // Stage each solid's xi (and phi) on the tile plus a one-node halo.
-        for (int idx = threadIdx.x; idx < n * PN; idx += blockDim.x) {
-            const int ks = idx / PN, p = idx % PN;
-            const int px = p % PX, py = p / PX;
-            const int gx = i0 - 1 + px, gy = j0 - 1 + py;
+        for (int ks = 0; ks < n; ks++) {
             const Frame fr = sfr[ks];
             const int T = sT[ks];
-            const int lx = sp.wall_x ? gx - fr.ox : wrapi(gx - fr.ox, sp.nx);
-            const int ly = sp.wall_y ? gy - fr.oy : wrapi(gy - fr.oy, sp.ny);
-            R X = nanv<R>(), Y = nanv<R>(), P = nanv<R>();
-            if (in_box(fr, lx, ly)) {
-                const R *Xs = a.xi + soff[ks];
-                X = Xs[ly * T + lx];
-                Y = Xs[T * T + ly * T + lx];
-                if (X == X) P = Xs[2 * T * T + ly * T + lx];  // the stored phi
+            const R *Xs = a.xi + soff[ks];
+            // local coordinates of patch node (0, 0) in the solid's frame (periodic: wrapped once here)
+            const int bx0 = sp.wall_x ? i0 - 1 - fr.ox : wrapi(i0 - 1 - fr.ox, sp.nx);
+            const int by0 = sp.wall_y ? j0 - 1 - fr.oy : wrapi(j0 - 1 - fr.oy, sp.ny);
+            BoxWalk wk(PX);
+            for (int p = threadIdx.x; p < PN; p += blockDim.x, wk.next()) {
+                int lx = bx0 + wk.c, ly = by0 + wk.r;
+                if (!sp.wall_x) while (lx >= sp.nx) lx -= sp.nx;
+                if (!sp.wall_y) while (ly >= sp.ny) ly -= sp.ny;
+                R X = nanv<R>(), Y = nanv<R>(), P = nanv<R>();
+                if (in_box(fr, lx, ly)) {
+                    X = Xs[ly * T + lx];
+                    Y = Xs[T * T + ly * T + lx];
+                    if (X == X) P = Xs[2 * T * T + ly * T + lx];  // the stored phi
+                }
+                sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
             }
-            sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
         }
         __syncthreads();
         // Half-edge stresses: blended solid stress (Eq. 3_6_global_stress) plus contact.
