@@ -240,11 +240,16 @@ struct Engine {
         return a;
     }
 
-    static LbArgs<R, S> lb_args(const DevState &d, int parity) {
+    static LbArgs<R, S> lb_args(const SimParams &sp, const DevState &d, int parity) {
         const int p = parity, q = 1 - parity;
         LbArgs<R, S> a;
         a.f_in = (const S *)d.f[p];
         a.f_out = (S *)d.f[q];
+        for (int k = 0; k < 9; k++) {
+            a.fin_q[k] = a.f_in + (long long)k * sp.P;
+            // the push target of an interior node: the offset is positive for k >= 1 (P > nx + 1)
+            a.fout_push[k] = a.f_out + (long long)k * sp.P + (long long)cyq(k) * sp.nx + cxq(k);
+        }
         a.carry = (S *)d.carry;
         a.fbody = (const R *)d.fbody;
         a.bfield = (const R *)d.bfield;
@@ -266,7 +271,7 @@ struct Engine {
         for (int p = 0; p < 2; p++) {
             b.rmt[p] = rmt_args(d, p, 0);
             b.frc[p] = force_args(d, 1 - p, p);
-            b.lb[p] = lb_args(d, p);
+            b.lb[p] = lb_args(sp, d, p);
         }
         std::memcpy(dst, &b, sizeof(b));
     }
@@ -286,7 +291,7 @@ struct Engine {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rmt_batch_kernel<R, S>, RMT_THREADS, bl->rmt_smem);
         if (e != cudaSuccess) return e;
         bl->rmt_blocks = std::max(1, std::min(nitems_rmt, nsm * std::max(per, 1)));
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_batch_kernel<R, S>, TILE_N, bl->force_smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_batch_kernel<R, S>, K3_THREADS, bl->force_smem);
         if (e != cudaSuccess) return e;
         bl->force_blocks = nsm * std::max(per, 1);
         return cudaSuccess;
@@ -298,7 +303,7 @@ struct Engine {
         if (ev) cudaEventRecord(ev[0], st);
         if (n_rmt > 0) rmt_batch_kernel<R, S><<<bl.rmt_blocks, RMT_THREADS, bl.rmt_smem, st>>>(ds, rmt_items, n_rmt, parity);
         if (ev) cudaEventRecord(ev[1], st);
-        if (n_rmt > 0) force_batch_kernel<R, S><<<bl.force_blocks, TILE_N, bl.force_smem, st>>>(ds, nsim, parity);
+        if (n_rmt > 0) force_batch_kernel<R, S><<<bl.force_blocks, K3_THREADS, bl.force_smem, st>>>(ds, nsim, parity);
         if (ev) cudaEventRecord(ev[2], st);
         if (n_lb > 0) lb_batch_kernel<R, S><<<n_lb, TILE_N, 0, st>>>(ds, lb_items, parity);
         if (ev) cudaEventRecord(ev[3], st);
@@ -331,7 +336,7 @@ struct Engine {
         const bool overlap = step_overlaps(sp, li) && !ev;
         const int prio = overlap ? li.prio_hi : 0;
         const dim3 grid(sp.nrx, sp.nty), blk(TILE_N);
-        LbArgs<R, S> la = lb_args(d, p);
+        LbArgs<R, S> la = lb_args(sp, d, p);
         la.tape = static_cast<R *>(tape);
         const int nreg = sp.nrx * sp.nty;
         if (overlap) {  // fork: classification and K1 of the free regions on the side stream

@@ -144,8 +144,8 @@ struct DevState {
 // ---------------------------------------------------------------------------
 // D2Q9 (Table d2q9): c_q and weights; opposite directions.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int cxq(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
-__device__ __forceinline__ int cyq(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
+__host__ __device__ __forceinline__ int cxq(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
+__host__ __device__ __forceinline__ int cyq(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
 __device__ __forceinline__ int oppq(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) & 3) + 1 : ((q - 3) & 3) + 5); }
 template <class R> __device__ __forceinline__ R wq(int q) { return q == 0 ? R(4) / R(9) : (q <= 4 ? R(1) / R(9) : R(1) / R(36)); }
 
@@ -1109,6 +1109,12 @@ __device__ __forceinline__ bool stress_from_grad(R Axx, R Axy, R Ayx, R Ayy, R G
 }
 
 // Per-tile constants of the registered solids (static shared memory of K3).
+// Threads per CTA of the batched K3: the 2 tx ty + tx + ty half-edges of a
+// 16x16 tile (544) take two rounds of 288 threads where 256 threads need three
+// (measured faster for the batch; the single-simulation K3 keeps TILE_N threads,
+// which fit one more CTA per SM).  The node phase uses the first TILE_N threads.
+constexpr int K3_THREADS = TILE_N + 32;
+
 template <class R>
 struct ForceShared {
     int ids[KMAX];
@@ -1257,7 +1263,7 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
         {
             const int cx = threadIdx.x & (TX - 1), cy = threadIdx.x >> sp.lx;
             const int i = i0 + cx, j = j0 + cy;
-            if (i < sp.nx && j < sp.ny) {
+            if (threadIdx.x < TILE_N && i < sp.nx && j < sp.ny) {
                 const R *tl = eT + 3 * (cy * (TX + 1) + cx), *tr = eT + 3 * (cy * (TX + 1) + cx + 1);
                 const R *tb = eT + 3 * (NXE + cy * TX + cx), *tt = eT + 3 * (NXE + (cy + 1) * TX + cx);
                 const R fsx = (tr[0] - tl[0]) + (tt[1] - tb[1]);
@@ -1299,6 +1305,10 @@ template <class R, class S>
 struct LbArgs {
     const S *f_in;
     S *f_out;
+    // plane q of f_in, and of f_out shifted by the push of direction q
+    // (f_out + q P + c_q,y nx + c_q,x): one address operation per interior access
+    const S *fin_q[9];
+    S *fout_push[9];
     S *carry;
     const R *fbody;            // per row x body force
     const R *bfield;           // force_kind 3: per-node body force (x plane, y plane)
@@ -1329,7 +1339,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     R f[9];
 #pragma unroll
     for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
-        f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.f_in + q * P + c);
+        f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.fin_q[q] + c);
     const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
     const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const R dr = dro + ds;  // rho - rho_f
@@ -1394,10 +1404,10 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
         for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q]);
         if (ov) atomicOr(a.err, ERR_OVERFLOW16);
     }
-    stS<S, R>(a.f_out + c, fh[0]);
+    stS<S, R>(a.fout_push[0] + c, fh[0]);
     if (interior) {
 #pragma unroll
-        for (int q = 1; q < 9; q++) stS<S, R>(a.f_out + q * P + c + cyq(q) * nx + cxq(q), fh[q]);
+        for (int q = 1; q < 9; q++) stS<S, R>(a.fout_push[q] + c, fh[q]);
     } else {
 #pragma unroll
         for (int q = 1; q < 9; q++) {
