@@ -1362,7 +1362,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
         const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
         Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
     }
-    if (!(rho == rho) || !(ux == ux) || !(uy == uy)) atomicOr(a.err, ERR_NAN);
+    if (!(ux + uy == ux + uy)) atomicOr(a.err, ERR_NAN);  // a NaN rho makes both velocities NaN
     const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
     const R u2 = ux * ux + uy * uy;
     const R uF = ux * Fx + uy * Fy;
