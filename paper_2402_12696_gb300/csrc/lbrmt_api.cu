@@ -274,7 +274,7 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         org[k].offy = (float)(std::rint(((double)org[k].oy - h.yc) * 16384.0) / 16384.0);
         org[k].bx0 = org[k].by0 = 1; org[k].bx1 = org[k].by1 = 0;  // empty until initialised
         sd[k].xc = h.xc; sd[k].yc = h.yc; sd[k].R = h.R; sd[k].rho_s = h.rho_s; sd[k].G = h.G;
-        sd[k].shape = h.shape; sd[k].a = h.a; sd[k].b = h.b;
+        sd[k].shape = h.shape; sd[k].a = h.a; sd[k].b = h.b; sd[k].eps = s->cfg.eps;
         sd[k].drho = h.rho_s - s->cfg.rho_f;
         sd[k].accel = -(1.0 - s->cfg.rho_f / h.rho_s) * s->cfg.gravity;
         const double r2 = h.R * h.R;

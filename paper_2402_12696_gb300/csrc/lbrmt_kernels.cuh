@@ -98,6 +98,7 @@ struct SolidDesc {
     double xc, yc, R, rho_s, G;  // R: disk radius (circumscribed radius of other shapes)
     int shape;                   // 0 disk, 1 axis-aligned ellipse, 2 axis-aligned rectangle
     double a, b;                 // semi-axes / half-sides along x and y
+    double eps;                  // the blur-zone half-width (a threshold of the level set)
     double r2lo, drho, accel;   // R^2 - (double)(float)R^2, rho_s - rho_f, -(1 - rho_f/rho_s) g
     float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f;
     int T;
@@ -534,7 +535,7 @@ template <class R>
 struct Rsq {
     R hi, lo, rad;
     int shape;
-    double a, b;
+    double a, b, eps;
     __device__ __forceinline__ Rsq() {}
     __device__ __forceinline__ explicit Rsq(const SolidDesc &sd) {
         hi = pick<R>(sd.R * sd.R, sd.r2hi_f);
@@ -543,6 +544,7 @@ struct Rsq {
         shape = sd.shape;
         a = sd.a;
         b = sd.b;
+        eps = sd.eps;
     }
 };
 
@@ -582,32 +584,33 @@ __device__ inline double ellipse_distance_q1(double e0, double e1, double y0, do
 }
 
 // The same distance with the root found in FP32 (the same monotone Newton
-// steps) and, within `band` of the ellipse, polished by two Newton steps in
-// double precision (quadratic convergence from the FP32 root) before the
-// distance is formed in double; farther out the FP32 distance is kept.  For
-// FP32 simulations, whose stored level set is FP32: there the value matters
-// within a few nodes of the interface (the labels at 0 and eps, the blur zone,
-// the normals), and GB300's FP64 pipe is narrow.
-__device__ inline double ellipse_distance_q1_mixed(double e0, double e1, double y0, double y1, double band) {
+// steps), for FP32 simulations (their stored level set is FP32; GB300's FP64
+// pipe is narrow).  The FP32 distance is within ~1e-6 of the exact one; where
+// that could move a node across a threshold of the method (phi = 0, the solid
+// set; phi = eps, the blur zone) -- within `shell` of either -- the root is
+// polished by two Newton steps in double and the distance formed in double.
+__device__ inline double ellipse_distance_q1_mixed(double e0, double e1, double y0, double y1, double eps,
+                                                   double shell) {
     if (!(y1 > 0.0 && y0 > 0.0)) return ellipse_distance_q1(e0, e1, y0, y1);  // no iteration on the axes
     const double z0 = y0 / e0, z1 = y1 / e1, g = z0 * z0 + z1 * z1 - 1.0;
     if (g == 0.0) return 0.0;
     const double r0 = (e0 / e1) * (e0 / e1), n0 = r0 * z0;
     const double hi = g < 0.0 ? 0.0 : hypot(n0, z1) - 1.0;
     const float r0f = (float)r0, n0f = (float)n0, z1f = (float)z1, hif = (float)hi;
+    // FP32 steps with CUDA's fast division (the iteration corrects its own rounding)
     float s = z1f - 1.0f;
     for (int it = 0; it < 100; it++) {
-        const float ia = 1.0f / (s + r0f), ib = 1.0f / (s + 1.0f);
+        const float ia = __fdividef(1.0f, s + r0f), ib = __fdividef(1.0f, s + 1.0f);
         const float ra = n0f * ia, rb = z1f * ib, f = ra * ra + rb * rb - 1.0f;
         if (!(f > 0.0f)) break;
         const float df = -2.0f * (ra * ra * ia + rb * rb * ib);
-        const float sn = s - f / df;
+        const float sn = s - __fdividef(f, df);
         if (!(sn > s) || sn > hif) break;
         s = sn;
     }
     const float y0f = (float)y0, y1f = (float)y1;
-    const float df32 = hypotf(r0f * y0f / (s + r0f) - y0f, y1f / (s + 1.0f) - y1f);
-    if (df32 >= (float)band) return (double)df32;
+    const float df32 = hypotf(__fdividef(r0f * y0f, s + r0f) - y0f, __fdividef(y1f, s + 1.0f) - y1f);
+    if (fabsf(df32) >= (float)shell && fabsf(df32 - (float)eps) >= (float)shell) return (double)df32;
     double sd = (double)s;
     for (int it = 0; it < 2; it++) {
         const double ia = 1.0 / (sd + r0), ib = 1.0 / (sd + 1.0);
@@ -637,14 +640,14 @@ __device__ inline double shape_sdf(int shape, double a, double b, double qx, dou
 }
 
 // shape_sdf with the ellipse distance of ellipse_distance_q1_mixed (FP32 simulations).
-__device__ inline double shape_sdf_mixed(int shape, double a, double b, double qx, double qy) {
+__device__ inline double shape_sdf_mixed(int shape, double a, double b, double qx, double qy, double eps) {
     if (shape == 2) return shape_sdf(shape, a, b, qx, qy);
     double y0 = fabs(qx), y1 = fabs(qy), e0 = a, e1 = b;
     if (e0 < e1) {
         double t = e0; e0 = e1; e1 = t;
         t = y0; y0 = y1; y1 = t;
     }
-    const double d = ellipse_distance_q1_mixed(e0, e1, y0, y1, 4.0);
+    const double d = ellipse_distance_q1_mixed(e0, e1, y0, y1, eps, 1e-3);
     return (y0 / e0) * (y0 / e0) + (y1 / e1) * (y1 / e1) < 1.0 ? -d : d;
 }
 
@@ -656,7 +659,7 @@ template <class R>
 __device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const Frame &fr, const Rsq<R> &q) {
     if (q.shape != 0) {  // ellipses and rectangles: q = eta + l + off, exact in double
         const double X = ((double)lx + (double)fr.offx) + (double)ex, Y = ((double)ly + (double)fr.offy) + (double)ey;
-        return R(sizeof(R) == 4 ? shape_sdf_mixed(q.shape, q.a, q.b, X, Y) : shape_sdf(q.shape, q.a, q.b, X, Y));
+        return R(sizeof(R) == 4 ? shape_sdf_mixed(q.shape, q.a, q.b, X, Y, q.eps) : shape_sdf(q.shape, q.a, q.b, X, Y));
     }
     const R px = add_rn<R>(R(lx), R(fr.offx)), py = add_rn<R>(R(ly), R(fr.offy));  // exact
     const R a = mul_rn<R>(px, px), ea = fma_rn<R>(px, px, -a);
