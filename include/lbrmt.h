@@ -189,13 +189,21 @@ lbrmt_status lbrmt_set_populations_host(lbrmt_sim *sim, const double *host_f);
  * mean over them; lambda = 1 - H_eps(phi) on domain nodes. */
 lbrmt_status lbrmt_solid_stats(lbrmt_sim *sim, int sim_index, double *host_out);
 
+/* The same statistics, enqueued on the simulation's stream without waiting:
+ * host_out (S x 8 doubles, page-locked host memory owned by the caller) is
+ * filled when the stream reaches the copy, so the caller keeps it alive and
+ * unread until lbrmt_sync returns; device error flags surface there.  Needs
+ * an initialised simulation (LBRMT_ERR_STATE otherwise).  Lets a caller read
+ * every step's statistics without stalling the stream between steps. */
+lbrmt_status lbrmt_solid_stats_async(lbrmt_sim *sim, int sim_index, double *host_out);
+
 /* Total mass sum_x rho over the domain after the last step (FP64, fixed
  * summation order), into host memory. */
 lbrmt_status lbrmt_total_mass(lbrmt_sim *sim, int sim_index, double *host_out);
 
-/* Number of 32x8 tiles that the last step registered for the stress/force
- * kernel (tiles touched by a blur zone), into host memory; 0 before the
- * first step. */
+/* Number of registry tiles (tile_x x 256/tile_x nodes) that the last step
+ * registered for the stress/force kernel (tiles touched by a blur zone), into
+ * host memory; 0 before the first step. */
 lbrmt_status lbrmt_active_tiles(lbrmt_sim *sim, int sim_index, long long *host_out);
 
 /* Total mass sum_x rho of the current populations, written as one double to

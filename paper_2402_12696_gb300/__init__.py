@@ -31,7 +31,7 @@ SHAPES = {"disk": 0, "ellipse": 1, "rect": 2}
 EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add_solid_shape",
            "lbrmt_batch_add_solid_shape", "lbrmt_init", "lbrmt_step",
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
-           "lbrmt_solid_stats", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
+           "lbrmt_solid_stats", "lbrmt_solid_stats_async", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
            "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
@@ -86,6 +86,7 @@ def load():
     L.lbrmt_read_fields_host.argtypes = [p, i, i, i, p]
     L.lbrmt_set_populations_host.argtypes = [p, p]
     L.lbrmt_solid_stats.argtypes = [p, i, p]
+    L.lbrmt_solid_stats_async.argtypes = [p, i, p]
     L.lbrmt_total_mass.argtypes = [p, i, p]
     L.lbrmt_sync.argtypes = [p]
     L.lbrmt_active_tiles.argtypes = [p, i, C.POINTER(ll)]
@@ -197,6 +198,10 @@ def lbrmt_set_populations_host(h, host_ptr):
 
 def lbrmt_solid_stats(h, sim_index, host_ptr):
     _check(h, load().lbrmt_solid_stats(h, sim_index, C.c_void_p(host_ptr)))
+
+
+def lbrmt_solid_stats_async(h, sim_index, host_ptr):
+    _check(h, load().lbrmt_solid_stats_async(h, sim_index, C.c_void_p(host_ptr)))
 
 
 def lbrmt_total_mass(h, sim_index, host_ptr):

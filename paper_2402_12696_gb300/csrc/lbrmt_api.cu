@@ -629,6 +629,18 @@ extern "C" lbrmt_status lbrmt_solid_stats(lbrmt_sim *s, int sim_index, double *h
     return check_flags(s);
 }
 
+extern "C" lbrmt_status lbrmt_solid_stats_async(lbrmt_sim *s, int sim_index, double *host_out) {
+    if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
+    if (!s->inited) return fail(s, LBRMT_ERR_STATE, "not initialised");
+    const int S = (int)s->solids.size();
+    if (S == 0) return LBRMT_OK;
+    cudaError_t e = s->eng->stats(s->sp, s->d, (int)(s->steps & 1), s->scratch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stats kernel");
+    e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * 64, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy stats");
+    return LBRMT_OK;
+}
+
 extern "C" lbrmt_status lbrmt_total_mass(lbrmt_sim *s, int sim_index, double *host_out) {
     if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
     if (s->steps == 0) return fail(s, LBRMT_ERR_STATE, "total mass is recorded by the first step");

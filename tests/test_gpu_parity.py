@@ -189,6 +189,24 @@ def test_heavy_disk_drift_matches_oracle():
     ref.close()
 
 
+def test_solid_stats_async_matches_sync():
+    # lbrmt_solid_stats_async enqueues the same statistics into page-locked host
+    # memory without waiting; after lbrmt_sync they equal lbrmt_solid_stats'
+    import torch
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.settling_small(0)
+    sim = pkg.Simulation(sc, precision="fp32")
+    sim.step(5)
+    bufs = torch.zeros((3, len(sc["solids"]), 8), dtype=torch.float64).pin_memory()
+    for k in range(3):
+        pkg.lbrmt_step(sim.h, 1)
+        pkg.lbrmt_solid_stats_async(sim.h, 0, bufs[k].data_ptr())
+    pkg.lbrmt_sync(sim.h)
+    assert np.array_equal(bufs[2].numpy(), sim.solid_stats())
+    assert not np.array_equal(bufs[0].numpy(), bufs[2].numpy())  # each step's own values
+    sim.close()
+
+
 def test_deterministic_rerun():
     import paper_2402_12696_gb300 as pkg
     sc = scenarios.mixing_small(0)
