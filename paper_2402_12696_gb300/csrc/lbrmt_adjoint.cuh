@@ -650,19 +650,9 @@ __device__ void rmt_adjoint_solid(const SimParams &sp, const RmtAdjArgs<R> &a) {
     const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
     if (sx0 > sx1) return;
     const int NL = sp.n_layers;
-    // layers by 4-neighbour dilation (breadth-first distance from S)
-    for (int l = 1; l <= NL; l++) {
-        const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
-        const int w = x1 - x0 + 1, nb = w * (y1 - y0 + 1);
-        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-            const int lx = x0 + k % w, ly = y0 + k / w, t = ly * T + lx;
-            if (lab[t] != -1 || !allowed_cell(sp, oo.x + lx, oo.y + ly)) continue;
-            if ((lx > 0 && lab[t - 1] == l - 1) || (lx < T - 1 && lab[t + 1] == l - 1) ||
-                (ly > 0 && lab[t - T] == l - 1) || (ly < T - 1 && lab[t + T] == l - 1))
-                lab[t] = (signed char)l;
-        }
-        __syncthreads();
-    }
+    // the layers, as the forward
+    label_layers_l1(sp, lab, T, sx0, sx1, sy0, sy1, oo, NL, nullptr);
+    __syncthreads();
     // extrapolated layers in reverse order
     for (int l = NL; l >= 1; l--) {
         const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);

@@ -719,6 +719,62 @@ struct BoxWalk {
     __device__ __forceinline__ void next() { c += dc; r += dr; if (c >= w) { c -= w; r++; } }
 };
 
+// Layers 1..NL around the solid set S (label 0) in a tile's label bytes (-1
+// free): layer l = the allowed nodes l 4-neighbour dilation steps from S (Sec.
+// 3.2; nodes beyond the pad of a no-slip side never count).  The allowed cells
+// of a tile form a rectangle, where that number of steps is the L1 distance to
+// S, so the labels come from a separable L1 distance transform in place on the
+// label bytes, over the box of S grown by NL: a sweep per row, then one per
+// column (distances capped at NL + 1), then the nodes beyond NL or outside the
+// allowed cells are freed again.  cnt (shared, may be null): per-layer counts
+// are added to cnt[1..NL].  The caller synchronises before reading the labels.
+__device__ __forceinline__ void label_layers_l1(const SimParams &sp, signed char *lab, int T, int sx0, int sx1,
+                                                int sy0, int sy1, int2 oo, int NL, int *cnt) {
+    const int x0 = max(sx0 - NL, 0), x1 = min(sx1 + NL, T - 1), y0 = max(sy0 - NL, 0), y1 = min(sy1 + NL, T - 1);
+    const int cap = NL + 1;
+    for (int y = y0 + (int)threadIdx.x; y <= y1; y += blockDim.x) {
+        signed char *row = lab + y * T;
+        int last = -(1 << 20);
+        for (int x = x0; x <= x1; x++) {
+            if (row[x] == 0) last = x;
+            else row[x] = (signed char)min(x - last, cap);
+        }
+        last = 1 << 20;
+        for (int x = x1; x >= x0; x--) {
+            if (row[x] == 0) last = x;
+            else row[x] = (signed char)min((int)row[x], min(last - x, cap));
+        }
+    }
+    __syncthreads();
+    for (int x = x0 + (int)threadIdx.x; x <= x1; x += blockDim.x) {
+        int d = cap;
+        for (int y = y0; y <= y1; y++) {
+            signed char *q = lab + y * T + x;
+            d = min((int)*q, d + 1);
+            *q = (signed char)d;
+        }
+        d = cap;
+        for (int y = y1; y >= y0; y--) {
+            signed char *q = lab + y * T + x;
+            d = min((int)*q, d + 1);
+            *q = (signed char)d;
+        }
+    }
+    __syncthreads();
+    const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+    BoxWalk wk(w);
+    for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
+        const int lx = x0 + wk.c, ly = y0 + wk.r, t = ly * T + lx;
+        const int d = lab[t];
+        if (d < 1) continue;
+        if (d <= NL && allowed_cell(sp, oo.x + lx, oo.y + ly)) {
+            if (cnt) atomicAdd(&cnt[d], 1);
+        } else {
+            lab[t] = -1;
+        }
+    }
+}
+
 // One node of pass 0 (advection): its stored state and the LB state at it,
 // gathered with independent loads (the rest base is loaded whatever the
 // registry count and selected after).
@@ -902,14 +958,9 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     }
     __syncthreads();
 
-    // Layers 1..n_layers by 4-neighbour dilation of S (Sec. 3.2; 11 layers, Sec. 4),
-    // within the allowed cells (nodes beyond the pad of a no-slip side never
-    // count).  The allowed cells of a tile form a rectangle, where the number of
-    // 4-neighbour dilation steps from S is the L1 distance to S: the labels come
-    // from a separable L1 distance transform in place on the label bytes (a
-    // sweep per row, then one per column, capped at n_layers + 1), and a
-    // counting pass lists the nodes of every layer.  The layers are then fitted
-    // one after another (Sec. 3.2), each from S and the layers before it.
+    // Layers 1..n_layers around S (Sec. 3.2; 11 layers, Sec. 4), labelled at once
+    // (label_layers_l1), then listed by a counting pass and fitted one after
+    // another, each from S and the layers before it.
     const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
     if (sx0 > sx1) {
         if (threadIdx.x == 0) atomicOr(a.err, ERR_TILE_OVERFLOW);  // the solid vanished
@@ -918,47 +969,8 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     bool listed = false;  // every layer's nodes are in the lists (else each layer scans the tile)
     if (sx0 <= sx1) {
         const int x0 = max(sx0 - NL, 0), x1 = min(sx1 + NL, T - 1), y0 = max(sy0 - NL, 0), y1 = min(sy1 + NL, T - 1);
-        const int cap = NL + 1;
-        for (int y = y0 + (int)threadIdx.x; y <= y1; y += blockDim.x) {
-            signed char *row = lab + y * T;
-            int last = -(1 << 20);
-            for (int x = x0; x <= x1; x++) {
-                if (row[x] == 0) last = x;
-                else row[x] = (signed char)min(x - last, cap);
-            }
-            last = 1 << 20;
-            for (int x = x1; x >= x0; x--) {
-                if (row[x] == 0) last = x;
-                else row[x] = (signed char)min((int)row[x], min(last - x, cap));
-            }
-        }
-        __syncthreads();
-        for (int x = x0 + (int)threadIdx.x; x <= x1; x += blockDim.x) {
-            int d = cap;
-            for (int y = y0; y <= y1; y++) {
-                signed char *q = lab + y * T + x;
-                d = min((int)*q, d + 1);
-                *q = (signed char)d;
-            }
-            d = cap;
-            for (int y = y1; y >= y0; y--) {
-                signed char *q = lab + y * T + x;
-                d = min((int)*q, d + 1);
-                *q = (signed char)d;
-            }
-        }
-        __syncthreads();
         const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
-        {
-            BoxWalk wk(w);
-            for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
-                const int lx = x0 + wk.c, ly = y0 + wk.r, t = ly * T + lx;
-                const int d = lab[t];
-                if (d < 1) continue;
-                if (d <= NL && allowed_cell(sp, oo.x + lx, oo.y + ly)) atomicAdd(&lcnt[d], 1);
-                else lab[t] = -1;
-            }
-        }
+        label_layers_l1(sp, lab, T, sx0, sx1, sy0, sy1, oo, NL, lcnt);
         __syncthreads();
         if (threadIdx.x == 0) {
             loff[1] = 0;
