@@ -206,7 +206,7 @@ static lbrmt_status backward_impl(lbrmt_sim *s, const double *dLdc, double *dLdG
                             force_adj_smem_max() * (int)sizeof(R)));
     ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_adjoint_kernel<R>, TILE_N, fsm));
     const int fblocks = nsm * std::max(per, 1);
-    const int rsm = ((s->li.tmax * s->li.tmax + 15) & ~15);
+    const int rsm = ((s->li.tmax * s->li.tmax + 15) & ~15) + 8 * LIST_CAP;  // labels and layer lists
     ok(cudaFuncSetAttribute(rmt_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX));
     // the forward's choice: 1024-thread CTAs for FP32 arithmetic and few solids
     constexpr bool can_big = sizeof(R) == 4;

@@ -602,6 +602,7 @@ template <class R>
 __device__ void rmt_adjoint_solid(const SimParams &sp, const RmtAdjArgs<R> &a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int bb[4];
+    __shared__ int lcnt[24], loff[24];
     const int s = blockIdx.x;
     const SolidDesc sd = a.solids[s];
     const int T = sd.T, TT = T * T;
@@ -618,6 +619,7 @@ __device__ void rmt_adjoint_solid(const SimParams &sp, const RmtAdjArgs<R> &a) {
     const R eps = pick<R>(sp.eps, sp.eps_f);
     const long long P = sp.P;
     if (threadIdx.x < 4) bb[threadIdx.x] = (threadIdx.x & 1) ? -(1 << 29) : (1 << 29);
+    if (threadIdx.x < 24) lcnt[threadIdx.x] = 0;
     for (int k = threadIdx.x; k < (TT + 15) >> 4; k += blockDim.x)
         reinterpret_cast<int4 *>(lab)[k] = make_int4(-1, -1, -1, -1);
     int sb[4] = {1 << 29, -(1 << 29), 1 << 29, -(1 << 29)};
@@ -650,16 +652,25 @@ __device__ void rmt_adjoint_solid(const SimParams &sp, const RmtAdjArgs<R> &a) {
     const int sx0 = bb[0], sx1 = bb[1], sy0 = bb[2], sy1 = bb[3];
     if (sx0 > sx1) return;
     const int NL = sp.n_layers;
-    // the layers, as the forward
-    label_layers_l1(sp, lab, T, sx0, sx1, sy0, sy1, oo, NL, nullptr);
+    // the layers, as the forward, listed so that a layer's targets fill whole warps
+    int *lists = reinterpret_cast<int *>(smem + ((TT + 15) & ~15));
+    label_layers_l1(sp, lab, T, sx0, sx1, sy0, sy1, oo, NL, lcnt);
     __syncthreads();
+    const bool listed = list_layers(lab, T, max(sx0 - NL, 0), min(sx1 + NL, T - 1), max(sy0 - NL, 0),
+                                    min(sy1 + NL, T - 1), NL, lcnt, loff, lists, 2 * LIST_CAP);
     // extrapolated layers in reverse order
     for (int l = NL; l >= 1; l--) {
-        const int x0 = max(sx0 - l, 0), x1 = min(sx1 + l, T - 1), y0 = max(sy0 - l, 0), y1 = min(sy1 + l, T - 1);
-        const int w = x1 - x0 + 1, nb = w * (y1 - y0 + 1);
-        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-            const int lx = x0 + k % w, ly = y0 + k / w, t = ly * T + lx;
-            if (lab[t] != l) continue;
+        const int nitems = listed ? loff[l + 1] - loff[l] : TT;
+        for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
+            int lx, ly;
+            if (listed) {
+                const int e = lists[loff[l] + k];
+                lx = e & 0xffff; ly = e >> 16;
+            } else {  // too many band nodes for the lists: scan the tile
+                lx = k % T; ly = k / T;
+                if (lab[k] != l) continue;
+            }
+            const int t = ly * T + lx;
             const R xb = XbO[t], yb = XbO[TT + t];
             if (xb == R(0) && yb == R(0)) continue;
             bool use_n = false;

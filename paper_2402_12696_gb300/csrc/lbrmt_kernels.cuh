@@ -775,6 +775,35 @@ __device__ __forceinline__ void label_layers_l1(const SimParams &sp, signed char
     }
 }
 
+// The nodes of layers 1..NL (labelled, in the box [x0, x1] x [y0, y1]) in one
+// list, layer l at lists[loff[l] .. loff[l + 1]) (packed lx | ly << 16), so
+// that a layer's targets fill whole warps.  cnt holds the per-layer counts of
+// label_layers_l1 and is used up.  False (and no list) when more than cap
+// nodes; the caller then scans the tile for each layer.  Synchronises.
+__device__ __forceinline__ bool list_layers(const signed char *lab, int T, int x0, int x1, int y0, int y1, int NL,
+                                            int *cnt, int *loff, int *lists, int cap) {
+    if (threadIdx.x == 0) {
+        loff[1] = 0;
+        for (int l = 1; l <= NL; l++) {
+            loff[l + 1] = loff[l] + cnt[l];
+            cnt[l] = loff[l];
+        }
+    }
+    __syncthreads();
+    const bool listed = loff[NL + 1] <= cap;
+    if (listed) {
+        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+        BoxWalk wk(w);
+        for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
+            const int lx = x0 + wk.c, ly = y0 + wk.r;
+            const int d = lab[ly * T + lx];
+            if (d >= 1) lists[atomicAdd(&cnt[d], 1)] = lx | (ly << 16);
+        }
+    }
+    __syncthreads();
+    return listed;
+}
+
 // One node of pass 0 (advection): its stored state and the LB state at it,
 // gathered with independent loads (the rest base is loaded whatever the
 // registry count and selected after).
@@ -969,27 +998,9 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     bool listed = false;  // every layer's nodes are in the lists (else each layer scans the tile)
     if (sx0 <= sx1) {
         const int x0 = max(sx0 - NL, 0), x1 = min(sx1 + NL, T - 1), y0 = max(sy0 - NL, 0), y1 = min(sy1 + NL, T - 1);
-        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
         label_layers_l1(sp, lab, T, sx0, sx1, sy0, sy1, oo, NL, lcnt);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            loff[1] = 0;
-            for (int l = 1; l <= NL; l++) {
-                loff[l + 1] = loff[l] + lcnt[l];
-                lcnt[l] = loff[l];
-            }
-        }
-        __syncthreads();
-        listed = loff[NL + 1] <= 2 * LIST_CAP;
-        if (listed) {
-            BoxWalk wk(w);
-            for (int k = threadIdx.x; k < n; k += blockDim.x, wk.next()) {
-                const int lx = x0 + wk.c, ly = y0 + wk.r;
-                const int d = lab[ly * T + lx];
-                if (d >= 1) lists[atomicAdd(&lcnt[d], 1)] = lx | (ly << 16);
-            }
-        }
-        __syncthreads();
+        listed = list_layers(lab, T, x0, x1, y0, y1, NL, lcnt, loff, lists, 2 * LIST_CAP);
     }
     for (int l = 1; l <= NL && sx0 <= sx1; l++) {
         const int nitems = listed ? loff[l + 1] - loff[l] : TT;
