@@ -54,6 +54,50 @@ def _dist():
     return ws, rank, local
 
 
+class Ranks:
+    """One process per GPU (replicas: no collective on the data path).  The
+    process group only times the job: a barrier on both sides of the timed
+    region and the maximum over ranks of each rank's time.  backend: "nccl" for
+    the GPU benchmark, "gloo" for host-only runs and tests."""
+
+    def __init__(self, backend="nccl", device=None):
+        import torch
+        self.ws, self.rank, self.local = _dist()
+        self.device = device if device is not None else torch.device("cpu")
+        self.dist = None
+        if self.ws > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=self.device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x):
+        if not self.dist:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def aggregate_mlups(nodes_per_rank, steps, ws, ms_max):
+    """Whole-job throughput: every rank advances its own replica of nodes_per_rank
+    nodes by `steps` steps; the job takes the slowest rank's time."""
+    return nodes_per_rank * steps * ws / (ms_max / 1e3) / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
 
@@ -289,25 +333,10 @@ def bench_lbrmt(args):
     import paper_2402_12696_gb300 as pkg
 
     ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl", dev)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     sc = scenarios.mixing_4096(seed=rank) if args.size == 4096 else crop_sample(rank, args.size)
     N = sc["nx"] * sc["ny"]
@@ -354,7 +383,7 @@ def bench_lbrmt(args):
     sim.sync()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     ms_max = max_over_ranks(ms)
-    value = N * args.steps * ws / (ms_max / 1e3) / 1e6
+    value = aggregate_mlups(N, args.steps, ws, ms_max)
 
     # ---- per-kernel durations (CUDA events on the simulation stream) --------
     kms = sim.step_timed(max(3, min(args.steps, 20)))
@@ -400,9 +429,7 @@ def bench_lbrmt(args):
     shapes = bench_shapes(args, dev) if args.shapes_steps > 0 and rank == 0 else None
 
     if rank != 0:
-        if ws > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+        ranks.close()
         return
 
     # ---- roofline of the dominant kernel (fused LB kernel) ------------------
@@ -469,9 +496,7 @@ def bench_lbrmt(args):
         "shapes": shapes,
     }
     print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def main():
