@@ -92,6 +92,15 @@ class Ranks:
             self.dist = None
 
 
+def k1_source_sha1(text):
+    """sha1 (12 hex digits) of the lattice Boltzmann kernel's own source: its
+    section of the kernels header, from the section banner to the next kernel."""
+    import hashlib
+    a = text.index("// K1: fused moments")
+    b = text.index("init_f_kernel", a)
+    return hashlib.sha1(text[a:b].encode()).hexdigest()[:12]
+
+
 def aggregate_mlups(nodes_per_rank, steps, ws, ms_max):
     """Whole-job throughput: every rank advances its own replica of nodes_per_rank
     nodes by `steps` steps; the job takes the slowest rank's time."""
@@ -342,7 +351,8 @@ def bench_lbrmt(args):
     N = sc["nx"] * sc["ny"]
     stream = torch.cuda.Stream(dev)
     sim = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream,
-                         use_tma=args.lb_loads == "tma", tile_x=args.tile_x or 32, overlap=not args.no_overlap)
+                         use_tma=args.lb_loads == "tma", tile_x=args.tile_x or 32, overlap=not args.no_overlap,
+                         rmt_threads=args.rmt_threads)
     sim.init()
     tune = None
     if args.tile_x == 0:  # the library's tile-shape autotuner (state back to initial afterwards)
@@ -351,6 +361,7 @@ def bench_lbrmt(args):
                 "ms_per_step": {f"{k[0]}/{'tma' if k[1] else 'direct'}": round(v, 4) for k, v in tms.items()}}
     tile_used, tma_used = sim.tile_x, sim.uses_tma
     overlap_used = sim.uses_overlap
+    rmt_threads_used = sim.rmt_threads
     # ---- timed region: K graph-replayed steps -------------------------------
     # The workload (tau 0.6, stiff heavy disks) leaves the method's stable range
     # after ~450 steps from rest (the disks lag the uniformly driven fluid and the
@@ -396,7 +407,7 @@ def bench_lbrmt(args):
     if args.e2e_steps > 0:
         f0 = None
         sim2 = pkg.Simulation(sc, precision=args.precision, device=str(dev), stream=stream, tile_x=tile_used,
-                              use_tma=tma_used, overlap=not args.no_overlap)
+                              use_tma=tma_used, overlap=not args.no_overlap, rmt_threads=args.rmt_threads)
         sim2.init()
         f0 = torch.from_numpy(sim2.populations_host()).pin_memory()
         ke = args.e2e_steps
@@ -448,7 +459,7 @@ def bench_lbrmt(args):
             import hashlib
             rec = json.load(open(tfile))
             src = os.path.join(ROOT, "paper_2402_12696_gb300", "csrc", "lbrmt_kernels.cuh")
-            same_src = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] == rec.get("kernel_source_sha1")
+            same_src = k1_source_sha1(open(src).read()) == rec.get("k1_source_sha1")
             same_cfg = rec.get("tile_x") == tile_used and rec.get("lb_loads") == ("tma" if tma_used else "direct")
             if same_src and same_cfg:
                 traffic = rec.get("bytes_per_launch")
@@ -473,7 +484,7 @@ def bench_lbrmt(args):
         "config": {"workload": BASE_WORKLOAD if args.size == 4096 else
                    f"{args.size}x{args.size} crop of " + BASE_WORKLOAD, "precision": args.precision, "seed": "rank",
                    "nodes": N, "solids": len(sc["solids"]), "tile_x": tile_used, "tile_autotune": tune,
-                   "overlap": overlap_used,
+                   "overlap": overlap_used, "rmt_threads": rmt_threads_used,
                    "kernel_ms_schedule": "sequential (lbrmt_step_timed: K2, K3, then K1 over every region); the "
                                          "timed steps overlap K1 of the solid-free regions with K2 and K3",
                    "segments": f"{len(segs)} timed segments of <= {SEG} steps, each from the initial state after a "
@@ -518,6 +529,8 @@ def main():
                     help="registry / LB tile width (height 256 / tile_x); 0: autotuned")
     ap.add_argument("--no-overlap", action="store_true",
                     help="sequential step schedule (no concurrent K1 of the solid-free regions)")
+    ap.add_argument("--rmt-threads", type=int, default=0, choices=[0, 256, 1024],
+                    help="CTA width of the reference-map kernel (one CTA per solid); 0: the library's choice")
     ap.add_argument("--lb-loads", default="tma", choices=["tma", "direct"],
                     help="LB kernel loads when the tile shape is fixed: tensor-memory staging or direct")
     ap.add_argument("--study", default="", choices=["", "convergence"],

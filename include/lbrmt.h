@@ -264,6 +264,16 @@ int lbrmt_uses_tma(const lbrmt_sim *sim);
 lbrmt_status lbrmt_set_overlap(lbrmt_sim *sim, int enable);
 int lbrmt_uses_overlap(const lbrmt_sim *sim);
 
+/* CTA width of the reference-map kernel (one CTA per solid, Sec. 3.1-3.2):
+ * 0 (default) chooses 1024 threads when the solids number at most half the
+ * SMs and FP32 arithmetic is used, else 256; 256 or 1024 fix it (1024 falls
+ * back to 256 with FP64 arithmetic).  The solids' statistics are summed in an
+ * order that depends on the width, so results agree to rounding, not bit for
+ * bit.  Any other value gives LBRMT_ERR_ARG.  Takes effect at the next step;
+ * lbrmt_rmt_threads tells the width in use (after initialisation, else 0). */
+lbrmt_status lbrmt_set_rmt_threads(lbrmt_sim *sim, int threads);
+int lbrmt_rmt_threads(const lbrmt_sim *sim);
+
 /* Text of the last error on this handle ("" if none). */
 const char *lbrmt_last_error(const lbrmt_sim *sim);
 

@@ -33,7 +33,7 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_solid_stats_async", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
-           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap",
+           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap", "lbrmt_set_rmt_threads", "lbrmt_rmt_threads",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
            "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward", "lbrmt_set_tile_x", "lbrmt_tile_x",
            "lbrmt_autotune_tile",
@@ -102,6 +102,8 @@ def load():
     L.lbrmt_uses_tma.argtypes = [p]
     L.lbrmt_set_overlap.argtypes = [p, i]
     L.lbrmt_uses_overlap.argtypes = [p]
+    L.lbrmt_set_rmt_threads.argtypes = [p, i]
+    L.lbrmt_rmt_threads.argtypes = [p]
     L.lbrmt_last_error.argtypes = [p]
     L.lbrmt_last_error.restype = C.c_char_p
     L.lbrmt_destroy.argtypes = [p]
@@ -366,7 +368,8 @@ class Simulation:
     """One LBRMT simulation on a CUDA device, built from a scenario dict."""
 
     def __init__(self, sc, precision="fp32", device="cuda:0", stream=None, use_graphs=True,
-                 max_solids_per_tile=8, rmax=11, tile_x=32, use_tma=True, overlap=True):
+                 max_solids_per_tile=8, rmax=11, tile_x=32, use_tma=True, overlap=True,
+                 rmt_threads=0):
         import torch
         self.torch = torch
         self.sc = sc
@@ -384,6 +387,7 @@ class Simulation:
             load().lbrmt_set_use_graphs(self.h, int(bool(use_graphs)))
             load().lbrmt_set_use_tma(self.h, int(bool(use_tma)))
             _check(self.h, load().lbrmt_set_overlap(self.h, int(bool(overlap))))
+            _check(self.h, load().lbrmt_set_rmt_threads(self.h, int(rmt_threads)))
             for s in sc["solids"]:
                 shape, a, b = _solid_geometry(s)
                 lbrmt_add_solid_shape(self.h, shape, s["x"], s["y"], a, b, s["rho_s"], s["G"])
@@ -460,6 +464,14 @@ class Simulation:
     @property
     def uses_overlap(self):
         return bool(load().lbrmt_uses_overlap(self.h))
+
+    def set_rmt_threads(self, threads):
+        """CTA width of the reference-map kernel: 0 (chosen), 256 or 1024 (lbrmt_set_rmt_threads)."""
+        _check(self.h, load().lbrmt_set_rmt_threads(self.h, int(threads)))
+
+    @property
+    def rmt_threads(self):
+        return load().lbrmt_rmt_threads(self.h)
 
     @property
     def last_launch_count(self):

@@ -210,7 +210,7 @@ static lbrmt_status backward_impl(lbrmt_sim *s, const double *dLdc, double *dLdG
     ok(cudaFuncSetAttribute(rmt_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX));
     // the forward's choice: 1024-thread CTAs for FP32 arithmetic and few solids
     constexpr bool can_big = sizeof(R) == 4;
-    const bool big = can_big && s->li.rmt_big;
+    const bool big = can_big && s->li.rmt_threads == RMT_THREADS_BIG;
     if constexpr (can_big)
         if (big) ok(cudaFuncSetAttribute(rmt_adjoint_kernel_big<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX));
     const int lblocks = (int)std::min<long long>((P + 255) / 256, (long long)nsm * 8);

@@ -710,6 +710,28 @@ extern "C" lbrmt_status lbrmt_set_overlap(lbrmt_sim *s, int enable) {
 
 extern "C" int lbrmt_uses_overlap(const lbrmt_sim *s) { return s && s->inited && step_overlaps(s->sp, s->li) ? 1 : 0; }
 
+extern "C" lbrmt_status lbrmt_set_rmt_threads(lbrmt_sim *s, int threads) {
+    if (!s) return LBRMT_ERR_ARG;
+    if (threads != 0 && threads != RMT_THREADS && threads != RMT_THREADS_BIG)
+        return fail(s, LBRMT_ERR_ARG, "reference-map CTA width must be 0, 256 or 1024");
+    if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    s->li.rmt_req = threads;
+    if (s->inited) {  // choose again (configure keeps the tensor-memory choice)
+        const bool use_tma = s->li.use_tma;
+        cudaError_t e = s->eng->configure(s->sp, s->d, s->li.tmax, &s->li);
+        s->li.use_tma = use_tma;
+        if (e != cudaSuccess) return cuda_fail(s, e, "configure kernels");
+    }
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return LBRMT_OK;
+}
+
+extern "C" int lbrmt_rmt_threads(const lbrmt_sim *s) { return s && s->inited ? s->li.rmt_threads : 0; }
+
 extern "C" void lbrmt_destroy(lbrmt_sim *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);

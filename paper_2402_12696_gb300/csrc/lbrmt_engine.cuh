@@ -16,7 +16,8 @@ struct LaunchInfo {
     int force_blocks;    // persistent grid of K3
     int rmt_smem;        // dynamic shared memory of K2
     int force_smem;      // dynamic shared memory of K3
-    bool rmt_big = false; // K2 with 1024-thread CTAs (few solids, FP32 arithmetic)
+    int rmt_req = 0;      // requested K2 CTA width (0: chosen by configure)
+    int rmt_threads = 256; // K2 CTA width in use: 256, or 1024 (FP32 arithmetic only)
     bool tma = false;    // tensor maps of the populations and half-force are valid
     bool use_tma = true; // K1 with TMA staging (else the direct-load kernel)
     int lb_blocks = 0, lb_smem = 0;
@@ -176,11 +177,15 @@ struct Engine {
         int nsm0 = 0, dev0 = 0;
         cudaGetDevice(&dev0);
         cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0);
-        li->rmt_big = sizeof(R) == 4 && sp.nsolids > 0 && 2 * sp.nsolids <= nsm0;
-        if (li->rmt_big) {
+        // K2's CTA width: the request, else 1024 threads when the solids number at
+        // most half the SMs (FP32 arithmetic: 64 registers hold it), else 256
+        int w = li->rmt_req;
+        if (w == 0) w = sizeof(R) == 4 && sp.nsolids > 0 && 2 * sp.nsolids <= nsm0 ? RMT_THREADS_BIG : RMT_THREADS;
+        if (w == RMT_THREADS_BIG && sizeof(R) != 4) w = RMT_THREADS;
+        li->rmt_threads = w;
+        if (w == RMT_THREADS_BIG)
             e = cudaFuncSetAttribute(rmt_solid_kernel_big<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX);
-            if (e != cudaSuccess) return e;
-        }
+        if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(force_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  force_smem_max() * (int)sizeof(R));
         if (e != cudaSuccess) return e;
@@ -312,7 +317,7 @@ struct Engine {
 
     static void launch_rmt(const SimParams &sp, const LaunchInfo &li, const RmtArgs<R, S> &a, cudaStream_t st,
                            int prio = 0) {
-        if (li.rmt_big)
+        if (li.rmt_threads == RMT_THREADS_BIG)
             launch_prio(rmt_solid_kernel_big<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS_BIG), li.rmt_smem, st, prio, sp, a);
         else launch_prio(rmt_solid_kernel<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS), li.rmt_smem, st, prio, sp, a);
     }

@@ -66,6 +66,13 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(lib):
     assert not h.value
 
 
+def test_knobs_reject_a_null_handle_without_touching_the_gpu(lib):
+    assert lib.lbrmt_set_rmt_threads(None, 128) == -1
+    assert lib.lbrmt_rmt_threads(None) == 0
+    assert lib.lbrmt_set_overlap(None, 1) == -1
+    assert lib.lbrmt_uses_overlap(None) == 0
+
+
 def test_product_path_does_not_reference_the_oracle():
     pkg_dir = os.path.join(ROOT, "paper_2402_12696_gb300")
     for dirpath, _, files in os.walk(pkg_dir):

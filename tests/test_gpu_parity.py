@@ -163,6 +163,48 @@ def test_overlapped_step_bit_identical(case, tile_x):
         assert np.array_equal(a, b, equal_nan=True)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("threads", [256, 1024])
+def test_rmt_cta_widths_match_oracle(prec, threads):
+    # The reference-map kernel runs one CTA per solid at 256 or 1024 threads;
+    # the width changes only the order of its per-solid sums, so every
+    # width follows the oracle to the precision's tolerance.  1024-thread CTAs
+    # are for FP32 arithmetic: FP64 runs 256 instead.
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.mixing_small(0)
+    sim = pkg.Simulation(sc, precision=prec, rmt_threads=threads)
+    sim.step(1)
+    assert sim.rmt_threads == (256 if threads == 1024 and prec == "fp64" else threads)
+    sim.set_rmt_threads(0)  # chosen: few solids (fewer than half the SMs) take 1024 in FP32
+    assert sim.rmt_threads == (1024 if prec == "fp32" else 256)
+    sim.close()
+    res = run_pair(sc, prec, [1, 10, 100], rmt_threads=threads)
+    _log(f"mixing_small_0/{prec}/rmt{threads}", res)
+    _check(res, prec, sc)
+
+
+def test_rmt_widths_agree_on_many_solids():
+    # More solids than four CTAs per SM (700 disks on a 2048^2 crop of the
+    # mixing workload): 1024-thread and 256-thread CTAs advance the same fields
+    # up to rounding in the per-solid sums.
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.mixing_4096(5, n=2048, count=700)
+    outs = []
+    for w in (1024, 256):
+        sim = pkg.Simulation(sc, precision="fp32", tile_x=16, rmt_threads=w)
+        sim.step(20)
+        assert sim.rmt_threads == w
+        outs.append((sim.field_host("ux"), sim.field_host("xi_x", 0), sim.solid_stats(), sim.total_mass()))
+        sim.close()
+    (u1, x1, s1, m1), (u2, x2, s2, m2) = outs
+    assert np.nanmax(np.abs(u1 - u2)) <= 1e-5 * np.nanmax(np.abs(u2)) + 1e-9
+    ok = np.isfinite(x1) & np.isfinite(x2)
+    assert np.array_equal(np.isfinite(x1), np.isfinite(x2))
+    assert np.max(np.abs(x1[ok] - x2[ok])) < 1e-3
+    assert np.allclose(s1, s2, rtol=1e-5, atol=1e-6)
+    assert abs(m1 - m2) <= 1e-6 * abs(m2)
+
+
 def test_heavy_disk_drift_matches_oracle():
     # A disk 1.5 times denser than the fluid, driven with it by a uniform
     # acceleration, lags the fluid in this method (the density-contrast
