@@ -145,6 +145,27 @@ lbrmt_status lbrmt_set_solid_params(lbrmt_sim *sim, int solid_id, double rho_s, 
  * (keeps the allocations and the body force field). */
 lbrmt_status lbrmt_reset(lbrmt_sim *sim);
 
+/* Checkpoint and resume: the whole state that Algorithm 1 carries from one
+ * step to the next (populations and half-force carry, both halves of every
+ * ping-pong pair of reference-map tiles, frames, tile registries and force
+ * pools, the body force, the solids' descriptors and statistics, and the step
+ * count).  lbrmt_save with dev_blob NULL stores the size needed in *bytes;
+ * with a caller-owned device buffer of *bytes >= that size it waits for the
+ * simulation's stream, checks the device error flags (a raised flag is
+ * returned as its status and nothing is written), copies the state into the
+ * buffer and stores the size written in *bytes.  Needs an initialised
+ * simulation (LBRMT_ERR_STATE otherwise).
+ * lbrmt_load restores a saved state into a simulation created with the same
+ * configuration and solids (same order, shape, position, size and tile side;
+ * densities and shear moduli are taken from the checkpoint) and initialises it
+ * first if needed; it adopts the checkpoint's tile shape.  A buffer that is not
+ * a checkpoint of a matching simulation gives LBRMT_ERR_ARG and leaves the
+ * state as it was.  Stepping on from a loaded state gives the same results,
+ * bit for bit, as stepping on from the state that was saved.  The buffer stays
+ * caller-owned and is not referenced after the call. */
+lbrmt_status lbrmt_save(lbrmt_sim *sim, void *dev_blob, size_t *bytes);
+lbrmt_status lbrmt_load(lbrmt_sim *sim, const void *dev_blob, size_t bytes);
+
 /* Registry / lattice Boltzmann tile shape: tile_x in {16, 32, 64, 128} (0:
  * 32), height 256 / tile_x.  After initialisation this returns the
  * simulation to its initial state.  The results do not depend on it. */

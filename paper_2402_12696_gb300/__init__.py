@@ -33,7 +33,7 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_solid_stats_async", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
-           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap", "lbrmt_set_rmt_threads", "lbrmt_rmt_threads",
+           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap", "lbrmt_set_rmt_threads", "lbrmt_rmt_threads", "lbrmt_save", "lbrmt_load",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
            "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward", "lbrmt_set_tile_x", "lbrmt_tile_x",
            "lbrmt_autotune_tile",
@@ -111,6 +111,8 @@ def load():
     L.lbrmt_set_body_force_field.argtypes = [p, i, p]
     L.lbrmt_set_solid_params.argtypes = [p, i, d, d]
     L.lbrmt_reset.argtypes = [p]
+    L.lbrmt_save.argtypes = [p, p, C.POINTER(C.c_size_t)]
+    L.lbrmt_load.argtypes = [p, p, C.c_size_t]
     L.lbrmt_set_tile_x.argtypes = [p, i]
     L.lbrmt_tile_x.argtypes = [p]
     L.lbrmt_autotune_tile.argtypes = [p, i, C.POINTER(i), C.POINTER(i), p]
@@ -244,6 +246,17 @@ def lbrmt_set_solid_params(h, solid_id, rho_s, G):
 
 def lbrmt_reset(h):
     _check(h, load().lbrmt_reset(h))
+
+
+def lbrmt_save(h, dev_ptr=None, nbytes=0):
+    """Checkpoint size (dev_ptr None), or write the checkpoint into nbytes of device memory; the bytes."""
+    n = C.c_size_t(nbytes)
+    _check(h, load().lbrmt_save(h, dev_ptr, C.byref(n)))
+    return n.value
+
+
+def lbrmt_load(h, dev_ptr, nbytes):
+    _check(h, load().lbrmt_load(h, dev_ptr, nbytes))
 
 
 def lbrmt_forward_checkpointed(h, nsteps, checkpoint_every, host_ptr):
@@ -410,6 +423,23 @@ class Simulation:
     def reset(self):
         with self.torch.cuda.device(self.device):
             lbrmt_reset(self.h)
+
+    def save(self):
+        """Checkpoint of the current state (lbrmt_save) in a new uint8 device tensor."""
+        torch = self.torch
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            n = lbrmt_save(self.h)
+            blob = torch.empty(n, dtype=torch.uint8, device=self.device)  # ordered on the sim's stream
+            lbrmt_save(self.h, blob.data_ptr(), n)
+        return blob
+
+    def load(self, blob):
+        """Restore a checkpoint made by save() (a uint8 tensor, moved to this device)."""
+        torch = self.torch
+        blob = blob.to(self.device).contiguous()
+        with torch.cuda.device(self.device):
+            torch.cuda.current_stream(self.device).synchronize()  # the blob's producers are done
+            lbrmt_load(self.h, blob.data_ptr(), blob.numel())
 
     @property
     def tile_x(self):

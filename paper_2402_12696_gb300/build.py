@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbrmt.so")
 SOURCES = ["lbrmt_api.cu", "lbrmt_batch.cu", "lbrmt_adjoint.cu", "engine_fp32.cu", "engine_fp64.cu", "engine_fp16.cu", "engine_bf16.cu",
-           "lbrmt_noalloc.cu"]
+           "lbrmt_noalloc.cu", "lbrmt_checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -71,6 +71,9 @@ def test_knobs_reject_a_null_handle_without_touching_the_gpu(lib):
     assert lib.lbrmt_rmt_threads(None) == 0
     assert lib.lbrmt_set_overlap(None, 1) == -1
     assert lib.lbrmt_uses_overlap(None) == 0
+    n = C.c_size_t(0)
+    assert lib.lbrmt_save(None, None, C.byref(n)) == -1
+    assert lib.lbrmt_load(None, None, 0) == -1
 
 
 def test_product_path_does_not_reference_the_oracle():
