@@ -295,6 +295,16 @@ int lbrmt_uses_overlap(const lbrmt_sim *sim);
 lbrmt_status lbrmt_set_rmt_threads(lbrmt_sim *sim, int threads);
 int lbrmt_rmt_threads(const lbrmt_sim *sim);
 
+/* Self-check of the failure path of the bounded device waits: one GPU
+ * thread waits, with the bounded wait that guards the tensor-memory copies of
+ * the lattice Boltzmann kernel, on a barrier that nothing completes, until the
+ * wait gives up (about 2^31 clock cycles, ~1 s), and records the timeout in
+ * the device error flags as that kernel does.  Returns LBRMT_ERR_TIMEOUT, as
+ * it must, and clears the flags; LBRMT_OK would mean that the wait did not
+ * give up.  A device error already pending is returned instead, without
+ * running the check.  The simulation's state is not touched. */
+lbrmt_status lbrmt_check_bounded_wait(lbrmt_sim *sim);
+
 /* Text of the last error on this handle ("" if none). */
 const char *lbrmt_last_error(const lbrmt_sim *sim);
 

@@ -33,7 +33,7 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add
            "lbrmt_read_fields", "lbrmt_read_fields_host", "lbrmt_set_populations_host",
            "lbrmt_solid_stats", "lbrmt_solid_stats_async", "lbrmt_total_mass", "lbrmt_sync", "lbrmt_total_mass_noalloc", "lbrmt_active_tiles", "lbrmt_step_timed", "lbrmt_steps_done",
            "lbrmt_num_solids", "lbrmt_last_launch_count", "lbrmt_set_use_graphs", "lbrmt_set_use_tma",
-           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap", "lbrmt_set_rmt_threads", "lbrmt_rmt_threads", "lbrmt_save", "lbrmt_load",
+           "lbrmt_uses_tma", "lbrmt_set_overlap", "lbrmt_uses_overlap", "lbrmt_set_rmt_threads", "lbrmt_rmt_threads", "lbrmt_save", "lbrmt_load", "lbrmt_check_bounded_wait",
            "lbrmt_last_error", "lbrmt_destroy", "lbrmt_set_body_force_field", "lbrmt_set_solid_params",
            "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward", "lbrmt_set_tile_x", "lbrmt_tile_x",
            "lbrmt_autotune_tile",
@@ -113,6 +113,7 @@ def load():
     L.lbrmt_reset.argtypes = [p]
     L.lbrmt_save.argtypes = [p, p, C.POINTER(C.c_size_t)]
     L.lbrmt_load.argtypes = [p, p, C.c_size_t]
+    L.lbrmt_check_bounded_wait.argtypes = [p]
     L.lbrmt_set_tile_x.argtypes = [p, i]
     L.lbrmt_tile_x.argtypes = [p]
     L.lbrmt_autotune_tile.argtypes = [p, i, C.POINTER(i), C.POINTER(i), p]

@@ -732,6 +732,20 @@ extern "C" lbrmt_status lbrmt_set_rmt_threads(lbrmt_sim *s, int threads) {
 
 extern "C" int lbrmt_rmt_threads(const lbrmt_sim *s) { return s && s->inited ? s->li.rmt_threads : 0; }
 
+extern "C" lbrmt_status lbrmt_check_bounded_wait(lbrmt_sim *s) {
+    if (!s) return LBRMT_ERR_ARG;
+    lbrmt_status st = check_flags(s);  // a pending error is reported, not overwritten
+    if (st != LBRMT_OK) return st;
+    bounded_wait_check_kernel<<<1, 32, 0, s->stream>>>(s->d.err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "bounded wait check");
+    st = check_flags(s);
+    e = cudaMemsetAsync(s->d.err, 0, 16, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "clear error flags");
+    return st;
+}
+
 extern "C" void lbrmt_destroy(lbrmt_sim *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);

@@ -1723,6 +1723,19 @@ __global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
     stC<S, R>(carry + sp.P + c, R(0));
 }
 
+// Self-check of the failure path of the tensor-copy pipeline: one thread
+// waits, with the pipeline's bounded wait, on an mbarrier that nothing
+// completes (no copy is issued, no thread arrives) and records the timeout as
+// lb_tma_kernel does.  Nothing is in flight when it gives up.
+static __global__ void bounded_wait_check_kernel(unsigned *err) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait_bounded(smem_u32(&bar), 0)) atomicOr(err, ERR_TIMEOUT);
+    }
+}
+
 // Fields to a double grid.  kind: 0 rho, 1 ux, 2 uy, 3 Fx, 4 Fy, 5 drho, 20+q f_q.
 template <class R, class S>
 __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *fbody, const R *bfield, const int *reg_count,
