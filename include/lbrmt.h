@@ -195,12 +195,19 @@ lbrmt_status lbrmt_step(lbrmt_sim *sim, int nsteps);
 lbrmt_status lbrmt_read_fields(lbrmt_sim *sim, int sim_index, int field, int solid_id,
                                double *dev_out);
 
-/* Same as lbrmt_read_fields but into host memory (nx*ny doubles). */
+/* Same as lbrmt_read_fields but into host memory (nx*ny doubles); waits for
+ * the stream.  A page-locked (or registered) buffer receives the fields written
+ * at every node (RHO .. DRHO, POP0 + q) from the field kernel directly, over
+ * the coherent CPU-GPU link; other buffers and the per-solid fields go through
+ * a device staging buffer and a copy. */
 lbrmt_status lbrmt_read_fields_host(lbrmt_sim *sim, int sim_index, int field, int solid_id,
                                     double *host_out);
 
 /* Overwrite the populations from host memory (9 planes of nx*ny doubles,
- * plane q = f_q) and reset the stored half-force to zero. */
+ * plane q = f_q) and reset the stored half-force to zero; waits for the
+ * stream.  A page-locked (or registered) buffer is read by the conversion
+ * kernel directly; other buffers are copied to a device staging buffer
+ * (9*nx*ny doubles, allocated on first use) first. */
 lbrmt_status lbrmt_set_populations_host(lbrmt_sim *sim, const double *host_f);
 
 /* Per-solid FP64 statistics of the current state, S x 8 doubles into host
@@ -212,7 +219,9 @@ lbrmt_status lbrmt_solid_stats(lbrmt_sim *sim, int sim_index, double *host_out);
 
 /* The same statistics, enqueued on the simulation's stream without waiting:
  * host_out (S x 8 doubles, page-locked host memory owned by the caller) is
- * filled when the stream reaches the copy, so the caller keeps it alive and
+ * written by the statistics kernel directly when the stream reaches it (a
+ * pageable buffer is filled by a copy from device memory instead), so the
+ * caller keeps it alive and
  * unread until lbrmt_sync returns; device error flags surface there.  Needs
  * an initialised simulation (LBRMT_ERR_STATE otherwise).  Lets a caller read
  * every step's statistics without stalling the stream between steps. */

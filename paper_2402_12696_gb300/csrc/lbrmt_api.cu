@@ -583,9 +583,28 @@ extern "C" lbrmt_status lbrmt_read_fields(lbrmt_sim *s, int sim_index, int field
     return LBRMT_OK;
 }
 
+// Device address of a page-locked (or registered) host buffer, which kernels
+// read and write directly over the coherent CPU-GPU link; null for pageable
+// memory, which goes through a device staging buffer and a copy instead.
+static void *mapped_view(const void *host) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();  // not an error of the simulation
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 extern "C" lbrmt_status lbrmt_read_fields_host(lbrmt_sim *s, int sim_index, int field, int solid_id,
                                                double *host_out) {
     if (!s || !host_out) return LBRMT_ERR_ARG;
+    // fields written at every node go straight into a page-locked buffer
+    // (the per-solid fields are cleared first and written on the band only)
+    if (void *dv = (field < 10 || field >= 20) ? mapped_view(host_out) : nullptr) {
+        lbrmt_status st = lbrmt_read_fields(s, sim_index, field, solid_id, (double *)dv);
+        if (st != LBRMT_OK) return st;
+        return check_flags(s);
+    }
     if (!s->staging) {
         s->staging = (double *)dalloc(s, (size_t)9 * s->sp.P * 8);
         if (!s->staging) return fail(s, LBRMT_ERR_CUDA, "out of device memory");
@@ -603,13 +622,19 @@ extern "C" lbrmt_status lbrmt_set_populations_host(lbrmt_sim *s, const double *h
         lbrmt_status st = lbrmt_init(s);
         if (st != LBRMT_OK) return st;
     }
-    if (!s->staging) {
-        s->staging = (double *)dalloc(s, (size_t)9 * s->sp.P * 8);
-        if (!s->staging) return fail(s, LBRMT_ERR_CUDA, "out of device memory");
+    // a page-locked buffer is read by the conversion kernel directly
+    const double *src = (const double *)mapped_view(host_f);
+    cudaError_t e = cudaSuccess;
+    if (!src) {
+        if (!s->staging) {
+            s->staging = (double *)dalloc(s, (size_t)9 * s->sp.P * 8);
+            if (!s->staging) return fail(s, LBRMT_ERR_CUDA, "out of device memory");
+        }
+        e = cudaMemcpyAsync(s->staging, host_f, (size_t)9 * s->sp.P * 8, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "copy populations");
+        src = s->staging;
     }
-    cudaError_t e = cudaMemcpyAsync(s->staging, host_f, (size_t)9 * s->sp.P * 8, cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "copy populations");
-    e = s->eng->set_pop(s->sp, s->d, (int)(s->steps & 1), s->staging, s->stream);
+    e = s->eng->set_pop(s->sp, s->d, (int)(s->steps & 1), src, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set populations");
     return check_flags(s);
 }
@@ -634,6 +659,11 @@ extern "C" lbrmt_status lbrmt_solid_stats_async(lbrmt_sim *s, int sim_index, dou
     if (!s->inited) return fail(s, LBRMT_ERR_STATE, "not initialised");
     const int S = (int)s->solids.size();
     if (S == 0) return LBRMT_OK;
+    if (double *dv = (double *)mapped_view(host_out)) {  // page-locked: the kernel writes it
+        cudaError_t e = s->eng->stats(s->sp, s->d, (int)(s->steps & 1), dv, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "stats kernel");
+        return LBRMT_OK;
+    }
     cudaError_t e = s->eng->stats(s->sp, s->d, (int)(s->steps & 1), s->scratch, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "stats kernel");
     e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * 64, cudaMemcpyDeviceToHost, s->stream);

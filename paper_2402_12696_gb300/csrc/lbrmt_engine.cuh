@@ -390,7 +390,7 @@ struct Engine {
 
     static cudaError_t stats(const SimParams &sp, const DevState &d, int cur, double *out, cudaStream_t st) {
         if (sp.nsolids == 0) return cudaSuccess;
-        solid_stats_kernel<R, S><<<sp.nsolids, 256, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry,
+        solid_stats_kernel<R, S><<<sp.nsolids, STATS_THREADS, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry,
                                                              d.reg_count[1 - cur], (const R *)d.pool[1 - cur],
                                                              (const R *)d.xi[cur], d.frame[cur], d.solids, out);
         return cudaGetLastError();

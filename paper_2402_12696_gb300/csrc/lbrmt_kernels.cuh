@@ -1831,49 +1831,114 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
 }
 
 // Per-solid FP64 statistics of the current state (one CTA per solid).
+// Per-solid statistics of the current state (FP64 sums; Sec. 4 outputs):
+// mass-like sum L = sum lambda, centroid, sum lambda rho, momentum, and over the
+// solid's nodes max |det F - 1| and its lambda-weighted mean.  One CTA per solid.
+// Each warp walks its share of the band box (outside it xi is invalid) and
+// queues, in shared memory, the nodes of the solid and blur zone (phi < eps);
+// every 64 queued nodes it takes two per lane with all loads issued first.
+constexpr int STATS_THREADS = 256;
 template <class R, class S>
-__global__ void solid_stats_kernel(SimParams sp, const S *f, const S *carry, const int *reg, const R *pool,
-                                   const R *xi, const Frame *frames, const SolidDesc *solids, double *out) {
+struct StatsNode {
+    int t, gx, gy;
+    R phi, f[9], dro, cx, cy;
+};
+template <class R, class S>
+__device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, const S *carry, const int *reg,
+                                             const R *pool, const R *xi, int T, int2 o, int t, StatsNode<R, S> &nd) {
+    nd.t = t;
+    nd.gx = o.x + t % T;
+    nd.gy = o.y + t / T;
+    nd.phi = xi[2 * T * T + t];
+    const int i = wrapi(nd.gx, sp.nx), j = wrapi(nd.gy, sp.ny);
+    const long long c = (long long)j * sp.nx + i;
+#pragma unroll
+    for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c);
+    nd.dro = rest_base<R>(sp, reg, pool, i, j);
+    nd.cx = ldC<S, R>(carry + c);
+    nd.cy = ldC<S, R>(carry + sp.P + c);
+}
+// One node's terms, added to the thread's partial sums in the arithmetic
+// precision (FP64 is a narrow pipe on this GPU; the FP32 path's inputs are FP32
+// anyway); positions relative to the tile origin.  The block sums them in FP64.
+template <class R, class S>
+__device__ __forceinline__ void stats_finish(const SimParams &sp, const StatsNode<R, S> &nd, const R *xi, int T,
+                                             const Frame &fr, R G, R eps, R (&acc)[8], R &mx) {
+    R rho, u, v;
+    moments_from<R>(sp, nd.f, nd.dro, nd.cx, nd.cy, rho, u, v);
+    const int lx = nd.t % T, ly = nd.t / T;
+    const R lam = R(1) - heaviside<R>(nd.phi, eps), lr = lam * rho;
+    acc[0] += lam; acc[1] += lam * R(lx); acc[2] += lam * R(ly);
+    acc[3] += lr; acc[4] += lr * u; acc[5] += lr * v;
+    R ddet, vm;
+    if (nd.phi < -R(PHI_TIE) && node_deformation<R>(xi, xi + T * T, T, lx, ly, fr, G, ddet, vm)) {
+        const R a = ddet < R(0) ? -ddet : ddet;
+        acc[6] += lam * a;
+        acc[7] += lam;
+        mx = a > mx ? a : mx;
+    }
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_stats_kernel(SimParams sp, const S *f, const S *carry,
+                                                                    const int *reg, const R *pool, const R *xi,
+                                                                    const Frame *frames, const SolidDesc *solids,
+                                                                    double *out) {
     __shared__ double red[32 * 8];
     __shared__ unsigned long long dmax;
+    __shared__ int queue[STATS_THREADS / 32][96];  // per warp: < 64 waiting + one round of 32
     const int s = blockIdx.x;
     const SolidDesc sd = solids[s];
     const Frame fr = frames[s];
     const int2 o = make_int2(fr.ox, fr.oy);
-    const Rsq<R> rq(sd);
     const int T = sd.T;
-    const R eps = pick<R>(sp.eps, sp.eps_f);
-    double st[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // ..., sum lambda |det F - 1|, sum lambda over them
-    double mx = 0.0;
+    const R *X = xi + sd.off;
+    const R eps = pick<R>(sp.eps, sp.eps_f), G = pick<R>(sd.G, sd.G_f);
+    R acc[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    R mx = R(0);
     if (threadIdx.x == 0) dmax = 0ull;
     __syncthreads();
-    for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
-        const int lx = t % T, ly = t / T;
-        const int gx = o.x + lx, gy = o.y + ly;
-        if (!in_box(fr, lx, ly)) continue;
-        const R X = xi[sd.off + t];
-        if (!(X == X) || !domain_cell(sp, gx, gy)) continue;
-        const R phi = xi[sd.off + 2 * T * T + t];
-        if (!(phi < eps)) continue;
-        R rho, u, v;
-        node_moments<R, S>(sp, f, carry, reg, pool, wrapi(gx, sp.nx), wrapi(gy, sp.ny), rho, u, v);
-        const double lam = 1.0 - (double)heaviside<R>(phi, eps);
-        st[0] += lam; st[1] += lam * gx; st[2] += lam * gy;
-        st[3] += lam * (double)rho; st[4] += lam * (double)rho * (double)u; st[5] += lam * (double)rho * (double)v;
-        R ddet, vm;
-        if (phi < -R(PHI_TIE) &&
-            node_deformation<R>(xi + sd.off, xi + sd.off + T * T, T, lx, ly, fr, pick<R>(sd.G, sd.G_f), ddet, vm)) {
-            const double a = fabs((double)ddet);
-            st[6] += lam * a;
-            st[7] += lam;
-            mx = fmax(mx, a);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int *qu = queue[warp];
+    int qn = 0;  // warp-uniform
+    auto drain = [&](int cnt) {  // the last cnt (<= 64) queued nodes, two per lane
+        const int e1 = qn - cnt + lane, e2 = e1 + 32;
+        StatsNode<R, S> n1, n2;
+        const bool h1 = lane < cnt, h2 = lane + 32 < cnt;
+        if (h1) stats_gather<R, S>(sp, f, carry, reg, pool, X, T, o, qu[e1], n1);
+        if (h2) stats_gather<R, S>(sp, f, carry, reg, pool, X, T, o, qu[e2], n2);
+        if (h1) stats_finish<R, S>(sp, n1, X, T, fr, G, eps, acc, mx);
+        if (h2) stats_finish<R, S>(sp, n2, X, T, fr, G, eps, acc, mx);
+        __syncwarp();
+        qn -= cnt;
+    };
+    const int w = fr.bx1 - fr.bx0 + 1, h = fr.by1 - fr.by0 + 1;
+    const int n = w > 0 && h > 0 ? w * h : 0;
+    for (int base = warp * 32; base < n; base += nw * 32) {
+        const int k = base + lane;
+        bool keep = false;
+        int t = 0;
+        if (k < n) {
+            const int lx = fr.bx0 + k % w, ly = fr.by0 + k / w;
+            t = ly * T + lx;
+            const R Xv = X[t], phi = X[2 * T * T + t];
+            keep = Xv == Xv && phi < eps && domain_cell(sp, o.x + lx, o.y + ly);
         }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) qu[qn + __popc(m & ((1u << lane) - 1u))] = t;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 64) drain(64);
     }
-    atomicMax(&dmax, (unsigned long long)__double_as_longlong(mx));  // non-negative: bits order as values
+    if (qn > 0) drain(qn);
+    atomicMax(&dmax, (unsigned long long)__double_as_longlong((double)mx));  // non-negative: bits order as values
+    double st[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) st[k] = (double)acc[k];
     block_sum<8>(st, red);
     if (threadIdx.x == 0) {
         double *q = out + 8 * s;
-        q[0] = st[0]; q[1] = st[1] / st[0]; q[2] = st[2] / st[0]; q[3] = st[3]; q[4] = st[4]; q[5] = st[5];
+        q[0] = st[0]; q[1] = o.x + st[1] / st[0]; q[2] = o.y + st[2] / st[0]; q[3] = st[3]; q[4] = st[4]; q[5] = st[5];
         q[6] = __longlong_as_double((long long)dmax);
         q[7] = st[7] > 0.0 ? st[6] / st[7] : 0.0;
     }
