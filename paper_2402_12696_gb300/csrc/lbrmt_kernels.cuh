@@ -1776,6 +1776,20 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
 // neo-Hookean stress of Eq. 3_3_solid_stress in plane strain (the out-of-plane
 // deviatoric component is -(tau_xx + tau_yy)).  False where a neighbour is
 // missing or J is singular.
+// det F - 1 (F = J^-1) from the 4-neighbour values of eta = xi - position
+// (d xi / dx = I + d eta / dx by central differences); false where a neighbour
+// is invalid or J is singular.  A = d eta / dx is returned for the stress.
+template <class R>
+__device__ __forceinline__ bool det_dev_from_stencil(R Xe, R Xw, R Xn, R Xs, R Ye, R Yw, R Yn, R Ys, R &Axx, R &Axy,
+                                                     R &Ayx, R &Ayy, R &ddet) {
+    if (!(Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs)) return false;
+    Axx = R(0.5) * (Xe - Xw); Axy = R(0.5) * (Xn - Xs); Ayx = R(0.5) * (Ye - Yw); Ayy = R(0.5) * (Yn - Ys);
+    const R dl = (Axx + Ayy) + (Axx * Ayy - Axy * Ayx);  // det J - 1
+    if (R(1) + dl == R(0)) return false;
+    ddet = -dl / (R(1) + dl);
+    return true;
+}
+
 template <class R>
 __device__ __forceinline__ bool node_deformation(const R *X, const R *Y, int T, int lx, int ly, const Frame &fr, R G,
                                                  R &ddet, R &vm) {
@@ -1783,12 +1797,8 @@ __device__ __forceinline__ bool node_deformation(const R *X, const R *Y, int T, 
     const int k = ly * T + lx;
     const R Xe = X[k + 1], Xw = X[k - 1], Xn = X[k + T], Xs = X[k - T];
     const R Ye = Y[k + 1], Yw = Y[k - 1], Yn = Y[k + T], Ys = Y[k - T];
-    if (!(Xe == Xe && Xw == Xw && Xn == Xn && Xs == Xs)) return false;
-    // eta = xi - position: d xi / dx = I + d eta / dx
-    const R Axx = R(0.5) * (Xe - Xw), Axy = R(0.5) * (Xn - Xs), Ayx = R(0.5) * (Ye - Yw), Ayy = R(0.5) * (Yn - Ys);
-    const R dl = (Axx + Ayy) + (Axx * Ayy - Axy * Ayx);  // det J - 1
-    if (R(1) + dl == R(0)) return false;
-    ddet = -dl / (R(1) + dl);
+    R Axx, Axy, Ayx, Ayy;
+    if (!det_dev_from_stencil<R>(Xe, Xw, Xn, Xs, Ye, Yw, Yn, Ys, Axx, Axy, Ayx, Ayy, ddet)) return false;
     R txx, txy, tyy;
     stress_from_grad<R>(Axx, Axy, Ayx, Ayy, G, txx, txy, tyy);
     const R tzz = -(txx + tyy);
@@ -1836,42 +1846,60 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
 // solid's nodes max |det F - 1| and its lambda-weighted mean.  One CTA per solid.
 // Each warp walks its share of the band box (outside it xi is invalid) and
 // queues, in shared memory, the nodes of the solid and blur zone (phi < eps);
-// every 64 queued nodes it takes two per lane with all loads issued first.
+// every 32 queued nodes it takes one per lane with all its loads issued first.
 constexpr int STATS_THREADS = 256;
 template <class R, class S>
 struct StatsNode {
-    int t, gx, gy;
-    R phi, f[9], dro, cx, cy;
+    int lx, ly, reg;
+    bool inner;  // strictly inside the band box: the deformation stencil is on the tile
+    R phi, f[9], pool, cx, cy, st[8];
 };
+// Every load of one queued node, issued before any is used: the populations,
+// carry and rest base (the pool entry is read alongside the registry count and
+// used only if the tile is registered; its address is valid either way), phi,
+// and the 4-neighbour stencil of eta for det F.
 template <class R, class S>
 __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, const S *carry, const int *reg,
-                                             const R *pool, const R *xi, int T, int2 o, int t, StatsNode<R, S> &nd) {
-    nd.t = t;
-    nd.gx = o.x + t % T;
-    nd.gy = o.y + t / T;
+                                             const R *pool, const R *xi, int T, int2 ow, const Frame &fr, int e,
+                                             StatsNode<R, S> &nd) {
+    nd.lx = e & 0xffff;
+    nd.ly = e >> 16;
+    const int t = nd.ly * T + nd.lx;
     nd.phi = xi[2 * T * T + t];
-    const int i = wrapi(nd.gx, sp.nx), j = wrapi(nd.gy, sp.ny);
+    // ow: the tile origin wrapped into the grid, so one subtraction wraps a node
+    int i = ow.x + nd.lx, j = ow.y + nd.ly;
+    while (i >= sp.nx) i -= sp.nx;
+    while (j >= sp.ny) j -= sp.ny;
     const long long c = (long long)j * sp.nx + i;
 #pragma unroll
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c);
-    nd.dro = rest_base<R>(sp, reg, pool, i, j);
+    const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    nd.reg = reg[tile];
+    nd.pool = pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
     nd.cx = ldC<S, R>(carry + c);
     nd.cy = ldC<S, R>(carry + sp.P + c);
+    nd.inner = nd.lx > fr.bx0 && nd.lx < fr.bx1 && nd.ly > fr.by0 && nd.ly < fr.by1;
+    if (nd.inner) {
+        const R *Y = xi + T * T;
+        nd.st[0] = xi[t + 1]; nd.st[1] = xi[t - 1]; nd.st[2] = xi[t + T]; nd.st[3] = xi[t - T];
+        nd.st[4] = Y[t + 1]; nd.st[5] = Y[t - 1]; nd.st[6] = Y[t + T]; nd.st[7] = Y[t - T];
+    }
 }
 // One node's terms, added to the thread's partial sums in the arithmetic
 // precision (FP64 is a narrow pipe on this GPU; the FP32 path's inputs are FP32
 // anyway); positions relative to the tile origin.  The block sums them in FP64.
 template <class R, class S>
-__device__ __forceinline__ void stats_finish(const SimParams &sp, const StatsNode<R, S> &nd, const R *xi, int T,
-                                             const Frame &fr, R G, R eps, R (&acc)[8], R &mx) {
+__device__ __forceinline__ void stats_finish(const SimParams &sp, const StatsNode<R, S> &nd, R eps, R (&acc)[8],
+                                             R &mx) {
     R rho, u, v;
-    moments_from<R>(sp, nd.f, nd.dro, nd.cx, nd.cy, rho, u, v);
-    const int lx = nd.t % T, ly = nd.t / T;
+    moments_from<R>(sp, nd.f, nd.reg > 0 ? nd.pool : R(0), nd.cx, nd.cy, rho, u, v);
     const R lam = R(1) - heaviside<R>(nd.phi, eps), lr = lam * rho;
-    acc[0] += lam; acc[1] += lam * R(lx); acc[2] += lam * R(ly);
+    acc[0] += lam; acc[1] += lam * R(nd.lx); acc[2] += lam * R(nd.ly);
     acc[3] += lr; acc[4] += lr * u; acc[5] += lr * v;
-    R ddet, vm;
-    if (nd.phi < -R(PHI_TIE) && node_deformation<R>(xi, xi + T * T, T, lx, ly, fr, G, ddet, vm)) {
+    R Axx, Axy, Ayx, Ayy, ddet;
+    if (nd.phi < -R(PHI_TIE) && nd.inner &&
+        det_dev_from_stencil<R>(nd.st[0], nd.st[1], nd.st[2], nd.st[3], nd.st[4], nd.st[5], nd.st[6], nd.st[7], Axx,
+                                Axy, Ayx, Ayy, ddet)) {
         const R a = ddet < R(0) ? -ddet : ddet;
         acc[6] += lam * a;
         acc[7] += lam;
@@ -1886,14 +1914,14 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
                                                                     double *out) {
     __shared__ double red[32 * 8];
     __shared__ unsigned long long dmax;
-    __shared__ int queue[STATS_THREADS / 32][96];  // per warp: < 64 waiting + one round of 32
+    __shared__ int queue[STATS_THREADS / 32][64];  // per warp: < 32 waiting + one round of 32
     const int s = blockIdx.x;
     const SolidDesc sd = solids[s];
     const Frame fr = frames[s];
-    const int2 o = make_int2(fr.ox, fr.oy);
+    const int2 o = make_int2(fr.ox, fr.oy), ow = make_int2(wrapi(fr.ox, sp.nx), wrapi(fr.oy, sp.ny));
     const int T = sd.T;
     const R *X = xi + sd.off;
-    const R eps = pick<R>(sp.eps, sp.eps_f), G = pick<R>(sd.G, sd.G_f);
+    const R eps = pick<R>(sp.eps, sp.eps_f);
     R acc[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     R mx = R(0);
     if (threadIdx.x == 0) dmax = 0ull;
@@ -1901,34 +1929,50 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int *qu = queue[warp];
     int qn = 0;  // warp-uniform
-    auto drain = [&](int cnt) {  // the last cnt (<= 64) queued nodes, two per lane
-        const int e1 = qn - cnt + lane, e2 = e1 + 32;
-        StatsNode<R, S> n1, n2;
-        const bool h1 = lane < cnt, h2 = lane + 32 < cnt;
-        if (h1) stats_gather<R, S>(sp, f, carry, reg, pool, X, T, o, qu[e1], n1);
-        if (h2) stats_gather<R, S>(sp, f, carry, reg, pool, X, T, o, qu[e2], n2);
-        if (h1) stats_finish<R, S>(sp, n1, X, T, fr, G, eps, acc, mx);
-        if (h2) stats_finish<R, S>(sp, n2, X, T, fr, G, eps, acc, mx);
+    auto drain = [&](int cnt) {  // the last cnt (<= 32) queued nodes, one per lane
+        StatsNode<R, S> nd;
+        if (lane < cnt) {
+            stats_gather<R, S>(sp, f, carry, reg, pool, X, T, ow, fr, qu[qn - cnt + lane], nd);
+            stats_finish<R, S>(sp, nd, eps, acc, mx);
+        }
         __syncwarp();
         qn -= cnt;
     };
     const int w = fr.bx1 - fr.bx0 + 1, h = fr.by1 - fr.by0 + 1;
     const int n = w > 0 && h > 0 ? w * h : 0;
-    for (int base = warp * 32; base < n; base += nw * 32) {
-        const int k = base + lane;
-        bool keep = false;
-        int t = 0;
-        if (k < n) {
-            const int lx = fr.bx0 + k % w, ly = fr.by0 + k / w;
-            t = ly * T + lx;
-            const R Xv = X[t], phi = X[2 * T * T + t];
-            keep = Xv == Xv && phi < eps && domain_cell(sp, o.x + lx, o.y + ly);
+    // four rounds of the walk per pass: their loads are issued together.  Each
+    // lane steps its box position (c, r) by the warps' stride, without divisions.
+    constexpr int WU = 4;
+    const int step = nw * 32;
+    int c = 0, r = 0, dc = 0, dr = 0;
+    if (w > 0) { c = (warp * 32 + lane) % w; r = (warp * 32 + lane) / w; dc = step % w; dr = step / w; }
+    for (int base = warp * 32; base < n; base += WU * step) {
+        int ee[WU];
+        bool keep[WU];
+        R xv[WU], pv[WU];
+#pragma unroll
+        for (int u = 0; u < WU; u++) {
+            const int lx = fr.bx0 + c, ly = fr.by0 + r;
+            keep[u] = base + u * step + lane < n && domain_cell(sp, o.x + lx, o.y + ly);
+            ee[u] = (ly << 16) | lx;
+            xv[u] = pv[u] = R(0);
+            if (keep[u]) {
+                const int t = ly * T + lx;
+                xv[u] = X[t];
+                pv[u] = X[2 * T * T + t];
+            }
+            c += dc; r += dr;
+            if (c >= w) { c -= w; r++; }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) qu[qn + __popc(m & ((1u << lane) - 1u))] = t;
-        qn += __popc(m);
-        __syncwarp();
-        if (qn >= 64) drain(64);
+#pragma unroll
+        for (int u = 0; u < WU; u++) {
+            const bool kp = keep[u] && xv[u] == xv[u] && pv[u] < eps;
+            const unsigned m = __ballot_sync(0xffffffffu, kp);
+            if (kp) qu[qn + __popc(m & ((1u << lane) - 1u))] = ee[u];
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) drain(32);
+        }
     }
     if (qn > 0) drain(qn);
     atomicMax(&dmax, (unsigned long long)__double_as_longlong((double)mx));  // non-negative: bits order as values
