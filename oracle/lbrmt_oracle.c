@@ -611,6 +611,9 @@ static void compute_force(osim_t *m) {
                     if (e < 0) continue;
                     double aX[3], bX[3], aY[3], bY[3], ap[3], bp[3];
                     if (!edge_stencil(s, dir, gx, gy, aX, bX, aY, bY, ap, bp)) continue;
+                    /* beyond the blur zone the solid's stress has weight lambda = 0 in
+                     * Eq. 3_6_global_stress: it is not formed (nor its Jacobian checked) */
+                    if (!(0.5 * (ap[1] + bp[1]) < c->eps)) continue;
                     double lam = 1.0 - oracle_heaviside(0.5 * (ap[1] + bp[1]), c->eps);
                     double dXn, dXt, dYn, dYt, tau[3] = {0, 0, 0};
                     edge_grad(aX, bX, &dXn, &dXt);

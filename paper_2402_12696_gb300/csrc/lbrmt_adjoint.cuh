@@ -307,6 +307,7 @@ __device__ void force_adjoint_tile(const SimParams &sp, const ForceAdjArgs<R> &a
             for (int k = 0; k < 3; k++) ok = ok && (Pp[pa[k]] == Pp[pa[k]]) && (Pp[pb[k]] == Pp[pb[k]]);
             if (!ok) continue;
             const R ph = R(0.5) * (Pp[pa[1]] + Pp[pb[1]]);
+            if (!(ph < eps)) continue;  // lambda = 0 and dlambda/dphi = 0: as the forward, no terms
             const R lam = R(1) - heaviside<R>(ph, eps);
             R dXn, dXt, dYn, dYt, txx, txy, tyy;
             edge_grad<R>(X[pa[0]], X[pa[1]], X[pa[2]], X[pb[0]], X[pb[1]], X[pb[2]], dXn, dXt);

@@ -1302,6 +1302,9 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 if (!ok) continue;
                 const R ph = R(0.5) * (P[pa[1]] + P[pb[1]]);
                 phh[ks] = ph;
+                // beyond the blur zone the solid's stress has weight lambda = 0 in
+                // Eq. 3_6_global_stress: it is not formed (nor its Jacobian checked)
+                if (!(ph < eps)) continue;
                 const R lam = R(1) - heaviside<R>(ph, eps);
                 R dXn, dXt, dYn, dYt, txx, txy, tyy;
                 edge_grad<R>(X[pa[0]], X[pa[1]], X[pa[2]], X[pb[0]], X[pb[1]], X[pb[2]], dXn, dXt);
