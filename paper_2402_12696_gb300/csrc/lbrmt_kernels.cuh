@@ -1978,12 +1978,25 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
         }
     }
     if (qn > 0) drain(qn);
-    atomicMax(&dmax, (unsigned long long)__double_as_longlong((double)mx));  // non-negative: bits order as values
-    double st[8];
+    // warp sums in the arithmetic precision, then the warps' sums in FP64
 #pragma unroll
-    for (int k = 0; k < 8; k++) st[k] = (double)acc[k];
-    block_sum<8>(st, red);
+    for (int k = 0; k < 8; k++)
+        for (int d = 16; d > 0; d >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], d);
+    for (int d = 16; d > 0; d >>= 1) {
+        const R m2 = __shfl_down_sync(0xffffffffu, mx, d);
+        mx = m2 > mx ? m2 : mx;
+    }
+    if (lane == 0) {
+        atomicMax(&dmax, (unsigned long long)__double_as_longlong((double)mx));  // non-negative: bits order as values
+        for (int k = 0; k < 8; k++) red[warp * 8 + k] = (double)acc[k];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double st[8];
+        for (int k = 0; k < 8; k++) {
+            st[k] = 0.0;
+            for (int ww = 0; ww < nw; ww++) st[k] += red[ww * 8 + k];
+        }
         double *q = out + 8 * s;
         q[0] = st[0]; q[1] = o.x + st[1] / st[0]; q[2] = o.y + st[2] / st[0]; q[3] = st[3]; q[4] = st[4]; q[5] = st[5];
         q[6] = __longlong_as_double((long long)dmax);
