@@ -1890,7 +1890,8 @@ __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, co
 }
 // One node's terms, added to the thread's partial sums in the arithmetic
 // precision (FP64 is a narrow pipe on this GPU; the FP32 path's inputs are FP32
-// anyway); positions relative to the tile origin.  The block sums them in FP64.
+// anyway); positions relative to the tile origin.  Each warp then sums its
+// threads' terms in that precision and the warps' sums are added in FP64.
 template <class R, class S>
 __device__ __forceinline__ void stats_finish(const SimParams &sp, const StatsNode<R, S> &nd, R eps, R (&acc)[8],
                                              R &mx) {
