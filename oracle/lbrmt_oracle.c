@@ -571,6 +571,22 @@ static long edge_index(const ocfg_t *c, int dir, int gx, int gy) {
     return (long)ey * (nx + 1) + ex;
 }
 
+/* Do the windows [a0, a0 + aw) and [b0, b0 + bw) share a coordinate, the
+ * periodic images of the second included? */
+static int windows_meet_1d(int a0, int aw, int b0, int bw, int n, int periodic) {
+    for (int k = periodic ? -2 : 0; k <= (periodic ? 2 : 0); k++) {
+        const int lo = b0 + k * n;
+        if (a0 < lo + bw && lo < a0 + aw) return 1;
+    }
+    return 0;
+}
+
+/* Do two solids' windows share a grid node? */
+static int windows_meet(const ocfg_t *c, const osolid_t *s, const osolid_t *t) {
+    return windows_meet_1d(s->x0, s->w, t->x0, t->w, c->nx, !c->wall_x) &&
+           windows_meet_1d(s->y0, s->h, t->y0, t->h, c->ny, !c->wall_y);
+}
+
 /* Gather the 2x3 stencil of an edge for one solid.  For dir 0 (x-edge at
  * (gx-1/2, gy)): a = column gx-1, b = column gx, rows gy-1..gy+1.  For dir 1
  * (y-edge at (gx, gy-1/2)): a = row gy-1, b = row gy, columns gx-1..gx+1.
@@ -642,10 +658,13 @@ static void compute_force(osim_t *m) {
                 m->na[2 * cell + 1] += lam * ay;
             }
     }
-    /* contact stress between every pair of solids (Sec. 3.6) */
+    /* contact stress between every pair of solids (Sec. 3.6); a pair whose
+     * windows share no grid node has no edge whose stencil lies in both, so it
+     * contributes nothing and is passed over */
     for (int si = 0; si < m->ns; si++)
         for (int ti = si + 1; ti < m->ns; ti++) {
             const osolid_t *s = &m->s[si], *t = &m->s[ti];
+            if (!windows_meet(c, s, t)) continue;
             for (int dir = 0; dir < 2; dir++)
                 for (int y = 0; y < s->h; y++)
                     for (int x = 0; x < s->w; x++) {

@@ -49,14 +49,14 @@ def _abs_vec(ax, ay, bx, by):
     return float(np.hypot(ax[m] - bx[m], ay[m] - by[m]).max()), float(np.hypot(bx[m], by[m]).max())
 
 
-def compare(sim, ref, sc, core_layers=4):
+def compare(sim, ref, sc, core_layers=4, solids=None):
     """Per-field errors (see module doc) and band-label mismatch counts.
 
     xi is compared on the solid and the first ``core_layers`` band layers
     (the nodes whose values enter the stress stencils and the advection
-    stencils), and separately over the whole band (``xi_band``).  The
-    absolute errors and the oracle's field magnitudes are returned too
-    (``*_abs``, ``*_max``)."""
+    stencils), and separately over the whole band (``xi_band``), for every
+    solid or for the ids in ``solids``.  The absolute errors and the
+    oracle's field magnitudes are returned too (``*_abs``, ``*_max``)."""
     out = {}
     rf = sc["rho_f"]
     ra, rb = sim.field_host("rho") - rf, ref.field("rho") - rf
@@ -73,7 +73,7 @@ def compare(sim, ref, sc, core_layers=4):
     X, Y = grid_x(sc)
     nx, ny = sc["nx"], sc["ny"]
     core, band, mism = 0.0, 0.0, 0
-    for s in range(len(sc["solids"])):
+    for s in (range(len(sc["solids"])) if solids is None else solids):
         xa, xb = sim.field_host("xi_x", s), ref.field("xi_x", s)
         ya, yb = sim.field_host("xi_y", s), ref.field("xi_y", s)
         lab = ref.field("label", s)

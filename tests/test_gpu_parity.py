@@ -205,6 +205,35 @@ def test_rmt_widths_agree_on_many_solids():
     assert abs(m1 - m2) <= 1e-6 * abs(m2)
 
 
+def test_full_size_mixing_workload_matches_oracle():
+    # The benchmark's workload at full size -- 4096^2 periodic, 1024 disks, seed
+    # 0 as rank 0 of bench.py -- in the launch configuration bench.py times
+    # (16x16 registry tiles, direct K1 loads, overlapped schedule, FP32, CUDA
+    # graphs), 4 steps against the FP64 oracle: rho, u, F and Delta rho at
+    # every node, and xi on 24 sampled solids (the 8 largest, 8 across the
+    # periodic edges, 8 at random), to the FP32 bounds of the small cases.
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.mixing_4096(0)
+    n = sc["nx"]
+    sim = pkg.Simulation(sc, precision="fp32", tile_x=16, use_tma=False)
+    ref = oracle.Oracle(sc)
+    sim.step(4)
+    ref.step(4)
+    assert sim.uses_overlap and sim.tile_x == 16 and not sim.uses_tma
+    sol = sc["solids"]
+    largest = sorted(range(len(sol)), key=lambda k: -sol[k]["r"])[:8]
+    edge = [k for k in range(len(sol)) if min(sol[k]["x"], sol[k]["y"], n - sol[k]["x"], n - sol[k]["y"])
+            < sol[k]["r"] + 12][:8]
+    rest = [k for k in range(len(sol)) if k not in largest and k not in edge]
+    picks = sorted(set(largest + edge + list(np.random.default_rng(7).choice(rest, 8, replace=False))))
+    assert len(edge) == 8
+    r = compare(sim, ref, sc, solids=picks)
+    _log("mixing_4096_full/fp32", {4: r})
+    _check({4: r}, "fp32", sc)
+    sim.close()
+    ref.close()
+
+
 def test_heavy_disk_drift_matches_oracle():
     # A disk 1.5 times denser than the fluid, driven with it by a uniform
     # acceleration, lags the fluid in this method (the density-contrast
