@@ -42,14 +42,46 @@ CASES = {
 }
 
 
+def _log(name, res):
+    if OUT:
+        with open(OUT, "a") as f:
+            f.write(json.dumps({"case": name, "res": {str(k): v for k, v in res.items()}}) + "\n")
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_half_storage_parity(case, prec):
     sc = CASES[case]()
     res = run_pair(sc, prec, [1, 10, 100])
-    if OUT:
-        with open(OUT, "a") as f:
-            f.write(json.dumps({"case": f"{case}/{prec}", "res": {str(k): v for k, v in res.items()}}) + "\n")
+    _log(f"{case}/{prec}", res)
+    _check_half(res, prec, sc)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_half_storage_full_size_mixing(prec):
+    # The 4096^2 mixing workload (1024 disks, seed 0) with 16-bit storage in the
+    # launch configuration of the benchmark (16x16 tiles, direct loads,
+    # overlapped schedule), 4 steps against the FP64 oracle: every node of the
+    # grid fields and xi on 16 sampled solids, to the bounds above.
+    import oracle
+    import paper_2402_12696_gb300 as pkg
+    from parity_util import compare
+    sc = scenarios.mixing_4096(0)
+    sim = pkg.Simulation(sc, precision=prec, tile_x=16, use_tma=False)
+    ref = oracle.Oracle(sc)
+    sim.step(4)
+    ref.step(4)
+    sol = sc["solids"]
+    picks = sorted(set(sorted(range(len(sol)), key=lambda k: -sol[k]["r"])[:8] +
+                       list(np.random.default_rng(11).choice(len(sol), 8, replace=False))))
+    res = {4: compare(sim, ref, sc, solids=picks)}
+    _log(f"mixing_4096_full/{prec}", res)
+    _check_half(res, prec, sc)
+    sim.close()
+    ref.close()
+
+
+def _check_half(res, prec, sc):
     us = US[prec]
     drho = max([abs(s["rho_s"] - sc["rho_f"]) for s in sc["solids"]] + [0.0])
     gmax = max([s["G"] for s in sc["solids"]] + [0.0])

@@ -234,6 +234,16 @@ def test_full_size_mixing_workload_matches_oracle():
     ref.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_settling_512_full_size(prec):
+    # The settling suspension at its full size: 512^2, periodic in x, no-slip
+    # in y, 24 disks (seed 0), gravity and contact; 60 steps against the oracle.
+    sc = scenarios.settling_512(0)
+    res = run_pair(sc, prec, [1, 20, 60])
+    _log(f"settling_512/{prec}", res)
+    _check(res, prec, sc)
+
+
 def test_heavy_disk_drift_matches_oracle():
     # A disk 1.5 times denser than the fluid, driven with it by a uniform
     # acceleration, lags the fluid in this method (the density-contrast
