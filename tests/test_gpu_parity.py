@@ -2,9 +2,11 @@
 
 Error measure: parity_util (relative L-infinity; vector fields as vectors;
 stated floors).  Tolerances:
-  FP64 GPU: 1e-8 on every field -- the two sides differ only in summation
-            order, in the 3x3 solve (cofactors vs. elimination) and in the
-            storage of xi (absolute in the oracle, eta on the GPU).
+  FP64 GPU: 1e-8 on every field, times L/64 for domain sides L above 64 --
+            the two sides differ only in summation order, in the 3x3 solve
+            (cofactors vs. elimination) and in the storage of xi (absolute in
+            the oracle, whose differences then round at ~L u_64; eta on the
+            GPU).
   FP32 GPU: relative 1e-5 (the bound the FP32 path is built to) on rho - rho_f,
             the velocity, the force density and xi - x on the solid and its
             first four band layers, plus an absolute allowance for what FP32
@@ -65,10 +67,14 @@ def _built():
 
 
 def _check(res, prec, sc):
+    # the oracle holds xi in absolute coordinates (up to the domain side L), so
+    # its differences round at ~L u_64; the GPU holds eta = xi - x + d: FP64
+    # agreement scales with L beyond 64 nodes
+    tol64 = FP64_TOL * max(1.0, max(sc["nx"], sc["ny"]) / 64.0)
     for n, r in res.items():
         if prec == "fp64":
             for k in ("rho", "u", "xi", "xi_band", "F", "drho"):
-                assert r[k] < FP64_TOL, (n, k, r)
+                assert r[k] < tol64, (n, k, r)
             assert r["label_mismatch"] == 0, (n, r)
         else:
             allow = fp32_allowance(sc, r, n)
