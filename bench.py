@@ -94,10 +94,11 @@ class Ranks:
 
 def k1_source_sha1(text):
     """sha1 (12 hex digits) of the lattice Boltzmann kernel's own source: its
-    section of the kernels header, from the section banner to the next kernel."""
+    section of the kernels header, from the section banner to the region
+    classification of the overlapped step (lb_node .. lb_step_kernel)."""
     import hashlib
     a = text.index("// K1: fused moments")
-    b = text.index("init_f_kernel", a)
+    b = text.index("// Classification of the K1 regions", a)
     return hashlib.sha1(text[a:b].encode()).hexdigest()[:12]
 
 
@@ -225,7 +226,7 @@ def bench_batch(args, dev):
            "sims": len(scs), "nodes": b.nodes, "solids": sum(len(sc["solids"]) for sc in scs),
            "kernel_ms": {"rmt_batch_kernel": kms[0], "force_batch_kernel": kms[1], "lb_batch_kernel": kms[2]},
            "gpu_launches": int(launches), "tile_x": chosen, "autotune_trials": len(b.tune_log()),
-           "setup_s": t_setup}
+           "overlap": b.uses_overlap, "setup_s": t_setup}
     b.close()
     return out
 

@@ -382,8 +382,19 @@ lbrmt_status lbrmt_batch_init(lbrmt_batch *batch, int autotune_steps);
 lbrmt_status lbrmt_batch_step(lbrmt_batch *batch, int nsteps);
 
 /* As lbrmt_step_timed, for the batched kernels (ms_out: 3 floats, mean ms of
- * the reference-map, force and lattice Boltzmann launches of a batch step). */
+ * the reference-map, force and lattice Boltzmann launches of a batch step;
+ * always the sequential schedule). */
 lbrmt_status lbrmt_batch_step_timed(lbrmt_batch *batch, int nsteps, float *ms_out);
+
+/* Overlapped batch step (1, default) or sequential (0), as lbrmt_set_overlap
+ * for one simulation: every member's regions are classified from its previous
+ * registry, and the lattice Boltzmann kernel of the solid-free regions of all
+ * members runs on an internal lowest-priority stream concurrently with the
+ * reference-map and force kernels, which run at the highest priority.  The
+ * results are the same bit for bit.  Not used without solids.
+ * lbrmt_batch_uses_overlap tells whether steps overlap (after initialisation). */
+lbrmt_status lbrmt_batch_set_overlap(lbrmt_batch *batch, int enable);
+int lbrmt_batch_uses_overlap(const lbrmt_batch *batch);
 
 /* Wait for the stream and check every member's device error flags. */
 lbrmt_status lbrmt_batch_sync(lbrmt_batch *batch);

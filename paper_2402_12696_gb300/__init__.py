@@ -38,6 +38,7 @@ EXPORTS = ["lbrmt_default_config", "lbrmt_create", "lbrmt_add_solid", "lbrmt_add
            "lbrmt_reset", "lbrmt_forward_checkpointed", "lbrmt_backward", "lbrmt_set_tile_x", "lbrmt_tile_x",
            "lbrmt_autotune_tile",
            "lbrmt_create_batch", "lbrmt_batch_add_solid", "lbrmt_batch_init", "lbrmt_batch_step",
+           "lbrmt_batch_set_overlap", "lbrmt_batch_uses_overlap",
            "lbrmt_batch_step_timed", "lbrmt_batch_sync", "lbrmt_batch_member", "lbrmt_batch_size",
            "lbrmt_batch_tile_x", "lbrmt_batch_tune_log", "lbrmt_batch_steps_done",
            "lbrmt_batch_last_launch_count", "lbrmt_batch_last_error", "lbrmt_destroy_batch"]
@@ -130,6 +131,8 @@ def load():
     L.lbrmt_batch_tile_x.argtypes = [p, i]
     L.lbrmt_batch_tune_log.argtypes = [p, p, p, p, p, i]
     L.lbrmt_batch_steps_done.argtypes = [p]
+    L.lbrmt_batch_set_overlap.argtypes = [p, i]
+    L.lbrmt_batch_uses_overlap.argtypes = [p]
     L.lbrmt_batch_steps_done.restype = ll
     L.lbrmt_batch_last_launch_count.argtypes = [p]
     L.lbrmt_batch_last_launch_count.restype = ll
@@ -606,7 +609,7 @@ class Batch:
     shape by timing batch steps."""
 
     def __init__(self, scs, precision="fp32", device="cuda:0", stream=None, tile_x=32, autotune_steps=0,
-                 max_solids_per_tile=8, rmax=11):
+                 max_solids_per_tile=8, rmax=11, overlap=True):
         import torch
         self.torch = torch
         self.scs = list(scs)
@@ -623,6 +626,7 @@ class Batch:
         self._cfgs = cfgs
         with torch.cuda.device(self.device):
             self.b = lbrmt_create_batch(cfgs, self.stream.cuda_stream)
+            _bcheck(self.b, load().lbrmt_batch_set_overlap(self.b, int(bool(overlap))))
             for k, sc in enumerate(self.scs):
                 for s in sc["solids"]:
                     shape, a, bb = _solid_geometry(s)
@@ -643,6 +647,14 @@ class Batch:
     def step_timed(self, n):
         with self.torch.cuda.device(self.device):
             return lbrmt_batch_step_timed(self.b, n)
+
+    def set_overlap(self, enable):
+        """Overlapped (True) or sequential (False) batch step (lbrmt_batch_set_overlap)."""
+        _bcheck(self.b, load().lbrmt_batch_set_overlap(self.b, int(bool(enable))))
+
+    @property
+    def uses_overlap(self):
+        return bool(load().lbrmt_batch_uses_overlap(self.b))
 
     def sync(self):
         lbrmt_batch_sync(self.b)

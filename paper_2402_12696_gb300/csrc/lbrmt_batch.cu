@@ -173,7 +173,7 @@ static lbrmt_status direct_batch_step(lbrmt_batch *b, cudaEvent_t *ev) {
     if (e != cudaSuccess) return bcuda(b, e, "batch step launch");
     b->steps++;
     for (Member &mb : b->m) mb.sim->steps++;
-    b->last_launches += b->n_rmt > 0 ? 3 : 1;
+    b->last_launches += batch_launches(b->bl, b->n_rmt, ev != nullptr);
     return LBRMT_OK;
 }
 
@@ -191,7 +191,8 @@ static lbrmt_status capture(lbrmt_batch *b, int nsteps, cudaGraphExec_t *out) {
         if (g) cudaGraphDestroy(g);
         return bcuda(b, e, "capture");
     }
-    e = cudaGraphInstantiate(out, g, 0);
+    // per-node priorities: the overlapped step runs K2, K3 and the busy K1 ahead of the free K1
+    e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         *out = nullptr;
@@ -310,8 +311,34 @@ extern "C" lbrmt_status lbrmt_create_batch(const lbrmt_config *cfgs, int nsim, v
         }
     }
     b->eng = b->m[0].sim->eng;
+    // side stream (lowest priority) and fork / join events of the overlapped step
+    int least = 0, greatest = 0;
+    BatchLaunch &bl = b->bl;
+    const bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+                    cudaStreamCreateWithPriority(&bl.side, cudaStreamNonBlocking, least) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&bl.fork, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&bl.join, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&bl.flags, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        lbrmt_destroy_batch(b);
+        return LBRMT_ERR_CUDA;
+    }
+    bl.prio_hi = greatest;
+    bl.split = true;
     *out = b;
     return LBRMT_OK;
+}
+
+extern "C" lbrmt_status lbrmt_batch_set_overlap(lbrmt_batch *b, int enable) {
+    if (!b) return LBRMT_ERR_ARG;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    b->bl.split = enable != 0;
+    drop_graphs(b);
+    return LBRMT_OK;
+}
+
+extern "C" int lbrmt_batch_uses_overlap(const lbrmt_batch *b) {
+    return b && b->inited && batch_overlaps(b->bl, b->n_rmt) ? 1 : 0;
 }
 
 extern "C" lbrmt_status lbrmt_batch_add_solid_shape(lbrmt_batch *b, int sim_index, int shape, double cx, double cy,
@@ -370,7 +397,7 @@ extern "C" lbrmt_status lbrmt_batch_step(lbrmt_batch *b, int nsteps) {
                 b->steps++;
                 for (Member &mb : b->m) mb.sim->steps++;
             }
-            b->last_launches += (long long)BATCH_GRAPH_STEPS * (b->n_rmt > 0 ? 3 : 1);
+            b->last_launches += (long long)BATCH_GRAPH_STEPS * batch_launches(b->bl, b->n_rmt);
             left -= BATCH_GRAPH_STEPS;
         }
         if (st == LBRMT_OK && left >= 2 && !b->g2) st = capture(b, 2, &b->g2);
@@ -381,7 +408,7 @@ extern "C" lbrmt_status lbrmt_batch_step(lbrmt_batch *b, int nsteps) {
                 b->steps++;
                 for (Member &mb : b->m) mb.sim->steps++;
             }
-            b->last_launches += 2 * (b->n_rmt > 0 ? 3 : 1);
+            b->last_launches += 2 * batch_launches(b->bl, b->n_rmt);
             left -= 2;
         }
     }
@@ -461,7 +488,11 @@ extern "C" const char *lbrmt_batch_last_error(const lbrmt_batch *b) { return b ?
 extern "C" void lbrmt_destroy_batch(lbrmt_batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->bl.side) cudaStreamSynchronize(b->bl.side);
     drop_graphs(b);
+    for (cudaEvent_t ev : {b->bl.fork, b->bl.join, b->bl.flags})
+        if (ev) cudaEventDestroy(ev);
+    if (b->bl.side) cudaStreamDestroy(b->bl.side);
     if (!b->m.empty()) bfree_all(b);
     for (Member &mb : b->m)
         if (mb.sim) lbrmt_destroy(mb.sim);

@@ -19,6 +19,9 @@ struct BatchSimDesc {
     RmtArgs<R, S> rmt[2];  // by step parity
     ForceArgs<R> frc[2];
     LbArgs<R, S> lb[2];
+    const int *reg_count[2];  // tile registries, by step parity (classification of the overlapped step)
+    unsigned char *busy[2];   // K1 region flags, by step parity
+    unsigned *err;
 };
 
 // K2 over every solid of every simulation: item = (simulation, solid).
@@ -82,14 +85,33 @@ __global__ void __launch_bounds__(K3_THREADS) force_batch_kernel(const BatchSimD
     }
 }
 
-// K1 over every region of every simulation: one CTA per item (simulation,
-// ry << 16 | rx) of the simulation-major list.
-template <class R, class S>
+// K1 over the regions of every simulation: one CTA per item (simulation,
+// ry << 16 | rx) of the simulation-major list.  MODE 0: every region; 1: the
+// busy regions of the overlapped step; 2: the free ones (no registry reads).
+template <class R, class S, int MODE>
 __global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S> - 1) lb_batch_kernel(const BatchSimDesc<R, S> *sims,
                                                                              const int2 *items, int parity) {
     const int2 w = items[blockIdx.x];
     const BatchSimDesc<R, S> *d = sims + w.x;  // uniform, L1-resident reads
-    lb_region<R, S>(d->sp, d->lb[parity], w.y & 0xffff, w.y >> 16);
+    const int rx = w.y & 0xffff, ry = w.y >> 16;
+    if (MODE != 0) {
+        const bool b = d->busy[parity][ry * d->sp.nrx + rx] != 0;
+        if (b != (MODE == 1)) return;  // uniform over the CTA, before any barrier
+    }
+    lb_region<R, S, MODE != 2>(d->sp, d->lb[parity], rx, ry);
+}
+
+// Classification of every simulation's K1 regions for the overlapped batch
+// step, one thread per region item, as in a single simulation's step.
+template <class R, class S>
+__global__ void busy_batch_kernel(const BatchSimDesc<R, S> *sims, const int2 *items, int nitems, int parity) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nitems) return;
+    const int2 w = items[k];
+    const BatchSimDesc<R, S> *d = sims + w.x;
+    const int q = 1 - parity;
+    classify_region(d->sp, (w.y >> 16) * d->sp.nrx + (w.y & 0xffff), d->reg_count[q], d->busy[q], d->busy[parity],
+                    d->err);
 }
 
 }  // namespace lbrmt

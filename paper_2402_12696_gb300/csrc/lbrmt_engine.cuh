@@ -87,7 +87,22 @@ template <> inline CUtensorMapDataType tma_dtype<__nv_bfloat16>() { return CU_TE
 struct BatchLaunch {
     int rmt_blocks, rmt_smem;      // K2: persistent grid, dynamic shared memory (largest solid tile)
     int force_blocks, force_smem;  // K3 (widest tile shape)
+    // Overlapped batch step, as a single simulation's: the classification and
+    // K1 of every member's solid-free regions on a side stream of the lowest
+    // priority, K2, K3 and K1 of the busy regions at the highest.  The stream
+    // and the fork / join events are owned by the batch.
+    bool split = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, flags = nullptr;
+    int prio_hi = 0;
 };
+
+// Does a batch step overlap (and how many kernels does it launch)?
+inline bool batch_overlaps(const BatchLaunch &bl, int n_rmt) { return bl.split && bl.side && n_rmt > 0; }
+inline int batch_launches(const BatchLaunch &bl, int n_rmt, bool timed = false) {
+    if (n_rmt == 0) return 1;
+    return batch_overlaps(bl, n_rmt) && !timed ? 5 : 4;  // classification, K2, K3, K1 (busy and free regions)
+}
 
 struct EngineOps {
     cudaError_t (*configure)(const SimParams &, const DevState &, int tmax, LaunchInfo *);
@@ -277,7 +292,10 @@ struct Engine {
             b.rmt[p] = rmt_args(d, p, 0);
             b.frc[p] = force_args(d, 1 - p, p);
             b.lb[p] = lb_args(sp, d, p);
+            b.reg_count[p] = d.reg_count[p];
+            b.busy[p] = d.busy[p];
         }
+        b.err = d.err;
         std::memcpy(dst, &b, sizeof(b));
     }
 
@@ -305,13 +323,36 @@ struct Engine {
     static cudaError_t batch_step(const void *descs, int nsim, const int2 *rmt_items, int n_rmt, const int2 *lb_items,
                                   int n_lb, const BatchLaunch &bl, int parity, cudaStream_t st, cudaEvent_t *ev) {
         const BatchSimDesc<R, S> *ds = static_cast<const BatchSimDesc<R, S> *>(descs);
+        const bool overlap = batch_overlaps(bl, n_rmt) && !ev;
+        const int prio = overlap ? bl.prio_hi : 0;
+        if (overlap) {  // fork: classification and K1 of the free regions on the side stream
+            cudaEventRecord(bl.fork, st);
+            cudaStreamWaitEvent(bl.side, bl.fork, 0);
+            busy_batch_kernel<R, S><<<(n_lb + 255) / 256, 256, 0, bl.side>>>(ds, lb_items, n_lb, parity);
+            cudaEventRecord(bl.flags, bl.side);
+            lb_batch_kernel<R, S, 2><<<n_lb, TILE_N, 0, bl.side>>>(ds, lb_items, parity);
+            cudaEventRecord(bl.join, bl.side);
+        } else if (n_rmt > 0) {
+            busy_batch_kernel<R, S><<<(n_lb + 255) / 256, 256, 0, st>>>(ds, lb_items, n_lb, parity);
+        }
         if (ev) cudaEventRecord(ev[0], st);
-        if (n_rmt > 0) rmt_batch_kernel<R, S><<<bl.rmt_blocks, RMT_THREADS, bl.rmt_smem, st>>>(ds, rmt_items, n_rmt, parity);
+        if (n_rmt > 0)
+            launch_prio(rmt_batch_kernel<R, S>, dim3(bl.rmt_blocks), dim3(RMT_THREADS), bl.rmt_smem, st, prio, ds,
+                        rmt_items, n_rmt, parity);
         if (ev) cudaEventRecord(ev[1], st);
-        if (n_rmt > 0) force_batch_kernel<R, S><<<bl.force_blocks, K3_THREADS, bl.force_smem, st>>>(ds, nsim, parity);
+        if (n_rmt > 0)
+            launch_prio(force_batch_kernel<R, S>, dim3(bl.force_blocks), dim3(K3_THREADS), bl.force_smem, st, prio, ds,
+                        nsim, parity);
         if (ev) cudaEventRecord(ev[2], st);
-        if (n_lb > 0) lb_batch_kernel<R, S><<<n_lb, TILE_N, 0, st>>>(ds, lb_items, parity);
+        if (n_lb > 0) {
+            if (overlap) {
+                cudaStreamWaitEvent(st, bl.flags, 0);  // the classification is done
+                launch_prio(lb_batch_kernel<R, S, 1>, dim3(n_lb), dim3(TILE_N), 0, st, prio, ds, lb_items, parity);
+            } else
+                lb_batch_kernel<R, S, 0><<<n_lb, TILE_N, 0, st>>>(ds, lb_items, parity);
+        }
         if (ev) cudaEventRecord(ev[3], st);
+        if (overlap) cudaStreamWaitEvent(st, bl.join, 0);  // join
         return cudaGetLastError();
     }
 

@@ -1593,10 +1593,8 @@ __global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_step_kernel(Si
 // registry n lies inside the busy regions and a free region needs neither
 // registry.  The previous classification is checked on the fly: a tile of a
 // region that step n - 1 treated as free must not be in registry n - 1.
-static __global__ void lb_busy_kernel(SimParams sp, const int *reg_prev, const unsigned char *busy_prev, unsigned char *busy,
-                               unsigned *err) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= sp.nrx * sp.nty) return;
+__device__ __forceinline__ void classify_region(const SimParams &sp, int r, const int *reg_prev,
+                                                const unsigned char *busy_prev, unsigned char *busy, unsigned *err) {
     const int rx = r % sp.nrx, ry = r / sp.nrx;
     const int b0 = rx << sp.lk, b1 = min(b0 + sp.rk, sp.ntx) - 1;  // the region's tile columns
     bool any = false, own = false;
@@ -1620,6 +1618,12 @@ static __global__ void lb_busy_kernel(SimParams sp, const int *reg_prev, const u
     }
     if (own && !busy_prev[r]) atomicOr(err, ERR_FREE_REGION);
     busy[r] = any ? 1 : 0;
+}
+
+static __global__ void lb_busy_kernel(SimParams sp, const int *reg_prev, const unsigned char *busy_prev, unsigned char *busy,
+                                      unsigned *err) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < sp.nrx * sp.nty) classify_region(sp, r, reg_prev, busy_prev, busy, err);
 }
 
 // ---------------------------------------------------------------------------

@@ -105,6 +105,25 @@ def test_batch_members_match_single_runs(prec):
     b.close()
 
 
+def test_batch_overlap_bit_identical_and_launch_count():
+    # The overlapped batch step (K1 of every member's solid-free regions on a
+    # side stream, concurrently with K2 and K3) gives the same fields, bit for
+    # bit, as the sequential one, and launches five kernels per step.
+    import paper_2402_12696_gb300 as pkg
+    scs = _batch_scs()
+    snaps = []
+    for ov in (True, False):
+        b = pkg.Batch(scs, precision="fp32", tile_x=[32, 16, 64, 128, 32], overlap=ov)
+        b.step(23)  # one 20-step graph, one 2-step graph, one direct step
+        b.sync()
+        assert b.uses_overlap == ov
+        assert b.last_launch_count == 23 * (5 if ov else 4)
+        snaps.append([_snapshot(b[k], sc) for k, sc in enumerate(scs)])
+        b.close()
+    for k, (x, y) in enumerate(zip(*snaps)):
+        assert _same(x, y), k
+
+
 def test_batch_fp64_oracle():
     import paper_2402_12696_gb300 as pkg
     scs = [scenarios.ldc_disk_64(), scenarios.mixing_small(1), scenarios.contact_pair(gap=0.8, nx=96, ny=64)]
