@@ -21,7 +21,9 @@
  *     with cudaMalloc.  Pointers passed by the caller stay caller-owned.
  *   - All work is enqueued asynchronously on the CUDA stream given to
  *     lbrmt_create.  Calls named *_host copy to/from host memory and return
- *     after the copy completed.
+ *     after the copy completed.  A page-locked (or registered) host buffer is
+ *     read or written by the kernels directly over the coherent CPU-GPU link;
+ *     a pageable one goes through a device staging buffer and a copy.
  *   - Every call returns an lbrmt_status and never aborts.  Device-side
  *     error flags (non-finite density, registry overflow, extrapolation
  *     failure, tile overflow) are raised asynchronously and reported by the
