@@ -70,6 +70,8 @@ def lib():
         L.oracle_stress_from_jacobian.restype = i
         L.oracle_stress_from_jacobian.argtypes = [d, d, d, d, d, dp]
         L.oracle_contact_stress.argtypes = [d, d, d, d, d, d, d, d, dp]
+        L.oracle_windows_meet.argtypes = [C.c_int] * 12
+        L.oracle_windows_meet.restype = C.c_int
         L.oracle_extrap_target.restype = i
         L.oracle_extrap_target.argtypes = [i, i, C.c_void_p, dp, dp, i, i, i, i, d, d, i, dp, dp]
         L.oracle_num_threads.restype = i
@@ -125,6 +127,11 @@ def contact_stress(phi_s, phi_t, Gs, Gt, eta, eps, gx, gy):
     out = np.zeros(3)
     lib().oracle_contact_stress(phi_s, phi_t, Gs, Gt, eta, eps, gx, gy, _dp(out))
     return out
+
+
+def windows_meet(a, b, nx, ny, wall_x, wall_y):
+    """Do two solid windows (x0, y0, w, h) share a grid node (periodic images included)?"""
+    return bool(lib().oracle_windows_meet(*a, *b, nx, ny, int(wall_x), int(wall_y)))
 
 
 def extrap_target(lab, X, Y, tx, ty, layer, normal=None, rmax=RMAX):

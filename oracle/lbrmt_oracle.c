@@ -587,6 +587,13 @@ static int windows_meet(const ocfg_t *c, const osolid_t *s, const osolid_t *t) {
            windows_meet_1d(s->y0, s->h, t->y0, t->h, c->ny, !c->wall_y);
 }
 
+/* Exported for the tests: do the windows (x0a, y0a, wa x ha) and
+ * (x0b, y0b, wb x hb) of a grid nx x ny (walls per axis) share a node? */
+int oracle_windows_meet(int x0a, int y0a, int wa, int ha, int x0b, int y0b, int wb, int hb, int nx, int ny,
+                        int wall_x, int wall_y) {
+    return windows_meet_1d(x0a, wa, x0b, wb, nx, !wall_x) && windows_meet_1d(y0a, ha, y0b, hb, ny, !wall_y);
+}
+
 /* Gather the 2x3 stencil of an edge for one solid.  For dir 0 (x-edge at
  * (gx-1/2, gy)): a = column gx-1, b = column gx, rows gy-1..gy+1.  For dir 1
  * (y-edge at (gx, gy-1/2)): a = row gy-1, b = row gy, columns gx-1..gx+1.

@@ -184,6 +184,35 @@ def test_contact_stress_properties():
     assert np.all(oracle.contact_stress(-1.0, 2.0, 0.01, 0.01, eta, eps, 1, 0) == 0)
 
 
+def test_contact_pair_window_test_matches_brute_force():
+    # The contact sum (Sec. 3.6) passes over solid pairs whose windows share no
+    # grid node.  The window test against explicit node sets (periodic images
+    # folded into the grid) on random windows of small periodic and walled
+    # grids; windows start within one window width of the domain, as a
+    # solid's window does (its centre lies in the domain).
+    rng = np.random.default_rng(5)
+    met = 0
+    for _ in range(600):
+        nx, ny = int(rng.integers(6, 24)), int(rng.integers(6, 24))
+        wall_x, wall_y = bool(rng.integers(2)), bool(rng.integers(2))
+
+        def window():
+            w, h = int(rng.integers(1, nx)), int(rng.integers(1, ny))
+            return (int(rng.integers(-w + 1, nx)), int(rng.integers(-h + 1, ny)), w, h)
+
+        def nodes(win):
+            x0, y0, w, h = win
+            xs = [x if wall_x else x % nx for x in range(x0, x0 + w)]
+            ys = [y if wall_y else y % ny for y in range(y0, y0 + h)]
+            return {(x, y) for x in xs for y in ys}
+
+        a, b = window(), window()
+        expect = bool(nodes(a) & nodes(b))
+        met += expect
+        assert oracle.windows_meet(a, b, nx, ny, wall_x, wall_y) == expect, (a, b, nx, ny, wall_x, wall_y)
+    assert 100 < met < 500  # both outcomes exercised
+
+
 # --------------------------------------------------------------------------
 # Extrapolation (Sec. 3.2, Eq. 3_2_extrap_weight)
 # --------------------------------------------------------------------------
