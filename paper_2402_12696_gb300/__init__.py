@@ -421,10 +421,12 @@ class Simulation:
             self._bfield = t  # kept alive until the copy kernel has run
 
     def set_solid_params(self, solid, rho_s, G):
+        """Change a solid's density and shear modulus (lbrmt_set_solid_params; back to the initial state)."""
         with self.torch.cuda.device(self.device):
             lbrmt_set_solid_params(self.h, solid, rho_s, G)
 
     def reset(self):
+        """Return to the initial state with the current parameters (lbrmt_reset)."""
         with self.torch.cuda.device(self.device):
             lbrmt_reset(self.h)
 
@@ -447,9 +449,11 @@ class Simulation:
 
     @property
     def tile_x(self):
+        """Registry / lattice Boltzmann tile width in use (lbrmt_tile_x)."""
         return load().lbrmt_tile_x(self.h)
 
     def set_tile_x(self, tx):
+        """Registry / lattice Boltzmann tile width 16, 32, 64 or 128 (lbrmt_set_tile_x; back to the initial state)."""
         with self.torch.cuda.device(self.device):
             _check(self.h, load().lbrmt_set_tile_x(self.h, int(tx)))
 
@@ -465,17 +469,21 @@ class Simulation:
 
     # -- time stepping ------------------------------------------------------
     def init(self):
+        """Initialise (Algorithm 1, initialisation; lbrmt_init)."""
         with self.torch.cuda.device(self.device):
             lbrmt_init(self.h)
 
     def step(self, n=1):
+        """Advance n steps, asynchronously on the simulation's stream (lbrmt_step)."""
         with self.torch.cuda.device(self.device):
             lbrmt_step(self.h, n)
 
     def sync(self):
+        """Wait for the stream and raise on a device error flag (lbrmt_sync)."""
         lbrmt_sync(self.h)
 
     def active_tiles(self):
+        """Registry tiles the last step registered for the force kernel (lbrmt_active_tiles)."""
         return lbrmt_active_tiles(self.h, 0)
 
     def step_timed(self, n):
@@ -485,10 +493,12 @@ class Simulation:
 
     @property
     def steps_done(self):
+        """Steps taken since the initial state (lbrmt_steps_done)."""
         return load().lbrmt_steps_done(self.h)
 
     @property
     def uses_tma(self):
+        """Whether the lattice Boltzmann kernel stages tiles with tensor-memory copies (lbrmt_uses_tma)."""
         return bool(load().lbrmt_uses_tma(self.h))
 
     def set_overlap(self, enable):
@@ -497,6 +507,7 @@ class Simulation:
 
     @property
     def uses_overlap(self):
+        """Whether steps run the overlapped schedule (lbrmt_uses_overlap)."""
         return bool(load().lbrmt_uses_overlap(self.h))
 
     def set_rmt_threads(self, threads):
@@ -505,10 +516,12 @@ class Simulation:
 
     @property
     def rmt_threads(self):
+        """CTA width of the reference-map kernel in use (lbrmt_rmt_threads)."""
         return load().lbrmt_rmt_threads(self.h)
 
     @property
     def last_launch_count(self):
+        """Kernel launches of the last step call (lbrmt_last_launch_count)."""
         return load().lbrmt_last_launch_count(self.h)
 
     # -- adjoint --------------------------------------------------------------
@@ -549,6 +562,7 @@ class Simulation:
         return out.view(self.ny, self.nx)
 
     def field_host(self, name, solid=0):
+        """One field (a FIELDS name or id; solid selects the solid for per-solid fields) as an (ny, nx) array."""
         out = np.empty(self.ny * self.nx, dtype=np.float64)
         fid = FIELDS[name] if isinstance(name, str) else int(name)
         with self.torch.cuda.device(self.device):
@@ -556,26 +570,31 @@ class Simulation:
         return out.reshape(self.ny, self.nx)
 
     def populations_host(self):
+        """The nine populations f_q as a (9, ny, nx) array."""
         return np.stack([self.field_host(20 + q) for q in range(9)])
 
     def set_populations_host(self, f):
+        """Overwrite the populations from a (9, ny, nx) array (lbrmt_set_populations_host)."""
         f = np.ascontiguousarray(f, dtype=np.float64)
         with self.torch.cuda.device(self.device):
             lbrmt_set_populations_host(self.h, f.ctypes.data)
 
     def solid_stats(self):
+        """Per-solid FP64 statistics of the current state, (S, 8) (lbrmt_solid_stats)."""
         out = np.zeros((max(self.nsolids, 1), 8))
         with self.torch.cuda.device(self.device):
             lbrmt_solid_stats(self.h, 0, out.ctypes.data)
         return out[: self.nsolids]
 
     def total_mass(self):
+        """Total mass sum rho of the current state (lbrmt_total_mass)."""
         out = np.zeros(1)
         with self.torch.cuda.device(self.device):
             lbrmt_total_mass(self.h, 0, out.ctypes.data)
         return float(out[0])
 
     def close(self):
+        """Free the simulation and its device memory (lbrmt_destroy)."""
         if getattr(self, "h", None):
             lbrmt_destroy(self.h)
             self.h = None
@@ -599,6 +618,7 @@ class _Member(Simulation):
         self._batch = batch
 
     def close(self):
+        """Members are freed with their batch."""
         self.h = None
 
 
@@ -641,10 +661,12 @@ class Batch:
         return self.members[k]
 
     def step(self, n=1):
+        """Advance every member n steps, asynchronously (lbrmt_batch_step)."""
         with self.torch.cuda.device(self.device):
             lbrmt_batch_step(self.b, n)
 
     def step_timed(self, n):
+        """Mean ms of the three batched kernels over n sequential steps (lbrmt_batch_step_timed)."""
         with self.torch.cuda.device(self.device):
             return lbrmt_batch_step_timed(self.b, n)
 
@@ -654,30 +676,38 @@ class Batch:
 
     @property
     def uses_overlap(self):
+        """Whether batch steps run the overlapped schedule (lbrmt_batch_uses_overlap)."""
         return bool(load().lbrmt_batch_uses_overlap(self.b))
 
     def sync(self):
+        """Wait for the stream and raise on any member's device error flag (lbrmt_batch_sync)."""
         lbrmt_batch_sync(self.b)
 
     def tile_x(self, k):
+        """Tile width in use by member k (lbrmt_batch_tile_x)."""
         return load().lbrmt_batch_tile_x(self.b, k)
 
     def tune_log(self):
+        """The autotuner's trials as (nx, ny, tile_x, ms per batch step) tuples (lbrmt_batch_tune_log)."""
         return lbrmt_batch_tune_log(self.b)
 
     @property
     def steps_done(self):
+        """Batch steps taken (lbrmt_batch_steps_done)."""
         return load().lbrmt_batch_steps_done(self.b)
 
     @property
     def last_launch_count(self):
+        """Kernel launches of the last batch step call (lbrmt_batch_last_launch_count)."""
         return load().lbrmt_batch_last_launch_count(self.b)
 
     @property
     def nodes(self):
+        """Total grid nodes over the members."""
         return sum(sc["nx"] * sc["ny"] for sc in self.scs)
 
     def close(self):
+        """Free the batch, its members and their device memory (lbrmt_destroy_batch)."""
         if getattr(self, "b", None):
             for m in self.members:
                 m.close()
@@ -703,6 +733,7 @@ def _make_function():
 
         @staticmethod
         def forward(ctx, G, ratio, body, sim, nsteps, checkpoint_every):
+            """Checkpointed forward run (lbrmt_forward_checkpointed): the solids' final centroids."""
             rho_f = sim.sc["rho_f"]
             for k in range(sim.nsolids):
                 sim.set_solid_params(k, float(ratio[k]) * rho_f, float(G[k]))
@@ -716,6 +747,7 @@ def _make_function():
 
         @staticmethod
         def backward(ctx, grad_c):
+            """Reverse run (lbrmt_backward): gradients for G, the density ratio and the body-force field."""
             dG, dr, db = ctx.sim.backward(grad_c.detach().cpu().numpy(), body=ctx.has_body)
             gb = db.to(ctx.body_device) if ctx.has_body else None
             return (torch.as_tensor(dG, dtype=torch.float64), torch.as_tensor(dr, dtype=torch.float64), gb,
