@@ -48,6 +48,8 @@ def lib():
         L.oracle_create.restype = p
         L.oracle_create.argtypes = [i, i, i, i, d, d, d, d, i, d, d, i, d, d, i]
         L.oracle_add_solid.argtypes = [p, d, d, d, d, d]
+        L.oracle_set_force_mode.argtypes = [p, i]
+        L.oracle_set_refmap.argtypes = [p, i, dp, dp]
         L.oracle_set_body_force.argtypes = [p, dp]
         L.oracle_deformation.argtypes = [dp, d, dp]
         L.oracle_add_solid_shape.argtypes = [p, i, d, d, d, d, d, d]
@@ -175,6 +177,8 @@ class Oracle:
             a, b = (s["r"], s["r"]) if shape == 0 else (s["a"], s["b"])
             if L.oracle_add_solid_shape(self.h, shape, s["x"], s["y"], a, b, s["rho_s"], s["G"]) < 0:
                 self._raise()
+        if sc.get("force_mode", 0) and L.oracle_set_force_mode(self.h, int(sc["force_mode"])) != 0:
+            self._raise()
         if sc["force_kind"] == 3:
             bf = np.ascontiguousarray(sc["body_field"], dtype=np.float64).reshape(2, self.ny, self.nx)
             if L.oracle_set_body_force(self.h, _dp(bf)) != 0:
@@ -210,6 +214,14 @@ class Oracle:
     def set_populations(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
         if lib().oracle_set_populations(self.h, _dp(f)) != 0:
+            self._raise()
+
+    def set_refmap(self, solid, X, Y):
+        """Prescribe a solid's reference map (absolute coordinates, (ny, nx)
+        grids) on its solid and band nodes and relabel its level set."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        if lib().oracle_set_refmap(self.h, int(solid), _dp(X), _dp(Y)) != 0:
             self._raise()
 
     def solid_stats(self, solid):

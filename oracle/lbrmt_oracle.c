@@ -75,6 +75,7 @@ typedef struct {
     double force_a[2];
     int rmax;
     double *bfield;  /* force_kind 3: per-node body force, x plane then y plane */
+    int force_mode;  /* 0: rho F in the Guo term (Eq. 3_4_Fi as printed); 1: rho on the accelerations only */
 } ocfg_t;
 
 typedef struct {
@@ -93,6 +94,8 @@ typedef struct {
     double *f, *fh, *Fi;   /* 9 planes of nx*ny */
     double *rho, *ux, *uy; /* moments */
     double *Fx, *Fy, *drho;/* force density and density difference of the last step */
+    double *Fsx, *Fsy;     /* its stress-divergence part (solid and contact stresses) */
+    double *Fax, *Fay;     /* and the rest: blended accelerations and body force */
     double *ex, *ey;       /* half-edge accumulators, 7 values per edge */
     double *nl, *nd, *na;  /* node accumulators: sum lambda, sum lambda(rho_s-rho_f), sum lambda a (2) */
     long step;
@@ -730,6 +733,10 @@ static void compute_force(osim_t *m) {
             body_force(c, i, j, &fbx, &fby);
             m->Fx[cell] = fsx + ax + Hf * fbx;
             m->Fy[cell] = fsy + ay + Hf * fby;
+            m->Fsx[cell] = fsx;
+            m->Fsy[cell] = fsy;
+            m->Fax[cell] = ax + Hf * fbx;
+            m->Fay[cell] = ay + Hf * fby;
             m->drho[cell] = dr;
         }
 }
@@ -744,7 +751,16 @@ static void lb_update(osim_t *m) {
     for (long cell = 0; cell < N; cell++) {
         double feq[NQ], Fi[NQ];
         oracle_feq(m->rho[cell], m->ux[cell], m->uy[cell], m->drho[cell], feq);
-        oracle_guo(m->rho[cell], m->ux[cell], m->uy[cell], m->Fx[cell], m->Fy[cell], Fi);
+        if (c->force_mode == 1) {
+            /* conservative form: the stress divergence without rho, the
+             * accelerations with it (the Guo term is linear in rho F) */
+            double Fs[NQ];
+            oracle_guo(m->rho[cell], m->ux[cell], m->uy[cell], m->Fax[cell], m->Fay[cell], Fi);
+            oracle_guo(1.0, m->ux[cell], m->uy[cell], m->Fsx[cell], m->Fsy[cell], Fs);
+            for (int q = 0; q < NQ; q++) Fi[q] += Fs[q];
+        } else {
+            oracle_guo(m->rho[cell], m->ux[cell], m->uy[cell], m->Fx[cell], m->Fy[cell], Fi);
+        }
         for (int q = 0; q < NQ; q++) {
             double fq = m->f[q * N + cell];
             m->fh[q * N + cell] = fq - (fq - feq[q]) / tau + (1.0 - 1.0 / (2.0 * tau)) * Fi[q];
@@ -811,18 +827,34 @@ void *oracle_create(int nx, int ny, int wall_x, int wall_y, double tau, double r
     m->Fx = calloc(N, sizeof(double));
     m->Fy = calloc(N, sizeof(double));
     m->drho = calloc(N, sizeof(double));
+    m->Fsx = calloc(N, sizeof(double));
+    m->Fsy = calloc(N, sizeof(double));
+    m->Fax = calloc(N, sizeof(double));
+    m->Fay = calloc(N, sizeof(double));
     m->ex = calloc(EV * NE, sizeof(double));
     m->ey = calloc(EV * NE, sizeof(double));
     m->nl = calloc(N, sizeof(double));
     m->nd = calloc(N, sizeof(double));
     m->na = calloc(2 * N, sizeof(double));
     if (!m->f || !m->fh || !m->Fi || !m->rho || !m->ux || !m->uy || !m->Fx || !m->Fy ||
-        !m->drho || !m->ex || !m->ey || !m->nl || !m->nd || !m->na) {
+        !m->drho || !m->ex || !m->ey || !m->nl || !m->nd || !m->na || !m->Fsx || !m->Fsy || !m->Fax ||
+        !m->Fay) {
         free(m);
         return NULL;
     }
     m->step = -1; /* not initialised */
     return m;
+}
+
+/* Form of the Guo term (Sec. 3.4): 0 multiplies the whole force density by
+ * rho, as the expanded Eq. 3_4_Fi prints it; 1 leaves the stress divergence
+ * (Eqs. 3_3_div_solid_stress, 3_6_global_stress) without rho, so its net
+ * force telescopes to zero in a periodic box. */
+int oracle_set_force_mode(void *h, int mode) {
+    osim_t *m = h;
+    if (mode != 0 && mode != 1) return seterr(m, "force_mode must be 0 or 1");
+    m->c.force_mode = mode;
+    return 0;
 }
 
 int oracle_add_solid(void *h, double xc, double yc, double R, double rho_s, double G) {
@@ -1031,6 +1063,31 @@ int oracle_set_populations(void *h, const double *f) {
 }
 
 long oracle_steps_done(void *h) { return ((osim_t *)h)->step; }
+/* Overwrite a solid's reference map on its solid and band nodes with the
+ * values of the grids X, Y (nx*ny doubles each, absolute reference
+ * coordinates of the grid nodes), then relabel phi = phi_0(xi) there (Sec.
+ * 3.2).  The labels (solid set and layers) are kept.  A node of the unwrapped
+ * window at gx takes X[i] + (gx - i) for its grid node i, so the map stays
+ * continuous across a periodic edge.  For tests that prescribe a deformation. */
+int oracle_set_refmap(void *h, int solid, const double *X, const double *Y) {
+    osim_t *m = h;
+    if (m->step < 0) return seterr(m, "the simulation is not initialised");
+    if (solid < 0 || solid >= m->ns) return seterr(m, "no such solid");
+    const ocfg_t *c = &m->c;
+    osolid_t *s = &m->s[solid];
+    for (int y = 0; y < s->h; y++)
+        for (int x = 0; x < s->w; x++) {
+            int k = y * s->w + x, gx = s->x0 + x, gy = s->y0 + y;
+            if (s->lab[k] < 0) continue;
+            int i = wrapi(gx, c->nx), j = wrapi(gy, c->ny);
+            long cell = (long)j * c->nx + i;
+            s->X[k] = X[cell] + (gx - i);
+            s->Y[k] = Y[cell] + (gy - j);
+            s->phi[k] = phi0(s, s->X[k], s->Y[k]);
+        }
+    return 0;
+}
+
 int oracle_num_solids(void *h) { return ((osim_t *)h)->ns; }
 const char *oracle_error(void *h) { return ((osim_t *)h)->err ? ((osim_t *)h)->msg : ""; }
 
@@ -1041,6 +1098,7 @@ void oracle_destroy(void *h) {
     free(m->s);
     free(m->f); free(m->fh); free(m->Fi); free(m->rho); free(m->ux); free(m->uy);
     free(m->Fx); free(m->Fy); free(m->drho); free(m->ex); free(m->ey);
+    free(m->Fsx); free(m->Fsy); free(m->Fax); free(m->Fay);
     free(m->nl); free(m->nd); free(m->na);
     free(m->c.bfield);
     free(m);

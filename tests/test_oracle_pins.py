@@ -617,3 +617,146 @@ def test_shapes_initial_area_and_rest():
 
 def _shape_r(s):
     return s["r"] if s.get("shape", "disk") == "disk" else max(s["a"], s["b"])
+
+
+# --------------------------------------------------------------------------
+# Upwind side, overlap normalisation and divergence assembly on prescribed
+# reference maps (oracle.set_refmap writes xi on the solid and band nodes)
+# --------------------------------------------------------------------------
+def _grid(nx, ny):
+    return (np.arange(nx)[None, :].repeat(ny, 0).astype(float),
+            np.arange(ny)[:, None].repeat(nx, 1).astype(float))
+
+
+@pytest.mark.parametrize("U", [0.02, -0.02])
+def test_upwind_side_on_a_quartic_reference_map(U):
+    # Eq. 3_1_eno differences against the flow: (3 xi_0 - 4 xi_-1 + xi_-2) / 2 for
+    # u > 0 and (-3 xi_0 + 4 xi_1 - xi_2) / 2 for u < 0.  Both are exact on
+    # quadratics and share the h^2 term; on a quartic they differ in the h^3
+    # term, exactly: backward = xi' - xi'''/3 + xi''''/4, forward = xi' - xi'''/3
+    # - xi''''/4.  So one advection step of xi_x = x + a (x - x0)^4 in a uniform
+    # flow (U, V) is xi_x - U (xi' - xi'''/3 + s xi''''/4), s = sign of U, on
+    # every node of the advected set (xi_x does not vary in y, so the y
+    # difference is exactly zero).
+    nx, ny, x0, a, V = 64, 48, 31.0, 1e-6, 0.013
+    sc = scenarios.fluid_only(nx, ny, 0, 0, 0.7)
+    sc["solids"].append({"x": 31.0, "y": 24.0, "r": 9.0, "rho_s": 1.0, "G": 0.0})
+    o = oracle.Oracle(sc)
+    f = np.zeros((9, ny, nx))
+    f[:] = oracle.feq(1.0, U, V, 0.0)[:, None, None]
+    o.set_populations(f)
+    x, y = _grid(nx, ny)
+    X = x + a * (x - x0) ** 4
+    o.set_refmap(0, X, y)
+    phi = o.field("phi", 0)
+    S = np.isfinite(phi) & (phi < -1e-9)
+    assert S.sum() > 200
+    o.step(1)
+    xi = o.field("xi_x", 0)
+    s = x - x0
+    d1, d3, d4 = 1 + 4 * a * s ** 3, 24 * a * s, 24 * a
+    side = 1.0 if U > 0 else -1.0
+    expect = X - U * (d1 - d3 / 3 + side * d4 / 4)
+    wrong = X - U * (d1 - d3 / 3 - side * d4 / 4)  # the stencil from the downwind side
+    assert np.abs(xi[S] - expect[S]).max() < 1e-12
+    assert np.abs(xi[S] - wrong[S]).min() > 0.5 * abs(U) * 12 * a
+    o.close()
+
+
+def _edge_weights(phi, eps, c=lambda lam: lam):
+    """Blend weights c(lambda) of the x-edges left/right and y-edges
+    below/above every node, lambda = 1 - H(mean phi of the edge's two nodes)
+    (zero where a node has no value: beyond the band lambda is zero)."""
+    H = np.vectorize(lambda p: oracle.heaviside(p, eps) if np.isfinite(p) else 1.0)
+    lx = c(1.0 - H(0.5 * (phi + np.roll(phi, 1, axis=1))))   # edge (i - 1/2, j)
+    ly = c(1.0 - H(0.5 * (phi + np.roll(phi, 1, axis=0))))   # edge (i, j - 1/2)
+    return lx, np.roll(lx, -1, axis=1), ly, np.roll(ly, -1, axis=0)
+
+
+def _stretched(sc, stretch, copies):
+    """Oracle with `copies` coincident copies of the scenario's solid, each
+    given the uniform stretch xi = c + diag(1/stretch, stretch) (x - c)."""
+    sc = dict(sc, solids=sc["solids"] * copies)
+    o = oracle.Oracle(sc)
+    x, y = _grid(sc["nx"], sc["ny"])
+    s0 = sc["solids"][0]
+    for k in range(copies):
+        o.set_refmap(k, s0["x"] + (x - s0["x"]) / stretch, s0["y"] + (y - s0["y"]) * stretch)
+    return o
+
+
+def test_overlap_blend_is_normalised_by_sum_lambda():
+    # Eq. 3_6_global_stress: the blended solid stress sum lambda_s tau_s is divided
+    # by sum lambda where that exceeds one; Delta rho (Eq. 2_3_drho) and the solid
+    # accelerations are blended the same way.  Two coincident copies of one
+    # uniformly stretched solid have lambda_1 = lambda_2 = lambda everywhere, so
+    # every blended quantity is min(1, 2 lambda) / lambda times the single
+    # copy's, and with the stretch's uniform tau_s (its closed form is pinned
+    # above) the force at a node is tau_s applied to the differences of the
+    # edge weights.  The copies' contact stress vanishes (phi_s - phi_t has no
+    # gradient).
+    stretch, G, rho_s = 1.03, 0.01, 1.4
+    sc = scenarios.fluid_only(64, 64, 0, 0, 0.8)
+    sc["solids"].append({"x": 32.2, "y": 31.7, "r": 10.0, "rho_s": rho_s, "G": G})
+    J = [[1.0 / stretch, 0.0], [0.0, stretch]]
+    txx, txy, tyy = oracle.stress_from_jacobian(J, G)
+    assert abs(txx) > 1e-4 and abs(txy) < 1e-18
+    one, two = _stretched(sc, stretch, 1), _stretched(sc, stretch, 2)
+    one.step(1)
+    two.step(1)
+    phi = one.field("phi", 0)
+    assert np.array_equal(np.isfinite(phi), np.isfinite(two.field("phi", 1)))
+    lam = np.where(np.isfinite(phi), 1.0 - np.vectorize(lambda p: oracle.heaviside(p, 1.5))(np.nan_to_num(phi, nan=9.0)), 0.0)
+    assert ((2 * lam > 1) & (lam < 1)).any() and ((2 * lam < 1) & (lam > 0)).any()
+    # Delta rho at the nodes
+    d1, d2 = one.field("drho"), two.field("drho")
+    assert np.abs(d1 - lam * (rho_s - 1.0)).max() < 1e-14
+    assert np.abs(d2 - np.minimum(1.0, 2 * lam) * (rho_s - 1.0)).max() < 1e-14
+    # force density: divergence of the blended uniform stress
+    for o, c in ((one, lambda l: l), (two, lambda l: np.minimum(1.0, 2 * l))):
+        wl, wr, wb, wt = _edge_weights(phi, 1.5, c)
+        fx = txx * (wr - wl) + txy * (wt - wb)
+        fy = txy * (wr - wl) + tyy * (wt - wb)
+        # (the band's least-squares fits reproduce the linear map to ~1e-13)
+        assert np.abs(o.field("Fx") - fx).max() < 1e-12
+        assert np.abs(o.field("Fy") - fy).max() < 1e-12
+    assert np.abs(two.field("Fx") - one.field("Fx")).max() > 1e-6  # the normalisation acts
+    one.close(); two.close()
+    # solid accelerations (G = 0: no stress): a_s = -(1 - rho_f / rho_s) g
+    g = 1e-4
+    sc0 = dict(sc, gravity=g, solids=[dict(sc["solids"][0], G=0.0)])
+    one, two = _stretched(sc0, stretch, 1), _stretched(sc0, stretch, 2)
+    one.step(1)
+    two.step(1)
+    a_s = -(1.0 - 1.0 / rho_s) * g
+    assert np.abs(one.field("Fy") - lam * a_s).max() < 1e-18
+    assert np.abs(two.field("Fy") - np.minimum(1.0, 2 * lam) * a_s).max() < 1e-18
+    one.close(); two.close()
+
+
+def test_divergence_of_a_sinusoidal_shear():
+    # Eqs. 3_3_refmap_jacobian .. 3_3_div_solid_stress on a small shear
+    # displacement u = (A sin(k y), 0) inside a large solid: xi = x - u, so
+    # J = I - grad u, F = J^-1 = I + grad u + O(A^2) and the neo-Hookean stress is
+    # tau_xy = G du_x/dy, tau_xx = tau_yy = O(A^2).  On the half-edge stencils the
+    # y-edge difference of xi_x is -2 A sin(k/2) cos(k (j - 1/2)), so the divergence
+    # at a node of the solid's interior is F_x = -4 G A sin^2(k/2) sin(k j), the
+    # discrete form of G d^2 u_x / dy^2, and F_y = O(A^2).  A swapped face, a
+    # transposed component or a sign slip in the assembly fails this.
+    nx = ny = 96
+    A, k, G = 1e-5, 2 * np.pi / 12, 0.02
+    sc = scenarios.fluid_only(nx, ny, 0, 0, 0.8)
+    sc["solids"].append({"x": 48.3, "y": 47.6, "r": 30.0, "rho_s": 1.0, "G": G})
+    o = oracle.Oracle(sc)
+    x, y = _grid(nx, ny)
+    o.set_refmap(0, x - A * np.sin(k * y), y)
+    o.step(1)
+    phi = o.field("phi", 0)
+    inner = np.isfinite(phi) & (phi < -(1.5 + 3.0))
+    assert inner.sum() > 1500
+    fx = -4 * G * A * np.sin(k / 2) ** 2 * np.sin(k * y)
+    amp = 4 * G * A * np.sin(k / 2) ** 2
+    assert np.abs(o.field("Fx")[inner] - fx[inner]).max() < 1e-3 * amp
+    assert np.abs(o.field("Fy")[inner]).max() < 1e-3 * amp
+    assert np.abs(o.field("Fx")[inner]).max() > 0.9 * amp
+    o.close()
