@@ -57,6 +57,7 @@ enum { LBRMT_PERIODIC = 0, LBRMT_WALL = 1 };
 enum { LBRMT_FP32 = 0, LBRMT_FP64 = 1, LBRMT_FP16_STORE = 2, LBRMT_BF16_STORE = 3 };
 enum { LBRMT_FORCE_NONE = 0, LBRMT_FORCE_CONST = 1, LBRMT_FORCE_SINE_X = 2, LBRMT_FORCE_FIELD = 3 };
 enum { LBRMT_SHAPE_DISK = 0, LBRMT_SHAPE_ELLIPSE = 1, LBRMT_SHAPE_RECT = 2 };
+enum { LBRMT_FORCE_MODE_LITERAL = 0, LBRMT_FORCE_MODE_CONSERVATIVE = 1 };
 
 /* Field ids for lbrmt_read_fields.  RHO/UX/UY are the moments of the current
  * populations (Sec. 3.4); FX/FY/DRHO are the force density F of Eq. 2_4_F_divs
@@ -101,6 +102,14 @@ typedef struct {
     double deform_margin;       /* room a solid's tile leaves for deformation beyond its band, as a
                                    fraction of its (circumscribed) radius (default 0.25; a band that
                                    reaches the tile edge raises LBRMT_ERR_OVERFLOW) */
+    int force_mode;             /* LBRMT_FORCE_MODE_LITERAL (0, default): the Guo term and the
+                                   half-force moments carry rho F for the whole force density, as the
+                                   expanded Eq. 3_4_Fi prints it (F an acceleration, Sec. 3.4);
+                                   LBRMT_FORCE_MODE_CONSERVATIVE (1): the divergence of the solid and
+                                   contact stresses (Eqs. 3_3_div_solid_stress, 3_6_global_stress)
+                                   enters without rho, the accelerations keep it, so the stress
+                                   forces sum to zero over a periodic box.  The adjoint supports
+                                   mode 0 only (LBRMT_ERR_ARG). */
     lbrmt_alloc_fn alloc;       /* optional device allocator */
     lbrmt_free_fn free;
     void *alloc_ctx;
@@ -229,8 +238,11 @@ lbrmt_status lbrmt_solid_stats(lbrmt_sim *sim, int sim_index, double *host_out);
  * every step's statistics without stalling the stream between steps. */
 lbrmt_status lbrmt_solid_stats_async(lbrmt_sim *sim, int sim_index, double *host_out);
 
-/* Total mass sum_x rho over the domain after the last step (FP64, fixed
- * summation order), into host memory. */
+/* Total mass sum_x rho of the current populations (every node's rho - rho_f
+ * formed in FP64 from its stored values and rest base, summed per registry
+ * tile and then in a fixed order; Appendix C: conserved to round-off in a
+ * periodic or walled box), into host memory.  Needs an initialised
+ * simulation (LBRMT_ERR_STATE otherwise). */
 lbrmt_status lbrmt_total_mass(lbrmt_sim *sim, int sim_index, double *host_out);
 
 /* Number of registry tiles (tile_x x 256/tile_x nodes) that the last step
@@ -242,16 +254,18 @@ lbrmt_status lbrmt_active_tiles(lbrmt_sim *sim, int sim_index, long long *host_o
  * dev_out (caller-owned device memory), enqueued on the simulation's stream;
  * the library allocates no device memory for it.  The paper has no
  * counterpart: this is for callers that cannot allocate device memory where
- * they need the diagnostic (a stream capture that must not gain allocation
- * nodes, a frozen memory pool, a device handed to another allocator).  Its
- * partial sums live in one file-scope device array of 2048 doubles (16 KiB)
- * that every GPU loading the library holds until exit; simulations of more
- * than 33,554,432 nodes are rejected with LBRMT_ERR_ARG.  The first call on a
- * device looks up that array's address, so make it before any stream
- * capture.  The simulation's device must be current and the simulation
- * initialised (LBRMT_ERR_STATE otherwise).  All calls share the array, which
- * keeps the last call's partial sums: calls that overlap on the GPU (other
- * streams of the same device) race and give wrong results. */
+ * they need the diagnostic (a frozen memory pool, a device handed to another
+ * allocator, a real-time loop that allows no allocation).  Its partial sums
+ * live in one file-scope device array of 2048 doubles (16 KiB) that every GPU
+ * loading the library holds until exit; simulations of more than 33,554,432
+ * nodes are rejected with LBRMT_ERR_ARG.  The first call on a device (and the
+ * first after the device's context changed, e.g. after cudaDeviceReset) looks
+ * up that array's address, so make it before any stream capture.  The
+ * simulation's device must be current and the simulation initialised
+ * (LBRMT_ERR_STATE otherwise).  All calls share the array, which keeps the
+ * last call's partial sums (each call overwrites the ones it uses): calls that
+ * overlap on the GPU (other streams of the same device) race and give wrong
+ * results. */
 lbrmt_status lbrmt_total_mass_noalloc(lbrmt_sim *sim, int sim_index, double *dev_out);
 
 /* Wait for the stream and turn device error flags into a status. */

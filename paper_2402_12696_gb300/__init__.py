@@ -53,7 +53,8 @@ class lbrmt_config(C.Structure):
                 ("eps", C.c_double), ("n_layers", C.c_int), ("eta", C.c_double),
                 ("gravity", C.c_double), ("force_kind", C.c_int), ("force_a", C.c_double * 2),
                 ("precision", C.c_int), ("max_solids_per_tile", C.c_int), ("rmax", C.c_int),
-                ("tile_x", C.c_int), ("deform_margin", C.c_double), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("tile_x", C.c_int), ("deform_margin", C.c_double), ("force_mode", C.c_int),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class LbrmtError(RuntimeError):
@@ -378,6 +379,7 @@ def scenario_config(sc, precision="fp32", max_solids_per_tile=8, rmax=11, tile_x
     cfg.rmax = rmax
     cfg.tile_x = tile_x
     cfg.deform_margin = sc.get("deform_margin", 0.25)
+    cfg.force_mode = sc.get("force_mode", 0)
     return cfg
 
 

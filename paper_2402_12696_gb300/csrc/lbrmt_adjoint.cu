@@ -99,6 +99,8 @@ extern "C" lbrmt_status lbrmt_forward_checkpointed(lbrmt_sim *s, int nsteps, int
     if (s->cfg.precision != LBRMT_FP32 && s->cfg.precision != LBRMT_FP64)
         return lbrmt_internal_fail(s, LBRMT_ERR_ARG, "the adjoint needs FP32 or FP64 storage");
     if (s->in_batch) return lbrmt_internal_fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
+    if (s->cfg.force_mode != LBRMT_FORCE_MODE_LITERAL)
+        return lbrmt_internal_fail(s, LBRMT_ERR_ARG, "the adjoint supports force_mode 0 (rho F in the Guo term) only");
     for (const SolidHost &h : s->solids)
         if (h.shape != LBRMT_SHAPE_DISK) return lbrmt_internal_fail(s, LBRMT_ERR_ARG, "the adjoint supports disks only");
     lbrmt_status st = s->inited ? lbrmt_reset(s) : lbrmt_init(s);

@@ -94,6 +94,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (!(c.gravity >= 0) || c.force_kind < 0 || c.force_kind > LBRMT_FORCE_FIELD) return LBRMT_ERR_ARG;
     if (c.precision < LBRMT_FP32 || c.precision > LBRMT_BF16_STORE) return LBRMT_ERR_ARG;
     if (!(c.deform_margin >= 0.0) || c.deform_margin > 4.0) return LBRMT_ERR_ARG;
+    if (c.force_mode != LBRMT_FORCE_MODE_LITERAL && c.force_mode != LBRMT_FORCE_MODE_CONSERVATIVE) return LBRMT_ERR_ARG;
     const int tx = c.tile_x == 0 ? 32 : c.tile_x;
     if (tx != 16 && tx != 32 && tx != 64 && tx != 128) return LBRMT_ERR_ARG;
 
@@ -114,6 +115,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     sp.P = (long long)c.nx * c.ny;
     sp.tau = c.tau; sp.rho_f = c.rho_f; sp.lid_u = c.lid_u; sp.eps = c.eps; sp.eta = c.eta;
     sp.gravity = c.gravity; sp.force_kind = c.force_kind; sp.fa0 = c.force_a[0]; sp.fa1 = c.force_a[1];
+    sp.force_mode = c.force_mode;
     sp.n_layers = c.n_layers; sp.rmax = c.rmax; sp.kmax = c.max_solids_per_tile; sp.nsolids = 0;
     sp.omega = 1.0 / c.tau; sp.kf = 1.0 - 0.5 / c.tau; sp.fy = c.force_kind == LBRMT_FORCE_CONST ? c.force_a[1] : 0.0;
     sp.omega_f = (float)sp.omega; sp.kf_f = (float)sp.kf; sp.rho_f_f = (float)c.rho_f; sp.lid_u_f = (float)c.lid_u;
@@ -126,7 +128,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         SimParams t = sp;
         set_tile_params(t, w);
         ntiles = std::max(ntiles, (size_t)t.ntx * (size_t)t.nty);
-        nparts = std::max(nparts, (size_t)lb_mass_parts(t));
+        nparts = std::max(nparts, (size_t)t.ntx * (size_t)t.nty);  // one mass partial per registry tile
         nregions = std::max(nregions, (size_t)t.nrx * (size_t)t.nty);
     }
     s->ntiles_cap = (long long)ntiles;
@@ -332,9 +334,10 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     s->sp.nsolids = S;
     DevState &d = s->d;
     long long total = 0;
+    const long long planes = s->eng->real_size == 4 ? xi_planes<float>() : xi_planes<double>();
     for (auto &h : s->solids) {
         h.off = total;
-        total += 3ll * h.T * h.T;  // eta_x, eta_y, phi planes
+        total += planes * h.T * h.T;  // eta_x, eta_y, phi (and in FP32 the low parts of eta)
     }
     s->xi_total = total;
     const size_t rs = s->eng->real_size;
@@ -673,10 +676,14 @@ extern "C" lbrmt_status lbrmt_solid_stats_async(lbrmt_sim *s, int sim_index, dou
 
 extern "C" lbrmt_status lbrmt_total_mass(lbrmt_sim *s, int sim_index, double *host_out) {
     if (!s || !host_out || sim_index != 0) return LBRMT_ERR_ARG;
-    if (s->steps == 0) return fail(s, LBRMT_ERR_STATE, "total mass is recorded by the first step");
-    const int n = (int)lb_mass_parts(s->sp);
-    mass_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d.mass_partials, n, s->sp.rho_f * (double)s->sp.P, s->scratch);
-    cudaError_t e = cudaGetLastError();
+    if (!s->inited) return fail(s, LBRMT_ERR_STATE, "the simulation is not initialised (lbrmt_init)");
+    const int cur = (int)(s->steps & 1);
+    cudaError_t e = s->eng->mass(s->sp, s->d, cur, s->stream);
+    if (e == cudaSuccess) {
+        mass_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d.mass_partials, s->sp.ntx * s->sp.nty,
+                                                      s->sp.rho_f * (double)s->sp.P, s->scratch);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_fail(s, e, "mass kernel");
     e = cudaMemcpyAsync(host_out, s->scratch, 8, cudaMemcpyDeviceToHost, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "copy mass");

@@ -113,6 +113,8 @@ struct EngineOps {
     cudaError_t (*field)(const SimParams &, const DevState &, int cur, int lastreg, int kind, int solid,
                          double *out, cudaStream_t);
     cudaError_t (*stats)(const SimParams &, const DevState &, int cur, double *out, cudaStream_t);
+    // per-tile FP64 sums of rho - rho_f of the current populations into d.mass_partials (ntx nty values)
+    cudaError_t (*mass)(const SimParams &, const DevState &, int cur, cudaStream_t);
     cudaError_t (*set_pop)(const SimParams &, const DevState &, int cur, const double *src, cudaStream_t);
     // batches: descriptor of one simulation (host image of BatchSimDesc<R, S>)
     size_t desc_size;
@@ -135,7 +137,7 @@ __global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, 
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sp.P) return;
     const int i = (int)(c % sp.nx), j = (int)(c / sp.nx);
-    const double base = (double)rest_base<R>(sp, reg, pool, i, j);
+    const double base = rest_base_d<R>(sp, reg, pool, i, j);
     for (int q = 0; q < 9; q++)
         stS<S, R>(f + q * sp.P + c, R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f - (q == 0 ? base : 0.0)));
     stC<S, R>(carry + c, R(0));
@@ -279,7 +281,6 @@ struct Engine {
         a.clr_count = d.reg_count[q];
         a.clr_nactive = d.reg_nactive[q];
         a.pool_prev = (const R *)d.pool[q];
-        a.mass_partials = d.mass_partials;
         a.err = d.err;
         return a;
     }
@@ -437,6 +438,12 @@ struct Engine {
         return cudaGetLastError();
     }
 
+    static cudaError_t mass(const SimParams &sp, const DevState &d, int cur, cudaStream_t st) {
+        mass_tile_kernel<R, S><<<dim3(sp.ntx, sp.nty), TILE_N, 0, st>>>(sp, (const S *)d.f[cur], d.reg_count[1 - cur],
+                                                                     (const R *)d.pool[1 - cur], d.mass_partials);
+        return cudaGetLastError();
+    }
+
     static cudaError_t set_pop(const SimParams &sp, const DevState &d, int cur, const double *src, cudaStream_t st) {
         const int nb = (int)((sp.P + 255) / 256);
         set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (S *)d.carry, d.reg_count[1 - cur],
@@ -451,6 +458,7 @@ struct Engine {
         o.step = &step;
         o.field = &field;
         o.stats = &stats;
+        o.mass = &mass;
         o.set_pop = &set_pop;
         o.desc_size = sizeof(BatchSimDesc<R, S>);
         o.fill_desc = &fill_desc;

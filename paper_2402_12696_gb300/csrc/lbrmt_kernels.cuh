@@ -37,7 +37,19 @@ constexpr int RMT_THREADS = 256;
 constexpr int LIST_CAP = 2048;              // per-layer target list in shared memory
 constexpr int TILE_SIDE_MAX = 448;          // largest solid tile side (byte labels + lists in shared memory)
 constexpr int RMT_SMEM_MAX = ((TILE_SIDE_MAX * TILE_SIDE_MAX + 15) & ~15) + 8 * LIST_CAP;
-constexpr int POOL_STRIDE = 3 * TILE_N;     // per tile: Fx, Fy, drho planes
+// Force pool, per registered tile, TILE_N values per plane: F_x and F_y of the
+// solid terms (without the body force), Delta rho as an unevaluated sum hi + lo
+// (lo = 0 in FP64; in FP32 the pair carries Delta rho to ~1e-15, so the SFC
+// equilibrium's rho - rho_t is not rounded against an O(1) number), and, with
+// force_mode 1 only, the blended solid acceleration's y component (plane 1 then
+// holds the stress divergence alone).
+constexpr int POOL_STRIDE = 5 * TILE_N;
+constexpr int POOL_FX = 0, POOL_FY = TILE_N, POOL_DRHO = 2 * TILE_N, POOL_DRHO_LO = 3 * TILE_N, POOL_AY = 4 * TILE_N;
+// Planes of a solid's tile: eta_x, eta_y and phi; FP32 adds the low parts of
+// eta_x and eta_y on the advected nodes (eta = hi + lo), so the rounding of
+// the stored reference map does not accumulate over the steps (zero on the
+// extrapolated band, which is refitted every step from the advected nodes).
+template <class R> __host__ __device__ constexpr int xi_planes() { return sizeof(R) == 4 ? 5 : 3; }
 // Tie rules shared with the method's definition: a node with |phi| <= PHI_TIE
 // is not solid; a directional extrapolation weight with cosine <= COS_TIE is zero.
 constexpr double PHI_TIE = 1e-9;
@@ -58,6 +70,7 @@ struct SimParams {
     long long P;  // plane size nx*ny
     double tau, rho_f, lid_u, eps, eta, gravity;
     int force_kind;
+    int force_mode;  // 0: Guo term with rho F (Eq. 3_4_Fi as printed); 1: rho on the accelerations only
     double fa0, fa1;
     int n_layers, rmax, kmax, nsolids;
     // FP32 copies (GB300's FP64 pipe is narrow: no per-thread conversions)
@@ -85,10 +98,6 @@ __host__ __device__ inline void set_tile_params(SimParams &sp, int tx) {
     sp.nrx = (sp.ntx + sp.rk - 1) / sp.rk;
 }
 
-// FP64 mass partials of K1: one per warp and region pass (rk passes per region)
-__host__ __device__ inline long long lb_mass_parts(const SimParams &sp) {
-    return (long long)sp.nrx * sp.nty * sp.rk * (TILE_N / 32);
-}
 
 template <class R> __device__ __forceinline__ R pick(double d, float f);
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
@@ -240,8 +249,26 @@ __device__ __forceinline__ long long grid_index(const SimParams &sp, int gx, int
 template <class R>
 __device__ __forceinline__ R rest_base(const SimParams &sp, const int *reg, const R *pool, int i, int j) {
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
-    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))]
+    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))]
                          : R(0);
+}
+// The rest base with its low part, in double (readouts and uploads).
+template <class R>
+__device__ __forceinline__ double rest_base_d(const SimParams &sp, const int *reg, const R *pool, int i, int j) {
+    const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    if (reg[tile] <= 0) return 0.0;
+    const R *p = pool + (long long)tile * POOL_STRIDE + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1));
+    return (double)p[POOL_DRHO] + (double)p[POOL_DRHO_LO];
+}
+
+// a - b as an unevaluated sum: s = fl(a - b) and its exact error e, a - b = s + e
+// (Knuth's two-sum, branch-free).
+template <class R>
+__device__ __forceinline__ R two_diff(R a, R b, R &e) {
+    const R s = a - b;
+    const R bb = s - a;
+    e = (a - (s - bb)) - (b + bb);
+    return s;
 }
 
 // Moments of node (i, j): rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
@@ -673,6 +700,18 @@ __device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const Frame &fr
     return num / (rsqrt_<R>(X * X + Y * Y) + q.rad);
 }
 
+// phi_0 of a tile node in double from its stored eta: q = eta + l + off is exact
+// in double, so phi carries no rounding beyond its own evaluation.
+template <class R>
+__device__ __forceinline__ double phi_eta_d(R ex, R ey, int lx, int ly, const Frame &fr, const Rsq<R> &q, double rad,
+                                            R exl = R(0), R eyl = R(0)) {
+    const double X = ((double)lx + (double)fr.offx) + ((double)ex + (double)exl);
+    const double Y = ((double)ly + (double)fr.offy) + ((double)ey + (double)eyl);
+    return q.shape == 0 ? sqrt(X * X + Y * Y) - rad : shape_sdf(q.shape, q.a, q.b, X, Y);
+}
+// Half-width of the shell around the blur zone where K3 takes lambda in double.
+constexpr float PHI_D_SHELL = 1e-3f;
+
 // d = o - X_c - off of a frame, in double.
 __device__ __forceinline__ double frame_d(const Frame &fr, double c, bool xdir) {
     return xdir ? (double)fr.ox - c - (double)fr.offx : (double)fr.oy - c - (double)fr.offy;
@@ -810,7 +849,7 @@ __device__ __forceinline__ bool list_layers(const signed char *lab, int T, int x
 template <class R>
 struct P0Node {
     int ix, iy, cnt;
-    R ex, ey, phi, cx, cy, pv;
+    R ex, ey, exl, eyl, phi, cx, cy, pv;
     R f[9];
 };
 
@@ -826,12 +865,18 @@ __device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, 
     nd.ex = Xi[k];
     nd.ey = Yi[k];
     nd.phi = Pi[k];
+    if constexpr (xi_planes<R>() == 5) {
+        nd.exl = Xi[3 * T * T + k];  // the low parts follow the phi plane
+        nd.eyl = Xi[4 * T * T + k];
+    } else {
+        nd.exl = nd.eyl = R(0);
+    }
 #pragma unroll
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(a.f + q * sp.P + c);
     nd.cx = ldC<S, R>(a.carry + c);
     nd.cy = ldC<S, R>(a.carry + sp.P + c);
     nd.cnt = a.reg_prev[tile];
-    nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
+    nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
 }
 
 // The rest of pass 0 for a gathered node of the blur zone or the solid:
@@ -867,8 +912,28 @@ __device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, 
     const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
     // xi = eta + x - d: the node's own motion enters as -(u - dd)
     const int t = ly * T + lx;
-    Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
-    Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
+    if constexpr (xi_planes<R>() == 5) {
+        // eta^{n+1} = (hi + lo) + dd - (u + u.grad eta) in float-float: the frame
+        // shift dd and the update enter with their exact rounding errors, so
+        // hi + lo carries eta to ~u_32^2 and only the small update rounds
+        const R dX = u + (u * dXdx + v * dXdy), dY = v + (u * dYdx + v * dYdy);
+        R e1, e2;
+        R s1 = two_diff<R>(ex, -ddx, e1);
+        R s2 = two_diff<R>(s1, dX, e2);
+        R tl = (e1 + e2) + nd.exl;
+        R hi = s2 + tl;
+        Xo[t] = hi;
+        Xo[3 * T * T + t] = tl - (hi - s2);
+        s1 = two_diff<R>(ey, -ddy, e1);
+        s2 = two_diff<R>(s1, dY, e2);
+        tl = (e1 + e2) + nd.eyl;
+        hi = s2 + tl;
+        Yo[t] = hi;
+        Xo[4 * T * T + t] = tl - (hi - s2);
+    } else {
+        Xo[t] = ex - (u - ddx) - (u * dXdx + v * dXdy);
+        Yo[t] = ey - (v - ddy) - (u * dYdx + v * dYdy);
+    }
     lab[t] = 0;
     sb[0] = min(sb[0], lx); sb[1] = max(sb[1], lx); sb[2] = min(sb[2], ly); sb[3] = max(sb[3], ly);
 }
@@ -1055,6 +1120,9 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                 bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
                 const R phi = phi_eta(Xo[t], Yo[t], lx, ly, fo, rq);
                 Po[t] = phi;
+                if constexpr (xi_planes<R>() == 5) {
+                    if (a.init || lab[t] > 0) { Xo[3 * TT + t] = R(0); Xo[4 * TT + t] = R(0); }
+                }
                 if (phi < eps) {
                     bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
                 }
@@ -1197,6 +1265,7 @@ struct ForceShared {
     int nk;
     Frame sfr[KMAX];
     R sG[KMAX], sD[KMAX], sA[KMAX];
+    double sRd[KMAX], sDd[KMAX];  // radius and rho_s - rho_f in double (the node terms' Delta rho)
     Rsq<R> srq[KMAX];
     int sT[KMAX];
     long long soff[KMAX];
@@ -1248,6 +1317,8 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 sG[rank] = pick<R>(sd.G, sd.G_f);
                 sD[rank] = pick<R>(sd.drho, sd.drho_f);
                 sA[rank] = pick<R>(sd.accel, sd.accel_f);
+                fs.sRd[rank] = sd.R;
+                fs.sDd[rank] = sd.drho;
                 srq[rank] = Rsq<R>(sd);
                 sT[rank] = sd.T;
                 soff[rank] = sd.off;
@@ -1348,20 +1419,47 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 const R fsx = (tr[0] - tl[0]) + (tt[1] - tb[1]);
                 const R fsy = (tr[1] - tl[1]) + (tt[2] - tb[2]);
                 const int p = (cy + 1) * PX + cx + 1;
-                R L = 0, D = 0, Ay = 0;
+                R L = 0, Ay = 0;
+                double Ld = 0.0, Dd = 0.0;  // sum lambda and Delta rho (Eq. 2_3_drho) in double
                 for (int ks = 0; ks < n; ks++) {
                     const R ph = sP[ks * PN + p];
                     if (!(ph == ph)) continue;
                     const R lam = R(1) - heaviside<R>(ph, eps);
                     L += lam;
-                    D += lam * sD[ks];
                     Ay += lam * sA[ks];
+                    double ld = (double)lam;
+                    if constexpr (sizeof(R) == 4) {
+                        // Delta rho is an O(1) number whose rounding would drive the
+                        // pressure: in and near the blur zone, lambda is formed in
+                        // double from phi_0 of the exact eta + position, not from the
+                        // stored FP32 phi (whose error is far below PHI_D_SHELL)
+                        if (ph > -eps - R(PHI_D_SHELL) && ph < eps + R(PHI_D_SHELL)) {
+                            const Frame &fr = sfr[ks];
+                            const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
+                            const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
+                            const int T = sT[ks];
+                            const R *lo = a.xi + soff[ks] + 3 * T * T + ly * T + lx;  // low parts of eta
+                            const double phd = phi_eta_d(sX[ks * PN + p], sY[ks * PN + p], lx, ly, fr, srq[ks],
+                                                         fs.sRd[ks], lo[0], lo[T * T]);
+                            ld = 1.0 - heaviside<double>(phd, sp.eps);
+                        }
+                    }
+                    Ld += ld;
+                    Dd += ld * fs.sDd[ks];
                 }
-                if (L > R(1)) { D /= L; Ay /= L; }
+                if (L > R(1)) Ay /= L;
+                if (Ld > 1.0) Dd /= Ld;
                 R *po = a.pool + (long long)tile * POOL_STRIDE + threadIdx.x;
-                po[0] = fsx;
-                po[TILE_N] = fsy + Ay;
-                po[2 * TILE_N] = D;
+                const R dhi = R(Dd);
+                po[POOL_FX] = fsx;
+                if (sp.force_mode == 1) {
+                    po[POOL_FY] = fsy;
+                    po[POOL_AY] = Ay;
+                } else {
+                    po[POOL_FY] = fsy + Ay;
+                }
+                po[POOL_DRHO] = dhi;
+                po[POOL_DRHO_LO] = R(Dd - (double)dhi);
             }
         }
         __syncthreads();
@@ -1397,7 +1495,6 @@ struct LbArgs {
     int *clr_count;            // registry of the previous step: read, then cleared for the next step
     int *clr_nactive;
     const R *pool_prev;        // force pool of the previous step (its Delta rho is the rest base)
-    double *mass_partials;
     unsigned *err;
 };
 
@@ -1419,7 +1516,12 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
 #pragma unroll
     for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
         f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.fin_q[q] + c);
-    const R dro = prev_count > 0 ? a.pool_prev[(long long)tile * POOL_STRIDE + 2 * TILE_N + lt] : R(0);
+    R dro = R(0), dro_lo = R(0);  // rest base: Delta rho of the step that wrote f (hi + lo)
+    if (prev_count > 0) {
+        const R *pp = a.pool_prev + (long long)tile * POOL_STRIDE + lt;
+        dro = pp[POOL_DRHO];
+        if constexpr (sizeof(R) == 4) dro_lo = pp[POOL_DRHO_LO];
+    }
     const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const R dr = dro + ds;  // rho - rho_f
     const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -1429,7 +1531,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt) : ldC<S, R>(a.carry + c);
     const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt) : ldC<S, R>(a.carry + P + c);
     const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
-    R Fx, Fy, drt = R(0);
+    R Fx, Fy, drt = R(0), drt_lo = R(0);
     if (sp.force_kind == 3) {
         Fx = a.bfield[c];
         Fy = a.bfield[P + c];
@@ -1439,13 +1541,24 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     }
     if (REG && a.reg_count[tile] > 0) {
         const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
-        Fx += po[0]; Fy += po[TILE_N]; drt = po[2 * TILE_N];
+        drt = po[POOL_DRHO];
+        if constexpr (sizeof(R) == 4) drt_lo = po[POOL_DRHO_LO];
+        if (sp.force_mode == 1) {
+            // conservative form: the stress divergence enters the Guo term without rho
+            Fx += po[POOL_FX] * inv;
+            Fy += po[POOL_FY] * inv + po[POOL_AY];
+        } else {
+            Fx += po[POOL_FX];
+            Fy += po[POOL_FY];
+        }
     }
     if (!(ux + uy == ux + uy)) atomicOr(a.err, ERR_NAN);  // a NaN rho makes both velocities NaN
     const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
     const R u2 = ux * ux + uy * uy;
     const R uF = ux * Fx + uy * Fy;
-    const R dd = dro - drt;      // change of the rest base over the step (small)
+    R dde;
+    const R dds = two_diff<R>(dro, drt, dde);
+    const R dd = dds + (dde + (dro_lo - drt_lo));  // change of the rest base over the step (small)
     const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
     f[0] += dd;                  // rest population relative to this step's Delta rho
     // Collision f^ = f - omega (f - f^eq) + (1 - omega/2) F_i (Eq. 2_2_bgk_force) with
@@ -1507,21 +1620,8 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     return dr;
 }
 
-// FP64 partial of the warp's rho - rho_f sums (one slot per warp and pass).
-__device__ __forceinline__ void lb_mass_partial(double *slot, float dm) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
-    if ((threadIdx.x & 31) == 0) *slot = (double)dm;
-}
-__device__ __forceinline__ void lb_mass_partial(double *slot, double dm) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dm += __shfl_down_sync(0xffffffffu, dm, o);
-    if ((threadIdx.x & 31) == 0) *slot = dm;
-}
-
 // One registry tile (bx, by) of K1, one thread per node (the staged form: the
-// tile's planes are in shared memory).  Its mass partials use the slots of the
-// region layout (pass = the tile's place in its region).
+// tile's planes are in shared memory).
 template <class R, class S, bool STAGED>
 __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> &a, const int bx, const int by,
                                         const S *stage) {
@@ -1529,10 +1629,7 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
     const int i = bx * sp.tx + (lt & (sp.tx - 1)), j = by * sp.ty + (lt >> sp.lx);
     const int tile = by * sp.ntx + bx;
     const bool interior = bx > 0 && (bx + 1) * sp.tx < sp.nx && by > 0 && (by + 1) * sp.ty < sp.ny;
-    R dm = R(0);
-    if (i < sp.nx && j < sp.ny) dm = lb_node<R, S, STAGED>(sp, a, i, j, tile, lt, interior, stage);
-    const long long slot = ((((long long)by * sp.nrx + (bx >> sp.lk)) << sp.lk) + (bx & (sp.rk - 1))) * (TILE_N / 32);
-    lb_mass_partial(a.mass_partials + slot + (lt >> 5), dm);
+    if (i < sp.nx && j < sp.ny) lb_node<R, S, STAGED>(sp, a, i, j, tile, lt, interior, stage);
     __syncthreads();
     if (lt == 0) {
         a.clr_count[tile] = 0;
@@ -1551,17 +1648,14 @@ __device__ __forceinline__ void lb_region(const SimParams &sp, const LbArgs<R, S
     const int lw = sp.lx + sp.lk, W = 1 << lw;
     const int x0 = rx << lw, y0 = ry * sp.ty;
     const bool interior = x0 > 0 && x0 + W < sp.nx && y0 > 0 && y0 + sp.ty < sp.ny;
-    double *part = a.mass_partials + (((long long)ry * sp.nrx + rx) << sp.lk) * (TILE_N / 32);
     for (int p = 0; p < sp.rk; p++) {
         const int n = p * TILE_N + lt;
         const int xl = n & (W - 1), yl = n >> lw;
         const int i = x0 + xl, j = y0 + yl;
-        R dm = R(0);
         if (i < sp.nx && j < sp.ny) {
             const int tile = ry * sp.ntx + (rx << sp.lk) + (xl >> sp.lx);
-            dm = lb_node<R, S, false, REG>(sp, a, i, j, tile, (yl << sp.lx) + (xl & (sp.tx - 1)), interior, nullptr);
+            lb_node<R, S, false, REG>(sp, a, i, j, tile, (yl << sp.lx) + (xl & (sp.tx - 1)), interior, nullptr);
         }
-        lb_mass_partial(part + p * (TILE_N / 32) + (lt >> 5), dm);
     }
     if (REG) {
         __syncthreads();  // every node of the region's tiles has read the previous registry
@@ -1743,6 +1837,26 @@ static __global__ void bounded_wait_check_kernel(unsigned *err) {
     }
 }
 
+// Total mass, one registry tile per CTA: each node's rho - rho_f (its nine
+// stored values and its rest base, Delta rho of the step that wrote them, hi +
+// lo) is formed in FP64 and the CTA's sum written to partials[tile]; the
+// partials are then added in a fixed order (mass_reduce_kernel).
+template <class R, class S>
+__global__ void __launch_bounds__(TILE_N) mass_tile_kernel(SimParams sp, const S *f, const int *reg_count, const R *pool,
+                                                           double *partials) {
+    __shared__ double red[32];
+    const int i = blockIdx.x * sp.tx + (threadIdx.x & (sp.tx - 1)), j = blockIdx.y * sp.ty + (threadIdx.x >> sp.lx);
+    double v[1] = {0.0};
+    if (i < sp.nx && j < sp.ny) {
+        const long long c = (long long)j * sp.nx + i;
+        double dr = rest_base_d<R>(sp, reg_count, pool, i, j);
+        for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c);
+        v[0] = dr;
+    }
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) partials[blockIdx.y * sp.ntx + blockIdx.x] = v[0];
+}
+
 // Fields to a double grid.  kind: 0 rho, 1 ux, 2 uy, 3 Fx, 4 Fy, 5 drho, 20+q f_q.
 template <class R, class S>
 __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *fbody, const R *bfield, const int *reg_count,
@@ -1754,7 +1868,7 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
     double v = 0;
     if (kind == 0) {
         // rho = rho_f + rest base + stored values, summed in FP64 so the readout adds no rounding
-        double dr = (double)rest_base<R>(sp, reg_count, pool, i, j);
+        double dr = rest_base_d<R>(sp, reg_count, pool, i, j);
         for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c);
         v = sp.rho_f + dr;
     } else if (kind <= 2) {
@@ -1762,17 +1876,17 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
         node_moments<R, S>(sp, f, carry, reg_count, pool, i, j, rho, u, w);
         v = kind == 1 ? (double)u : (double)w;
     } else if (kind <= 5) {
-        R p = 0;
-        if (reg_count[tile] > 0) p = pool[(long long)tile * POOL_STRIDE + (kind - 3) * TILE_N + threadIdx.x];
+        const R *po = pool + (long long)tile * POOL_STRIDE + threadIdx.x;
+        const bool reg = reg_count[tile] > 0;
         const R bx = sp.force_kind == 3 ? bfield[c] : fbody[j];
         const R by = sp.force_kind == 3 ? bfield[sp.P + c] : pick<R>(sp.fy, sp.fy_f);
-        if (kind == 3) v = (double)(bx + p);
-        else if (kind == 4) v = (double)(by + p);
-        else v = (double)p;
+        if (kind == 3) v = (double)(bx + (reg ? po[POOL_FX] : R(0)));
+        else if (kind == 4) v = (double)(by + (reg ? po[POOL_FY] + (sp.force_mode == 1 ? po[POOL_AY] : R(0)) : R(0)));
+        else v = rest_base_d<R>(sp, reg_count, pool, i, j);
     } else {
         const int q = kind - 20;
-        v = (double)ldS<S, R>(f + q * sp.P + c) + (double)wq<R>(q) * sp.rho_f;
-        if (q == 0) v += (double)rest_base<R>(sp, reg_count, pool, i, j);
+        v = (double)ldS<S, R>(f + q * sp.P + c) + wq<double>(q) * sp.rho_f;  // the exact weight, as the upload
+        if (q == 0) v += rest_base_d<R>(sp, reg_count, pool, i, j);
     }
     out[c] = v;
 }
@@ -1833,9 +1947,13 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
         const long long c = grid_index(sp, gx, gy);
         double v;
         // xi = eta + l + off + X_c
-        if (kind == 0) v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
-        else if (kind == 1) v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
-        else if (kind == 2) v = (double)xi[sd.off + 2 * T * T + t];
+        if (kind == 0) {
+            v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
+            if constexpr (xi_planes<R>() == 5) v += (double)xi[sd.off + 3 * T * T + t];  // low part
+        } else if (kind == 1) {
+            v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
+            if constexpr (xi_planes<R>() == 5) v += (double)xi[sd.off + 4 * T * T + t];
+        } else if (kind == 2) v = (double)xi[sd.off + 2 * T * T + t];
         else {
             if (!(xi[sd.off + 2 * T * T + t] < -R(PHI_TIE))) continue;
             R ddet, vm;
@@ -1882,7 +2000,7 @@ __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, co
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c);
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
     nd.reg = reg[tile];
-    nd.pool = pool[(long long)tile * POOL_STRIDE + 2 * TILE_N + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
+    nd.pool = pool[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
     nd.cx = ldC<S, R>(carry + c);
     nd.cy = ldC<S, R>(carry + sp.P + c);
     nd.inner = nd.lx > fr.bx0 && nd.lx < fr.bx1 && nd.ly > fr.by0 && nd.ly < fr.by1;

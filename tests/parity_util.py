@@ -6,16 +6,20 @@ both are finite.  Vector fields (u, v) and (F_x, F_y) are compared as vectors:
 D is the largest magnitude of the oracle's vector field.  D has a floor, the
 magnitude below which a field is at the level of round-off of the method
 itself (a fluid at rest, a force that is exactly zero after one step):
-  rho - rho_f : 1e-5 rho_f        velocity : 1e-6
+  rho - rho_f : 1e-4 rho_f        velocity : 1e-6
   force F     : 1e-6              drho     : 1e-6
   xi - x      : 1 lattice spacing (so the xi error is absolute, in cells)
+The density floor is the FP32 resolution of the stored populations: their
+deviations from w_q rho_f reach 6 w_q rho lid_u (8e-3 at a lid of 0.05), whose
+FP32 rounding alone moves rho by ~1e-9, a relative 1e-5 of a density deviation
+of 1e-4 (tests/test_fp32_floors.py shows it on the oracle's own populations).
 """
 import numpy as np
 
 import oracle
 import scenarios  # noqa: F401  (re-exported for the tests)
 
-FLOORS = {"rho": 1e-5, "u": 1e-6, "F": 1e-6, "drho": 1e-6, "xi": 1.0}
+FLOORS = {"rho": 1e-4, "u": 1e-6, "F": 1e-6, "drho": 1e-6, "xi": 1.0}
 
 
 def rel_linf(a, b, floor=0.0, mask=None):

@@ -1,26 +1,22 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Error measure: parity_util (relative L-infinity; vector fields as vectors;
-stated floors).  Tolerances:
+stated floors for fields that are zero up to round-off).  Tolerances:
   FP64 GPU: 1e-8 on every field, times L/64 for domain sides L above 64 --
             the two sides differ only in summation order, in the 3x3 solve
             (cofactors vs. elimination) and in the storage of xi (absolute in
             the oracle, whose differences then round at ~L u_64; eta on the
             GPU).
-  FP32 GPU: relative 1e-5 (the bound the FP32 path is built to) on rho - rho_f,
-            the velocity, the force density and xi - x on the solid and its
-            first four band layers, plus an absolute allowance for what FP32
-            cannot represent (u_32 = 2^-24): the SFC target density
-            Delta rho = sum lambda (rho_s - rho_f) (Eq. 2_3_drho) is an O(1)
-            number held to ~u_32 |rho_s - rho_f| per node and its noise drives
-            the pressure, and the stored populations (O(rho |u|) deviations)
-            round to ~u_32 |u| each step, a random walk over n steps: rho and u
-            get 4 u_32 (max|rho_s - rho_f| + max|u| sqrt(n)); the stress is G
-            times differences of FP32 Jacobian entries, so F gets 8 u_32 max G.
-            The outer band layers are extrapolated from inner ones and amplify
-            their rounding (XI_BAND_TOL_FP32).
+  FP32 GPU: relative 1e-5 on every field: rho - rho_f, the velocity, the force
+            density, Delta rho, and xi - x on the solid and its whole band.
+            FP32 holds this because the O(1) quantities of the method are
+            never rounded against the small ones: the populations are stored
+            as deviations from the SFC rest state, the SFC density difference
+            Delta rho = sum lambda (rho_s - rho_f) (Eq. 2_3_drho) is formed in
+            double from the level set of the exact eta + position and kept as a
+            float pair, and the reference map is held as eta = xi - x + d.
 Band-label mismatches (nodes inside one side's band but not the other's) are
-counted; FP64 must have none.
+counted; none is allowed.
 """
 import json
 import os
@@ -36,15 +32,6 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-8
 FP32_TOL = 1e-5
-U32 = 2.0 ** -24
-XI_BAND_TOL_FP32 = 1e-4
-
-
-def fp32_allowance(sc, r, n):
-    drho = max([abs(s["rho_s"] - sc["rho_f"]) for s in sc["solids"]] + [0.0])
-    gmax = max([s["G"] for s in sc["solids"]] + [0.0])
-    walk = 4 * U32 * (drho + r["u_max"] * np.sqrt(n))
-    return {"rho": walk, "u": walk, "F": 8 * U32 * gmax}
 
 OUT = os.environ.get("LBRMT_PARITY_LOG", "")
 
@@ -70,19 +57,11 @@ def _check(res, prec, sc):
     # the oracle holds xi in absolute coordinates (up to the domain side L), so
     # its differences round at ~L u_64; the GPU holds eta = xi - x + d: FP64
     # agreement scales with L beyond 64 nodes
-    tol64 = FP64_TOL * max(1.0, max(sc["nx"], sc["ny"]) / 64.0)
+    tol = FP64_TOL * max(1.0, max(sc["nx"], sc["ny"]) / 64.0) if prec == "fp64" else FP32_TOL
     for n, r in res.items():
-        if prec == "fp64":
-            for k in ("rho", "u", "xi", "xi_band", "F", "drho"):
-                assert r[k] < tol64, (n, k, r)
-            assert r["label_mismatch"] == 0, (n, r)
-        else:
-            allow = fp32_allowance(sc, r, n)
-            for k in ("rho", "u", "F"):
-                scale = max(r[k + "_max"], FLOORS[k] * (sc["rho_f"] if k == "rho" else 1.0))
-                assert r[k + "_abs"] <= FP32_TOL * scale + allow[k], (n, k, r)
-            assert r["xi"] < FP32_TOL, (n, r)
-            assert r["xi_band"] < XI_BAND_TOL_FP32, (n, r)
+        for k in ("rho", "u", "xi", "xi_band", "F", "drho"):
+            assert r[k] < tol, (n, k, r)
+        assert r["label_mismatch"] == 0, (n, r)
 
 
 CASES = {
@@ -94,6 +73,8 @@ CASES = {
     "contact_pair": lambda: scenarios.contact_pair(gap=0.8, nx=96, ny=64),
     "ldc_body_field_64": lambda: scenarios.adjoint_ldc(64, r=12, body=scenarios.smooth_body_field(0, 64, amp=1e-4)),
     "shapes_small_0": lambda: scenarios.shapes_small(0),
+    # force_mode 1: the stress divergence enters the Guo term without rho
+    "settling_small_0_conservative": lambda: dict(scenarios.settling_small(0), force_mode=1),
 }
 
 
@@ -243,9 +224,9 @@ def test_full_size_mixing_workload_matches_oracle():
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_settling_512_full_size(prec):
     # The settling suspension at its full size: 512^2, periodic in x, no-slip
-    # in y, 24 disks (seed 0), gravity and contact; 60 steps against the oracle.
+    # in y, 24 disks (seed 0), gravity and contact; 100 steps against the oracle.
     sc = scenarios.settling_512(0)
-    res = run_pair(sc, prec, [1, 20, 60])
+    res = run_pair(sc, prec, [1, 10, 100])
     _log(f"settling_512/{prec}", res)
     _check(res, prec, sc)
 
@@ -353,7 +334,7 @@ def test_total_mass_and_solid_stats(prec):
     sim.step(20)
     ref.step(20)
     m = sim.total_mass()
-    assert abs(m - ref.field("rho").sum()) < (1e-9 if prec == "fp64" else 1e-4) * m
+    assert abs(m - ref.field("rho").sum()) < (1e-9 if prec == "fp64" else 1e-4) * m  # (tightened below)
     st = sim.solid_stats()
     for s in range(len(sc["solids"])):
         o = ref.solid_stats(s)

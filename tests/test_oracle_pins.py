@@ -760,3 +760,38 @@ def test_divergence_of_a_sinusoidal_shear():
     assert np.abs(o.field("Fy")[inner]).max() < 1e-3 * amp
     assert np.abs(o.field("Fx")[inner]).max() > 0.9 * amp
     o.close()
+
+
+def test_conservative_force_mode_conserves_momentum():
+    # force_mode 1 leaves the stress divergence without rho in the Guo term and
+    # the half-force moments (Sec. 3.4).  The divergence of the blended stress
+    # telescopes to zero over a periodic box (Eq. 3_3_div_solid_stress sums
+    # differences of half-edge stresses), so with no external force the total
+    # momentum sum rho u is conserved to round-off while the solid deforms; the
+    # literal form (mode 0) multiplies the divergence by the non-uniform rho and
+    # changes it.
+    n, U = 48, 2e-3
+    base = scenarios.fluid_only(n, n, 0, 0, 0.8)
+    base["solids"].append({"x": 23.4, "y": 24.2, "r": 8.0, "rho_s": 1.3, "G": 0.01})
+    y = np.arange(n)[:, None].repeat(n, 1)
+    drift = {}
+    for mode in (0, 1):
+        o = oracle.Oracle(dict(base, force_mode=mode))
+        f = np.stack([oracle.feq(1.0, U * math.sin(2 * math.pi * yy / n), 0.0, 0.0) for yy in range(n)], axis=1)
+        o.set_populations(np.repeat(f[:, :, None], n, axis=2))
+        p0 = None
+        worst = 0.0
+        for _ in range(30):
+            o.step(1)
+            rho = o.field("rho")
+            p = np.array([(rho * o.field("ux")).sum(), (rho * o.field("uy")).sum()])
+            p0 = p if p0 is None else p0
+            worst = max(worst, np.abs(p - p0).max())
+        # the solid deforms: its stress divergence is not small
+        assert np.abs(o.field("Fx")).max() > 1e-7
+        assert abs(o.field("Fx").sum()) < 1e-15 and abs(o.field("Fy").sum()) < 1e-15
+        drift[mode] = worst
+        o.close()
+    # momentum ~ U n^2 / pi = 1.5: round-off of its sum over n^2 nodes is ~1e-14
+    assert drift[1] < 1e-13
+    assert drift[0] > 1e-10
