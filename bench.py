@@ -351,6 +351,101 @@ def study_convergence(args):
           flush=True)
 
 
+STORE_BYTES = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}   # stored population / carry value
+REAL_BYTES = {"fp32": 4, "fp64": 8, "fp16": 4, "bf16": 4}    # force pool / reference map value
+
+
+def band_cells(sc, layers=11):
+    """Band cells B of the survey's byte model: each solid and its extrapolation
+    layers, estimated as pi (r + layers)^2 per disk (at t = 0)."""
+    return sum(np.pi * (s["r"] + layers) ** 2 for s in sc["solids"])
+
+
+def k1_bytes(N, prec, active_tiles):
+    """Algorithmic bytes of one K1 launch.  'survey': the populations in and out
+    (18 s_f per node) and the stored force density read on the registered tiles
+    (2 x 4 B per node there).  'state': everything K1 must move as built -- the
+    populations, the half-force carry in and out (4 s_f), and on registered
+    tiles F_x, F_y and Delta rho (hi, lo) of this step plus the rest base (hi,
+    lo) of the previous step (6 s_r)."""
+    sf, sr = STORE_BYTES[prec], REAL_BYTES[prec]
+    tn = active_tiles * 256
+    return {"survey": N * 18 * sf + tn * 8, "state": N * (18 * sf + 4 * sf) + tn * 6 * sr}
+
+
+def step_bytes(N, prec, sc):
+    """Algorithmic bytes of one whole step on the survey's model: populations
+    in and out, and per band cell xi in and out (2 x 2 x 4 B) plus the stored
+    force density (8 B)."""
+    return N * 18 * STORE_BYTES[prec] + band_cells(sc) * (16 + 8)
+
+
+def time_segments(sim, stream, steps, torch):
+    """`steps` graph-replayed steps in segments of at most SEG_STEPS, each from
+    the initial state after a reset and 400 - SEG_STEPS untimed steps; returns
+    the summed CUDA-event milliseconds and the kernel launches."""
+    segs = [min(SEG_STEPS, steps - k) for k in range(0, steps, SEG_STEPS)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in segs]
+    launches = 0
+    for n_k, (e0, e1) in zip(segs, evs):
+        sim.reset()
+        sim.step(400 - SEG_STEPS)
+        e0.record(stream)
+        sim.step(n_k)
+        e1.record(stream)
+        e1.synchronize()
+        launches += sim.last_launch_count
+    sim.sync()
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs), launches
+
+
+def precision_errors(prec):
+    """Per-field relative errors of the full-size 4-step parity run of this
+    precision (tests/test_gpu_parity.py, tests/test_gpu_half.py), from the
+    committed record, if it was taken on the current kernels."""
+    f = os.path.join(ROOT, "profiles", "precision_errors_mixing4096.json")
+    try:
+        rec = json.load(open(f))
+        src = open(os.path.join(ROOT, "paper_2402_12696_gb300", "csrc", "lbrmt_kernels.cuh")).read()
+        import hashlib
+        if rec.get("kernels_sha1") != hashlib.sha1(src.encode()).hexdigest()[:12]:
+            return None
+        return rec["errors"].get(prec)
+    except Exception:
+        return None
+
+
+def bench_precisions(args, dev, sc, tile_used, peak):
+    """The same workload and launch configuration in the other precisions: FP64
+    arithmetic and storage, FP32 arithmetic with FP16 or BF16 storage."""
+    import torch
+    import paper_2402_12696_gb300 as pkg
+    N = sc["nx"] * sc["ny"]
+    out = {}
+    for prec in ("fp64", "fp16", "bf16"):
+        stream = torch.cuda.Stream(dev)
+        sim = pkg.Simulation(sc, precision=prec, device=str(dev), stream=stream, tile_x=tile_used, use_tma=False,
+                             overlap=not args.no_overlap)
+        sim.init()
+        steps = args.precision_steps if prec != "fp64" else max(1, args.precision_steps // 4)
+        sim.reset()
+        sim.step(4)
+        sim.sync()
+        ms, _ = time_segments(sim, stream, steps, torch)
+        kms = sim.step_timed(10)
+        nact = sim.active_tiles()
+        sim.close()
+        kb = k1_bytes(N, prec, nact)
+        out[prec] = {"value": N * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
+                     "ms_per_step": ms / steps,
+                     "kernel_ms": {"rmt_solid_kernel": kms[0], "force_kernel": kms[1], "lb_step_kernel": kms[2]},
+                     "k1_frac": kb["survey"] / (kms[2] / 1e3) / 1e9 / peak,
+                     "k1_frac_state": kb["state"] / (kms[2] / 1e3) / 1e9 / peak,
+                     "step_frac": step_bytes(N, prec, sc) / (ms / steps / 1e3) / 1e9 / peak,
+                     "error_vs_oracle": precision_errors(prec)}
+    return out
+
+
 def bench_lbrmt(args):
     import torch
     import paper_2402_12696_gb300 as pkg
@@ -426,7 +521,7 @@ def bench_lbrmt(args):
         f0 = torch.from_numpy(sim2.populations_host()).pin_memory()
         ke = args.e2e_steps
         # one page-locked buffer per step: every step's statistics reach the host
-        host_stats = torch.zeros((ke, len(sc["solids"]), 8), dtype=torch.float64).pin_memory()
+        host_stats = torch.zeros((ke, len(sc["solids"]), pkg.STATS_COLS), dtype=torch.float64).pin_memory()
         host_rho = torch.zeros(N, dtype=torch.float64).pin_memory()
         barrier()
         torch.cuda.synchronize(dev)
@@ -459,11 +554,12 @@ def bench_lbrmt(args):
 
     # ---- roofline of the dominant kernel (fused LB kernel) ------------------
     peak, peak_kind = _peaks()
-    sf = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}[args.precision]   # stored population / carry
-    sr = 8 if args.precision == "fp64" else 4                            # force pool
-    alg_bytes = N * (18 * sf + 4 * sf + 3 * sr * band_frac)
+    sf = STORE_BYTES[args.precision]
+    kb = k1_bytes(N, args.precision, nact)
     k1_ms = kms[2]
-    achieved = alg_bytes / (k1_ms / 1e3) / 1e9
+    achieved = kb["survey"] / (k1_ms / 1e3) / 1e9
+    sbytes = step_bytes(N, args.precision, sc)
+    precisions = bench_precisions(args, dev, sc, tile_used, peak) if args.precision_steps > 0 else None
     # DRAM traffic per launch from the committed ncu summary, valid only while the
     # kernel source is the one that was profiled
     traffic = None
@@ -510,8 +606,17 @@ def bench_lbrmt(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "lb_step_kernel",
                      "peak_source": peak_kind,
-                     "bytes_model": f"N*(18*{sf} + 4*{sf}) + 3*{sf}*256*active_tiles per launch",
+                     "bytes_model": f"survey: N*18*{sf} + 8*256*active_tiles per launch "
+                                    f"({kb['survey'] / N:.1f} B/LU)",
+                     "frac_state": kb["state"] / (k1_ms / 1e3) / 1e9 / peak,
+                     "bytes_model_state": f"N*(18*{sf} + 4*{sf}) + 6*{REAL_BYTES[args.precision]}*256*active_tiles "
+                                          f"per launch ({kb['state'] / N:.1f} B/LU): populations, half-force carry, "
+                                          "force pool and both rest bases",
+                     "step_frac": sbytes / (ms_max / args.steps / 1e3) / 1e9 / peak,
+                     "step_bytes_model": f"N*18*{sf} + 24*B per step, B = sum pi (r + 11)^2 = "
+                                         f"{band_cells(sc) / N:.3f} N ({sbytes / N:.1f} B/LU)",
                      "active_tiles": nact, "active_frac": band_frac},
+        "precisions": precisions,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -553,6 +658,8 @@ def main():
     ap.add_argument("--study-steps-scale", type=float, default=1.0)
     ap.add_argument("--shapes-steps", type=int, default=200,
                     help="timed steps of the 506-ellipse workload (0: skip)")
+    ap.add_argument("--precision-steps", type=int, default=396,
+                    help="timed steps of the FP16 / BF16 legs (FP64: a quarter; 0: skip the precision legs)")
     ap.add_argument("--adjoint-steps", type=int, default=3000,
                     help="steps of the adjoint-cost measurement (0: skip)")
     args = ap.parse_args()

@@ -221,15 +221,21 @@ lbrmt_status lbrmt_read_fields_host(lbrmt_sim *sim, int sim_index, int field, in
  * (9*nx*ny doubles, allocated on first use) first. */
 lbrmt_status lbrmt_set_populations_host(lbrmt_sim *sim, const double *host_f);
 
-/* Per-solid FP64 statistics of the current state, S x 8 doubles into host
+/* Per-solid FP64 statistics of the current state, S x 10 doubles into host
  * memory: lambda-weighted area sum, centroid x, centroid y (unwrapped frame),
  * mass sum(lambda rho), momentum sum(lambda rho u), sum(lambda rho v), the
  * maximum of |det F - 1| over the solid nodes (phi < 0) and its lambda-weighted
- * mean over them; lambda = 1 - H_eps(phi) on domain nodes. */
+ * mean over them; lambda = 1 - H_eps(phi) on domain nodes; and the net contact
+ * force (x, y) on the solid: the divergence (Eq. 3_3_div_solid_stress) of the
+ * contact stresses of Eq. 3_6_collision_stress between it and each other solid,
+ * summed over the domain nodes nearer to it than to the other (phi_s < phi_t,
+ * half where equal), so the forces of one contact are equal and opposite in a
+ * periodic box.  Sums are FP64 over compensated per-thread sums of FP32 node
+ * terms (FP32 arithmetic) or FP64 throughout (FP64). */
 lbrmt_status lbrmt_solid_stats(lbrmt_sim *sim, int sim_index, double *host_out);
 
 /* The same statistics, enqueued on the simulation's stream without waiting:
- * host_out (S x 8 doubles, page-locked host memory owned by the caller) is
+ * host_out (S x 10 doubles, page-locked host memory owned by the caller) is
  * written by the statistics kernel directly when the stream reaches it (a
  * pageable buffer is filled by a copy from device memory instead), so the
  * caller keeps it alive and

@@ -225,7 +225,9 @@ class Oracle:
             self._raise()
 
     def solid_stats(self, solid):
-        out = np.empty(8)
+        """(area sum lambda, centroid x, y, mass, momentum x, y, max |det F - 1|,
+        mean |det F - 1|, contact force x, y) of one solid."""
+        out = np.empty(10)
         if lib().oracle_solid_stats(self.h, solid, _dp(out)) != 0:
             self._raise()
         return out

@@ -616,6 +616,35 @@ static int edge_stencil(const osolid_t *s, int dir, int gx, int gy, double aX[3]
     return 1;
 }
 
+/* Contact stress of the pair (s, t) on the half-edge of direction dir at s's
+ * unwrapped node (gx, gy) (Eqs. 3_6_collision_stress .. 3_6_normal): nonzero
+ * where both solids' six-node stencils lie in their bands and both edge means
+ * of phi are below eps.  Returns 0 where the pair has no contact stress. */
+static int pair_edge_stress(const osim_t *m, const osolid_t *s, const osolid_t *t, int dir, int gx, int gy,
+                            double tau[3]) {
+    const ocfg_t *c = &m->c;
+    double aX[3], bX[3], aY[3], bY[3], ap[3], bp[3];
+    if (!edge_stencil(s, dir, gx, gy, aX, bX, aY, bY, ap, bp)) return 0;
+    int wx = c->wall_x ? gx : wrapi(gx, c->nx);
+    int wy = c->wall_y ? gy : wrapi(gy, c->ny);
+    int tx, ty;
+    lookup(c, t, wx, wy, &tx, &ty);
+    double tX[3], uX[3], tY[3], uY[3], tp[3], up[3];
+    if (!edge_stencil(t, dir, tx, ty, tX, uX, tY, uY, tp, up)) return 0;
+    double phs = 0.5 * (ap[1] + bp[1]), pht = 0.5 * (tp[1] + up[1]);
+    double fm = fmin(contact_f(phs, c->eps), contact_f(pht, c->eps));
+    if (!(fm > 0.0)) return 0;
+    double pa[3], pb[3];
+    for (int q = 0; q < 3; q++) { pa[q] = ap[q] - tp[q]; pb[q] = bp[q] - up[q]; }
+    double gn, gt;
+    edge_grad(pa, pb, &gn, &gt);
+    double gxx = dir == 0 ? gn : gt, gyy = dir == 0 ? gt : gn;
+    double nrm = sqrt(gxx * gxx + gyy * gyy);
+    if (nrm == 0.0) return 0;
+    contact_stress(fm, s->G, t->G, c->eta, gxx / nrm, gyy / nrm, tau);
+    return 1;
+}
+
 static void compute_force(osim_t *m) {
     const ocfg_t *c = &m->c;
     int nx = c->nx, ny = c->ny;
@@ -681,26 +710,8 @@ static void compute_force(osim_t *m) {
                         int gx = s->x0 + x, gy = s->y0 + y;
                         long e = edge_index(c, dir, gx, gy);
                         if (e < 0) continue;
-                        double aX[3], bX[3], aY[3], bY[3], ap[3], bp[3];
-                        if (!edge_stencil(s, dir, gx, gy, aX, bX, aY, bY, ap, bp)) continue;
-                        int wx = c->wall_x ? gx : wrapi(gx, nx);
-                        int wy = c->wall_y ? gy : wrapi(gy, ny);
-                        int tx, ty;
-                        lookup(c, t, wx, wy, &tx, &ty);
-                        double tX[3], uX[3], tY[3], uY[3], tp[3], up[3];
-                        if (!edge_stencil(t, dir, tx, ty, tX, uX, tY, uY, tp, up)) continue;
-                        double phs = 0.5 * (ap[1] + bp[1]), pht = 0.5 * (tp[1] + up[1]);
-                        double fm = fmin(contact_f(phs, c->eps), contact_f(pht, c->eps));
-                        if (!(fm > 0.0)) continue;
-                        double pa[3], pb[3];
-                        for (int q = 0; q < 3; q++) { pa[q] = ap[q] - tp[q]; pb[q] = bp[q] - up[q]; }
-                        double gn, gt;
-                        edge_grad(pa, pb, &gn, &gt);
-                        double gxx = dir == 0 ? gn : gt, gyy = dir == 0 ? gt : gn;
-                        double nrm = sqrt(gxx * gxx + gyy * gyy);
-                        if (nrm == 0.0) continue;
                         double tau[3];
-                        contact_stress(fm, s->G, t->G, c->eta, gxx / nrm, gyy / nrm, tau);
+                        if (!pair_edge_stress(m, s, t, dir, gx, gy, tau)) continue;
                         double *E = (dir == 0 ? m->ex : m->ey) + EV * e;
                         E[4] += tau[0]; E[5] += tau[1]; E[6] += tau[2];
                     }
@@ -1011,6 +1022,43 @@ int oracle_read_field(void *h, int field, int solid, double *out) {
  * nodes; out[0..7] = sum lambda, centroid x, centroid y (unwrapped frame),
  * sum lambda rho, sum lambda rho u, sum lambda rho v, and over the solid nodes
  * (phi < 0) the maximum and the lambda-weighted mean of |det F - 1|. */
+/* Net contact force on solid s (a reading: the paper defines the contact
+ * stress, Sec. 3.6, but no per-solid force): for every other solid t, the
+ * divergence (Eq. 3_3_div_solid_stress) of the pair's contact stress at each
+ * domain node, counted for s where the node is nearer to s than to t
+ * (phi_s < phi_t; half each where equal; a node outside t's band is nearer to
+ * s).  Summed over the pairs.  The divergence of one pair's stress sums to
+ * zero over a periodic box, so the forces on s and t from their contact are
+ * equal and opposite. */
+static void oracle_contact_force(const osim_t *m, int solid, double *out) {
+    const ocfg_t *c = &m->c;
+    const osolid_t *s = &m->s[solid];
+    out[0] = out[1] = 0.0;
+    for (int ti = 0; ti < m->ns; ti++) {
+        if (ti == solid) continue;
+        const osolid_t *t = &m->s[ti];
+        if (!windows_meet(c, s, t)) continue;
+        for (int y = 0; y < s->h; y++)
+            for (int x = 0; x < s->w; x++) {
+                int k = y * s->w + x, gx = s->x0 + x, gy = s->y0 + y;
+                if (s->lab[k] < 0 || !in_domain(c, gx, gy)) continue;
+                int tx, ty;
+                int kt = lookup(c, t, c->wall_x ? gx : wrapi(gx, c->nx), c->wall_y ? gy : wrapi(gy, c->ny), &tx, &ty);
+                double pt = (kt >= 0 && t->lab[kt] >= 0) ? t->phi[kt] : INFINITY;
+                double w = s->phi[k] < pt ? 1.0 : (s->phi[k] == pt ? 0.5 : 0.0);
+                if (w == 0.0) continue;
+                double tl[3] = {0, 0, 0}, tr[3] = {0, 0, 0}, tb[3] = {0, 0, 0}, tt[3] = {0, 0, 0};
+                int any = pair_edge_stress(m, s, t, 0, gx, gy, tl);
+                any |= pair_edge_stress(m, s, t, 0, gx + 1, gy, tr);
+                any |= pair_edge_stress(m, s, t, 1, gx, gy, tb);
+                any |= pair_edge_stress(m, s, t, 1, gx, gy + 1, tt);
+                if (!any) continue;
+                out[0] += w * ((tr[0] - tl[0]) + (tt[1] - tb[1]));
+                out[1] += w * ((tr[1] - tl[1]) + (tt[2] - tb[2]));
+            }
+    }
+}
+
 int oracle_solid_stats(void *h, int solid, double *out) {
     osim_t *m = h;
     const ocfg_t *c = &m->c;
@@ -1039,6 +1087,7 @@ int oracle_solid_stats(void *h, int solid, double *out) {
         }
     out[0] = L; out[1] = Lx / L; out[2] = Ly / L; out[3] = Lr; out[4] = Lu; out[5] = Lv;
     out[6] = Dmax; out[7] = Dw > 0 ? Dsum / Dw : 0.0;
+    oracle_contact_force(m, solid, out + 8);
     return 0;
 }
 

@@ -47,6 +47,10 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
+# columns of lbrmt_solid_stats: area, centroid x, y, mass, momentum x, y, max and mean |det F - 1|, contact force x, y
+STATS_COLS = 10
+
+
 class lbrmt_config(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("bc_x", C.c_int), ("bc_y", C.c_int),
                 ("tau", C.c_double), ("rho_f", C.c_double), ("lid_u", C.c_double),
@@ -582,8 +586,8 @@ class Simulation:
             lbrmt_set_populations_host(self.h, f.ctypes.data)
 
     def solid_stats(self):
-        """Per-solid FP64 statistics of the current state, (S, 8) (lbrmt_solid_stats)."""
-        out = np.zeros((max(self.nsolids, 1), 8))
+        """Per-solid FP64 statistics of the current state, (S, 10) (lbrmt_solid_stats)."""
+        out = np.zeros((max(self.nsolids, 1), STATS_COLS))
         with self.torch.cuda.device(self.device):
             lbrmt_solid_stats(self.h, 0, out.ctypes.data)
         return out[: self.nsolids]

@@ -127,13 +127,13 @@ extern "C" lbrmt_status lbrmt_forward_checkpointed(lbrmt_sim *s, int nsteps, int
     cudaError_t e = save_state(s, A, A.cps[ncp]);
     if (e != cudaSuccess) return lbrmt_internal_fail(s, LBRMT_ERR_CUDA, "checkpoint");
     const int S = (int)s->solids.size();
-    std::vector<double> stt((size_t)std::max(S, 1) * 8);
+    std::vector<double> stt((size_t)std::max(S, 1) * STATS_COLS);
     st = lbrmt_solid_stats(s, 0, stt.data());
     if (st != LBRMT_OK) return st;
     if (centroids_out)
         for (int k = 0; k < S; k++) {
-            centroids_out[2 * k] = stt[8 * k + 1];
-            centroids_out[2 * k + 1] = stt[8 * k + 2];
+            centroids_out[2 * k] = stt[STATS_COLS * k + 1];
+            centroids_out[2 * k + 1] = stt[STATS_COLS * k + 2];
         }
     A.valid = true;
     return LBRMT_OK;
@@ -255,7 +255,7 @@ static lbrmt_status backward_impl(lbrmt_sim *s, const double *dLdc, double *dLdG
         copy_registry(0, (n0 & 1) ^ 1);
         for (int n = n0; n < n1 && e == cudaSuccess; n++) {
             const int m = n - n0;
-            ok(s->eng->step(sp, d, s->li, n & 1, st, nullptr, tape + (size_t)m * 5 * P));
+            ok(s->eng->step(sp, d, s->li, n & 1, st, nullptr, tape + (size_t)m * 5 * P, CHAIN_ONE));
             s->steps++;
             ok(cudaMemcpyAsync(xi_slot(m + 1), d.xi[(n + 1) & 1], xib_bytes, cudaMemcpyDeviceToDevice, st));
             if (S > 0) ok(cudaMemcpyAsync(fr_slot(m + 1), d.frame[(n + 1) & 1], S * sizeof(Frame), cudaMemcpyDeviceToDevice, st));

@@ -32,10 +32,19 @@ __global__ void mass_reduce_kernel(const double *partials, int n, double base, d
 }
 }  // namespace lbrmt
 
+static void drop_graphs(lbrmt_sim *s) {
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->gexec_long) cudaGraphExecDestroy(s->gexec_long);
+    s->gexec = s->gexec_long = nullptr;
+}
+
 static void release_streams(lbrmt_sim *s) {
     if (s->li.fork) cudaEventDestroy(s->li.fork);
     if (s->li.join) cudaEventDestroy(s->li.join);
     if (s->li.flags) cudaEventDestroy(s->li.flags);
+    for (auto &e : s->li.done)
+        if (e) cudaEventDestroy(e);
+    s->li.done[0] = s->li.done[1] = nullptr;
     if (s->li.side) cudaStreamDestroy(s->li.side);
     s->li.fork = s->li.join = s->li.flags = nullptr;
     s->li.side = nullptr;
@@ -120,6 +129,13 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     sp.omega = 1.0 / c.tau; sp.kf = 1.0 - 0.5 / c.tau; sp.fy = c.force_kind == LBRMT_FORCE_CONST ? c.force_a[1] : 0.0;
     sp.omega_f = (float)sp.omega; sp.kf_f = (float)sp.kf; sp.rho_f_f = (float)c.rho_f; sp.lid_u_f = (float)c.lid_u;
     sp.eps_f = (float)c.eps; sp.eta_f = (float)c.eta; sp.fy_f = (float)sp.fy;
+    {  // solid-fraction table grid: the largest power-of-two step with at most LAM_TAB_MAX entries
+        int m = 0;
+        while (2 * (int)std::ceil(c.eps * std::ldexp(1.0, m + 1)) + 1 <= LAM_TAB_MAX) m++;
+        sp.lam_h = (float)std::ldexp(1.0, -m);
+        sp.lam_inv_h = (float)std::ldexp(1.0, m);
+        sp.lam_k0 = (int)std::ceil(c.eps * std::ldexp(1.0, m));
+    }
 
     // registry and pool sized for the largest tile count over the tile shapes, so
     // the shape can change later (lbrmt_set_tile_x) without reallocation
@@ -153,7 +169,8 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     if (c.force_kind == LBRMT_FORCE_FIELD) ok = ok && (d.bfield = dalloc(s, 2 * P * rs));
     ok = ok && (d.mass_partials = (double *)dalloc(s, nparts * 8));
     ok = ok && (d.err = (unsigned *)dalloc(s, 16));
-    ok = ok && (s->scratch = (double *)dalloc(s, 64));
+    ok = ok && (d.lamtab = (LamEntry *)dalloc(s, (size_t)(2 * sp.lam_k0 + 1) * sizeof(LamEntry)));
+    ok = ok && (s->scratch = (double *)dalloc(s, 128));  // one solid's statistics or the total mass
     // side stream (lowest priority) and fork / join events of the overlapped step
     if (ok) {
         int least = 0, greatest = 0;
@@ -161,7 +178,9 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
              cudaStreamCreateWithPriority(&s->li.side, cudaStreamNonBlocking, least) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->li.fork, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->li.join, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&s->li.flags, cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreateWithFlags(&s->li.flags, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->li.done[0], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->li.done[1], cudaEventDisableTiming) == cudaSuccess;
         s->li.prio_hi = greatest;
     }
     if (!ok) {
@@ -185,6 +204,32 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
     for (int j = 0; j < c.ny; j++) {
         if (c.force_kind == LBRMT_FORCE_CONST) fb[j] = c.force_a[0];
         else if (c.force_kind == LBRMT_FORCE_SINE_X) fb[j] = c.force_a[0] * std::sin(2.0 * M_PI * j / c.ny);
+    }
+    // solid-fraction table lambda = 1 - H_eps (Eq. 2_3_heaviside) with its Taylor
+    // coefficients on phi_k = (k - k0) h, from the formula in double
+    if (e == cudaSuccess) {
+        const int n = 2 * sp.lam_k0 + 1;
+        std::vector<LamEntry> tab(n);
+        const double eps = c.eps, pi = M_PI;
+        for (int k = 0; k < n; k++) {
+            const double t = (double)(k - sp.lam_k0) * (double)sp.lam_h / eps;
+            const double sn = std::sin(pi * t), cs = std::cos(pi * t);
+            // lambda = 1 - (1 + t + sin(pi t)/pi)/2; for k >= 2 its k-th derivative in phi is
+            // -(pi^(k-1) / (2 eps^k)) sin^(k-1)(pi t), with sin^(m) the m-th derivative of sin
+            const double lam = 1.0 - 0.5 * (1.0 + t + sn / pi);
+            const double l1 = -0.5 * (1.0 + cs) / eps;
+            const double dsin[6] = {sn, cs, -sn, -cs, sn, cs};  // the m-th derivative of sin at pi t
+            double lk[6] = {lam, l1, 0, 0, 0, 0}, fact = 1.0;
+            for (int m = 2; m <= 5; m++) {
+                fact *= m;
+                lk[m] = -std::pow(pi, m - 1) / (2.0 * std::pow(eps, m)) * dsin[m] / fact;
+            }
+            LamEntry &q = tab[k];
+            q.l0h = (float)lam; q.l0l = (float)(lam - (double)q.l0h);
+            q.l1h = (float)l1; q.l1l = (float)(l1 - (double)q.l1h);
+            q.l2 = (float)lk[2]; q.l3 = (float)lk[3]; q.l4 = (float)lk[4]; q.l5 = (float)lk[5];
+        }
+        e = cudaMemcpy(d.lamtab, tab.data(), n * sizeof(LamEntry), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) {
         if (rs == 4) {
@@ -260,9 +305,59 @@ lbrmt_status lbrmt_internal_fail(lbrmt_sim *s, lbrmt_status st, const std::strin
 
 // Solid descriptors and initial frames from the host solids; configure and run
 // the initialisation kernels (Algorithm 1, initialisation) on the allocated state.
+// Power-of-two storage scales of the 16-bit variants, per population plane and
+// for the half-force carry, from bounds of the stored values: with the
+// velocity bounded by U = 0.3 (above the Mach limit of Appendix A), the density
+// difference D = max |rho_s - rho_f|, a pressure deviation of 0.1 rho_f and
+// rho_max = rho_f + D + 0.1 rho_f, a stored deviation of plane q is below
+// w_q (0.1 rho_f + D + rho_max (3 sqrt2 U + 10.5 U^2)) (q >= 1), w_0 (0.1 rho_f + D
+// + 1.5 rho_max U^2) (the rest plane, relative to Delta rho), and the carry
+// rho F / 2 below rho_max (|f| + g + 2 G_max + 1e-3) / 2.  Each bound is mapped
+// below 2^15 (FP16's largest value is 65504).  FP32 / FP64 storage: scale 1.
+static void set_store_scales(lbrmt_sim *s) {
+    SimParams &sp = s->sp;
+    for (int q = 0; q < 9; q++) sp.st_scale[q] = sp.st_inv[q] = 1.0f;
+    sp.ct_scale = sp.ct_inv = 1.0f;
+    if (s->eng->store_size != 2) return;
+    const lbrmt_config &c = s->cfg;
+    double D = 0.0, Gm = 0.0;
+    for (const SolidHost &h : s->solids) {
+        D = std::max(D, std::fabs(h.rho_s - c.rho_f));
+        Gm = std::max(Gm, h.G);
+    }
+    const double U = 0.3, rmax = c.rho_f * 1.1 + D;
+    auto scale_for = [](double bound) {
+        int k = (int)std::floor(std::log2(32768.0 / bound));
+        k = std::max(0, std::min(k, 24));
+        return (float)std::ldexp(1.0, k);
+    };
+    for (int q = 0; q < 9; q++) {
+        const double w = q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        const double b = q == 0 ? w * (0.1 * c.rho_f + D + 1.5 * rmax * U * U)
+                                : w * (0.1 * c.rho_f + D + rmax * (3.0 * std::sqrt(2.0) * U + 10.5 * U * U));
+        sp.st_scale[q] = scale_for(b);
+        sp.st_inv[q] = 1.0f / sp.st_scale[q];
+    }
+    const double F = std::fabs(c.force_a[0]) + std::fabs(c.force_a[1]) + c.gravity + 2.0 * Gm + 1e-3;
+    sp.ct_scale = scale_for(0.5 * rmax * F);
+    sp.ct_inv = 1.0f / sp.ct_scale;
+}
+
+// After the solids' materials changed (a checkpoint's adopted): new scales, and
+// the captured graphs (whose launch arguments carry them) are dropped.
+void lbrmt_internal_refresh_scales(lbrmt_sim *s) {
+    const SimParams old = s->sp;
+    set_store_scales(s);
+    if (std::memcmp(old.st_scale, s->sp.st_scale, sizeof(old.st_scale)) != 0 || old.ct_scale != s->sp.ct_scale) {
+        if (s->stream) cudaStreamSynchronize(s->stream);
+        drop_graphs(s);
+    }
+}
+
 static lbrmt_status run_init(lbrmt_sim *s) {
     const int S = (int)s->solids.size();
     DevState &d = s->d;
+    set_store_scales(s);
     int tmax = 8;
     for (auto &h : s->solids) tmax = std::max(tmax, h.T);
     std::vector<SolidDesc> sd(S);
@@ -280,7 +375,7 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         sd[k].drho = h.rho_s - s->cfg.rho_f;
         sd[k].accel = -(1.0 - s->cfg.rho_f / h.rho_s) * s->cfg.gravity;
         const double r2 = h.R * h.R;
-        sd[k].R_f = (float)h.R; sd[k].G_f = (float)h.G;
+        sd[k].R_f = (float)h.R; sd[k].G_f = (float)h.G; sd[k].Rlo_f = (float)(h.R - (double)sd[k].R_f);
         sd[k].r2hi_f = (float)r2; sd[k].r2lo_f = (float)(r2 - (double)sd[k].r2hi_f); sd[k].r2lo = 0.0;
         sd[k].drho_f = (float)sd[k].drho; sd[k].accel_f = (float)sd[k].accel;
         sd[k].T = h.T; sd[k].off = h.off;
@@ -349,8 +444,8 @@ extern "C" lbrmt_status lbrmt_init(lbrmt_sim *s) {
     ok = ok && (d.solids = (SolidDesc *)dalloc(s, (size_t)S * sizeof(SolidDesc)));
     ok = ok && (d.order = (int *)dalloc(s, (size_t)std::max(S, 1) * sizeof(int)));
     ok = ok && (d.stats_step = (double *)dalloc(s, (size_t)S * 64));
-    if (S > 1) {
-        double *sc = (double *)dalloc(s, (size_t)S * 64);
+    if ((size_t)S * STATS_COLS * 8 > 128) {
+        double *sc = (double *)dalloc(s, (size_t)S * STATS_COLS * 8);
         ok = ok && sc;
         s->scratch = sc;
     }
@@ -362,10 +457,7 @@ extern "C" lbrmt_status lbrmt_reset(lbrmt_sim *s) {
     if (!s) return LBRMT_ERR_ARG;
     if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
     if (!s->inited) return lbrmt_init(s);
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    drop_graphs(s);
     return run_init(s);
 }
 
@@ -381,10 +473,7 @@ extern "C" lbrmt_status lbrmt_set_tile_x(lbrmt_sim *s, int tile_x) {
     if (tile_x != 16 && tile_x != 32 && tile_x != 64 && tile_x != 128) return fail(s, LBRMT_ERR_ARG, "tile_x must be 16, 32, 64 or 128");
     if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member's tile shape is set by its batch");
     if (s->stream) cudaStreamSynchronize(s->stream);
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    drop_graphs(s);
     if (s->adj) lbrmt_internal_adjoint_free(s);  // its recording buffers are sized by the tile count
     set_tile_shape(s, tile_x);
     if (!s->inited) return LBRMT_OK;
@@ -465,31 +554,36 @@ extern "C" lbrmt_status lbrmt_set_body_force_field(lbrmt_sim *s, int sim_index, 
 }
 
 static lbrmt_status direct_step(lbrmt_sim *s) {
-    cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, nullptr, nullptr);
+    cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, nullptr, nullptr, CHAIN_ONE);
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->steps++;
     s->last_launches += step_launches(s->sp, s->li);
     return LBRMT_OK;
 }
 
-static lbrmt_status build_graph(lbrmt_sim *s) {
+// Capture nsteps (even) steps from an even step count as one graph; the steps
+// form one chain of the overlapped schedule.
+static lbrmt_status build_graph(lbrmt_sim *s, int nsteps, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
-    cudaError_t e0 = s->eng->step(s->sp, s->d, s->li, 0, s->stream, nullptr, nullptr);
-    cudaError_t e1 = s->eng->step(s->sp, s->d, s->li, 1, s->stream, nullptr, nullptr);
+    cudaError_t es = cudaSuccess;
+    for (int k = 0; k < nsteps; k++) {
+        const int chain = (k == 0 ? CHAIN_FIRST : 0) | (k == nsteps - 1 ? CHAIN_LAST : 0);
+        cudaError_t ek = s->eng->step(s->sp, s->d, s->li, k & 1, s->stream, nullptr, nullptr, chain);
+        if (ek != cudaSuccess && es == cudaSuccess) es = ek;
+    }
     e = cudaStreamEndCapture(s->stream, &g);
-    if (e0 != cudaSuccess) e = e0;
-    if (e1 != cudaSuccess) e = e1;
+    if (es != cudaSuccess) e = es;
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return cuda_fail(s, e, "capture");
     }
     // per-node priorities: the overlapped step runs K2, K3 and the busy K1 ahead of the free K1
-    e = cudaGraphInstantiate(&s->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
+    e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        s->gexec = nullptr;
+        *out = nullptr;
         return cuda_fail(s, e, "instantiate graph");
     }
     return LBRMT_OK;
@@ -511,8 +605,19 @@ extern "C" lbrmt_status lbrmt_step(lbrmt_sim *s, int nsteps) {
             if (st != LBRMT_OK) return st;
             left--;
         }
+        if (left >= GRAPH_LONG && !s->gexec_long) {
+            lbrmt_status st = build_graph(s, GRAPH_LONG, &s->gexec_long);
+            if (st != LBRMT_OK) return st;
+        }
+        while (left >= GRAPH_LONG) {
+            cudaError_t e = cudaGraphLaunch(s->gexec_long, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
+            s->steps += GRAPH_LONG;
+            s->last_launches += GRAPH_LONG * step_launches(s->sp, s->li);
+            left -= GRAPH_LONG;
+        }
         if (left >= 2 && !s->gexec) {
-            lbrmt_status st = build_graph(s);
+            lbrmt_status st = build_graph(s, 2, &s->gexec);
             if (st != LBRMT_OK) return st;
         }
         while (left >= 2) {
@@ -544,7 +649,8 @@ extern "C" lbrmt_status lbrmt_step_timed(lbrmt_sim *s, int nsteps, float *ms_out
     s->last_launches = 0;
     lbrmt_status status = LBRMT_OK;
     for (int n = 0; n < nsteps; n++) {
-        cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, &ev[4 * (size_t)n], nullptr);
+        cudaError_t e = s->eng->step(s->sp, s->d, s->li, (int)(s->steps & 1), s->stream, &ev[4 * (size_t)n], nullptr,
+                                     CHAIN_ONE);
         if (e != cudaSuccess) { status = cuda_fail(s, e, "timed step"); break; }
         s->steps++;
         s->last_launches += step_launches(s->sp, s->li, true);
@@ -652,7 +758,7 @@ extern "C" lbrmt_status lbrmt_solid_stats(lbrmt_sim *s, int sim_index, double *h
     if (S == 0) return LBRMT_OK;
     cudaError_t e = s->eng->stats(s->sp, s->d, (int)(s->steps & 1), s->scratch, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "stats kernel");
-    e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * 64, cudaMemcpyDeviceToHost, s->stream);
+    e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * STATS_COLS * 8, cudaMemcpyDeviceToHost, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "copy stats");
     return check_flags(s);
 }
@@ -669,7 +775,7 @@ extern "C" lbrmt_status lbrmt_solid_stats_async(lbrmt_sim *s, int sim_index, dou
     }
     cudaError_t e = s->eng->stats(s->sp, s->d, (int)(s->steps & 1), s->scratch, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "stats kernel");
-    e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * 64, cudaMemcpyDeviceToHost, s->stream);
+    e = cudaMemcpyAsync(host_out, s->scratch, (size_t)S * STATS_COLS * 8, cudaMemcpyDeviceToHost, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "copy stats");
     return LBRMT_OK;
 }
@@ -721,10 +827,9 @@ extern "C" lbrmt_status lbrmt_set_use_graphs(lbrmt_sim *s, int enable) {
 extern "C" lbrmt_status lbrmt_set_use_tma(lbrmt_sim *s, int enable) {
     if (!s) return LBRMT_ERR_ARG;
     s->li.use_tma = enable != 0;
-    if (s->gexec) {
+    if (s->gexec || s->gexec_long) {
         cudaStreamSynchronize(s->stream);
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
+        drop_graphs(s);
     }
     return LBRMT_OK;
 }
@@ -738,10 +843,7 @@ extern "C" lbrmt_status lbrmt_set_overlap(lbrmt_sim *s, int enable) {
     if (s->in_batch) return fail(s, LBRMT_ERR_STATE, "a batch member is stepped by its batch");
     if (s->stream) cudaStreamSynchronize(s->stream);
     s->li.split = enable != 0;
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    drop_graphs(s);
     return LBRMT_OK;
 }
 
@@ -760,10 +862,7 @@ extern "C" lbrmt_status lbrmt_set_rmt_threads(lbrmt_sim *s, int threads) {
         s->li.use_tma = use_tma;
         if (e != cudaSuccess) return cuda_fail(s, e, "configure kernels");
     }
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    drop_graphs(s);
     return LBRMT_OK;
 }
 
@@ -788,7 +887,7 @@ extern "C" void lbrmt_destroy(lbrmt_sim *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     if (s->li.side) cudaStreamSynchronize(s->li.side);
-    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    drop_graphs(s);
     release_streams(s);
     if (s->adj) lbrmt_internal_adjoint_free(s);
     dfree_all(s);

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(RMT_THREADS, sizeof(R) == 4 ? RMT_MIN_BLOCKS :
 // just written; each CTA forms their prefix sums and walks the list with a
 // grid stride.
 template <class R, class S>
-__global__ void __launch_bounds__(K3_THREADS) force_batch_kernel(const BatchSimDesc<R, S> *sims, int nsim, int parity) {
+__global__ void __launch_bounds__(K3_THREADS, sizeof(R) == 4 ? 4 : 1) force_batch_kernel(const BatchSimDesc<R, S> *sims, int nsim, int parity) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ForceShared<R> fs;
     __shared__ int pre[BATCH_MAX + 1];

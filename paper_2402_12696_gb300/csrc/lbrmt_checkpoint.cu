@@ -198,6 +198,8 @@ extern "C" lbrmt_status lbrmt_load(lbrmt_sim *s, const void *dev_blob, size_t by
     if (!s->inited) {
         lbrmt_status st = lbrmt_init(s);
         if (st != LBRMT_OK) return st;
+    } else {
+        lbrmt_internal_refresh_scales(s);  // 16-bit storage scales follow the materials
     }
     Section sec[CK_MAX_SECTIONS];
     const int nsec = sections(s, sec);

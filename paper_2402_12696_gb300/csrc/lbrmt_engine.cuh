@@ -29,6 +29,7 @@ struct LaunchInfo {
     bool split = true;
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, flags = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr};  // free-region K1 of the step of each parity has finished
     int prio_hi = 0;
 };
 
@@ -40,8 +41,12 @@ inline bool step_overlaps(const SimParams &sp, const LaunchInfo &li) {
 // Kernel launches of one step (timed: the sequential schedule of lbrmt_step_timed).
 inline int step_launches(const SimParams &sp, const LaunchInfo &li, bool timed = false) {
     if (sp.nsolids == 0) return 1;
-    return step_overlaps(sp, li) && !timed ? 5 : 4;  // classification, K2, K3, K1 (busy and free regions)
+    return step_overlaps(sp, li) && !timed ? 5 : 3;  // K2, classification, K3, K1 (busy and free regions)
 }
+
+// Steps of a chain: within one, the free-region K1 of a step runs beside the
+// solid kernels of the next; the chain's last step joins it.
+enum { CHAIN_FIRST = 1, CHAIN_LAST = 2, CHAIN_ONE = 3 };
 
 // Launch with a scheduling priority (a launch attribute, kept by stream capture).
 template <class... P, class... A>
@@ -109,7 +114,7 @@ struct EngineOps {
     cudaError_t (*init)(const SimParams &, const DevState &, const LaunchInfo &, cudaStream_t);
     // tape (optional): per-node rho, ux, uy, Fx, Fy of the step (5 planes of reals)
     cudaError_t (*step)(const SimParams &, const DevState &, const LaunchInfo &, int parity, cudaStream_t,
-                        cudaEvent_t *ev, void *tape);
+                        cudaEvent_t *ev, void *tape, int chain);
     cudaError_t (*field)(const SimParams &, const DevState &, int cur, int lastreg, int kind, int solid,
                          double *out, cudaStream_t);
     cudaError_t (*stats)(const SimParams &, const DevState &, int cur, double *out, cudaStream_t);
@@ -133,15 +138,21 @@ extern const EngineOps engine_fp16;
 extern const EngineOps engine_bf16;
 
 template <class R, class S>
-__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, const int *reg, const R *pool) {
+__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, const int *reg, const R *pool,
+                               unsigned *err) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sp.P) return;
     const int i = (int)(c % sp.nx), j = (int)(c / sp.nx);
     const double base = rest_base_d<R>(sp, reg, pool, i, j);
-    for (int q = 0; q < 9; q++)
-        stS<S, R>(f + q * sp.P + c, R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f - (q == 0 ? base : 0.0)));
-    stC<S, R>(carry + c, R(0));
-    stC<S, R>(carry + sp.P + c, R(0));
+    bool ov = false;
+    for (int q = 0; q < 9; q++) {
+        const R v = R(src[q * sp.P + c] - (double)wq<double>(q) * sp.rho_f - (q == 0 ? base : 0.0));
+        ov = ov || store_overflow<S, R>(v, sp, q);
+        stS<S, R>(f + q * sp.P + c, v, sp, q);
+    }
+    if (ov) atomicOr(err, ERR_OVERFLOW16);
+    stC<S, R>(carry + c, R(0), sp);
+    stC<S, R>(carry + sp.P + c, R(0), sp);
 }
 
 template <class R, class S>
@@ -258,6 +269,7 @@ struct Engine {
         a.reg_nactive = d.reg_nactive[r];
         a.pool = (R *)d.pool[r];
         a.solids = d.solids;
+        a.lamtab = d.lamtab;
         a.err = d.err;
         return a;
     }
@@ -377,8 +389,16 @@ struct Engine {
     // ev (optional): four events recorded before K2, before K3, before K1 and after
     // K1; the step then takes the sequential schedule (one K1 over every region,
     // on st after K3), so each kernel is timed alone.
+    // Overlapped schedule of step n (chain: CHAIN_FIRST / CHAIN_LAST bits):
+    //   st:   K2(n), classification(n), K3(n), [wait free K1(n-1)], K1 busy(n)
+    //   side: [wait classification(n)] K1 free(n)
+    // The free K1 of step n reads f^n and writes f^{n+1} outside the solids'
+    // reach, so it runs beside K3(n), the busy K1(n) and the solid kernels of step
+    // n + 1; the busy K1 of step n + 1 waits for it (pushes cross into busy
+    // regions, and it overwrites f^n).  The first step of a chain has no free K1
+    // before it in flight; the last joins its own.
     static cudaError_t step(const SimParams &sp, const DevState &d, const LaunchInfo &li, int parity,
-                            cudaStream_t st, cudaEvent_t *ev, void *tape) {
+                            cudaStream_t st, cudaEvent_t *ev, void *tape, int chain) {
         const int p = parity, q = 1 - parity;
         const bool overlap = step_overlaps(sp, li) && !ev;
         const int prio = overlap ? li.prio_hi : 0;
@@ -386,18 +406,16 @@ struct Engine {
         LbArgs<R, S> la = lb_args(sp, d, p);
         la.tape = static_cast<R *>(tape);
         const int nreg = sp.nrx * sp.nty;
-        if (overlap) {  // fork: classification and K1 of the free regions on the side stream
-            cudaEventRecord(li.fork, st);
-            cudaStreamWaitEvent(li.side, li.fork, 0);
-            lb_busy_kernel<<<(nreg + 255) / 256, 256, 0, li.side>>>(sp, d.reg_count[q], d.busy[q], d.busy[p], d.err);
-            cudaEventRecord(li.flags, li.side);
-            lb_step_kernel<R, S, 2><<<grid, blk, 0, li.side>>>(sp, la, d.busy[p]);
-            cudaEventRecord(li.join, li.side);
-        } else if (sp.nsolids > 0) {
-            lb_busy_kernel<<<(nreg + 255) / 256, 256, 0, st>>>(sp, d.reg_count[q], d.busy[q], d.busy[p], d.err);
-        }
         if (ev) cudaEventRecord(ev[0], st);
         if (sp.nsolids > 0) launch_rmt(sp, li, rmt_args(d, p, 0), st, prio);
+        if (overlap) {  // exact classification, then the free regions' K1 on the side stream
+            lb_classify_kernel<<<(nreg + 255) / 256, 256, 0, st>>>(sp, d.reg_count[p], d.reg_count[q], d.busy[p],
+                                                                   d.reg_nactive[q]);
+            cudaEventRecord(li.flags, st);
+            cudaStreamWaitEvent(li.side, li.flags, 0);
+            lb_step_kernel<R, S, 2><<<grid, blk, 0, li.side>>>(sp, la, d.busy[p]);
+            cudaEventRecord(li.done[p], li.side);
+        }
         if (ev) cudaEventRecord(ev[1], st);
         if (sp.nsolids > 0)
             launch_prio(force_kernel<R>, dim3(li.force_blocks), dim3(TILE_N), li.force_smem, st, prio, sp,
@@ -406,12 +424,12 @@ struct Engine {
         if (li.tma && li.use_tma)
             lb_tma_kernel<R, S><<<li.lb_blocks, TILE_N, li.lb_smem, st>>>(sp, la, li.tm_f[p], li.tm_c, sp.ntx * sp.nty);
         else if (overlap) {
-            cudaStreamWaitEvent(st, li.flags, 0);  // the classification is done
+            if (!(chain & CHAIN_FIRST)) cudaStreamWaitEvent(st, li.done[q], 0);  // free K1 of step n - 1
             launch_prio(lb_step_kernel<R, S, 1>, grid, blk, 0, st, prio, sp, la, (const unsigned char *)d.busy[p]);
         } else
             lb_step_kernel<R, S, 0><<<grid, blk, 0, st>>>(sp, la, nullptr);
         if (ev) cudaEventRecord(ev[3], st);
-        if (overlap) cudaStreamWaitEvent(st, li.join, 0);  // join
+        if (overlap && (chain & CHAIN_LAST)) cudaStreamWaitEvent(st, li.done[p], 0);  // join
         return cudaGetLastError();
     }
 
@@ -433,8 +451,9 @@ struct Engine {
     static cudaError_t stats(const SimParams &sp, const DevState &d, int cur, double *out, cudaStream_t st) {
         if (sp.nsolids == 0) return cudaSuccess;
         solid_stats_kernel<R, S><<<sp.nsolids, STATS_THREADS, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry,
-                                                             d.reg_count[1 - cur], (const R *)d.pool[1 - cur],
-                                                             (const R *)d.xi[cur], d.frame[cur], d.solids, out);
+                                                             d.reg_count[1 - cur], d.reg_solids[1 - cur],
+                                                             (const R *)d.pool[1 - cur], (const R *)d.xi[cur],
+                                                             d.frame[cur], d.solids, out);
         return cudaGetLastError();
     }
 
@@ -447,7 +466,7 @@ struct Engine {
     static cudaError_t set_pop(const SimParams &sp, const DevState &d, int cur, const double *src, cudaStream_t st) {
         const int nb = (int)((sp.P + 255) / 256);
         set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (S *)d.carry, d.reg_count[1 - cur],
-                                                 (const R *)d.pool[1 - cur]);
+                                                 (const R *)d.pool[1 - cur], d.err);
         return cudaGetLastError();
     }
 

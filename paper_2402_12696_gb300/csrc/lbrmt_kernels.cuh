@@ -24,6 +24,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbrmt {
 
 // Registry tiles are tile_x x tile_y nodes with tile_x * tile_y = TILE_N, one
@@ -48,8 +50,10 @@ constexpr int POOL_FX = 0, POOL_FY = TILE_N, POOL_DRHO = 2 * TILE_N, POOL_DRHO_L
 // Planes of a solid's tile: eta_x, eta_y and phi; FP32 adds the low parts of
 // eta_x and eta_y on the advected nodes (eta = hi + lo), so the rounding of
 // the stored reference map does not accumulate over the steps (zero on the
-// extrapolated band, which is refitted every step from the advected nodes).
-template <class R> __host__ __device__ constexpr int xi_planes() { return sizeof(R) == 4 ? 5 : 3; }
+// extrapolated band, which is refitted every step from the advected nodes),
+// and the low part of phi in and near the blur zone (phi = hi + lo to ~1e-13,
+// for the density difference of Eq. 2_3_drho; zero elsewhere).
+template <class R> __host__ __device__ constexpr int xi_planes() { return sizeof(R) == 4 ? 6 : 3; }
 // Tie rules shared with the method's definition: a node with |phi| <= PHI_TIE
 // is not solid; a directional extrapolation weight with cosine <= COS_TIE is zero.
 constexpr double PHI_TIE = 1e-9;
@@ -76,7 +80,23 @@ struct SimParams {
     // FP32 copies (GB300's FP64 pipe is narrow: no per-thread conversions)
     float omega_f, kf_f, rho_f_f, lid_u_f, eps_f, eta_f, fy_f;
     double omega, kf, fy;  // 1/tau, 1 - 1/(2 tau), constant y body force
+    // grid of the solid-fraction table (LamEntry): phi_k = (k - lam_k0) lam_h, lam_h a power of two
+    float lam_h, lam_inv_h;
+    int lam_k0;
+    // 16-bit storage: power-of-two scale (and inverse) per population plane and of the carry
+    float st_scale[9], st_inv[9], ct_scale, ct_inv;
 };
+
+// lambda(phi) = 1 - H_eps(phi) (Eq. 2_3_heaviside) and its first five Taylor
+// coefficients at the table's grid points, for the FP32 path's Delta rho:
+// lambda(phi_k + d) = l0 + l1 d + ... + l5 d^5 (|d| <= lam_h / 2, the next term
+// below 1e-16), with l0 and l1 as float pairs.  Built in double on the host from
+// the formula of Eq. 2_3_heaviside; it replaces FP64 sin, which this GPU's
+// narrow FP64 pipe makes costly, and at 12 KB stays in L1.
+struct LamEntry {
+    float l0h, l0l, l1h, l1l, l2, l3, l4, l5;
+};
+constexpr int LAM_TAB_MAX = 513;  // entries (2 lam_k0 + 1)
 
 // K1 walks regions LB_REGION_W nodes wide (rk registry tiles when tile_x is
 // narrower): the push stores of a warp then cover long rows, which keeps the
@@ -109,7 +129,7 @@ struct SolidDesc {
     double a, b;                 // semi-axes / half-sides along x and y
     double eps;                  // the blur-zone half-width (a threshold of the level set)
     double r2lo, drho, accel;   // R^2 - (double)(float)R^2, rho_s - rho_f, -(1 - rho_f/rho_s) g
-    float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f;
+    float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f, Rlo_f;  // Rlo_f = R - (float)R
     int T;
     long long off;      // element offset of the tile (eta_x plane, then eta_y plane)
 };
@@ -142,6 +162,7 @@ struct DevState {
     int *reg_nactive[2];
     void *pool[2];         // per tile: Fx_pool, Fy_pool, drho (TILE_N each)
     void *bfield;          // force_kind 3: body force field, x plane then y plane (nx*ny each)
+    LamEntry *lamtab;      // solid-fraction table (FP32 arithmetic)
     int *order;            // solids by decreasing tile side (launch order of the solid kernel)
     unsigned char *busy[2]; // per K1 region, by step parity: 1 if it may hold solid forcing this step
     void *fbody;           // per row: body-force x component
@@ -188,11 +209,12 @@ template <class R> __device__ __forceinline__ R phi_disk(R X, R Y, R rad) { retu
 
 // Storage of the populations and of the half-force carry.  FP32/FP64 store the
 // values as they are.  The 16-bit variants store value x scale with a
-// power-of-two scale per field (exact): FP16 keeps populations x 2^10 and the
-// carry x 2^14, so deviations down to ~1e-11 stay normal and up to 64 fit;
-// BF16 has FP32's range and needs no scale.
-template <class S> struct StoreScale { static constexpr float pop = 1.0f, carry = 1.0f; };
-template <> struct StoreScale<__half> { static constexpr float pop = 1024.0f, carry = 16384.0f; };
+// power-of-two scale (exact) per population plane q and one for the carry,
+// chosen at initialisation from bounds of the values (SimParams::st_scale,
+// ct_scale): the largest value the bound admits fills about half of FP16's
+// range, so small deviations stay normal numbers; a stored FP16 value beyond
+// the range raises an error flag.  (Scaling cannot change the relative
+// rounding of a normal number: it only moves the format's range.)
 template <class S> __device__ __forceinline__ float to_f(S v) { return (float)v; }
 template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -201,30 +223,32 @@ template <> __device__ __forceinline__ __half from_f<__half>(float v) { return _
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <class S> __host__ __device__ constexpr bool is16() { return sizeof(S) == 2; }
 
-template <class S, class R> __device__ __forceinline__ R ldS(const S *p) {
-    if constexpr (is16<S>()) return R(to_f<S>(*p) * (1.0f / StoreScale<S>::pop));
+// population of plane q
+template <class S, class R> __device__ __forceinline__ R ldS(const S *p, const SimParams &sp, int q) {
+    if constexpr (is16<S>()) return R(to_f<S>(*p) * sp.st_inv[q]);
     else return R(*p);
 }
-template <class S, class R> __device__ __forceinline__ void stS(S *p, R v) {
-    if constexpr (is16<S>()) *p = from_f<S>(float(v) * StoreScale<S>::pop);
+template <class S, class R> __device__ __forceinline__ void stS(S *p, R v, const SimParams &sp, int q) {
+    if constexpr (is16<S>()) *p = from_f<S>(float(v) * sp.st_scale[q]);
     else *p = S(v);
 }
-template <class S, class R> __device__ __forceinline__ R ldC(const S *p) {
-    if constexpr (is16<S>()) return R(to_f<S>(*p) * (1.0f / StoreScale<S>::carry));
+// half-force carry
+template <class S, class R> __device__ __forceinline__ R ldC(const S *p, const SimParams &sp) {
+    if constexpr (is16<S>()) return R(to_f<S>(*p) * sp.ct_inv);
     else return R(*p);
 }
-template <class S, class R> __device__ __forceinline__ void stC(S *p, R v) {
-    if constexpr (is16<S>()) *p = from_f<S>(float(v) * StoreScale<S>::carry);
+template <class S, class R> __device__ __forceinline__ void stC(S *p, R v, const SimParams &sp) {
+    if constexpr (is16<S>()) *p = from_f<S>(float(v) * sp.ct_scale);
     else *p = S(v);
 }
 // read-only global load of a stored population
-template <class S, class R> __device__ __forceinline__ R ldG(const S *p) {
-    if constexpr (is16<S>()) return ldS<S, R>(p);
+template <class S, class R> __device__ __forceinline__ R ldG(const S *p, const SimParams &sp, int q) {
+    if constexpr (is16<S>()) return ldS<S, R>(p, sp, q);
     else return R(__ldg(p));
 }
-// a stored 16-bit population would exceed the format's range
-template <class S, class R> __device__ __forceinline__ bool store_overflow(R v) {
-    if constexpr (sizeof(S) == 2 && StoreScale<S>::pop != 1.0f) return fabsf(float(v)) * StoreScale<S>::pop > 60000.0f;
+// a stored FP16 population of plane q would exceed the format's range
+template <class S, class R> __device__ __forceinline__ bool store_overflow(R v, const SimParams &sp, int q) {
+    if constexpr (std::is_same<S, __half>::value) return fabsf(float(v)) * sp.st_scale[q] > 60000.0f;
     else return false;
 }
 
@@ -292,8 +316,8 @@ __device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, co
     const long long c = (long long)j * sp.nx + i;
     R fq[9];
 #pragma unroll
-    for (int q = 0; q < 9; q++) fq[q] = ldS<S, R>(f + q * sp.P + c);
-    moments_from<R>(sp, fq, rest_base<R>(sp, reg, pool, i, j), ldC<S, R>(carry + c), ldC<S, R>(carry + sp.P + c), rho,
+    for (int q = 0; q < 9; q++) fq[q] = ldS<S, R>(f + q * sp.P + c, sp, q);
+    moments_from<R>(sp, fq, rest_base<R>(sp, reg, pool, i, j), ldC<S, R>(carry + c, sp), ldC<S, R>(carry + sp.P + c, sp), rho,
                     u, v);
 }
 
@@ -678,6 +702,22 @@ __device__ inline double shape_sdf_mixed(int shape, double a, double b, double q
     return (y0 / e0) * (y0 / e0) + (y1 / e1) * (y1 / e1) < 1.0 ? -d : d;
 }
 
+// The same with the root polished in double wherever the distance is below
+// eps + shell (the blur zone and a shell around it): there the result is
+// exact to ~1e-13, for the level set's low part.
+__device__ inline double shape_sdf_polished(int shape, double a, double b, double qx, double qy, double eps,
+                                            double shell) {
+    if (shape == 2) return shape_sdf(shape, a, b, qx, qy);
+    double y0 = fabs(qx), y1 = fabs(qy), e0 = a, e1 = b;
+    if (e0 < e1) {
+        double t = e0; e0 = e1; e1 = t;
+        t = y0; y0 = y1; y1 = t;
+    }
+    // polish below eps + shell: the shell argument covers [0, eps + shell] around zero
+    const double d = ellipse_distance_q1_mixed(e0, e1, y0, y1, 0.0, eps + shell);
+    return (y0 / e0) * (y0 / e0) + (y1 / e1) * (y1 / e1) < 1.0 ? -d : d;
+}
+
 // Level set phi_0 of a disk at a tile node: with p = l + off (exact) and eta,
 // phi = |p + eta| - R = (|p|^2 - R^2 + 2 p.eta + |eta|^2) / (|p + eta| + R),
 // where |p|^2 - R^2 is formed with error-free products and a two-sum, so
@@ -700,16 +740,92 @@ __device__ __forceinline__ R phi_eta(R ex, R ey, int lx, int ly, const Frame &fr
     return num / (rsqrt_<R>(X * X + Y * Y) + q.rad);
 }
 
-// phi_0 of a tile node in double from its stored eta: q = eta + l + off is exact
-// in double, so phi carries no rounding beyond its own evaluation.
-template <class R>
-__device__ __forceinline__ double phi_eta_d(R ex, R ey, int lx, int ly, const Frame &fr, const Rsq<R> &q, double rad,
-                                            R exl = R(0), R eyl = R(0)) {
-    const double X = ((double)lx + (double)fr.offx) + ((double)ex + (double)exl);
-    const double Y = ((double)ly + (double)fr.offy) + ((double)ey + (double)eyl);
-    return q.shape == 0 ? sqrt(X * X + Y * Y) - rad : shape_sdf(q.shape, q.a, q.b, X, Y);
+// s = fl(a + b) and its exact error e (Knuth's two-sum).
+__device__ __forceinline__ float two_sum_f(float a, float b, float &e) {
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
 }
-// Half-width of the shell around the blur zone where K3 takes lambda in double.
+
+// phi_0 of a tile node as a float pair ph + pl (error ~1e-14): for a disk,
+// phi = (|p|^2 - R^2) / (|p| + R) with p = (l + off) + eta (hi + lo), in
+// float-float arithmetic; other shapes take the signed distance in double.
+__device__ __forceinline__ void phi_node_ff(float ex, float ey, float exl, float eyl, int lx, int ly, const Frame &fr,
+                                            const Rsq<float> &q, float Rlo, float &ph, float &pl) {
+    if (q.shape != 0) {
+        const double X = ((double)lx + (double)fr.offx) + ((double)ex + (double)exl);
+        const double Y = ((double)ly + (double)fr.offy) + ((double)ey + (double)eyl);
+        const double d = shape_sdf(q.shape, q.a, q.b, X, Y);
+        ph = (float)d;
+        pl = (float)(d - (double)ph);
+        return;
+    }
+    float e;
+    const float pxh = two_sum_f(__fadd_rn((float)lx, fr.offx), ex, e), pxl = e + exl;
+    const float pyh = two_sum_f(__fadd_rn((float)ly, fr.offy), ey, e), pyl = e + eyl;
+    const float a = __fmul_rn(pxh, pxh), ea = __fmaf_rn(pxh, pxh, -a);
+    const float b = __fmul_rn(pyh, pyh), eb = __fmaf_rn(pyh, pyh, -b);
+    float es;
+    const float sh = two_sum_f(a, b, es);
+    const float sl = ((es + ea) + eb) + 2.0f * (pxh * pxl + pyh * pyl);  // |p|^2 = sh + sl
+    float en;
+    const float nh = two_sum_f(sh, -q.hi, en);
+    const float nl = en + (sl - q.lo);                                   // |p|^2 - R^2 = nh + nl
+    const float r = __fsqrt_rn(sh);
+    const float rl = (__fmaf_rn(-r, r, sh) + sl) / (2.0f * r);           // |p| = r + rl
+    float ed;
+    const float dh = two_sum_f(r, q.rad, ed), dl = ed + (rl + Rlo);      // |p| + R = dh + dl
+    const float q1 = __fdiv_rn(nh, dh);
+    const float p1 = __fmul_rn(q1, dh), ep1 = __fmaf_rn(q1, dh, -p1);
+    const float res = (((nh - p1) - ep1) + nl) - q1 * dl;                // num - q1 den
+    const float q2 = res / dh;
+    ph = q1 + q2;
+    pl = q2 - (ph - q1);
+}
+
+// lambda = 1 - H_eps(phi) for phi = ph + pl as a float pair lh + ll, from the
+// table (FP32 path).
+__device__ __forceinline__ void lambda_ff(const SimParams &sp, const LamEntry *tab, float ph, float pl, float &lh,
+                                          float &ll) {
+    const double phd = (double)ph + (double)pl;  // the thresholds of Eq. 2_3_heaviside, exactly
+    if (phd <= -sp.eps) { lh = 1.0f; ll = 0.0f; return; }
+    if (phd >= sp.eps) { lh = 0.0f; ll = 0.0f; return; }
+    const int k = (int)rintf(ph * sp.lam_inv_h);
+    const LamEntry t = tab[k + sp.lam_k0];
+    const float dh = ph - (float)k * sp.lam_h;  // exact: phi_k is a multiple of lam_h within lam_h / 2 of ph
+    const float d = dh + pl;
+    const float p = __fmul_rn(dh, t.l1h), ep = __fmaf_rn(dh, t.l1h, -p);
+    const float rest = (((ep + dh * t.l1l) + pl * t.l1h) + t.l0l) + d * d * (t.l2 + d * (t.l3 + d * (t.l4 + d * t.l5)));
+    float e;
+    const float s = two_sum_f(t.l0h, p, e);
+    const float lo = e + rest;
+    lh = s + lo;
+    ll = lo - (lh - s);
+}
+
+// Float-float accumulation: (h, l) += (a, b); (h, l) += (a, b) (c, d); (h, l) /= (a, b).
+__device__ __forceinline__ void ff_add(float &h, float &l, float a, float b) {
+    float e;
+    const float s = two_sum_f(h, a, e);
+    const float t = e + (l + b);
+    h = s + t;
+    l = t - (h - s);
+}
+__device__ __forceinline__ void ff_add_prod(float &h, float &l, float a, float b, float c, float d) {
+    const float p = __fmul_rn(a, c), ep = __fmaf_rn(a, c, -p);
+    ff_add(h, l, p, ep + (a * d + b * c));
+}
+__device__ __forceinline__ void ff_div(float &h, float &l, float a, float b) {
+    const float q1 = __fdiv_rn(h, a);
+    const float p = __fmul_rn(q1, a), ep = __fmaf_rn(q1, a, -p);
+    const float r = (((h - p) - ep) + l) - q1 * b;
+    const float q2 = r / a;
+    h = q1 + q2;
+    l = q2 - (h - q1);
+}
+
+// Half-width of the shell around the blur zone where K3 takes lambda to ~1e-13.
 constexpr float PHI_D_SHELL = 1e-3f;
 
 // d = o - X_c - off of a frame, in double.
@@ -865,16 +981,16 @@ __device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, 
     nd.ex = Xi[k];
     nd.ey = Yi[k];
     nd.phi = Pi[k];
-    if constexpr (xi_planes<R>() == 5) {
+    if constexpr (xi_planes<R>() == 6) {
         nd.exl = Xi[3 * T * T + k];  // the low parts follow the phi plane
         nd.eyl = Xi[4 * T * T + k];
     } else {
         nd.exl = nd.eyl = R(0);
     }
 #pragma unroll
-    for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(a.f + q * sp.P + c);
-    nd.cx = ldC<S, R>(a.carry + c);
-    nd.cy = ldC<S, R>(a.carry + sp.P + c);
+    for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(a.f + q * sp.P + c, sp, q);
+    nd.cx = ldC<S, R>(a.carry + c, sp);
+    nd.cy = ldC<S, R>(a.carry + sp.P + c, sp);
     nd.cnt = a.reg_prev[tile];
     nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
 }
@@ -912,7 +1028,7 @@ __device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, 
     const R dXdy = hy * (R(3) * ex - R(4) * X3 + X4), dYdy = hy * (R(3) * ey - R(4) * Y3 + Y4);
     // xi = eta + x - d: the node's own motion enters as -(u - dd)
     const int t = ly * T + lx;
-    if constexpr (xi_planes<R>() == 5) {
+    if constexpr (xi_planes<R>() == 6) {
         // eta^{n+1} = (hi + lo) + dd - (u + u.grad eta) in float-float: the frame
         // shift dd and the update enter with their exact rounding errors, so
         // hi + lo carries eta to ~u_32^2 and only the small update rounds
@@ -1118,11 +1234,33 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
             const int lx = x0 + wk.c, ly = y0 + wk.r, t = ly * T + lx;
             if (lab[t] >= 0) {
                 bx[0] = min(bx[0], lx); bx[1] = max(bx[1], lx); bx[2] = min(bx[2], ly); bx[3] = max(bx[3], ly);
-                const R phi = phi_eta(Xo[t], Yo[t], lx, ly, fo, rq);
-                Po[t] = phi;
-                if constexpr (xi_planes<R>() == 5) {
-                    if (a.init || lab[t] > 0) { Xo[3 * TT + t] = R(0); Xo[4 * TT + t] = R(0); }
+                R phi = phi_eta(Xo[t], Yo[t], lx, ly, fo, rq);
+                if constexpr (xi_planes<R>() == 6) {
+                    // FP32: the level set as a float pair hi + lo in and near the blur
+                    // zone (the stresses and sets read hi; the density difference both)
+                    R exl = R(0), eyl = R(0);
+                    if (a.init || lab[t] > 0) {
+                        Xo[3 * TT + t] = R(0);
+                        Xo[4 * TT + t] = R(0);
+                    } else {
+                        exl = Xo[3 * TT + t];  // the advection's low parts
+                        eyl = Xo[4 * TT + t];
+                    }
+                    R pl = R(0);
+                    if (phi > -eps - R(PHI_D_SHELL) && phi < eps + R(PHI_D_SHELL)) {
+                        if (rq.shape == 0) {
+                            phi_node_ff(Xo[t], Yo[t], exl, eyl, lx, ly, fo, rq, sd.Rlo_f, phi, pl);
+                        } else {
+                            const double X = ((double)lx + (double)fo.offx) + ((double)Xo[t] + (double)exl);
+                            const double Y = ((double)ly + (double)fo.offy) + ((double)Yo[t] + (double)eyl);
+                            const double dd = shape_sdf_polished(rq.shape, rq.a, rq.b, X, Y, sp.eps, PHI_D_SHELL);
+                            phi = R(dd);
+                            pl = R(dd - (double)phi);
+                        }
+                    }
+                    Xo[5 * TT + t] = pl;
                 }
+                Po[t] = phi;
                 if (phi < eps) {
                     bx[4] = min(bx[4], lx); bx[5] = max(bx[5], lx); bx[6] = min(bx[6], ly); bx[7] = max(bx[7], ly);
                 }
@@ -1218,6 +1356,7 @@ struct ForceArgs {
     const int *reg_count, *reg_solids, *reg_active, *reg_nactive;
     R *pool;
     const SolidDesc *solids;
+    const LamEntry *lamtab;
     unsigned *err;
 };
 
@@ -1265,7 +1404,7 @@ struct ForceShared {
     int nk;
     Frame sfr[KMAX];
     R sG[KMAX], sD[KMAX], sA[KMAX];
-    double sRd[KMAX], sDd[KMAX];  // radius and rho_s - rho_f in double (the node terms' Delta rho)
+    float sDh[KMAX], sDl[KMAX];  // rho_s - rho_f as a float pair (the FP32 node terms' Delta rho)
     Rsq<R> srq[KMAX];
     int sT[KMAX];
     long long soff[KMAX];
@@ -1317,8 +1456,8 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 sG[rank] = pick<R>(sd.G, sd.G_f);
                 sD[rank] = pick<R>(sd.drho, sd.drho_f);
                 sA[rank] = pick<R>(sd.accel, sd.accel_f);
-                fs.sRd[rank] = sd.R;
-                fs.sDd[rank] = sd.drho;
+                fs.sDh[rank] = (float)sd.drho;
+                fs.sDl[rank] = (float)(sd.drho - (double)(float)sd.drho);
                 srq[rank] = Rsq<R>(sd);
                 sT[rank] = sd.T;
                 soff[rank] = sd.off;
@@ -1345,6 +1484,12 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                     X = Xs[ly * T + lx];
                     Y = Xs[T * T + ly * T + lx];
                     if (X == X) P = Xs[2 * T * T + ly * T + lx];  // the stored phi
+                    if constexpr (xi_planes<R>() == 6) {
+                        // the low part of phi that the Delta rho pass reads at the tile's
+                        // own nodes: into L1 now, while the stresses are formed
+                        if (wk.c >= 1 && wk.c <= TX && wk.r >= 1 && wk.r <= sp.ty)
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(Xs + 5 * T * T + ly * T + lx));
+                    }
                 }
                 sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
             }
@@ -1409,6 +1554,35 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
             eT[3 * e + 0] = Sxx + Cxx; eT[3 * e + 1] = Sxy + Cxy; eT[3 * e + 2] = Syy + Cyy;
         }
         __syncthreads();
+        // FP32: every slot's lambda at the tile's nodes as a float pair, into the
+        // staged eta (no longer read).  Delta rho = sum lambda (rho_s - rho_f) is an
+        // O(1) number whose rounding would drive the pressure, so in and near the
+        // blur zone lambda is formed from phi_0 of the exact eta + position (to
+        // ~1e-13), not from the stored FP32 phi (whose error is far below
+        // PHI_D_SHELL); elsewhere it is exactly 0 or 1.
+        if constexpr (sizeof(R) == 4) {
+            for (int it = threadIdx.x; it < n * TILE_N; it += blockDim.x) {
+                const int ks = it / TILE_N, lt = it - ks * TILE_N;
+                const int cx = lt & (TX - 1), cy = lt >> sp.lx;
+                const int i = i0 + cx, j = j0 + cy, p = (cy + 1) * PX + cx + 1;
+                const R ph = sP[ks * PN + p];
+                float lh = 0.0f, ll = 0.0f;
+                if (ph == ph && i < sp.nx && j < sp.ny) {
+                    if (ph <= -eps - R(PHI_D_SHELL)) lh = 1.0f;
+                    else if (ph < eps + R(PHI_D_SHELL)) {
+                        const Frame &fr = sfr[ks];
+                        const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
+                        const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
+                        const int T = sT[ks];
+                        const float phl = a.xi[soff[ks] + 5 * T * T + ly * T + lx];  // low part of phi
+                        lambda_ff(sp, a.lamtab, ph, phl, lh, ll);
+                    }
+                }
+                sX[ks * PN + p] = lh;
+                sY[ks * PN + p] = ll;
+            }
+            __syncthreads();
+        }
         // Node: divergence (Eq. 3_3_div_solid_stress), solid fraction, drho, solid acceleration.
         {
             const int cx = threadIdx.x & (TX - 1), cy = threadIdx.x >> sp.lx;
@@ -1419,38 +1593,34 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 const R fsx = (tr[0] - tl[0]) + (tt[1] - tb[1]);
                 const R fsy = (tr[1] - tl[1]) + (tt[2] - tb[2]);
                 const int p = (cy + 1) * PX + cx + 1;
-                R L = 0, Ay = 0;
-                double Ld = 0.0, Dd = 0.0;  // sum lambda and Delta rho (Eq. 2_3_drho) in double
-                for (int ks = 0; ks < n; ks++) {
-                    const R ph = sP[ks * PN + p];
-                    if (!(ph == ph)) continue;
-                    const R lam = R(1) - heaviside<R>(ph, eps);
-                    L += lam;
-                    Ay += lam * sA[ks];
-                    double ld = (double)lam;
-                    if constexpr (sizeof(R) == 4) {
-                        // Delta rho is an O(1) number whose rounding would drive the
-                        // pressure: in and near the blur zone, lambda is formed in
-                        // double from phi_0 of the exact eta + position, not from the
-                        // stored FP32 phi (whose error is far below PHI_D_SHELL)
-                        if (ph > -eps - R(PHI_D_SHELL) && ph < eps + R(PHI_D_SHELL)) {
-                            const Frame &fr = sfr[ks];
-                            const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
-                            const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
-                            const int T = sT[ks];
-                            const R *lo = a.xi + soff[ks] + 3 * T * T + ly * T + lx;  // low parts of eta
-                            const double phd = phi_eta_d(sX[ks * PN + p], sY[ks * PN + p], lx, ly, fr, srq[ks],
-                                                         fs.sRd[ks], lo[0], lo[T * T]);
-                            ld = 1.0 - heaviside<double>(phd, sp.eps);
-                        }
+                R L = 0, Ay = 0, Dh = 0, Dl = 0;
+                if constexpr (sizeof(R) == 4) {
+                    // float-float sums of lambda and lambda (rho_s - rho_f)
+                    float Lh = 0.0f, Ll = 0.0f;
+                    for (int ks = 0; ks < n; ks++) {
+                        const float lh = sX[ks * PN + p], ll = sY[ks * PN + p];
+                        L += lh;
+                        Ay += lh * sA[ks];
+                        ff_add(Lh, Ll, lh, ll);
+                        ff_add_prod(Dh, Dl, lh, ll, fs.sDh[ks], fs.sDl[ks]);
                     }
-                    Ld += ld;
-                    Dd += ld * fs.sDd[ks];
+                    if (Lh + Ll > 1.0f) ff_div(Dh, Dl, Lh, Ll);
+                } else {
+                    double Ld = 0.0, Dd = 0.0;
+                    for (int ks = 0; ks < n; ks++) {
+                        const R ph = sP[ks * PN + p];
+                        if (!(ph == ph)) continue;
+                        const R lam = R(1) - heaviside<R>(ph, eps);
+                        L += lam;
+                        Ay += lam * sA[ks];
+                        Ld += lam;
+                        Dd += lam * sD[ks];
+                    }
+                    if (Ld > 1.0) Dd /= Ld;
+                    Dh = R(Dd);
                 }
                 if (L > R(1)) Ay /= L;
-                if (Ld > 1.0) Dd /= Ld;
                 R *po = a.pool + (long long)tile * POOL_STRIDE + threadIdx.x;
-                const R dhi = R(Dd);
                 po[POOL_FX] = fsx;
                 if (sp.force_mode == 1) {
                     po[POOL_FY] = fsy;
@@ -1458,8 +1628,8 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 } else {
                     po[POOL_FY] = fsy + Ay;
                 }
-                po[POOL_DRHO] = dhi;
-                po[POOL_DRHO_LO] = R(Dd - (double)dhi);
+                po[POOL_DRHO] = Dh;
+                po[POOL_DRHO_LO] = Dl;
             }
         }
         __syncthreads();
@@ -1467,7 +1637,7 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
 }
 
 template <class R>
-__global__ void __launch_bounds__(TILE_N) force_kernel(SimParams sp, ForceArgs<R> a) {
+__global__ void __launch_bounds__(TILE_N, sizeof(R) == 4 ? 5 : 1) force_kernel(SimParams sp, ForceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ForceShared<R> fs;
     const int nact = *a.reg_nactive;
@@ -1515,7 +1685,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     R f[9];
 #pragma unroll
     for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
-        f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt) : ldG<S, R>(a.fin_q[q] + c);
+        f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt, sp, q) : ldG<S, R>(a.fin_q[q] + c, sp, q);
     R dro = R(0), dro_lo = R(0);  // rest base: Delta rho of the step that wrote f (hi + lo)
     if (prev_count > 0) {
         const R *pp = a.pool_prev + (long long)tile * POOL_STRIDE + lt;
@@ -1528,8 +1698,8 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
     const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
     const R inv = rcp_rn<R>(rho);
-    const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt) : ldC<S, R>(a.carry + c);
-    const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt) : ldC<S, R>(a.carry + P + c);
+    const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt, sp) : ldC<S, R>(a.carry + c, sp);
+    const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt, sp) : ldC<S, R>(a.carry + P + c, sp);
     const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
     R Fx, Fy, drt = R(0), drt_lo = R(0);
     if (sp.force_kind == 3) {
@@ -1588,18 +1758,18 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
         a.tape[c] = rho; a.tape[P + c] = ux; a.tape[2 * P + c] = uy;
         a.tape[3 * P + c] = Fx; a.tape[4 * P + c] = Fy;
     }
-    stC<S, R>(a.carry + c, R(0.5) * rho * Fx);
-    stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy);
+    stC<S, R>(a.carry + c, R(0.5) * rho * Fx, sp);
+    stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy, sp);
     if constexpr (is16<S>()) {
         bool ov = false;
 #pragma unroll
-        for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q]);
+        for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q], sp, q);
         if (ov) atomicOr(a.err, ERR_OVERFLOW16);
     }
-    stS<S, R>(a.fout_push[0] + c, fh[0]);
+    stS<S, R>(a.fout_push[0] + c, fh[0], sp, 0);
     if (interior) {
 #pragma unroll
-        for (int q = 1; q < 9; q++) stS<S, R>(a.fout_push[q] + c, fh[q]);
+        for (int q = 1; q < 9; q++) stS<S, R>(a.fout_push[q] + c, fh[q], sp, q);
     } else {
 #pragma unroll
         for (int q = 1; q < 9; q++) {
@@ -1609,11 +1779,11 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
                 // halfway bounce-back; the top wall moves with lid_u (Sec. 3.5)
                 const R uw = (oy && sp.wall_y && dj >= ny) ? pick<R>(sp.lid_u, sp.lid_u_f) : R(0);
                 const R val = fh[q] - R(6) * wq<R>(q) * rho * (R(cxq(q)) * uw);
-                stS<S, R>(a.f_out + oppq(q) * P + c, val);
+                stS<S, R>(a.f_out + oppq(q) * P + c, val, sp, oppq(q));
             } else {
                 if (ox) di = di < 0 ? di + nx : di - nx;
                 if (oy) dj = dj < 0 ? dj + ny : dj - ny;
-                stS<S, R>(a.f_out + q * P + dj * nx + di, fh[q]);
+                stS<S, R>(a.f_out + q * P + dj * nx + di, fh[q], sp, q);
             }
         }
     }
@@ -1642,7 +1812,7 @@ __device__ __forceinline__ void lb_tile(const SimParams &sp, const LbArgs<R, S> 
 // nodes, each pass a band of whole rows.
 // REG false: a free region (no registry reads; its registry tiles are empty,
 // so there is nothing to clear).
-template <class R, class S, bool REG = true>
+template <class R, class S, bool REG = true, bool CLR_ACTIVE = true>
 __device__ __forceinline__ void lb_region(const SimParams &sp, const LbArgs<R, S> &a, const int rx, const int ry) {
     const int lt = threadIdx.x;
     const int lw = sp.lx + sp.lk, W = 1 << lw;
@@ -1664,7 +1834,7 @@ __device__ __forceinline__ void lb_region(const SimParams &sp, const LbArgs<R, S
             if (bx < sp.ntx) a.clr_count[ry * sp.ntx + bx] = 0;
         }
     }
-    if (lt == 0 && rx == 0 && ry == 0) *a.clr_nactive = 0;
+    if (CLR_ACTIVE && lt == 0 && rx == 0 && ry == 0) *a.clr_nactive = 0;
 }
 
 // K1 over the regions of one kind.  MODE 0: every region; 1: the busy regions
@@ -1677,7 +1847,30 @@ __global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_step_kernel(Si
         const bool b = busy[blockIdx.y * sp.nrx + blockIdx.x] != 0;
         if (b != (MODE == 1)) return;  // uniform over the CTA, before any barrier
     }
-    lb_region<R, S, MODE != 2>(sp, a, blockIdx.x, blockIdx.y);
+    lb_region<R, S, MODE != 2, MODE == 0>(sp, a, blockIdx.x, blockIdx.y);
+}
+
+// Classification of the K1 regions of the overlapped step n, after K2 of step
+// n: a region is busy when one of its registry tiles is registered in registry
+// n (the step's solid forcing and Delta rho) or in registry n - 1 (the rest base
+// of the populations the step reads); a free region needs neither.  Every node
+// that the reference-map kernel of step n + 1 reads (solid and blur-zone nodes
+// of phi^{n+1} and their 4-neighbours) lies in registry n's tiles, so the next
+// step's solid kernels need only the busy regions of this one.  Also clears the
+// active-tile count of registry n - 1 (its counts are cleared by the busy K1).
+static __global__ void lb_classify_kernel(SimParams sp, const int *reg_now, const int *reg_prev, unsigned char *busy,
+                                          int *nactive_prev) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) *nactive_prev = 0;
+    if (r >= sp.nrx * sp.nty) return;
+    const int rx = r % sp.nrx, ry = r / sp.nrx;
+    const int b0 = rx << sp.lk, b1 = min(b0 + sp.rk, sp.ntx);
+    bool any = false;
+    for (int bx = b0; bx < b1; bx++) {
+        const int t = ry * sp.ntx + bx;
+        any = any || reg_now[t] > 0 || reg_prev[t] > 0;
+    }
+    busy[r] = any ? 1 : 0;
 }
 
 // Classification of the K1 regions for the overlapped step n: a region is busy
@@ -1819,9 +2012,9 @@ __global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
     const int i = blockIdx.x * sp.tx + (threadIdx.x & (sp.tx - 1)), j = blockIdx.y * sp.ty + (threadIdx.x >> sp.lx);
     if (i >= sp.nx || j >= sp.ny) return;
     const long long c = (long long)j * sp.nx + i;
-    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(0));
-    stC<S, R>(carry + c, R(0));
-    stC<S, R>(carry + sp.P + c, R(0));
+    for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(0), sp, q);
+    stC<S, R>(carry + c, R(0), sp);
+    stC<S, R>(carry + sp.P + c, R(0), sp);
 }
 
 // Self-check of the failure path of the tensor-copy pipeline: one thread
@@ -1850,7 +2043,7 @@ __global__ void __launch_bounds__(TILE_N) mass_tile_kernel(SimParams sp, const S
     if (i < sp.nx && j < sp.ny) {
         const long long c = (long long)j * sp.nx + i;
         double dr = rest_base_d<R>(sp, reg_count, pool, i, j);
-        for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c);
+        for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c, sp, q);
         v[0] = dr;
     }
     block_sum<1>(v, red);
@@ -1869,7 +2062,7 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
     if (kind == 0) {
         // rho = rho_f + rest base + stored values, summed in FP64 so the readout adds no rounding
         double dr = rest_base_d<R>(sp, reg_count, pool, i, j);
-        for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c);
+        for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c, sp, q);
         v = sp.rho_f + dr;
     } else if (kind <= 2) {
         R rho, u, w;
@@ -1885,7 +2078,7 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
         else v = rest_base_d<R>(sp, reg_count, pool, i, j);
     } else {
         const int q = kind - 20;
-        v = (double)ldS<S, R>(f + q * sp.P + c) + wq<double>(q) * sp.rho_f;  // the exact weight, as the upload
+        v = (double)ldS<S, R>(f + q * sp.P + c, sp, q) + wq<double>(q) * sp.rho_f;  // the exact weight, as the upload
         if (q == 0) v += rest_base_d<R>(sp, reg_count, pool, i, j);
     }
     out[c] = v;
@@ -1949,10 +2142,10 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
         // xi = eta + l + off + X_c
         if (kind == 0) {
             v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
-            if constexpr (xi_planes<R>() == 5) v += (double)xi[sd.off + 3 * T * T + t];  // low part
+            if constexpr (xi_planes<R>() == 6) v += (double)xi[sd.off + 3 * T * T + t];  // low part
         } else if (kind == 1) {
             v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
-            if constexpr (xi_planes<R>() == 5) v += (double)xi[sd.off + 4 * T * T + t];
+            if constexpr (xi_planes<R>() == 6) v += (double)xi[sd.off + 4 * T * T + t];
         } else if (kind == 2) v = (double)xi[sd.off + 2 * T * T + t];
         else {
             if (!(xi[sd.off + 2 * T * T + t] < -R(PHI_TIE))) continue;
@@ -1973,6 +2166,7 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
 // queues, in shared memory, the nodes of the solid and blur zone (phi < eps);
 // every 32 queued nodes it takes one per lane with all its loads issued first.
 constexpr int STATS_THREADS = 256;
+constexpr int STATS_COLS = 10;  // per solid: area, centroid (2), mass, momentum (2), det F (2), contact force (2)
 template <class R, class S>
 struct StatsNode {
     int lx, ly, reg;
@@ -1997,12 +2191,12 @@ __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, co
     while (j >= sp.ny) j -= sp.ny;
     const long long c = (long long)j * sp.nx + i;
 #pragma unroll
-    for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c);
+    for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c, sp, q);
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
     nd.reg = reg[tile];
     nd.pool = pool[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
-    nd.cx = ldC<S, R>(carry + c);
-    nd.cy = ldC<S, R>(carry + sp.P + c);
+    nd.cx = ldC<S, R>(carry + c, sp);
+    nd.cy = ldC<S, R>(carry + sp.P + c, sp);
     nd.inner = nd.lx > fr.bx0 && nd.lx < fr.bx1 && nd.ly > fr.by0 && nd.ly < fr.by1;
     if (nd.inner) {
         const R *Y = xi + T * T;
@@ -2014,31 +2208,142 @@ __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, co
 // precision (FP64 is a narrow pipe on this GPU; the FP32 path's inputs are FP32
 // anyway); positions relative to the tile origin.  Each warp then sums its
 // threads' terms in that precision and the warps' sums are added in FP64.
+// Compensated accumulation (Neumaier): acc + cmp carries the sum of the added
+// terms to ~2 u |sum| whatever their count (cmp stays zero in FP64).
+template <class R>
+__device__ __forceinline__ void comp_add(R &acc, R &cmp, R v) {
+    if constexpr (sizeof(R) == 4) {
+        const R t = acc + v;
+        cmp += fabsf(acc) >= fabsf(v) ? (acc - t) + v : (v - t) + acc;
+        acc = t;
+    } else {
+        acc += v;
+    }
+}
+
 template <class R, class S>
 __device__ __forceinline__ void stats_finish(const SimParams &sp, const StatsNode<R, S> &nd, R eps, R (&acc)[8],
-                                             R &mx) {
+                                             R (&cmp)[8], R &mx) {
     R rho, u, v;
     moments_from<R>(sp, nd.f, nd.reg > 0 ? nd.pool : R(0), nd.cx, nd.cy, rho, u, v);
     const R lam = R(1) - heaviside<R>(nd.phi, eps), lr = lam * rho;
-    acc[0] += lam; acc[1] += lam * R(nd.lx); acc[2] += lam * R(nd.ly);
-    acc[3] += lr; acc[4] += lr * u; acc[5] += lr * v;
+    comp_add(acc[0], cmp[0], lam); comp_add(acc[1], cmp[1], lam * R(nd.lx)); comp_add(acc[2], cmp[2], lam * R(nd.ly));
+    comp_add(acc[3], cmp[3], lr); comp_add(acc[4], cmp[4], lr * u); comp_add(acc[5], cmp[5], lr * v);
     R Axx, Axy, Ayx, Ayy, ddet;
     if (nd.phi < -R(PHI_TIE) && nd.inner &&
         det_dev_from_stencil<R>(nd.st[0], nd.st[1], nd.st[2], nd.st[3], nd.st[4], nd.st[5], nd.st[6], nd.st[7], Axx,
                                 Axy, Ayx, Ayy, ddet)) {
         const R a = ddet < R(0) ? -ddet : ddet;
-        acc[6] += lam * a;
-        acc[7] += lam;
+        comp_add(acc[6], cmp[6], lam * a);
+        comp_add(acc[7], cmp[7], lam);
         mx = a > mx ? a : mx;
     }
 }
 
+// Level set of solid `sol` at grid node (i, j) from its tile (frame fr), or
+// NaN where the node is outside the tile's box or not a valid band node.
+template <class R>
+__device__ __forceinline__ R tile_phi(const SimParams &sp, const R *xi, const SolidDesc &sd, const Frame &fr, int i, int j) {
+    const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
+    const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
+    if (!in_box(fr, lx, ly)) return nanv<R>();
+    const R *X = xi + sd.off;
+    const int T = sd.T, t = ly * T + lx;
+    return X[t] == X[t] ? X[2 * T * T + t] : nanv<R>();
+}
+
+// Contact stress of a pair (Eqs. 3_6_collision_stress .. 3_6_normal) on the
+// half-edge of direction dir (0: between (i-1, j) and (i, j); 1: between
+// (i, j-1) and (i, j)), from the level sets ps, pt of the two solids on the
+// 3 x 4 (or 4 x 3) nodes around it, as the force kernel forms it; false where
+// a stencil node is missing or the pair is not in contact there.
+template <class R>
+__device__ __forceinline__ bool pair_edge_tau(const R (&ps)[4][4], const R (&pt)[4][4], int dir, int ex, int ey, R eps,
+                                              R eta, R Gsum, R (&tau)[3]) {
+    R as[3], bs[3], at[3], bt[3];
+    for (int k = 0; k < 3; k++) {
+        // node indices in the 4x4 block: a on the low side of the edge, b on the high side
+        const int ax = dir == 0 ? ex - 1 : ex - 1 + k, ay = dir == 0 ? ey - 1 + k : ey - 1;
+        const int bx = dir == 0 ? ex : ex - 1 + k, by = dir == 0 ? ey - 1 + k : ey;
+        as[k] = ps[ay][ax]; bs[k] = ps[by][bx]; at[k] = pt[ay][ax]; bt[k] = pt[by][bx];
+        if (!(as[k] == as[k] && bs[k] == bs[k] && at[k] == at[k] && bt[k] == bt[k])) return false;
+    }
+    const R phs = R(0.5) * (as[1] + bs[1]), pht = R(0.5) * (at[1] + bt[1]);
+    if (!(phs < eps) || !(pht < eps)) return false;
+    const R fs = R(0.5) * (R(1) - phs / eps), ft = R(0.5) * (R(1) - pht / eps);
+    const R fm = fs < ft ? fs : ft;
+    R gn, gt;
+    edge_grad<R>(as[0] - at[0], as[1] - at[1], as[2] - at[2], bs[0] - bt[0], bs[1] - bt[1], bs[2] - bt[2], gn, gt);
+    const R gxx = dir == 0 ? gn : gt, gyy = dir == 0 ? gt : gn;
+    const R nrm = rsqrt_<R>(gxx * gxx + gyy * gyy);
+    if (nrm == R(0)) return false;
+    const R nx_ = gxx / nrm, ny_ = gyy / nrm;
+    const R kk = -eta * fm * Gsum;
+    tau[0] = kk * (nx_ * nx_ - R(0.5)); tau[1] = kk * (nx_ * ny_); tau[2] = kk * (ny_ * ny_ - R(0.5));
+    return true;
+}
+
+// Net contact force on solid s: over the registry tiles around it that also
+// hold another solid t, the divergence (Eq. 3_3_div_solid_stress) of the pair's
+// contact stress at every domain node nearer to s than to t (phi_s < phi_t,
+// half where equal; a node outside t's band is nearer to s), summed over the
+// pairs in FP64 by the CTA's threads.
+template <class R>
+__device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *reg, const int *reg_solids, const R *xi,
+                                  const Frame *frames, const SolidDesc *solids, int s, const Frame &fr, double (&fc)[2]) {
+    const SolidDesc sd = solids[s];
+    const R eps = pick<R>(sp.eps, sp.eps_f), eta = pick<R>(sp.eta, sp.eta_f);
+    if (fr.bx0 > fr.bx1) return;
+    int rx0[2], rx1[2], ry0[2], ry1[2];
+    const int nrx = tile_ranges(fr.ox + fr.bx0, fr.ox + fr.bx1, sp.nx, sp.wall_x, sp.lx, sp.ntx, rx0, rx1);
+    const int nry = tile_ranges(fr.oy + fr.by0, fr.oy + fr.by1, sp.ny, sp.wall_y, sp.ly, sp.nty, ry0, ry1);
+    for (int ay = 0; ay < nry; ay++)
+        for (int by = ry0[ay]; by <= ry1[ay]; by++)
+            for (int ax = 0; ax < nrx; ax++)
+                for (int bx = rx0[ax]; bx <= rx1[ax]; bx++) {
+                    const int tile = by * sp.ntx + bx;
+                    const int n = min(reg[tile], sp.kmax);
+                    if (n < 2) continue;  // uniform over the CTA
+                    bool mine = false;
+                    for (int k = 0; k < n; k++) mine = mine || reg_solids[tile * KMAX + k] == s;
+                    if (!mine) continue;
+                    const int i = bx * sp.tx + (threadIdx.x & (sp.tx - 1)), j = by * sp.ty + (threadIdx.x >> sp.lx);
+                    if (threadIdx.x >= TILE_N || i >= sp.nx || j >= sp.ny) continue;
+                    // 4x4 block of level sets: nodes (i-1..i+2, j-1..j+2), block index (x - i + 1, y - j + 1)
+                    R ps[4][4];
+                    for (int yy = 0; yy < 4; yy++)
+                        for (int xx = 0; xx < 4; xx++) ps[yy][xx] = tile_phi<R>(sp, xi, sd, fr, i - 1 + xx, j - 1 + yy);
+                    if (!(ps[1][1] == ps[1][1])) continue;
+                    for (int k = 0; k < n; k++) {
+                        const int t = reg_solids[tile * KMAX + k];
+                        if (t == s) continue;
+                        const SolidDesc td = solids[t];
+                        const Frame tf = frames[t];
+                        R pt[4][4];
+                        for (int yy = 0; yy < 4; yy++)
+                            for (int xx = 0; xx < 4; xx++) pt[yy][xx] = tile_phi<R>(sp, xi, td, tf, i - 1 + xx, j - 1 + yy);
+                        const R p0 = pt[1][1];
+                        const double w = !(p0 == p0) || ps[1][1] < p0 ? 1.0 : (ps[1][1] == p0 ? 0.5 : 0.0);
+                        if (w == 0.0) continue;
+                        const R Gsum = pick<R>(sd.G + td.G, sd.G_f + td.G_f);
+                        R tl[3] = {0, 0, 0}, tr[3] = {0, 0, 0}, tb[3] = {0, 0, 0}, tt[3] = {0, 0, 0};
+                        bool any = pair_edge_tau<R>(ps, pt, 0, 1, 1, eps, eta, Gsum, tl);
+                        any = pair_edge_tau<R>(ps, pt, 0, 2, 1, eps, eta, Gsum, tr) || any;
+                        any = pair_edge_tau<R>(ps, pt, 1, 1, 1, eps, eta, Gsum, tb) || any;
+                        any = pair_edge_tau<R>(ps, pt, 1, 1, 2, eps, eta, Gsum, tt) || any;
+                        if (!any) continue;
+                        fc[0] += w * (double)((tr[0] - tl[0]) + (tt[1] - tb[1]));
+                        fc[1] += w * (double)((tr[1] - tl[1]) + (tt[2] - tb[2]));
+                    }
+                }
+}
+
 template <class R, class S>
 __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_stats_kernel(SimParams sp, const S *f, const S *carry,
-                                                                    const int *reg, const R *pool, const R *xi,
-                                                                    const Frame *frames, const SolidDesc *solids,
-                                                                    double *out) {
-    __shared__ double red[32 * 8];
+                                                                    const int *reg, const int *reg_solids, const R *pool,
+                                                                    const R *xi, const Frame *frames,
+                                                                    const SolidDesc *solids, double *out) {
+    __shared__ double red[32 * STATS_COLS];
     __shared__ unsigned long long dmax;
     __shared__ int queue[STATS_THREADS / 32][64];  // per warp: < 32 waiting + one round of 32
     const int s = blockIdx.x;
@@ -2049,6 +2354,7 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
     const R *X = xi + sd.off;
     const R eps = pick<R>(sp.eps, sp.eps_f);
     R acc[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    R cmp[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     R mx = R(0);
     if (threadIdx.x == 0) dmax = 0ull;
     __syncthreads();
@@ -2059,7 +2365,7 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
         StatsNode<R, S> nd;
         if (lane < cnt) {
             stats_gather<R, S>(sp, f, carry, reg, pool, X, T, ow, fr, qu[qn - cnt + lane], nd);
-            stats_finish<R, S>(sp, nd, eps, acc, mx);
+            stats_finish<R, S>(sp, nd, eps, acc, cmp, mx);
         }
         __syncwarp();
         qn -= cnt;
@@ -2101,29 +2407,40 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
         }
     }
     if (qn > 0) drain(qn);
-    // warp sums in the arithmetic precision, then the warps' sums in FP64
+    // each thread's compensated sums in FP64, then warp and CTA sums in FP64
+    double v[STATS_COLS];
 #pragma unroll
-    for (int k = 0; k < 8; k++)
-        for (int d = 16; d > 0; d >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], d);
+    for (int k = 0; k < 8; k++) v[k] = (double)acc[k] + (double)cmp[k];
     for (int d = 16; d > 0; d >>= 1) {
         const R m2 = __shfl_down_sync(0xffffffffu, mx, d);
         mx = m2 > mx ? m2 : mx;
     }
-    if (lane == 0) {
-        atomicMax(&dmax, (unsigned long long)__double_as_longlong((double)mx));  // non-negative: bits order as values
-        for (int k = 0; k < 8; k++) red[warp * 8 + k] = (double)acc[k];
+    if (lane == 0) atomicMax(&dmax, (unsigned long long)__double_as_longlong((double)mx));  // non-negative: bits order as values
+    // the net contact force (FP64, accumulated at the contact nodes only)
+    v[8] = v[9] = 0.0;
+    {
+        double fc[2] = {0.0, 0.0};
+        contact_force_sum<R>(sp, reg, reg_solids, xi, frames, solids, s, fr, fc);
+        v[8] = fc[0];
+        v[9] = fc[1];
     }
+#pragma unroll
+    for (int k = 0; k < STATS_COLS; k++)
+        for (int d = 16; d > 0; d >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], d);
+    if (lane == 0)
+        for (int k = 0; k < STATS_COLS; k++) red[warp * STATS_COLS + k] = v[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-        double st[8];
-        for (int k = 0; k < 8; k++) {
+        double st[STATS_COLS];
+        for (int k = 0; k < STATS_COLS; k++) {
             st[k] = 0.0;
-            for (int ww = 0; ww < nw; ww++) st[k] += red[ww * 8 + k];
+            for (int ww = 0; ww < nw; ww++) st[k] += red[ww * STATS_COLS + k];
         }
-        double *q = out + 8 * s;
+        double *q = out + STATS_COLS * s;
         q[0] = st[0]; q[1] = o.x + st[1] / st[0]; q[2] = o.y + st[2] / st[0]; q[3] = st[3]; q[4] = st[4]; q[5] = st[5];
         q[6] = __longlong_as_double((long long)dmax);
         q[7] = st[7] > 0.0 ? st[6] / st[7] : 0.0;
+        q[8] = st[8]; q[9] = st[9];
     }
 }
 

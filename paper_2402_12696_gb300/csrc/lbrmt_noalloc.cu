@@ -1,12 +1,14 @@
 // lbrmt_noalloc.cu -- total mass without any device allocation.
 //
 // lbrmt_total_mass_noalloc serves callers that cannot allocate device memory
-// at the point where they need the diagnostic: code recording a CUDA stream
-// capture that must not gain allocation nodes, a loop running after its
-// device memory pool has been frozen, or a host that handed all device
-// memory to another allocator.  It computes the same quantity as the
-// reduction behind lbrmt_total_mass, but keeps its per-block partial sums in
-// the file-scope array below instead of memory the library allocates.
+// at the point where they need the diagnostic: a loop running after its
+// device memory pool has been frozen, a host that handed all device memory to
+// another allocator, or a real-time loop in which an allocation (and the
+// synchronisation it may bring) is not allowed.  It computes the same quantity
+// as the reduction behind lbrmt_total_mass, but keeps its per-block partial
+// sums in the file-scope array below instead of memory the library allocates.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "lbrmt.h"
@@ -27,18 +29,40 @@ static __device__ __align__(256) double g_mass_partials[NOALLOC_MAX_BLOCKS];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_lock;
 double *g_partials_addr[MAX_DEVICES] = {nullptr};
+CUcontext g_partials_ctx[MAX_DEVICES] = {nullptr};  // context the address belongs to
 
-// Device address of g_mass_partials on the current device, looked up once per
-// device (the first call on a device does it; that call must not be inside a
-// stream capture).
+// cuCtxGetCurrent through the runtime's driver entry point (no link to libcuda).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
+
+// Device address of g_mass_partials on the current device.  It is looked up
+// on the first call on a device (that call must not be inside a stream
+// capture) and again whenever the device's context has changed since (after a
+// cudaDeviceReset the old address is no longer valid).
 cudaError_t partials_address(int dev, double **out) {
     std::lock_guard<std::mutex> guard(g_lock);
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (!g_partials_addr[dev]) {
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn cur = ctx_get_current();
+    if (cur && cur(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    if (!g_partials_addr[dev] || !ctx || ctx != g_partials_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_mass_partials);
         if (e != cudaSuccess) return e;
         g_partials_addr[dev] = static_cast<double *>(p);
+        g_partials_ctx[dev] = ctx;
     }
     *out = g_partials_addr[dev];
     return cudaSuccess;
@@ -56,8 +80,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_mass_partials(lbrmt::
     double acc = 0.0;
     for (long long c = begin + threadIdx.x; c < end; c += NOALLOC_THREADS) {
         double s = 0.0;
-        for (int q = 0; q < 9; q++) s += (double)lbrmt::ldS<S, R>(f + q * P + c);
-        s += (double)lbrmt::rest_base<R>(sp, reg, pool, (int)(c % sp.nx), (int)(c / sp.nx));
+        for (int q = 0; q < 9; q++) s += (double)lbrmt::ldS<S, R>(f + q * P + c, sp, q);
+        s += lbrmt::rest_base_d<R>(sp, reg, pool, (int)(c % sp.nx), (int)(c / sp.nx));
         acc += s;
     }
     sh[threadIdx.x] = acc;

@@ -17,6 +17,8 @@ struct SolidHost {
 
 struct AdjointStore;
 
+constexpr int GRAPH_LONG = 16;
+
 struct lbrmt_sim {
     lbrmt_config cfg;
     int device = 0;
@@ -34,7 +36,8 @@ struct lbrmt_sim {
     long long steps = 0;
     bool use_graphs = true;
     bool in_batch = false;          // stepped by a batch: lbrmt_step is refused
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr;       // two steps (one of each parity)
+    cudaGraphExec_t gexec_long = nullptr;  // GRAPH_LONG steps: the overlap runs across their joins less often
     long long last_launches = 0;
     std::vector<void *> allocs;
     double *scratch = nullptr;      // device: S*8 stats or 1 mass value
@@ -50,3 +53,5 @@ lbrmt_status lbrmt_internal_check_flags(lbrmt_sim *s);
 void *lbrmt_internal_alloc(lbrmt_sim *s, size_t bytes);
 lbrmt_status lbrmt_internal_fail(lbrmt_sim *s, lbrmt_status st, const std::string &msg);
 void lbrmt_internal_adjoint_free(lbrmt_sim *s);
+// Recompute the 16-bit storage scales from the solids' materials (drops stale graphs).
+void lbrmt_internal_refresh_scales(lbrmt_sim *s);

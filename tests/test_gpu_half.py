@@ -2,13 +2,15 @@
 half-force stored as FP16 or BF16) with the FP64 oracle.
 
 The stored values are small deviations (f_q - w_q rho_f, the rest population
-relative to its SFC rest value) rounded to 2^-11 (FP16) or 2^-8 (BF16)
-relative each step; the error bounds below are the FP32 bound of
-test_gpu_parity.py with u_32 replaced by the storage unit roundoff u_s and
-the random walk of n roundings: fields rho, u and F must satisfy
-|err| <= 1e-5 |field|_max + 4 u_s (max|rho_s - rho_f| + |u|_max sqrt(n)) (rho, u),
-|err| <= 1e-5 |F|_max + 8 u_s max G + 4 u_s |F|_max (F, which feels the rounded velocity)
-and xi - x on the solid and first four layers within 64 u_s |u|_max n.
+relative to its SFC rest value, each plane scaled by its own power of two)
+rounded to the storage unit roundoff u_s (2^-11 for FP16, 2^-8 for BF16) at
+every step; everything else (Delta rho, the reference map, the stresses) is
+held as in the FP32 variant.  The bound is relative L-infinity per field, as
+for FP32, in units of u_s:
+  rho - rho_f, u : 4 u_s      F : 16 u_s (the stresses follow the rounded
+  xi - x (solid and first 4 layers): 2 u_s, whole band 4 u_s     velocity)
+measured over 1, 10 and 100 steps (4 at 4096^2): u, rho ~1.5 u_s, F up to
+~7 u_s, xi below 0.5 u_s.
 """
 import json
 import os
@@ -17,7 +19,7 @@ import numpy as np
 import pytest
 
 import scenarios
-from parity_util import FLOORS, run_pair
+from parity_util import run_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -83,12 +85,7 @@ def test_half_storage_full_size_mixing(prec):
 
 def _check_half(res, prec, sc):
     us = US[prec]
-    drho = max([abs(s["rho_s"] - sc["rho_f"]) for s in sc["solids"]] + [0.0])
-    gmax = max([s["G"] for s in sc["solids"]] + [0.0])
     for n, r in res.items():
-        walk = 4 * us * (drho + r["u_max"] * np.sqrt(n))
-        for k in ("rho", "u"):
-            scale = max(r[k + "_max"], FLOORS[k] * (sc["rho_f"] if k == "rho" else 1.0))
-            assert r[k + "_abs"] <= 1e-5 * scale + walk, (n, k, r)
-        assert r["F_abs"] <= 1e-5 * r["F_max"] + 8 * us * gmax + 4 * us * r["F_max"], (n, r)
-        assert r["xi"] <= 64 * us * max(r["u_max"], 1e-6) * n + 1e-6, (n, r)
+        for k, c in (("rho", 4), ("u", 4), ("F", 16), ("xi", 2), ("xi_band", 4), ("drho", 4)):
+            assert r[k] <= c * us, (n, k, r[k], c * us, r)
+        assert r["label_mismatch"] == 0, (n, r)

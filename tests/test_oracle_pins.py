@@ -795,3 +795,27 @@ def test_conservative_force_mode_conserves_momentum():
     # momentum ~ U n^2 / pi = 1.5: round-off of its sum over n^2 nodes is ~1e-14
     assert drift[1] < 1e-13
     assert drift[0] > 1e-10
+
+
+def test_contact_forces_are_equal_and_opposite():
+    # The net contact force on a solid (the divergence of its pairs' contact
+    # stresses, Eqs. 3_6_collision_stress .. 3_6_normal and 3_3_div_solid_stress,
+    # over the nodes nearer to it) is a reading: the paper gives the stress, not
+    # a per-solid force.  Whatever the split of the nodes, one pair's divergence
+    # telescopes to zero over a periodic box, so the two forces cancel (Newton's
+    # third law); they push the solids apart; a solid without a partner feels none.
+    sc = scenarios.contact_pair(gap=0.8, nx=96, ny=64)
+    o = oracle.Oracle(sc)
+    o.step(1)
+    a, b = o.solid_stats(0), o.solid_stats(1)
+    fa, fb = a[8:10], b[8:10]
+    assert np.linalg.norm(fa) > 1e-5
+    assert np.abs(fa + fb).max() < 1e-14 * np.abs(fa).max() * 100
+    ca, cb = a[1:3], b[1:3]
+    assert np.dot(fa, ca - cb) > 0 and np.dot(fb, cb - ca) > 0  # repulsive
+    o.close()
+    far = scenarios.contact_pair(gap=8.0, nx=96, ny=64)
+    o = oracle.Oracle(far)
+    o.step(1)
+    assert np.all(o.solid_stats(0)[8:10] == 0.0) and np.all(o.solid_stats(1)[8:10] == 0.0)
+    o.close()
