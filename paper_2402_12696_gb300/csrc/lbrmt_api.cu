@@ -133,6 +133,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         int m = 0;
         while (2 * (int)std::ceil(c.eps * std::ldexp(1.0, m + 1)) + 1 <= LAM_TAB_MAX) m++;
         sp.lam_h = (float)std::ldexp(1.0, -m);
+        sp.eps_lo = (float)(c.eps - (double)sp.eps_f);
         sp.lam_inv_h = (float)std::ldexp(1.0, m);
         sp.lam_k0 = (int)std::ceil(c.eps * std::ldexp(1.0, m));
     }
@@ -378,6 +379,7 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         sd[k].R_f = (float)h.R; sd[k].G_f = (float)h.G; sd[k].Rlo_f = (float)(h.R - (double)sd[k].R_f);
         sd[k].r2hi_f = (float)r2; sd[k].r2lo_f = (float)(r2 - (double)sd[k].r2hi_f); sd[k].r2lo = 0.0;
         sd[k].drho_f = (float)sd[k].drho; sd[k].accel_f = (float)sd[k].accel;
+        sd[k].drho_lo_f = (float)(sd[k].drho - (double)sd[k].drho_f);
         sd[k].T = h.T; sd[k].off = h.off;
     }
     // solid kernel launch order: largest tiles first, so the last CTAs to start are short

@@ -41,12 +41,24 @@ constexpr int TILE_SIDE_MAX = 448;          // largest solid tile side (byte lab
 constexpr int RMT_SMEM_MAX = ((TILE_SIDE_MAX * TILE_SIDE_MAX + 15) & ~15) + 8 * LIST_CAP;
 // Force pool, per registered tile, TILE_N values per plane: F_x and F_y of the
 // solid terms (without the body force), Delta rho as an unevaluated sum hi + lo
-// (lo = 0 in FP64; in FP32 the pair carries Delta rho to ~1e-15, so the SFC
-// equilibrium's rho - rho_t is not rounded against an O(1) number), and, with
-// force_mode 1 only, the blended solid acceleration's y component (plane 1 then
-// holds the stress divergence alone).
+// (two planes' worth, the pair of node lt at POOL_DRHO + 2 lt, read as one
+// 64-bit load in FP32; lo = 0 in FP64; in FP32 the pair carries Delta rho to
+// ~1e-15, so the SFC equilibrium's rho - rho_t is not rounded against an O(1)
+// number), and, with force_mode 1 only, the blended solid acceleration's y
+// component (plane 1 then holds the stress divergence alone).
 constexpr int POOL_STRIDE = 5 * TILE_N;
-constexpr int POOL_FX = 0, POOL_FY = TILE_N, POOL_DRHO = 2 * TILE_N, POOL_DRHO_LO = 3 * TILE_N, POOL_AY = 4 * TILE_N;
+constexpr int POOL_FX = 0, POOL_FY = TILE_N, POOL_DRHO = 2 * TILE_N, POOL_AY = 4 * TILE_N;
+// Delta rho (hi, lo) of the pool entry p (p points at the tile's plane 0 + lt)
+template <class R> __device__ __forceinline__ void pool_drho(const R *p, int lt, R &hi, R &lo) {
+    if constexpr (sizeof(R) == 4) {
+        const float2 v = *reinterpret_cast<const float2 *>(p - lt + POOL_DRHO + 2 * lt);
+        hi = v.x;
+        lo = v.y;
+    } else {
+        hi = p[POOL_DRHO + lt];
+        lo = R(0);
+    }
+}
 // Planes of a solid's tile: eta_x, eta_y and phi; FP32 adds the low parts of
 // eta_x and eta_y on the advected nodes (eta = hi + lo), so the rounding of
 // the stored reference map does not accumulate over the steps (zero on the
@@ -81,7 +93,7 @@ struct SimParams {
     float omega_f, kf_f, rho_f_f, lid_u_f, eps_f, eta_f, fy_f;
     double omega, kf, fy;  // 1/tau, 1 - 1/(2 tau), constant y body force
     // grid of the solid-fraction table (LamEntry): phi_k = (k - lam_k0) lam_h, lam_h a power of two
-    float lam_h, lam_inv_h;
+    float lam_h, lam_inv_h, eps_lo;  // eps_lo = eps - (float)eps
     int lam_k0;
     // 16-bit storage: power-of-two scale (and inverse) per population plane and of the carry
     float st_scale[9], st_inv[9], ct_scale, ct_inv;
@@ -129,7 +141,7 @@ struct SolidDesc {
     double a, b;                 // semi-axes / half-sides along x and y
     double eps;                  // the blur-zone half-width (a threshold of the level set)
     double r2lo, drho, accel;   // R^2 - (double)(float)R^2, rho_s - rho_f, -(1 - rho_f/rho_s) g
-    float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f, Rlo_f;  // Rlo_f = R - (float)R
+    float R_f, G_f, r2hi_f, r2lo_f, drho_f, accel_f, Rlo_f, drho_lo_f;  // *_lo_f: the double minus its float
     int T;
     long long off;      // element offset of the tile (eta_x plane, then eta_y plane)
 };
@@ -273,7 +285,7 @@ __device__ __forceinline__ long long grid_index(const SimParams &sp, int gx, int
 template <class R>
 __device__ __forceinline__ R rest_base(const SimParams &sp, const int *reg, const R *pool, int i, int j) {
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
-    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))]
+    return reg[tile] > 0 ? pool[(long long)tile * POOL_STRIDE + POOL_DRHO + 2 * (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)))]
                          : R(0);
 }
 // The rest base with its low part, in double (readouts and uploads).
@@ -281,8 +293,10 @@ template <class R>
 __device__ __forceinline__ double rest_base_d(const SimParams &sp, const int *reg, const R *pool, int i, int j) {
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
     if (reg[tile] <= 0) return 0.0;
-    const R *p = pool + (long long)tile * POOL_STRIDE + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1));
-    return (double)p[POOL_DRHO] + (double)p[POOL_DRHO_LO];
+    const int lt = ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1));
+    R hi, lo;
+    pool_drho<R>(pool + (long long)tile * POOL_STRIDE + lt, lt, hi, lo);
+    return (double)hi + (double)lo;
 }
 
 // a - b as an unevaluated sum: s = fl(a - b) and its exact error e, a - b = s + e
@@ -788,9 +802,10 @@ __device__ __forceinline__ void phi_node_ff(float ex, float ey, float exl, float
 // table (FP32 path).
 __device__ __forceinline__ void lambda_ff(const SimParams &sp, const LamEntry *tab, float ph, float pl, float &lh,
                                           float &ll) {
-    const double phd = (double)ph + (double)pl;  // the thresholds of Eq. 2_3_heaviside, exactly
-    if (phd <= -sp.eps) { lh = 1.0f; ll = 0.0f; return; }
-    if (phd >= sp.eps) { lh = 0.0f; ll = 0.0f; return; }
+    // the thresholds of Eq. 2_3_heaviside, exactly: phi + eps and phi - eps as
+    // float sums (ph -/+ eps_hi is exact near the threshold, Sterbenz)
+    if ((ph + sp.eps_f) + (pl + sp.eps_lo) <= 0.0f) { lh = 1.0f; ll = 0.0f; return; }
+    if ((ph - sp.eps_f) + (pl - sp.eps_lo) >= 0.0f) { lh = 0.0f; ll = 0.0f; return; }
     const int k = (int)rintf(ph * sp.lam_inv_h);
     const LamEntry t = tab[k + sp.lam_k0];
     const float dh = ph - (float)k * sp.lam_h;  // exact: phi_k is a multiple of lam_h within lam_h / 2 of ph
@@ -992,7 +1007,7 @@ __device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, 
     nd.cx = ldC<S, R>(a.carry + c, sp);
     nd.cy = ldC<S, R>(a.carry + sp.P + c, sp);
     nd.cnt = a.reg_prev[tile];
-    nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
+    nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + POOL_DRHO + 2 * (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)))];
 }
 
 // The rest of pass 0 for a gathered node of the blur zone or the solid:
@@ -1240,14 +1255,19 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                     // zone (the stresses and sets read hi; the density difference both)
                     R exl = R(0), eyl = R(0);
                     if (a.init || lab[t] > 0) {
-                        Xo[3 * TT + t] = R(0);
-                        Xo[4 * TT + t] = R(0);
+                        // the next step advects only nodes within a layer of this
+                        // step's solid (interfaces move less than one node per step):
+                        // their extrapolated eta has no low part
+                        if (a.init || lab[t] <= 2) {
+                            Xo[3 * TT + t] = R(0);
+                            Xo[4 * TT + t] = R(0);
+                        }
                     } else {
                         exl = Xo[3 * TT + t];  // the advection's low parts
                         eyl = Xo[4 * TT + t];
                     }
-                    R pl = R(0);
                     if (phi > -eps - R(PHI_D_SHELL) && phi < eps + R(PHI_D_SHELL)) {
+                        R pl;
                         if (rq.shape == 0) {
                             phi_node_ff(Xo[t], Yo[t], exl, eyl, lx, ly, fo, rq, sd.Rlo_f, phi, pl);
                         } else {
@@ -1257,8 +1277,8 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                             phi = R(dd);
                             pl = R(dd - (double)phi);
                         }
+                        Xo[5 * TT + t] = pl;  // read only where |phi| < eps + PHI_D_SHELL
                     }
-                    Xo[5 * TT + t] = pl;
                 }
                 Po[t] = phi;
                 if (phi < eps) {
@@ -1456,8 +1476,8 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 sG[rank] = pick<R>(sd.G, sd.G_f);
                 sD[rank] = pick<R>(sd.drho, sd.drho_f);
                 sA[rank] = pick<R>(sd.accel, sd.accel_f);
-                fs.sDh[rank] = (float)sd.drho;
-                fs.sDl[rank] = (float)(sd.drho - (double)(float)sd.drho);
+                fs.sDh[rank] = sd.drho_f;
+                fs.sDl[rank] = sd.drho_lo_f;
                 srq[rank] = Rsq<R>(sd);
                 sT[rank] = sd.T;
                 soff[rank] = sd.off;
@@ -1484,12 +1504,6 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                     X = Xs[ly * T + lx];
                     Y = Xs[T * T + ly * T + lx];
                     if (X == X) P = Xs[2 * T * T + ly * T + lx];  // the stored phi
-                    if constexpr (xi_planes<R>() == 6) {
-                        // the low part of phi that the Delta rho pass reads at the tile's
-                        // own nodes: into L1 now, while the stresses are formed
-                        if (wk.c >= 1 && wk.c <= TX && wk.r >= 1 && wk.r <= sp.ty)
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(Xs + 5 * T * T + ly * T + lx));
-                    }
                 }
                 sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
             }
@@ -1554,35 +1568,6 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
             eT[3 * e + 0] = Sxx + Cxx; eT[3 * e + 1] = Sxy + Cxy; eT[3 * e + 2] = Syy + Cyy;
         }
         __syncthreads();
-        // FP32: every slot's lambda at the tile's nodes as a float pair, into the
-        // staged eta (no longer read).  Delta rho = sum lambda (rho_s - rho_f) is an
-        // O(1) number whose rounding would drive the pressure, so in and near the
-        // blur zone lambda is formed from phi_0 of the exact eta + position (to
-        // ~1e-13), not from the stored FP32 phi (whose error is far below
-        // PHI_D_SHELL); elsewhere it is exactly 0 or 1.
-        if constexpr (sizeof(R) == 4) {
-            for (int it = threadIdx.x; it < n * TILE_N; it += blockDim.x) {
-                const int ks = it / TILE_N, lt = it - ks * TILE_N;
-                const int cx = lt & (TX - 1), cy = lt >> sp.lx;
-                const int i = i0 + cx, j = j0 + cy, p = (cy + 1) * PX + cx + 1;
-                const R ph = sP[ks * PN + p];
-                float lh = 0.0f, ll = 0.0f;
-                if (ph == ph && i < sp.nx && j < sp.ny) {
-                    if (ph <= -eps - R(PHI_D_SHELL)) lh = 1.0f;
-                    else if (ph < eps + R(PHI_D_SHELL)) {
-                        const Frame &fr = sfr[ks];
-                        const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
-                        const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
-                        const int T = sT[ks];
-                        const float phl = a.xi[soff[ks] + 5 * T * T + ly * T + lx];  // low part of phi
-                        lambda_ff(sp, a.lamtab, ph, phl, lh, ll);
-                    }
-                }
-                sX[ks * PN + p] = lh;
-                sY[ks * PN + p] = ll;
-            }
-            __syncthreads();
-        }
         // Node: divergence (Eq. 3_3_div_solid_stress), solid fraction, drho, solid acceleration.
         {
             const int cx = threadIdx.x & (TX - 1), cy = threadIdx.x >> sp.lx;
@@ -1595,10 +1580,26 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 const int p = (cy + 1) * PX + cx + 1;
                 R L = 0, Ay = 0, Dh = 0, Dl = 0;
                 if constexpr (sizeof(R) == 4) {
-                    // float-float sums of lambda and lambda (rho_s - rho_f)
+                    // Delta rho = sum lambda (rho_s - rho_f) is an O(1) number whose
+                    // rounding would drive the pressure: lambda comes as a float pair
+                    // from the level set's pair (the relabel's low part) in and near
+                    // the blur zone, exactly 0 or 1 elsewhere; float-float sums
                     float Lh = 0.0f, Ll = 0.0f;
                     for (int ks = 0; ks < n; ks++) {
-                        const float lh = sX[ks * PN + p], ll = sY[ks * PN + p];
+                        const R ph = sP[ks * PN + p];
+                        if (!(ph == ph)) continue;
+                        float lh = 0.0f, ll = 0.0f;
+                        // phi's low part exists where |phi| < eps + PHI_D_SHELL (the relabel's
+                        // test, on its FP32 phi); within half that shell it is read
+                        if (ph <= -eps - R(0.5f * PHI_D_SHELL)) lh = 1.0f;
+                        else if (ph < eps + R(0.5f * PHI_D_SHELL)) {
+                            const Frame &fr = sfr[ks];
+                            const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
+                            const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
+                            const int T = sT[ks];
+                            lambda_ff(sp, a.lamtab, ph, a.xi[soff[ks] + 5 * T * T + ly * T + lx], lh, ll);
+                        }
+                        if (lh == 0.0f) continue;
                         L += lh;
                         Ay += lh * sA[ks];
                         ff_add(Lh, Ll, lh, ll);
@@ -1628,8 +1629,9 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 } else {
                     po[POOL_FY] = fsy + Ay;
                 }
-                po[POOL_DRHO] = Dh;
-                po[POOL_DRHO_LO] = Dl;
+                R *pd = a.pool + (long long)tile * POOL_STRIDE + POOL_DRHO + 2 * threadIdx.x;
+                pd[0] = Dh;
+                pd[1] = Dl;
             }
         }
         __syncthreads();
@@ -1687,11 +1689,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
         f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt, sp, q) : ldG<S, R>(a.fin_q[q] + c, sp, q);
     R dro = R(0), dro_lo = R(0);  // rest base: Delta rho of the step that wrote f (hi + lo)
-    if (prev_count > 0) {
-        const R *pp = a.pool_prev + (long long)tile * POOL_STRIDE + lt;
-        dro = pp[POOL_DRHO];
-        if constexpr (sizeof(R) == 4) dro_lo = pp[POOL_DRHO_LO];
-    }
+    if (prev_count > 0) pool_drho<R>(a.pool_prev + (long long)tile * POOL_STRIDE + lt, lt, dro, dro_lo);
     const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const R dr = dro + ds;  // rho - rho_f
     const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -1711,8 +1709,7 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     }
     if (REG && a.reg_count[tile] > 0) {
         const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
-        drt = po[POOL_DRHO];
-        if constexpr (sizeof(R) == 4) drt_lo = po[POOL_DRHO_LO];
+        pool_drho<R>(po, lt, drt, drt_lo);
         if (sp.force_mode == 1) {
             // conservative form: the stress divergence enters the Guo term without rho
             Fx += po[POOL_FX] * inv;
@@ -2140,12 +2137,15 @@ __global__ void solid_field_kernel(SimParams sp, const R *xi, const Frame *frame
         const long long c = grid_index(sp, gx, gy);
         double v;
         // xi = eta + l + off + X_c
+        // the low parts of eta are kept on the solid's nodes (phi < 0; the band's are
+        // refitted every step and carry none)
+        const bool low = xi_planes<R>() == 6 && xi[sd.off + 2 * T * T + t] < R(0);
         if (kind == 0) {
             v = (double)X + ((double)lx + (double)fr.offx + sd.xc);
-            if constexpr (xi_planes<R>() == 6) v += (double)xi[sd.off + 3 * T * T + t];  // low part
+            if (low) v += (double)xi[sd.off + 3 * T * T + t];
         } else if (kind == 1) {
             v = (double)Y + ((double)ly + (double)fr.offy + sd.yc);
-            if constexpr (xi_planes<R>() == 6) v += (double)xi[sd.off + 4 * T * T + t];
+            if (low) v += (double)xi[sd.off + 4 * T * T + t];
         } else if (kind == 2) v = (double)xi[sd.off + 2 * T * T + t];
         else {
             if (!(xi[sd.off + 2 * T * T + t] < -R(PHI_TIE))) continue;
@@ -2194,7 +2194,7 @@ __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, co
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c, sp, q);
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
     nd.reg = reg[tile];
-    nd.pool = pool[(long long)tile * POOL_STRIDE + POOL_DRHO + ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1))];
+    nd.pool = pool[(long long)tile * POOL_STRIDE + POOL_DRHO + 2 * (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)))];
     nd.cx = ldC<S, R>(carry + c, sp);
     nd.cy = ldC<S, R>(carry + sp.P + c, sp);
     nd.inner = nd.lx > fr.bx0 && nd.lx < fr.bx1 && nd.ly > fr.by0 && nd.ly < fr.by1;
