@@ -616,6 +616,7 @@ def bench_lbrmt(args):
                      "step_bytes_model": f"N*18*{sf} + 24*B per step, B = sum pi (r + 11)^2 = "
                                          f"{band_cells(sc) / N:.3f} N ({sbytes / N:.1f} B/LU)",
                      "active_tiles": nact, "active_frac": band_frac},
+        "error_vs_oracle": precision_errors(args.precision) if args.size == 4096 else None,
         "precisions": precisions,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

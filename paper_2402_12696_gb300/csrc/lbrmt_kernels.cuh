@@ -980,7 +980,7 @@ __device__ __forceinline__ bool list_layers(const signed char *lab, int T, int x
 template <class R>
 struct P0Node {
     int ix, iy, cnt;
-    R ex, ey, exl, eyl, phi, cx, cy, pv;
+    R ex, ey, phi, cx, cy, pv;
     R f[9];
 };
 
@@ -996,12 +996,6 @@ __device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, 
     nd.ex = Xi[k];
     nd.ey = Yi[k];
     nd.phi = Pi[k];
-    if constexpr (xi_planes<R>() == 6) {
-        nd.exl = Xi[3 * T * T + k];  // the low parts follow the phi plane
-        nd.eyl = Xi[4 * T * T + k];
-    } else {
-        nd.exl = nd.eyl = R(0);
-    }
 #pragma unroll
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(a.f + q * sp.P + c, sp, q);
     nd.cx = ldC<S, R>(a.carry + c, sp);
@@ -1035,6 +1029,9 @@ __device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, 
     const int k1 = k + sx, k2 = k + 2 * sx, k3 = k + sy * T, k4 = k + 2 * sy * T;
     const R X1 = Xi[k1], X2 = Xi[k2], X3 = Xi[k3], X4 = Xi[k4];
     const R Y1 = Yi[k1], Y2 = Yi[k2], Y3 = Yi[k3], Y4 = Yi[k4];
+    // the low parts of eta (FP32) follow the phi plane; loaded with the stencil
+    const R exl = xi_planes<R>() == 6 ? Xi[3 * T * T + k] : R(0);
+    const R eyl = xi_planes<R>() == 6 ? Xi[4 * T * T + k] : R(0);
     if (!(X1 == X1 && X2 == X2 && X3 == X3 && X4 == X4)) atomicOr(a.err, ERR_STENCIL);
     // one-sided second-order differences of eta; xi = eta + position adds (1,0)/(0,1)
     const R ex = nd.ex, ey = nd.ey;
@@ -1051,13 +1048,13 @@ __device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, 
         R e1, e2;
         R s1 = two_diff<R>(ex, -ddx, e1);
         R s2 = two_diff<R>(s1, dX, e2);
-        R tl = (e1 + e2) + nd.exl;
+        R tl = (e1 + e2) + exl;
         R hi = s2 + tl;
         Xo[t] = hi;
         Xo[3 * T * T + t] = tl - (hi - s2);
         s1 = two_diff<R>(ey, -ddy, e1);
         s2 = two_diff<R>(s1, dY, e2);
-        tl = (e1 + e2) + nd.eyl;
+        tl = (e1 + e2) + eyl;
         hi = s2 + tl;
         Yo[t] = hi;
         Xo[4 * T * T + t] = tl - (hi - s2);
