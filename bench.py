@@ -364,13 +364,15 @@ def band_cells(sc, layers=11):
 def k1_bytes(N, prec, active_tiles):
     """Algorithmic bytes of one K1 launch.  'survey': the populations in and out
     (18 s_f per node) and the stored force density read on the registered tiles
-    (2 x 4 B per node there).  'state': everything K1 must move as built -- the
-    populations, the half-force carry in and out (4 s_f), and on registered
-    tiles F_x, F_y and Delta rho (hi, lo) of this step plus the rest base (hi,
-    lo) of the previous step (6 s_r)."""
+    (2 x 4 B per node there).  'state': everything K1 moves as built -- the
+    populations, the density plane read at every node (s_f) and written off
+    the registered tiles (s_f), and on registered tiles F_x, F_y, Delta rho
+    (hi, lo) and the half-force written, plus the previous step's rest base
+    (hi, lo) and half-force read (10 s_r; the previous registry is taken to be
+    as large as this one)."""
     sf, sr = STORE_BYTES[prec], REAL_BYTES[prec]
     tn = active_tiles * 256
-    return {"survey": N * 18 * sf + tn * 8, "state": N * (18 * sf + 4 * sf) + tn * 6 * sr}
+    return {"survey": N * 18 * sf + tn * 8, "state": N * 19 * sf + (N - tn) * sf + tn * 10 * sr}
 
 
 def step_bytes(N, prec, sc):
@@ -609,9 +611,10 @@ def bench_lbrmt(args):
                      "bytes_model": f"survey: N*18*{sf} + 8*256*active_tiles per launch "
                                     f"({kb['survey'] / N:.1f} B/LU)",
                      "frac_state": kb["state"] / (k1_ms / 1e3) / 1e9 / peak,
-                     "bytes_model_state": f"N*(18*{sf} + 4*{sf}) + 6*{REAL_BYTES[args.precision]}*256*active_tiles "
-                                          f"per launch ({kb['state'] / N:.1f} B/LU): populations, half-force carry, "
-                                          "force pool and both rest bases",
+                     "bytes_model_state": f"N*19*{sf} + (N - 256*active_tiles)*{sf} + "
+                                          f"10*{REAL_BYTES[args.precision]}*256*active_tiles per launch "
+                                          f"({kb['state'] / N:.1f} B/LU): populations, density plane, force pool "
+                                          "with both half-force planes and both rest bases",
                      "step_frac": sbytes / (ms_max / args.steps / 1e3) / 1e9 / peak,
                      "step_bytes_model": f"N*18*{sf} + 24*B per step, B = sum pi (r + 11)^2 = "
                                          f"{band_cells(sc) / N:.3f} N ({sbytes / N:.1f} B/LU)",

@@ -63,7 +63,7 @@ static void collect_state(lbrmt_sim *s, AdjointStore &A) {
         A.bufs.push_back({d.pool[k], ntiles * POOL_STRIDE * rs});
         A.bufs.push_back({d.busy[k], (size_t)s->sp.nrx * s->sp.nty});
     }
-    A.bufs.push_back({d.carry, 2 * P * ss});
+    A.bufs.push_back({d.carry, P * ss});
     A.bufs.push_back({d.stats_step, S * 64});
     A.state_bytes = 0;
     for (auto &b : A.bufs) A.state_bytes += (b.second + 255) & ~(size_t)255;

@@ -165,7 +165,7 @@ extern "C" lbrmt_status lbrmt_create(const lbrmt_config *cfg, void *cuda_stream,
         ok = ok && (d.pool[k] = dalloc(s, ntiles * POOL_STRIDE * rs));
         ok = ok && (d.busy[k] = (unsigned char *)dalloc(s, nregions));
     }
-    ok = ok && (d.carry = dalloc(s, 2 * P * ss));
+    ok = ok && (d.carry = dalloc(s, P * ss));
     ok = ok && (d.fbody = dalloc(s, (size_t)c.ny * rs));
     if (c.force_kind == LBRMT_FORCE_FIELD) ok = ok && (d.bfield = dalloc(s, 2 * P * rs));
     ok = ok && (d.mass_partials = (double *)dalloc(s, nparts * 8));
@@ -307,13 +307,13 @@ lbrmt_status lbrmt_internal_fail(lbrmt_sim *s, lbrmt_status st, const std::strin
 // Solid descriptors and initial frames from the host solids; configure and run
 // the initialisation kernels (Algorithm 1, initialisation) on the allocated state.
 // Power-of-two storage scales of the 16-bit variants, per population plane and
-// for the half-force carry, from bounds of the stored values: with the
+// for the density plane, from bounds of the stored values: with the
 // velocity bounded by U = 0.3 (above the Mach limit of Appendix A), the density
 // difference D = max |rho_s - rho_f|, a pressure deviation of 0.1 rho_f and
 // rho_max = rho_f + D + 0.1 rho_f, a stored deviation of plane q is below
 // w_q (0.1 rho_f + D + rho_max (3 sqrt2 U + 10.5 U^2)) (q >= 1), w_0 (0.1 rho_f + D
-// + 1.5 rho_max U^2) (the rest plane, relative to Delta rho), and the carry
-// rho F / 2 below rho_max (|f| + g + 2 G_max + 1e-3) / 2.  Each bound is mapped
+// + 1.5 rho_max U^2) (the rest plane, relative to Delta rho), and the density
+// plane rho - rho_f below 0.1 rho_f + D.  Each bound is mapped
 // below 2^15 (FP16's largest value is 65504).  FP32 / FP64 storage: scale 1.
 static void set_store_scales(lbrmt_sim *s) {
     SimParams &sp = s->sp;
@@ -321,11 +321,8 @@ static void set_store_scales(lbrmt_sim *s) {
     sp.ct_scale = sp.ct_inv = 1.0f;
     if (s->eng->store_size != 2) return;
     const lbrmt_config &c = s->cfg;
-    double D = 0.0, Gm = 0.0;
-    for (const SolidHost &h : s->solids) {
-        D = std::max(D, std::fabs(h.rho_s - c.rho_f));
-        Gm = std::max(Gm, h.G);
-    }
+    double D = 0.0;
+    for (const SolidHost &h : s->solids) D = std::max(D, std::fabs(h.rho_s - c.rho_f));
     const double U = 0.3, rmax = c.rho_f * 1.1 + D;
     auto scale_for = [](double bound) {
         int k = (int)std::floor(std::log2(32768.0 / bound));
@@ -339,8 +336,7 @@ static void set_store_scales(lbrmt_sim *s) {
         sp.st_scale[q] = scale_for(b);
         sp.st_inv[q] = 1.0f / sp.st_scale[q];
     }
-    const double F = std::fabs(c.force_a[0]) + std::fabs(c.force_a[1]) + c.gravity + 2.0 * Gm + 1e-3;
-    sp.ct_scale = scale_for(0.5 * rmax * F);
+    sp.ct_scale = scale_for(0.1 * c.rho_f + D);
     sp.ct_inv = 1.0f / sp.ct_scale;
 }
 
@@ -407,7 +403,11 @@ static lbrmt_status run_init(lbrmt_sim *s) {
         e = cudaMemsetAsync(d.reg_count[k], 0, ntiles * 4, s->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(d.reg_nactive[k], 0, 16, s->stream);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.carry, 0, 2 * (size_t)s->sp.P * s->eng->store_size, s->stream);
+    // the pools' half-force planes of the initial registry must read zero (the
+    // density plane is marked "no collision yet" by the initialisation kernel)
+    const size_t rsz = s->eng->real_size;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++)
+        e = cudaMemsetAsync(d.pool[k], 0, ntiles * POOL_STRIDE * rsz, s->stream);
     // the slots a tile shape's K1 does not write must hold zero (a previous shape may have written them)
     if (e == cudaSuccess) e = cudaMemsetAsync(d.mass_partials, 0, (size_t)s->mass_parts_cap * 8, s->stream);
     // every region counts as busy for the first step's check of the previous classification

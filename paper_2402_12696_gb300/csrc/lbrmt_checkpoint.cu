@@ -2,8 +2,9 @@
 // lbrmt_load): the whole state that Algorithm 1 carries from step n to n+1.
 //
 // The state is every persistent device buffer of the simulation, both halves
-// of each ping-pong pair: the populations f and the half-force carry of the
-// last collision (Sec. 3.4), the reference-map tiles xi with the level-set
+// of each ping-pong pair: the populations f and the density plane of the
+// last collision (with the pools' half-force planes, the term rho F / 2 of
+// Sec. 3.4's moments), the reference-map tiles xi with the level-set
 // plane and their frames (Sec. 3.1-3.2), the tile registries with the force
 // pools of the last step (Sec. 3.3), the regions' busy flags of the overlapped
 // schedule, the body-force rows or field, the per-solid descriptors and
@@ -73,7 +74,7 @@ int sections(const lbrmt_sim *s, Section *out) {
         add(d.xi[k], (size_t)s->xi_total * rs);
         add(d.frame[k], S * sizeof(Frame));
     }
-    add(d.carry, 2 * P * ss);
+    add(d.carry, P * ss);
     add(d.fbody, (size_t)s->sp.ny * rs);
     if (s->cfg.force_kind == LBRMT_FORCE_FIELD) add(d.bfield, 2 * P * rs);
     add(d.mass_partials, (size_t)s->mass_parts_cap * 8);

@@ -138,7 +138,7 @@ extern const EngineOps engine_fp16;
 extern const EngineOps engine_bf16;
 
 template <class R, class S>
-__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, const int *reg, const R *pool,
+__global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, const int *reg, R *pool,
                                unsigned *err) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sp.P) return;
@@ -151,23 +151,29 @@ __global__ void set_pop_kernel(SimParams sp, const double *src, S *f, S *carry, 
         stS<S, R>(f + q * sp.P + c, v, sp, q);
     }
     if (ov) atomicOr(err, ERR_OVERFLOW16);
-    stC<S, R>(carry + c, R(0), sp);
-    stC<S, R>(carry + sp.P + c, R(0), sp);
+    // no previous collision: a zero half-force term in the next step's moments
+    stC<S, R>(carry + c, R(NAN), sp);
+    const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    if (reg[tile] > 0) {
+        R *po = pool + (long long)tile * POOL_STRIDE + (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)));
+        po[POOL_CX] = R(0);
+        po[POOL_CY] = R(0);
+    }
 }
 
 template <class R, class S>
 struct Engine {
-    // Tensor maps over the population buffers (nx x ny x 9) and the half-force
-    // (nx x ny x 2) with one registry tile per box; needs rows of 16-byte multiples.
+    // Tensor maps over the population buffers (nx x ny x 9) and the density
+    // plane (nx x ny x 1) with one registry tile per box; needs rows of 16-byte multiples.
     static void configure_tma(const SimParams &sp, const DevState &d, LaunchInfo *li, int nsm) {
         li->tma = false;
         EncodeTiledFn enc = encode_tiled_fn();
         const size_t ss = sizeof(S);
         if (!enc || ((size_t)sp.nx * ss) % 16 != 0) return;
         const cuuint64_t dimf[3] = {(cuuint64_t)sp.nx, (cuuint64_t)sp.ny, 9};
-        const cuuint64_t dimc[3] = {(cuuint64_t)sp.nx, (cuuint64_t)sp.ny, 2};
+        const cuuint64_t dimc[3] = {(cuuint64_t)sp.nx, (cuuint64_t)sp.ny, 1};
         const cuuint64_t str[2] = {(cuuint64_t)sp.nx * ss, (cuuint64_t)sp.P * ss};
-        const cuuint32_t boxf[3] = {(cuuint32_t)sp.tx, (cuuint32_t)sp.ty, 9}, boxc[3] = {(cuuint32_t)sp.tx, (cuuint32_t)sp.ty, 2};
+        const cuuint32_t boxf[3] = {(cuuint32_t)sp.tx, (cuuint32_t)sp.ty, 9}, boxc[3] = {(cuuint32_t)sp.tx, (cuuint32_t)sp.ty, 1};
         const cuuint32_t es[3] = {1, 1, 1};
         bool ok = true;
         for (int k = 0; k < 2 && ok; k++)
@@ -178,7 +184,7 @@ struct Engine {
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
         if (!ok) return;
-        li->lb_smem = 2 * 11 * TILE_N * (int)ss + 128;  // + alignment of the stages
+        li->lb_smem = 2 * 10 * TILE_N * (int)ss + 128;  // + alignment of the stages
         if (cudaFuncSetAttribute(lb_tma_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, li->lb_smem) !=
             cudaSuccess)
             return;
@@ -232,6 +238,8 @@ struct Engine {
         const int p = parity, q = 1 - parity;
         a.f = (const S *)d.f[p];
         a.carry = (const S *)d.carry;
+        a.fbody = (const R *)d.fbody;
+        a.bfield = (const R *)d.bfield;
         a.reg_prev = d.reg_count[q];
         a.pool_prev = (const R *)d.pool[q];
         a.xi_in = (const R *)d.xi[p];
@@ -289,7 +297,7 @@ struct Engine {
         a.bfield = (const R *)d.bfield;
         a.tape = nullptr;
         a.reg_count = d.reg_count[p];
-        a.pool = (const R *)d.pool[p];
+        a.pool = (R *)d.pool[p];
         a.clr_count = d.reg_count[q];
         a.clr_nactive = d.reg_nactive[q];
         a.pool_prev = (const R *)d.pool[q];
@@ -451,6 +459,7 @@ struct Engine {
     static cudaError_t stats(const SimParams &sp, const DevState &d, int cur, double *out, cudaStream_t st) {
         if (sp.nsolids == 0) return cudaSuccess;
         solid_stats_kernel<R, S><<<sp.nsolids, STATS_THREADS, 0, st>>>(sp, (const S *)d.f[cur], (const S *)d.carry,
+                                                             (const R *)d.fbody, (const R *)d.bfield,
                                                              d.reg_count[1 - cur], d.reg_solids[1 - cur],
                                                              (const R *)d.pool[1 - cur], (const R *)d.xi[cur],
                                                              d.frame[cur], d.solids, out);
@@ -466,7 +475,7 @@ struct Engine {
     static cudaError_t set_pop(const SimParams &sp, const DevState &d, int cur, const double *src, cudaStream_t st) {
         const int nb = (int)((sp.P + 255) / 256);
         set_pop_kernel<R, S><<<nb, 256, 0, st>>>(sp, src, (S *)d.f[cur], (S *)d.carry, d.reg_count[1 - cur],
-                                                 (const R *)d.pool[1 - cur], d.err);
+                                                 (R *)d.pool[1 - cur], d.err);
         return cudaGetLastError();
     }
 

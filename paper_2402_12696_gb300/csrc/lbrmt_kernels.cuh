@@ -44,10 +44,13 @@ constexpr int RMT_SMEM_MAX = ((TILE_SIDE_MAX * TILE_SIDE_MAX + 15) & ~15) + 8 * 
 // (two planes' worth, the pair of node lt at POOL_DRHO + 2 lt, read as one
 // 64-bit load in FP32; lo = 0 in FP64; in FP32 the pair carries Delta rho to
 // ~1e-15, so the SFC equilibrium's rho - rho_t is not rounded against an O(1)
-// number), and, with force_mode 1 only, the blended solid acceleration's y
-// component (plane 1 then holds the stress divergence alone).
-constexpr int POOL_STRIDE = 5 * TILE_N;
+// number), with force_mode 1 only, the blended solid acceleration's y
+// component (plane 1 then holds the stress divergence alone), and the
+// half-force rho F / 2 of the collision that used the entry (planes 5 and 6,
+// written by the LB kernel, read by the next step's moments).
+constexpr int POOL_STRIDE = 7 * TILE_N;
 constexpr int POOL_FX = 0, POOL_FY = TILE_N, POOL_DRHO = 2 * TILE_N, POOL_AY = 4 * TILE_N;
+constexpr int POOL_CX = 5 * TILE_N, POOL_CY = 6 * TILE_N;
 // Delta rho (hi, lo) of the pool entry p (p points at the tile's plane 0 + lt)
 template <class R> __device__ __forceinline__ void pool_drho(const R *p, int lt, R &hi, R &lo) {
     if constexpr (sizeof(R) == 4) {
@@ -165,14 +168,15 @@ __host__ __device__ __forceinline__ bool in_box(const Frame &f, int x, int y) {
 // Device pointers of one simulation (type-erased; the kernels cast).
 struct DevState {
     void *f[2];            // 9 planes each
-    void *carry;           // 2 planes: rho^n F^n / 2 of the last collision
+    void *carry;           // 1 plane: rho^n - rho_f of the last collision where its
+                           // registry did not hold the node's tile (NaN: no collision yet)
     void *xi[2];           // solid tiles
     Frame *frame[2];       // frame of xi[k] per solid
     int *reg_count[2];     // per tile: solids registered
     int *reg_solids[2];    // per tile: KMAX ids
     int *reg_active[2];    // list of tiles with count > 0
     int *reg_nactive[2];
-    void *pool[2];         // per tile: Fx_pool, Fy_pool, drho (TILE_N each)
+    void *pool[2];         // per tile: POOL_STRIDE values (layout above)
     void *bfield;          // force_kind 3: body force field, x plane then y plane (nx*ny each)
     LamEntry *lamtab;      // solid-fraction table (FP32 arithmetic)
     int *order;            // solids by decreasing tile side (launch order of the solid kernel)
@@ -219,9 +223,11 @@ template <class R> __device__ __forceinline__ R heaviside(R phi, R eps) {
 // Level set of a disk in solid-local reference coordinates, phi_0(X) = |X - c| - R.
 template <class R> __device__ __forceinline__ R phi_disk(R X, R Y, R rad) { return rsqrt_<R>(X * X + Y * Y) - rad; }
 
-// Storage of the populations and of the half-force carry.  FP32/FP64 store the
-// values as they are.  The 16-bit variants store value x scale with a
-// power-of-two scale (exact) per population plane q and one for the carry,
+// Storage of the populations and of the density plane (rho - rho_f of the last
+// collision, from which the next step rebuilds its half-force term off the
+// registered tiles).  FP32/FP64 store the values as they are.  The 16-bit
+// variants store value x scale with a power-of-two scale (exact) per population
+// plane q and one for the density plane,
 // chosen at initialisation from bounds of the values (SimParams::st_scale,
 // ct_scale): the largest value the bound admits fills about half of FP16's
 // range, so small deviations stay normal numbers; a stored FP16 value beyond
@@ -244,7 +250,7 @@ template <class S, class R> __device__ __forceinline__ void stS(S *p, R v, const
     if constexpr (is16<S>()) *p = from_f<S>(float(v) * sp.st_scale[q]);
     else *p = S(v);
 }
-// half-force carry
+// density plane
 template <class S, class R> __device__ __forceinline__ R ldC(const S *p, const SimParams &sp) {
     if constexpr (is16<S>()) return R(to_f<S>(*p) * sp.ct_inv);
     else return R(*p);
@@ -261,6 +267,11 @@ template <class S, class R> __device__ __forceinline__ R ldG(const S *p, const S
 // a stored FP16 population of plane q would exceed the format's range
 template <class S, class R> __device__ __forceinline__ bool store_overflow(R v, const SimParams &sp, int q) {
     if constexpr (std::is_same<S, __half>::value) return fabsf(float(v)) * sp.st_scale[q] > 60000.0f;
+    else return false;
+}
+// the same for the density plane
+template <class S, class R> __device__ __forceinline__ bool store_overflow_c(R v, const SimParams &sp) {
+    if constexpr (std::is_same<S, __half>::value) return fabsf(float(v)) * sp.ct_scale > 60000.0f;
     else return false;
 }
 
@@ -324,15 +335,63 @@ __device__ __forceinline__ void moments_from(const SimParams &sp, const R (&fq)[
     v = (jy + cy) * inv;
 }
 
+// Body force of node c in row j (Eq. 2_4_F_divs' f): the per-node field of
+// force_kind 3, else the per-row x component and the constant y component.
+template <class R>
+__device__ __forceinline__ void body_force(const SimParams &sp, const R *fbody, const R *bfield, int j, long long c,
+                                           R &Fx, R &Fy) {
+    if (sp.force_kind == 3) {
+        Fx = bfield[c];
+        Fy = bfield[sp.P + c];
+    } else {
+        Fx = fbody[j];
+        Fy = pick<R>(sp.fy, sp.fy_f);
+    }
+}
+
+// Half-force term rho^{n-1} F^{n-1} / 2 of the moments (Sec. 3.4) at a node
+// whose tile the previous step's registry did not hold: that step's force was
+// the body force alone (Fx, Fy: the field is the same at every step) and its
+// density rho_f + drp, so the product is the one the LB kernel formed then, to
+// the bit.  (On registered tiles the pool holds the product itself, planes
+// POOL_CX / POOL_CY.)  drp NaN: the populations have no previous collision
+// (initialisation, an upload), and the term is zero.
+template <class R>
+__device__ __forceinline__ void free_carry(const SimParams &sp, R drp, R Fx, R Fy, R &cx, R &cy) {
+    const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + drp;
+    const bool none = !(drp == drp);
+    cx = none ? R(0) : R(0.5) * rho * Fx;
+    cy = none ? R(0) : R(0.5) * rho * Fy;
+}
+
+// The half-force term of node (i, j), c = j nx + i: from the pool of the
+// registry reg where it holds the node's tile, else from the density plane.
 template <class R, class S>
-__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const S *carry, const int *reg,
-                                             const R *pool, int i, int j, R &rho, R &u, R &v) {
+__device__ __forceinline__ void node_carry(const SimParams &sp, const S *carry, const R *fbody, const R *bfield,
+                                           const int *reg, const R *pool, int i, int j, long long c, R &cx, R &cy) {
+    const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    if (reg[tile] > 0) {
+        const R *po = pool + (long long)tile * POOL_STRIDE + (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)));
+        cx = po[POOL_CX];
+        cy = po[POOL_CY];
+    } else {
+        R Fx, Fy;
+        body_force<R>(sp, fbody, bfield, j, c, Fx, Fy);
+        free_carry<R>(sp, ldC<S, R>(carry + c, sp), Fx, Fy, cx, cy);
+    }
+}
+
+template <class R, class S>
+__device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, const S *carry, const R *fbody,
+                                             const R *bfield, const int *reg, const R *pool, int i, int j, R &rho,
+                                             R &u, R &v) {
     const long long c = (long long)j * sp.nx + i;
     R fq[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) fq[q] = ldS<S, R>(f + q * sp.P + c, sp, q);
-    moments_from<R>(sp, fq, rest_base<R>(sp, reg, pool, i, j), ldC<S, R>(carry + c, sp), ldC<S, R>(carry + sp.P + c, sp), rho,
-                    u, v);
+    R cx, cy;
+    node_carry<R, S>(sp, carry, fbody, bfield, reg, pool, i, j, c, cx, cy);
+    moments_from<R>(sp, fq, rest_base<R>(sp, reg, pool, i, j), cx, cy, rho, u, v);
 }
 
 // Block-wide sum of NV doubles (blockDim.x multiple of 32, <= 1024).
@@ -362,7 +421,8 @@ __device__ void block_sum(double (&v)[NV], double *sh /* 32*NV */) {
 template <class R, class S>
 struct RmtArgs {
     const S *f;          // populations f^n
-    const S *carry;
+    const S *carry;      // density plane of the step that wrote f^n
+    const R *fbody, *bfield;  // body force (per row; per node with force_kind 3)
     const int *reg_prev; // registry and pool of the step that wrote f^n
     const R *pool_prev;
     const R *xi_in;      // xi^n tiles (unused at init)
@@ -998,10 +1058,14 @@ __device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, 
     nd.phi = Pi[k];
 #pragma unroll
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(a.f + q * sp.P + c, sp, q);
-    nd.cx = ldC<S, R>(a.carry + c, sp);
-    nd.cy = ldC<S, R>(a.carry + sp.P + c, sp);
     nd.cnt = a.reg_prev[tile];
-    nd.pv = a.pool_prev[(long long)tile * POOL_STRIDE + POOL_DRHO + 2 * (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)))];
+    // rest base and half-force term from the pool (its address is valid whether
+    // or not the tile is registered; every node listed here is: see p0_finish)
+    const int lt = ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1));
+    const R *po = a.pool_prev + (long long)tile * POOL_STRIDE + lt;
+    nd.pv = po[POOL_DRHO + lt];  // hi part of the (hi, lo) pair of node lt
+    nd.cx = po[POOL_CX];
+    nd.cy = po[POOL_CY];
 }
 
 // The rest of pass 0 for a gathered node of the blur zone or the solid:
@@ -1010,11 +1074,21 @@ __device__ __forceinline__ void p0_gather(const SimParams &sp, const RmtArgs<R, 
 template <class R, class S>
 __device__ __forceinline__ void p0_finish(const SimParams &sp, const RmtArgs<R, S> &a, const P0Node<R> &nd,
                                           const R *Xi, const R *Yi, R *Xo, R *Yo, signed char *lab, int T,
-                                          const Frame &fi, int shx, int shy, R ddx, R ddy, R eps, R (&stl)[6],
+                                          const Frame &fi, int2 oo, int shx, int shy, R ddx, R ddy, R eps, R (&stl)[6],
                                           int (&sb)[4]) {
     const int ix = nd.ix, iy = nd.iy, lx = ix - shx, ly = iy - shy;
-    R rho, u, v;
-    moments_from<R>(sp, nd.f, nd.cnt > 0 ? nd.pv : R(0), nd.cx, nd.cy, rho, u, v);
+    R rho, u, v, cx = nd.cx, cy = nd.cy;
+    if (nd.cnt <= 0) {
+        // Not expected: the previous registry covers the blur zone of phi^n grown
+        // by one node, which holds every node listed here.  Then the half-force
+        // term comes from the density plane and the body force.
+        const int i = wrapi(oo.x + ix - shx, sp.nx), j = wrapi(oo.y + iy - shy, sp.ny);
+        const long long c = (long long)j * sp.nx + i;
+        R Fx, Fy;
+        body_force<R>(sp, a.fbody, a.bfield, j, c, Fx, Fy);
+        free_carry<R>(sp, ldC<S, R>(a.carry + c, sp), Fx, Fy, cx, cy);
+    }
+    moments_from<R>(sp, nd.f, nd.cnt > 0 ? nd.pv : R(0), cx, cy, rho, u, v);
     const R lam = R(1) - heaviside<R>(nd.phi, eps);
     stl[0] += lam; stl[1] += lam * R(lx); stl[2] += lam * R(ly);
     stl[3] += lam * rho; stl[4] += lam * rho * u; stl[5] += lam * rho * v;
@@ -1158,8 +1232,8 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                 P0Node<R> n1, n2;
                 p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[e], n1);
                 p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[two ? e + 32 : e], n2);
-                p0_finish<R, S>(sp, a, n1, Xi, Yi, Xo, Yo, lab, T, fi, shx, shy, ddx, ddy, eps, stl, sb);
-                if (two) p0_finish<R, S>(sp, a, n2, Xi, Yi, Xo, Yo, lab, T, fi, shx, shy, ddx, ddy, eps, stl, sb);
+                p0_finish<R, S>(sp, a, n1, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
+                if (two) p0_finish<R, S>(sp, a, n2, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
             }
         } else {
             BoxWalk wk2(bw);
@@ -1170,7 +1244,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
                 if (lx < 0 || ly < 0 || lx >= T || ly >= T) continue;  // flagged in (a)
                 P0Node<R> nd;
                 p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, ix | (iy << 16), nd);
-                p0_finish<R, S>(sp, a, nd, Xi, Yi, Xo, Yo, lab, T, fi, shx, shy, ddx, ddy, eps, stl, sb);
+                p0_finish<R, S>(sp, a, nd, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
             }
         }
     }
@@ -1655,12 +1729,12 @@ struct LbArgs {
     // (f_out + q P + c_q,y nx + c_q,x): one address operation per interior access
     const S *fin_q[9];
     S *fout_push[9];
-    S *carry;
+    S *carry;                  // density plane: read (previous step), then written
     const R *fbody;            // per row x body force
     const R *bfield;           // force_kind 3: per-node body force (x plane, y plane)
     R *tape;                   // optional: rho, ux, uy, Fx, Fy of every node (5 planes)
     const int *reg_count;      // registry of this step
-    const R *pool;
+    R *pool;                   // its pool: solid terms read, half-force written
     int *clr_count;            // registry of the previous step: read, then cleared for the next step
     int *clr_nactive;
     const R *pool_prev;        // force pool of the previous step (its Delta rho is the rest base)
@@ -1670,9 +1744,14 @@ struct LbArgs {
 // One node (i, j) of K1: moments, SFC equilibrium, Guo forcing, BGK collision,
 // walls and push streaming.  tile / lt: the node's registry tile and its index
 // there (the pool's layout); interior: every push target of the caller's block
-// lies inside the domain.  STAGED: the node's populations and half-force were
-// staged in shared memory (9 + 2 planes of TILE_N values, node lt at offset lt).
-// Returns rho - rho_f.
+// lies inside the domain.  STAGED: the node's populations and density plane
+// were staged in shared memory (9 + 1 planes of TILE_N values, node lt at
+// offset lt).  Returns rho - rho_f.
+// The half-force term rho F / 2 that the next step's moments need is kept
+// where its force came from: on a tile this step's registry holds, in the
+// pool (planes POOL_CX / POOL_CY); elsewhere the force is the body force
+// alone and only rho - rho_f is stored (the density plane, one value instead
+// of two), the next step multiplying it out again (free_carry).
 // REG false: the node's tile is registered in neither this step's nor the
 // previous step's registry (a free region), so neither is read.
 template <class R, class S, bool STAGED, bool REG = true>
@@ -1685,27 +1764,30 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
 #pragma unroll
     for (int q = 0; q < 9; q++)  // shared-memory stage: plain loads (the read-only path is global only)
         f[q] = STAGED ? ldS<S, R>(stage + q * TILE_N + lt, sp, q) : ldG<S, R>(a.fin_q[q] + c, sp, q);
+    const R drp = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt, sp) : ldC<S, R>(a.carry + c, sp);
+    R Fx, Fy;  // the body force (this step's and the previous step's)
+    body_force<R>(sp, a.fbody, a.bfield, j, c, Fx, Fy);
     R dro = R(0), dro_lo = R(0);  // rest base: Delta rho of the step that wrote f (hi + lo)
-    if (prev_count > 0) pool_drho<R>(a.pool_prev + (long long)tile * POOL_STRIDE + lt, lt, dro, dro_lo);
+    R cx0, cy0;                   // rho^{n-1} F^{n-1} / 2
+    if (prev_count > 0) {
+        const R *pp = a.pool_prev + (long long)tile * POOL_STRIDE + lt;
+        pool_drho<R>(pp, lt, dro, dro_lo);
+        cx0 = pp[POOL_CX];
+        cy0 = pp[POOL_CY];
+    } else {
+        free_carry<R>(sp, drp, Fx, Fy, cx0, cy0);
+    }
     const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const R dr = dro + ds;  // rho - rho_f
     const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
     const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
     const R inv = rcp_rn<R>(rho);
-    const R cx0 = STAGED ? ldC<S, R>(stage + 9 * TILE_N + lt, sp) : ldC<S, R>(a.carry + c, sp);
-    const R cy0 = STAGED ? ldC<S, R>(stage + 10 * TILE_N + lt, sp) : ldC<S, R>(a.carry + P + c, sp);
     const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
-    R Fx, Fy, drt = R(0), drt_lo = R(0);
-    if (sp.force_kind == 3) {
-        Fx = a.bfield[c];
-        Fy = a.bfield[P + c];
-    } else {
-        Fx = a.fbody[j];
-        Fy = pick<R>(sp.fy, sp.fy_f);
-    }
+    R drt = R(0), drt_lo = R(0);
+    R *po = nullptr;  // this step's pool entry, if the registry holds the tile
     if (REG && a.reg_count[tile] > 0) {
-        const R *po = a.pool + (long long)tile * POOL_STRIDE + lt;
+        po = a.pool + (long long)tile * POOL_STRIDE + lt;
         pool_drho<R>(po, lt, drt, drt_lo);
         if (sp.force_mode == 1) {
             // conservative form: the stress divergence enters the Guo term without rho
@@ -1752,10 +1834,14 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
         a.tape[c] = rho; a.tape[P + c] = ux; a.tape[2 * P + c] = uy;
         a.tape[3 * P + c] = Fx; a.tape[4 * P + c] = Fy;
     }
-    stC<S, R>(a.carry + c, R(0.5) * rho * Fx, sp);
-    stC<S, R>(a.carry + P + c, R(0.5) * rho * Fy, sp);
+    if (REG && po) {
+        po[POOL_CX] = R(0.5) * rho * Fx;
+        po[POOL_CY] = R(0.5) * rho * Fy;
+    } else {
+        stC<S, R>(a.carry + c, dr, sp);
+    }
     if constexpr (is16<S>()) {
-        bool ov = false;
+        bool ov = store_overflow_c<S, R>(dr, sp);
 #pragma unroll
         for (int q = 0; q < 9; q++) ov = ov || store_overflow<S, R>(fh[q], sp, q);
         if (ov) atomicOr(a.err, ERR_OVERFLOW16);
@@ -1957,7 +2043,7 @@ __global__ void __launch_bounds__(TILE_N, LB_MIN_BLOCKS<R, S>) lb_tma_kernel(Sim
     // reserves 128 bytes for this): tensor copies write to 128-byte aligned addresses
     const unsigned pad = (128u - (smem_u32(smem) & 127u)) & 127u;
     S *stage0 = reinterpret_cast<S *>(smem + pad);
-    const unsigned stage_elems = 11u * TILE_N, stage_bytes = stage_elems * (unsigned)sizeof(S);
+    const unsigned stage_elems = 10u * TILE_N, stage_bytes = stage_elems * (unsigned)sizeof(S);
     const int lt = threadIdx.x;
     if (lt == 0) {
         ok = ((smem_u32(stage0) & 127u) == 0u && ((stage_bytes & 127u) == 0u)) ? 1 : 0;
@@ -2007,8 +2093,7 @@ __global__ void init_f_kernel(SimParams sp, S *f, S *carry) {
     if (i >= sp.nx || j >= sp.ny) return;
     const long long c = (long long)j * sp.nx + i;
     for (int q = 0; q < 9; q++) stS<S, R>(f + q * sp.P + c, R(0), sp, q);
-    stC<S, R>(carry + c, R(0), sp);
-    stC<S, R>(carry + sp.P + c, R(0), sp);
+    stC<S, R>(carry + c, R(NAN), sp);  // no previous collision (the pools start at zero)
 }
 
 // Self-check of the failure path of the tensor-copy pipeline: one thread
@@ -2060,7 +2145,7 @@ __global__ void field_kernel(SimParams sp, const S *f, const S *carry, const R *
         v = sp.rho_f + dr;
     } else if (kind <= 2) {
         R rho, u, w;
-        node_moments<R, S>(sp, f, carry, reg_count, pool, i, j, rho, u, w);
+        node_moments<R, S>(sp, f, carry, fbody, bfield, reg_count, pool, i, j, rho, u, w);
         v = kind == 1 ? (double)u : (double)w;
     } else if (kind <= 5) {
         const R *po = pool + (long long)tile * POOL_STRIDE + threadIdx.x;
@@ -2175,9 +2260,9 @@ struct StatsNode {
 // used only if the tile is registered; its address is valid either way), phi,
 // and the 4-neighbour stencil of eta for det F.
 template <class R, class S>
-__device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, const S *carry, const int *reg,
-                                             const R *pool, const R *xi, int T, int2 ow, const Frame &fr, int e,
-                                             StatsNode<R, S> &nd) {
+__device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, const S *carry, const R *fbody,
+                                             const R *bfield, const int *reg, const R *pool, const R *xi, int T,
+                                             int2 ow, const Frame &fr, int e, StatsNode<R, S> &nd) {
     nd.lx = e & 0xffff;
     nd.ly = e >> 16;
     const int t = nd.ly * T + nd.lx;
@@ -2190,15 +2275,25 @@ __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, co
 #pragma unroll
     for (int q = 0; q < 9; q++) nd.f[q] = ldS<S, R>(f + q * sp.P + c, sp, q);
     const int tile = (j >> sp.ly) * sp.ntx + (i >> sp.lx);
+    const int lt = ((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1));
+    const R *po = pool + (long long)tile * POOL_STRIDE + lt;
     nd.reg = reg[tile];
-    nd.pool = pool[(long long)tile * POOL_STRIDE + POOL_DRHO + 2 * (((j & (sp.ty - 1)) << sp.lx) + (i & (sp.tx - 1)))];
-    nd.cx = ldC<S, R>(carry + c, sp);
-    nd.cy = ldC<S, R>(carry + sp.P + c, sp);
+    nd.pool = po[POOL_DRHO + lt];
+    const R pcx = po[POOL_CX], pcy = po[POOL_CY], drp = ldC<S, R>(carry + c, sp);
+    R Fx, Fy;
+    body_force<R>(sp, fbody, bfield, j, c, Fx, Fy);
     nd.inner = nd.lx > fr.bx0 && nd.lx < fr.bx1 && nd.ly > fr.by0 && nd.ly < fr.by1;
     if (nd.inner) {
         const R *Y = xi + T * T;
         nd.st[0] = xi[t + 1]; nd.st[1] = xi[t - 1]; nd.st[2] = xi[t + T]; nd.st[3] = xi[t - T];
         nd.st[4] = Y[t + 1]; nd.st[5] = Y[t - 1]; nd.st[6] = Y[t + T]; nd.st[7] = Y[t - T];
+    }
+    // the half-force term: from the pool on a registered tile, else rebuilt
+    if (nd.reg > 0) {
+        nd.cx = pcx;
+        nd.cy = pcy;
+    } else {
+        free_carry<R>(sp, drp, Fx, Fy, nd.cx, nd.cy);
     }
 }
 // One node's terms, added to the thread's partial sums in the arithmetic
@@ -2337,7 +2432,7 @@ __device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *r
 
 template <class R, class S>
 __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_stats_kernel(SimParams sp, const S *f, const S *carry,
-                                                                    const int *reg, const int *reg_solids, const R *pool,
+                                                                    const R *fbody, const R *bfield, const int *reg, const int *reg_solids, const R *pool,
                                                                     const R *xi, const Frame *frames,
                                                                     const SolidDesc *solids, double *out) {
     __shared__ double red[32 * STATS_COLS];
@@ -2361,7 +2456,7 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_s
     auto drain = [&](int cnt) {  // the last cnt (<= 32) queued nodes, one per lane
         StatsNode<R, S> nd;
         if (lane < cnt) {
-            stats_gather<R, S>(sp, f, carry, reg, pool, X, T, ow, fr, qu[qn - cnt + lane], nd);
+            stats_gather<R, S>(sp, f, carry, fbody, bfield, reg, pool, X, T, ow, fr, qu[qn - cnt + lane], nd);
             stats_finish<R, S>(sp, nd, eps, acc, cmp, mx);
         }
         __syncwarp();
