@@ -761,7 +761,7 @@ __global__ void centroid_seed_kernel(SimParams sp, const R *xi, const Frame *fra
         const double lam = 1.0 - (double)heaviside<R>(phi, eps);
         st[0] += lam; st[1] += lam * (fr.ox + lx); st[2] += lam * (fr.oy + ly);
     }
-    block_sum<3>(st, red);
+    block_sum<double, 3>(st, red);
     if (threadIdx.x == 0) { tot[0] = st[0]; tot[1] = st[1]; tot[2] = st[2]; }
     __syncthreads();
     const double lsum = tot[0];

@@ -14,11 +14,12 @@ namespace lbrmt {
 struct LaunchInfo {
     int tmax;            // largest solid tile side
     int force_blocks;    // persistent grid of K3
+    int force_blocks_ov; // the same in the overlapped step (fewer CTAs per SM)
     int rmt_smem;        // dynamic shared memory of K2
     int force_smem;      // dynamic shared memory of K3
     int rmt_req = 0;      // requested K2 CTA width (0: chosen by configure)
     int rmt_threads = 256; // K2 CTA width in use: 256, or 1024 (FP32 arithmetic only)
-    bool tma = false;    // tensor maps of the populations and half-force are valid
+    bool tma = false;    // tensor maps of the populations and density plane are valid
     bool use_tma = true; // K1 with TMA staging (else the direct-load kernel)
     int lb_blocks = 0, lb_smem = 0;
     CUtensorMap tm_f[2], tm_c;
@@ -226,9 +227,13 @@ struct Engine {
         int dev = 0, nsm = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_kernel<R>, TILE_N, li->force_smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_kernel<R>, K3_THREADS, li->force_smem);
         if (e != cudaSuccess) return e;
         li->force_blocks = nsm * (per > 0 ? per : 1);
+        // In the overlapped step K3 runs beside the free regions' K1: three of its
+        // CTAs per SM (of four that fit) leave the registers of two K1 CTAs, and
+        // the step is shorter although K3 alone takes longer.
+        li->force_blocks_ov = nsm * std::min(std::max(per, 1), 3);
         configure_tma(sp, d, li, nsm);
         return cudaSuccess;
     }
@@ -387,7 +392,7 @@ struct Engine {
     static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
         if (sp.nsolids > 0) {
             launch_rmt(sp, li, rmt_args(d, 0, 1), st);
-            force_kernel<R><<<li.force_blocks, TILE_N, li.force_smem, st>>>(sp, force_args(d, 0, 1));
+            force_kernel<R><<<li.force_blocks, K3_THREADS, li.force_smem, st>>>(sp, force_args(d, 0, 1));
         }
         dim3 grid(sp.ntx, sp.nty), blk(TILE_N);
         init_f_kernel<R, S><<<grid, blk, 0, st>>>(sp, (S *)d.f[0], (S *)d.carry);
@@ -426,7 +431,8 @@ struct Engine {
         }
         if (ev) cudaEventRecord(ev[1], st);
         if (sp.nsolids > 0)
-            launch_prio(force_kernel<R>, dim3(li.force_blocks), dim3(TILE_N), li.force_smem, st, prio, sp,
+            launch_prio(force_kernel<R>, dim3(overlap ? li.force_blocks_ov : li.force_blocks), dim3(K3_THREADS),
+                        li.force_smem, st, prio, sp,
                         force_args(d, q, p));
         if (ev) cudaEventRecord(ev[2], st);
         if (li.tma && li.use_tma)

@@ -394,9 +394,9 @@ __device__ __forceinline__ void node_moments(const SimParams &sp, const S *f, co
     moments_from<R>(sp, fq, rest_base<R>(sp, reg, pool, i, j), cx, cy, rho, u, v);
 }
 
-// Block-wide sum of NV doubles (blockDim.x multiple of 32, <= 1024).
-template <int NV>
-__device__ void block_sum(double (&v)[NV], double *sh /* 32*NV */) {
+// Block-wide sum of NV values (blockDim.x multiple of 32, <= 1024).
+template <class T, int NV>
+__device__ void block_sum(T (&v)[NV], T *sh /* 32*NV */) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
@@ -408,7 +408,7 @@ __device__ void block_sum(double (&v)[NV], double *sh /* 32*NV */) {
     __syncthreads();
     if (warp == 0) {
         for (int k = 0; k < NV; k++) {
-            double t = lane < nw ? sh[lane * NV + k] : 0.0;
+            T t = lane < nw ? sh[lane * NV + k] : T(0);
             for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
             v[k] = t;
         }
@@ -1365,9 +1365,11 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     for (int k = 0; k < 8; k++) warp_minmax(bx[k], (k & 1) == 0);
     if (lane == 0)
         for (int k = 0; k < 8; k += 2) { atomicMin(&bb[4 + k], bx[k]); atomicMax(&bb[5 + k], bx[k + 1]); }
+    // the solid's sums (its mean velocity sets the next frame's offset): in the
+    // arithmetic precision (the terms are; FP64 is a narrow pipe on this GPU)
     double st[6];
+    if (a.stats) block_sum<R, 6>(stl, reinterpret_cast<R *>(red));
     for (int k = 0; k < 6; k++) st[k] = (double)stl[k];
-    if (a.stats) block_sum<6>(st, red);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (a.stats) {
@@ -1483,10 +1485,11 @@ __device__ __forceinline__ bool stress_from_grad(R Axx, R Axy, R Ayx, R Ayy, R G
 }
 
 // Per-tile constants of the registered solids (static shared memory of K3).
-// Threads per CTA of the batched K3: the 2 tx ty + tx + ty half-edges of a
-// 16x16 tile (544) take two rounds of 288 threads where 256 threads need three
-// (measured faster for the batch; the single-simulation K3 keeps TILE_N threads,
-// which fit one more CTA per SM).  The node phase uses the first TILE_N threads.
+// Threads per CTA of K3: the 2 tx ty + tx + ty half-edges of a 16x16 tile
+// (544) take two rounds of 288 threads where 256 threads need three.  Four
+// such CTAs fit an SM (48 registers); the overlapped step launches three per
+// SM so that the free regions' K1 runs beside them.  The node phase uses the
+// first TILE_N threads.
 constexpr int K3_THREADS = TILE_N + 32;
 
 template <class R>
@@ -1572,10 +1575,13 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
                 if (!sp.wall_y) while (ly >= sp.ny) ly -= sp.ny;
                 R X = nanv<R>(), Y = nanv<R>(), P = nanv<R>();
                 if (in_box(fr, lx, ly)) {
+                    // the three loads at once (the phi plane's address is valid in
+                    // the box); phi counts only where eta does
                     X = Xs[ly * T + lx];
                     Y = Xs[T * T + ly * T + lx];
-                    if (X == X) P = Xs[2 * T * T + ly * T + lx];  // the stored phi
+                    P = Xs[2 * T * T + ly * T + lx];
                 }
+                if (!(X == X)) P = nanv<R>();
                 sX[ks * PN + p] = X; sY[ks * PN + p] = Y; sP[ks * PN + p] = P;
             }
         }
@@ -1710,7 +1716,7 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
 }
 
 template <class R>
-__global__ void __launch_bounds__(TILE_N, sizeof(R) == 4 ? 5 : 1) force_kernel(SimParams sp, ForceArgs<R> a) {
+__global__ void __launch_bounds__(K3_THREADS, sizeof(R) == 4 ? 4 : 1) force_kernel(SimParams sp, ForceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ForceShared<R> fs;
     const int nact = *a.reg_nactive;
@@ -1740,6 +1746,71 @@ struct LbArgs {
     const R *pool_prev;        // force pool of the previous step (its Delta rho is the rest base)
     unsigned *err;
 };
+
+// The arithmetic of one node of K1 once its inputs are loaded: moments, SFC
+// equilibrium, Guo forcing and BGK collision.  f: the stored populations (f[0]
+// becomes relative to this step's Delta rho); fh: the post-collision values in
+// stored form.  dro, dro_lo: the rest base (Delta rho of the step that wrote
+// f); cx0, cy0: rho^{n-1} F^{n-1} / 2; Fx, Fy: the body force in, the whole
+// force out; po: this step's pool entry of the node (lt) if the registry holds
+// its tile, else null.  Returns rho - rho_f; rho, ux, uy for the tape.
+template <class R>
+__device__ __forceinline__ R lb_collide(const SimParams &sp, R (&f)[9], R (&fh)[9], const R dro, const R dro_lo,
+                                        const R cx0, const R cy0, R &Fx, R &Fy, const R *po, const int lt, R &rho,
+                                        R &ux, R &uy, unsigned *err) {
+    const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const R dr = dro + ds;  // rho - rho_f
+    const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
+    const R inv = rcp_rn<R>(rho);
+    ux = (jx + cx0) * inv;
+    uy = (jy + cy0) * inv;
+    R drt = R(0), drt_lo = R(0);
+    if (po) {
+        pool_drho<R>(po, lt, drt, drt_lo);
+        if (sp.force_mode == 1) {
+            // conservative form: the stress divergence enters the Guo term without rho
+            Fx += po[POOL_FX] * inv;
+            Fy += po[POOL_FY] * inv + po[POOL_AY];
+        } else {
+            Fx += po[POOL_FX];
+            Fy += po[POOL_FY];
+        }
+    }
+    if (!(ux + uy == ux + uy)) atomicOr(err, ERR_NAN);  // a NaN rho makes both velocities NaN
+    const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
+    const R u2 = ux * ux + uy * uy;
+    const R uF = ux * Fx + uy * Fy;
+    R dde;
+    const R dds = two_diff<R>(dro, drt, dde);
+    const R dd = dds + (dde + (dro_lo - drt_lo));  // change of the rest base over the step (small)
+    const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
+    f[0] += dd;                  // rest population relative to this step's Delta rho
+    // Collision f^ = f - omega (f - f^eq) + (1 - omega/2) F_i (Eq. 2_2_bgk_force) with
+    // f^eq of Eq. 2_3_feq_sfc in the stored form (minus w rho_f, minus Delta rho for
+    // q = 0) and the Guo term of Eq. 2_2_Fi times rho.  Opposite directions share the
+    // even parts (in c) of f^eq and F_i and differ in the sign of the odd parts.
+    const R om1 = R(1) - omega;
+    const R r15u2 = R(1.5) * u2, r3uF = R(3) * uF;
+    {
+        const R w = R(4) / R(9), rw = rho * w;
+        fh[0] = om1 * f[0] + omega * (w * ddr - rw * r15u2) - kf * rw * r3uF;
+    }
+#pragma unroll
+    for (int pr = 0; pr < 4; pr++) {
+        const int q = pr + 1 + (pr >= 2 ? 2 : 0);  // 1, 2, 5, 6; partners 3, 4, 7, 8
+        const int qo = oppq(q);
+        const R w = wq<R>(q), rw = rho * w;
+        const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
+        const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
+        const R even = omega * (w * ddr + rw * (R(4.5) * cu * cu - r15u2)) + kf * rw * (R(9) * cu * cF - r3uF);
+        const R odd = R(3) * rw * (omega * cu + kf * cF);
+        fh[q] = om1 * f[q] + even + odd;
+        fh[qo] = om1 * f[qo] + even - odd;
+    }
+    return dr;
+}
 
 // One node (i, j) of K1: moments, SFC equilibrium, Guo forcing, BGK collision,
 // walls and push streaming.  tile / lt: the node's registry tile and its index
@@ -1777,59 +1848,9 @@ __device__ __forceinline__ R lb_node(const SimParams &sp, const LbArgs<R, S> &a,
     } else {
         free_carry<R>(sp, drp, Fx, Fy, cx0, cy0);
     }
-    const R ds = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const R dr = dro + ds;  // rho - rho_f
-    const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-    const R rho = pick<R>(sp.rho_f, sp.rho_f_f) + dr;
-    const R inv = rcp_rn<R>(rho);
-    const R ux = (jx + cx0) * inv, uy = (jy + cy0) * inv;
-    R drt = R(0), drt_lo = R(0);
-    R *po = nullptr;  // this step's pool entry, if the registry holds the tile
-    if (REG && a.reg_count[tile] > 0) {
-        po = a.pool + (long long)tile * POOL_STRIDE + lt;
-        pool_drho<R>(po, lt, drt, drt_lo);
-        if (sp.force_mode == 1) {
-            // conservative form: the stress divergence enters the Guo term without rho
-            Fx += po[POOL_FX] * inv;
-            Fy += po[POOL_FY] * inv + po[POOL_AY];
-        } else {
-            Fx += po[POOL_FX];
-            Fy += po[POOL_FY];
-        }
-    }
-    if (!(ux + uy == ux + uy)) atomicOr(a.err, ERR_NAN);  // a NaN rho makes both velocities NaN
-    const R omega = pick<R>(sp.omega, sp.omega_f), kf = pick<R>(sp.kf, sp.kf_f);
-    const R u2 = ux * ux + uy * uy;
-    const R uF = ux * Fx + uy * Fy;
-    R dde;
-    const R dds = two_diff<R>(dro, drt, dde);
-    const R dd = dds + (dde + (dro_lo - drt_lo));  // change of the rest base over the step (small)
-    const R ddr = dd + ds;       // rho - rho_t, without rounding against Delta rho
-    f[0] += dd;                  // rest population relative to this step's Delta rho
-    // Collision f^ = f - omega (f - f^eq) + (1 - omega/2) F_i (Eq. 2_2_bgk_force) with
-    // f^eq of Eq. 2_3_feq_sfc in the stored form (minus w rho_f, minus Delta rho for
-    // q = 0) and the Guo term of Eq. 2_2_Fi times rho.  Opposite directions share the
-    // even parts (in c) of f^eq and F_i and differ in the sign of the odd parts.
-    const R om1 = R(1) - omega;
-    const R r15u2 = R(1.5) * u2, r3uF = R(3) * uF;
-    R fh[9];
-    {
-        const R w = R(4) / R(9), rw = rho * w;
-        fh[0] = om1 * f[0] + omega * (w * ddr - rw * r15u2) - kf * rw * r3uF;
-    }
-#pragma unroll
-    for (int pr = 0; pr < 4; pr++) {
-        const int q = pr + 1 + (pr >= 2 ? 2 : 0);  // 1, 2, 5, 6; partners 3, 4, 7, 8
-        const int qo = oppq(q);
-        const R w = wq<R>(q), rw = rho * w;
-        const R cu = R(cxq(q)) * ux + R(cyq(q)) * uy;
-        const R cF = R(cxq(q)) * Fx + R(cyq(q)) * Fy;
-        const R even = omega * (w * ddr + rw * (R(4.5) * cu * cu - r15u2)) + kf * rw * (R(9) * cu * cF - r3uF);
-        const R odd = R(3) * rw * (omega * cu + kf * cF);
-        fh[q] = om1 * f[q] + even + odd;
-        fh[qo] = om1 * f[qo] + even - odd;
-    }
+    R *po = (REG && a.reg_count[tile] > 0) ? a.pool + (long long)tile * POOL_STRIDE + lt : nullptr;
+    R fh[9], rho, ux, uy;
+    const R dr = lb_collide<R>(sp, f, fh, dro, dro_lo, cx0, cy0, Fx, Fy, po, lt, rho, ux, uy, a.err);
     if (a.tape) {
         a.tape[c] = rho; a.tape[P + c] = ux; a.tape[2 * P + c] = uy;
         a.tape[3 * P + c] = Fx; a.tape[4 * P + c] = Fy;
@@ -2125,7 +2146,7 @@ __global__ void __launch_bounds__(TILE_N) mass_tile_kernel(SimParams sp, const S
         for (int q = 0; q < 9; q++) dr += (double)ldS<S, R>(f + q * sp.P + c, sp, q);
         v[0] = dr;
     }
-    block_sum<1>(v, red);
+    block_sum<double, 1>(v, red);
     if (threadIdx.x == 0) partials[blockIdx.y * sp.ntx + blockIdx.x] = v[0];
 }
 
