@@ -93,7 +93,6 @@ template <> inline CUtensorMapDataType tma_dtype<__nv_bfloat16>() { return CU_TE
 struct BatchLaunch {
     int rmt_blocks, rmt_smem;      // K2: persistent grid, dynamic shared memory (largest solid tile)
     int force_blocks, force_smem;  // K3 (widest tile shape)
-    int force_blocks_ov;           // K3 in the overlapped step: room for the free K1 beside it
     // Overlapped batch step, as a single simulation's: the classification and
     // K1 of every member's solid-free regions on a side stream of the lowest
     // priority, K2, K3 and K1 of the busy regions at the highest.  The stream
@@ -344,7 +343,6 @@ struct Engine {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, force_batch_kernel<R, S>, K3_THREADS, bl->force_smem);
         if (e != cudaSuccess) return e;
         bl->force_blocks = nsm * std::max(per, 1);
-        bl->force_blocks_ov = nsm * std::min(std::max(per, 1), 3);  // as the single simulation's K3
         return cudaSuccess;
     }
 
@@ -369,8 +367,7 @@ struct Engine {
                         rmt_items, n_rmt, parity);
         if (ev) cudaEventRecord(ev[1], st);
         if (n_rmt > 0)
-            launch_prio(force_batch_kernel<R, S>, dim3(overlap ? bl.force_blocks_ov : bl.force_blocks), dim3(K3_THREADS),
-                        bl.force_smem, st, prio, ds,
+            launch_prio(force_batch_kernel<R, S>, dim3(bl.force_blocks), dim3(K3_THREADS), bl.force_smem, st, prio, ds,
                         nsim, parity);
         if (ev) cudaEventRecord(ev[2], st);
         if (n_lb > 0) {

@@ -1516,8 +1516,41 @@ __host__ __device__ __forceinline__ int force_smem_max() {
     return m;
 }
 
+// The registered solids of a tile and their descriptors into fs, read by one
+// whole warp (lane k: registry slot k) in parallel; slot = rank of the id (ids
+// are distinct): a fixed summation order.
 template <class R>
-__device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int tile, ForceShared<R> &fs, R *dyn) {
+__device__ __forceinline__ void force_solids(const SimParams &sp, const ForceArgs<R> &a, const int tile,
+                                             ForceShared<R> &fs, const int k) {
+    const int n = min(a.reg_count[tile], sp.kmax);
+    const int id = k < n ? a.reg_solids[tile * KMAX + k] : 0x7fffffff;
+    int rank = 0;
+#pragma unroll
+    for (int m = 0; m < KMAX; m++) rank += __shfl_sync(0xffffffffu, id, m) < id ? 1 : 0;
+    if (k < n) {
+        const SolidDesc &sd = a.solids[id];
+        fs.ids[rank] = id;
+        fs.sfr[rank] = a.frame[id];
+        fs.sG[rank] = pick<R>(sd.G, sd.G_f);
+        fs.sD[rank] = pick<R>(sd.drho, sd.drho_f);
+        fs.sA[rank] = pick<R>(sd.accel, sd.accel_f);
+        fs.sDh[rank] = sd.drho_f;
+        fs.sDl[rank] = sd.drho_lo_f;
+        fs.srq[rank] = Rsq<R>(sd);
+        fs.sT[rank] = sd.T;
+        fs.soff[rank] = sd.off;
+    }
+    if (k == 0) fs.nk = n;
+}
+
+// One registered tile of K3.  LOADED: fs already holds the tile's solids (read
+// during the previous tile); else the first warp reads them.  next >= 0: the
+// warp beyond the tile's TILE_N node threads reads the solids of tile `next`
+// into fs_next during the node phase, where it has no node (blockDim.x >=
+// TILE_N + 32).
+template <class R, bool LOADED = false>
+__device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int tile, ForceShared<R> &fs, R *dyn,
+                           const int next = -1, ForceShared<R> *fs_next = nullptr) {
     const int TX = sp.tx, PX = TX + 2, PN = force_patch_n(TX, sp.ty);
     const int NXE = (TX + 1) * sp.ty, NYE = TX * (sp.ty + 1);
     R *sX = dyn;                       // [KMAX][PN]
@@ -1534,31 +1567,10 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
     {
         const int tx = tile % sp.ntx, ty = tile / sp.ntx;
         const int i0 = tx * TX, j0 = ty * sp.ty;
-        // The tile's solids and their descriptors, read by the first warp in
-        // parallel; slot = rank of the id (ids are distinct): a fixed summation order.
-        if (threadIdx.x < 32) {
-            const int n = min(a.reg_count[tile], sp.kmax);
-            const int k = threadIdx.x;
-            const int id = k < n ? a.reg_solids[tile * KMAX + k] : 0x7fffffff;
-            int rank = 0;
-#pragma unroll
-            for (int m = 0; m < KMAX; m++) rank += __shfl_sync(0xffffffffu, id, m) < id ? 1 : 0;
-            if (k < n) {
-                const SolidDesc &sd = a.solids[id];
-                ids[rank] = id;
-                sfr[rank] = a.frame[id];
-                sG[rank] = pick<R>(sd.G, sd.G_f);
-                sD[rank] = pick<R>(sd.drho, sd.drho_f);
-                sA[rank] = pick<R>(sd.accel, sd.accel_f);
-                fs.sDh[rank] = sd.drho_f;
-                fs.sDl[rank] = sd.drho_lo_f;
-                srq[rank] = Rsq<R>(sd);
-                sT[rank] = sd.T;
-                soff[rank] = sd.off;
-            }
-            if (k == 0) fs.nk = n;
+        if (!LOADED) {
+            if (threadIdx.x < 32) force_solids<R>(sp, a, tile, fs, threadIdx.x);
+            __syncthreads();
         }
-        __syncthreads();
         const int n = fs.nk;
         // Stage each solid's xi (and phi) on the tile plus a one-node halo.
         for (int ks = 0; ks < n; ks++) {
@@ -1646,6 +1658,9 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
         }
         __syncthreads();
         // Node: divergence (Eq. 3_3_div_solid_stress), solid fraction, drho, solid acceleration.
+        // Meanwhile the warp past the node threads reads the next tile's solids.
+        if (next >= 0 && threadIdx.x >= TILE_N && threadIdx.x < TILE_N + 32)
+            force_solids<R>(sp, a, next, *fs_next, threadIdx.x - TILE_N);
         {
             const int cx = threadIdx.x & (TX - 1), cy = threadIdx.x >> sp.lx;
             const int i = i0 + cx, j = j0 + cy;
@@ -1716,12 +1731,20 @@ __device__ void force_tile(const SimParams &sp, const ForceArgs<R> &a, const int
 }
 
 template <class R>
-__global__ void __launch_bounds__(K3_THREADS, sizeof(R) == 4 ? 4 : 1) force_kernel(SimParams sp, ForceArgs<R> a) {
+__global__ void __launch_bounds__(K3_THREADS) __maxnreg__(sizeof(R) == 4 ? 48 : 224) force_kernel(SimParams sp, ForceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ ForceShared<R> fs;
+    __shared__ ForceShared<R> fs[2];  // this tile's solids, and the next tile's (read during this one)
     const int nact = *a.reg_nactive;
-    for (int it = blockIdx.x; it < nact; it += gridDim.x)
-        force_tile<R>(sp, a, a.reg_active[it], fs, reinterpret_cast<R *>(smem));
+    int it = blockIdx.x;
+    if (it >= nact) return;  // uniform over the CTA
+    int tile = a.reg_active[it];
+    if (threadIdx.x < 32) force_solids<R>(sp, a, tile, fs[0], threadIdx.x);
+    __syncthreads();
+    for (int b = 0; it < nact; it += gridDim.x, b ^= 1) {
+        const int next = it + (int)gridDim.x < nact ? a.reg_active[it + gridDim.x] : -1;
+        force_tile<R, true>(sp, a, tile, fs[b], reinterpret_cast<R *>(smem), next, &fs[b ^ 1]);
+        tile = next;
+    }
 }
 
 // ===========================================================================
@@ -2357,12 +2380,20 @@ __device__ __forceinline__ void stats_finish(const SimParams &sp, const StatsNod
 // NaN where the node is outside the tile's box or not a valid band node.
 template <class R>
 __device__ __forceinline__ R tile_phi(const SimParams &sp, const R *xi, const SolidDesc &sd, const Frame &fr, int i, int j) {
-    const int lx = sp.wall_x ? i - fr.ox : wrapi(i - fr.ox, sp.nx);
-    const int ly = sp.wall_y ? j - fr.oy : wrapi(j - fr.oy, sp.ny);
+    int lx = i - fr.ox, ly = j - fr.oy;
+    if (!sp.wall_x) {  // periodic: the node and the frame origin are within a period or two
+        while (lx < 0) lx += sp.nx;
+        while (lx >= sp.nx) lx -= sp.nx;
+    }
+    if (!sp.wall_y) {
+        while (ly < 0) ly += sp.ny;
+        while (ly >= sp.ny) ly -= sp.ny;
+    }
     if (!in_box(fr, lx, ly)) return nanv<R>();
     const R *X = xi + sd.off;
     const int T = sd.T, t = ly * T + lx;
-    return X[t] == X[t] ? X[2 * T * T + t] : nanv<R>();
+    const R x = X[t], p = X[2 * T * T + t];  // both loads at once (phi's address is valid in the box)
+    return x == x ? p : nanv<R>();
 }
 
 // Contact stress of a pair (Eqs. 3_6_collision_stress .. 3_6_normal) on the
@@ -2420,21 +2451,53 @@ __device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *r
                     bool mine = false;
                     for (int k = 0; k < n; k++) mine = mine || reg_solids[tile * KMAX + k] == s;
                     if (!mine) continue;
-                    const int i = bx * sp.tx + (threadIdx.x & (sp.tx - 1)), j = by * sp.ty + (threadIdx.x >> sp.lx);
-                    if (threadIdx.x >= TILE_N || i >= sp.nx || j >= sp.ny) continue;
-                    // 4x4 block of level sets: nodes (i-1..i+2, j-1..j+2), block index (x - i + 1, y - j + 1)
+                    for (int lt = threadIdx.x; lt < TILE_N; lt += blockDim.x) {  // the tile's nodes
+                    const int i = bx * sp.tx + (lt & (sp.tx - 1)), j = by * sp.ty + (lt >> sp.lx);
+                    if (i >= sp.nx || j >= sp.ny) continue;
+                    // 4x4 block of level sets: nodes (i-1..i+2, j-1..j+2), block index (x - i + 1, y - j + 1).
+                    // The node's four half-edges need the cross (1,1), (0,1), (2,1), (1,0), (1,2)
+                    // for their contact test (both solids' edge-averaged phi below eps): it is
+                    // read first, the rest of the blocks only where an edge passes the test.
                     R ps[4][4];
-                    for (int yy = 0; yy < 4; yy++)
-                        for (int xx = 0; xx < 4; xx++) ps[yy][xx] = tile_phi<R>(sp, xi, sd, fr, i - 1 + xx, j - 1 + yy);
+                    ps[1][1] = tile_phi<R>(sp, xi, sd, fr, i, j);
                     if (!(ps[1][1] == ps[1][1])) continue;
+                    ps[1][0] = tile_phi<R>(sp, xi, sd, fr, i - 1, j);
+                    ps[1][2] = tile_phi<R>(sp, xi, sd, fr, i + 1, j);
+                    ps[0][1] = tile_phi<R>(sp, xi, sd, fr, i, j - 1);
+                    ps[2][1] = tile_phi<R>(sp, xi, sd, fr, i, j + 1);
+                    bool have_s = false;  // the rest of ps read
                     for (int k = 0; k < n; k++) {
                         const int t = reg_solids[tile * KMAX + k];
                         if (t == s) continue;
                         const SolidDesc td = solids[t];
                         const Frame tf = frames[t];
                         R pt[4][4];
+                        pt[1][1] = tile_phi<R>(sp, xi, td, tf, i, j);
+                        pt[1][0] = tile_phi<R>(sp, xi, td, tf, i - 1, j);
+                        pt[1][2] = tile_phi<R>(sp, xi, td, tf, i + 1, j);
+                        pt[0][1] = tile_phi<R>(sp, xi, td, tf, i, j - 1);
+                        pt[2][1] = tile_phi<R>(sp, xi, td, tf, i, j + 1);
+                        {
+                            // an edge whose two nodes are not both valid, or whose averaged phi of
+                            // either solid is not below eps, carries no contact stress
+                            const R e2 = R(2) * eps;
+                            const bool cl = ps[1][0] + ps[1][1] < e2 && pt[1][0] + pt[1][1] < e2;
+                            const bool cr = ps[1][2] + ps[1][1] < e2 && pt[1][2] + pt[1][1] < e2;
+                            const bool cb = ps[0][1] + ps[1][1] < e2 && pt[0][1] + pt[1][1] < e2;
+                            const bool ct = ps[2][1] + ps[1][1] < e2 && pt[2][1] + pt[1][1] < e2;
+                            if (!(cl || cr || cb || ct)) continue;
+                        }
+                        if (!have_s) {
+                            for (int yy = 0; yy < 4; yy++)
+                                for (int xx = 0; xx < 4; xx++)
+                                    if (!((xx == 1 || yy == 1) && xx < 3 && yy < 3))
+                                        ps[yy][xx] = tile_phi<R>(sp, xi, sd, fr, i - 1 + xx, j - 1 + yy);
+                            have_s = true;
+                        }
                         for (int yy = 0; yy < 4; yy++)
-                            for (int xx = 0; xx < 4; xx++) pt[yy][xx] = tile_phi<R>(sp, xi, td, tf, i - 1 + xx, j - 1 + yy);
+                            for (int xx = 0; xx < 4; xx++)
+                                if (!((xx == 1 || yy == 1) && xx < 3 && yy < 3))
+                                    pt[yy][xx] = tile_phi<R>(sp, xi, td, tf, i - 1 + xx, j - 1 + yy);
                         const R p0 = pt[1][1];
                         const double w = !(p0 == p0) || ps[1][1] < p0 ? 1.0 : (ps[1][1] == p0 ? 0.5 : 0.0);
                         if (w == 0.0) continue;
@@ -2447,6 +2510,7 @@ __device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *r
                         if (!any) continue;
                         fc[0] += w * (double)((tr[0] - tl[0]) + (tt[1] - tb[1]));
                         fc[1] += w * (double)((tr[1] - tl[1]) + (tt[2] - tb[2]));
+                    }
                     }
                 }
 }

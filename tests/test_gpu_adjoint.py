@@ -211,15 +211,20 @@ def test_backward_needs_a_forward_run():
 
 
 @pytest.mark.slow
+def _agreements(g, fds, rtol=1e-4):
+    """Relative errors of the adjoint gradient g against each central difference."""
+    return [abs(g - fd) / abs(fd) for fd in fds]
+
+
 def test_adjoint_256_cavity_full_length():
     # 256^2 cavity, disk r = 40, 3000 steps, checkpoints every 100: FP64 adjoint
     # against GPU central differences on G and rho_s / rho_f.  Over 3000 steps
     # interface nodes cross phi = 0 (advected <-> extrapolated); a difference
     # whose +-h interval contains such a crossing is not a derivative, and the
-    # crossings do not become smaller with h, only rarer.  So three step sizes
-    # are tried and the adjoint must match at least one of them (measured:
-    # dG 13.173702 vs 13.173699 at h = 1e-5; d ratio -70.693911 vs -70.693897
-    # at h = 1e-7, -52.6 at h = 1e-5 where a crossing falls inside).
+    # crossings do not become smaller with h, only rarer.  So four step sizes
+    # are taken and the adjoint must match at least two of them: one lucky
+    # difference cannot pass the test, and one step size that straddles a
+    # crossing cannot fail it.
     import paper_2402_12696_gb300 as pkg
     sc = scenarios.adjoint_ldc(256, r=40.0, G=0.01, rho_ratio=1.0)
     sim = pkg.Simulation(sc, precision="fp64")
@@ -233,15 +238,47 @@ def test_adjoint_256_cavity_full_length():
         c = sim.forward_checkpointed(3000, 100)
         return float(((c - target) ** 2).sum())
 
-    errs = []
-    for hr in (1e-5, 1e-6, 1e-7):
-        h = hr * 0.01
-        fd = (loss(G=0.01 + h) - loss(G=0.01 - h)) / (2 * h)
-        errs.append(abs(dG[0] - fd) / abs(fd))
-    assert min(errs) < 1e-4, (dG[0], errs)
-    errs = []
-    for hr in (1e-5, 1e-6, 1e-7):
-        fd = (loss(ratio=1.0 + hr) - loss(ratio=1.0 - hr)) / (2 * hr)
-        errs.append(abs(dr[0] - fd) / abs(fd))
-    assert min(errs) < 1e-4, (dr[0], errs)
+    steps = (1e-5, 1e-6, 1e-7, 3e-8)
+    fds = [(loss(G=0.01 + hr * 0.01) - loss(G=0.01 - hr * 0.01)) / (2 * hr * 0.01) for hr in steps]
+    errs = _agreements(dG[0], fds)
+    assert sum(e < 1e-4 for e in errs) >= 2, (dG[0], fds, errs)
+    fds = [(loss(ratio=1.0 + hr) - loss(ratio=1.0 - hr)) / (2 * hr) for hr in steps]
+    errs = _agreements(dr[0], fds)
+    assert sum(e < 1e-4 for e in errs) >= 2, (dr[0], fds, errs)
+    sim.close()
+
+
+def test_adjoint_256_cavity_body_force_direction():
+    # The body-force gradient at the configured size, over a shorter horizon
+    # (100 steps, checkpoints every 20): the adjoint's dL/df along two smooth
+    # seeded directions against central differences.  Over tens of steps the
+    # loss has kinks (interface nodes crossing phi = 0 or the blur-zone edge),
+    # so a difference over +-h is the local derivative only when no kink falls
+    # inside; measured on this case: at h = 1e-8 the difference matches the
+    # adjoint to 3e-8, at h = 1e-5 .. 1e-7 (kinks inside) to 3e-4 .. 4e-4, and
+    # at 20 steps every h from 1e-5 down matches.  So the check asks for a
+    # match to 1e-6 at one of three tiny step sizes: a kinked difference misses
+    # by ~1e-4, and a chance agreement to 1e-6 is not plausible.
+    import paper_2402_12696_gb300 as pkg
+    body = scenarios.smooth_body_field(3, 256, amp=1e-5)
+    sc = scenarios.adjoint_ldc(256, r=40.0, G=0.01, rho_ratio=1.2, body=body)
+    sim = pkg.Simulation(sc, precision="fp64")
+    c0 = sim.forward_checkpointed(1, 1)
+    target = c0 + np.array([[2.0, -1.0]])
+    sim.set_body_force_field(body)
+    cT = sim.forward_checkpointed(100, 20)
+    _, _, db = sim.backward(2 * (cT - target), body=True)
+    db = db.cpu().numpy()
+
+    def loss(b):
+        sim.set_body_force_field(b)
+        c = sim.forward_checkpointed(100, 20)
+        return float(((c - target) ** 2).sum())
+
+    for seed in (11, 12):
+        v = scenarios.smooth_body_field(seed, 256, amp=1.0)
+        g = float((db * v).sum())
+        fds = [(loss(body + h * v) - loss(body - h * v)) / (2 * h) for h in (1e-8, 3e-9, 1e-9)]
+        errs = _agreements(g, fds)
+        assert min(errs) < 1e-6, (seed, g, fds, errs)
     sim.close()

@@ -369,12 +369,26 @@ def test_total_mass_and_solid_stats(prec, case):
     ref.close()
 
 
-def test_ldc_full_2000_steps_fp64():
-    # the small cavity case run to its full length in FP64
-    res = run_pair(scenarios.ldc_disk_64(), "fp64", [2000])
-    _log("ldc_disk_64_2000/fp64", res)
-    for k in ("rho", "u", "xi", "F"):
-        assert res[2000][k] < 1e-8, (k, res)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ldc_full_2000_steps(prec):
+    # The small cavity case (64^2, one disk) run to its full length.  FP64 to
+    # 1e-8 per field.  FP32: rho - rho_f, u and xi - x to the same relative
+    # 1e-5 as the 100-step cases (measured 1.1e-6, 3.1e-6, 4.6e-6); over 2000
+    # steps the FP32 rounding of the reference map accumulates, and F, formed
+    # from differences of xi across one node on each side of a half-edge and
+    # then across the node, carries it amplified (measured 4.0e-5), so F is held
+    # to 1e-4 at this horizon.
+    sc = scenarios.ldc_disk_64()
+    res = run_pair(sc, prec, [2000])
+    _log(f"ldc_disk_64_2000/{prec}", res)
+    if prec == "fp64":
+        _check(res, prec, sc)
+        return
+    r = res[2000]
+    for k in ("rho", "u", "xi", "xi_band", "drho"):
+        assert r[k] < FP32_TOL, (k, r)
+    assert r["F"] < 1e-4, r
+    assert r["label_mismatch"] == 0, r
 
 
 def test_rest_state_fixed_point_gpu():
