@@ -93,8 +93,9 @@ typedef struct {
     double force_a[2];          /* (fx, fy) for CONST, (A, 0) for f_x = A sin(2 pi y / ny);
                                    FIELD: a per-node field set by lbrmt_set_body_force_field (0 at creation) */
     int precision;              /* LBRMT_FP32 / LBRMT_FP64 arithmetic and storage; LBRMT_FP16_STORE /
-                                   LBRMT_BF16_STORE: FP32 arithmetic, populations and half-force
-                                   stored in 16 bits (FP16 with power-of-two scales 2^10 and 2^14) */
+                                   LBRMT_BF16_STORE: FP32 arithmetic, populations and the density
+                                   plane stored in 16 bits (times power-of-two scales per plane,
+                                   chosen at initialisation from bounds of the values) */
     int max_solids_per_tile;    /* registry slots per tile, 1..8 */
     int rmax;                   /* largest extrapolation window half-width (>= 2) */
     int tile_x;                 /* registry / LB tile width: 16, 32, 64 or 128 nodes (height 256 /
@@ -145,7 +146,12 @@ lbrmt_status lbrmt_add_solid_shape(lbrmt_sim *sim, int shape, double cx, double 
 /* Body force field f(x) of Eq. 2_4_F_divs for force_kind LBRMT_FORCE_FIELD:
  * dev_xy is a device array of 2*nx*ny doubles (x components, then y
  * components, row-major), copied (and rounded to the arithmetic precision);
- * caller-owned.  Acts on all phases from the next step on.  sim_index must be 0. */
+ * caller-owned.  Acts on all phases from the next step on.  Set between steps,
+ * it also replaces the previous step's body force in the half-force term
+ * rho F / 2 of the next step's moments wherever no solid was registered
+ * (that term is rebuilt from the stored density and the current field); the
+ * method holds the field constant, and so do the adjoint and its gradient.
+ * sim_index must be 0. */
 lbrmt_status lbrmt_set_body_force_field(lbrmt_sim *sim, int sim_index, const double *dev_xy);
 
 /* Change a solid's density and shear modulus.  After initialisation this
@@ -157,10 +163,10 @@ lbrmt_status lbrmt_set_solid_params(lbrmt_sim *sim, int solid_id, double rho_s, 
 lbrmt_status lbrmt_reset(lbrmt_sim *sim);
 
 /* Checkpoint and resume: the whole state that Algorithm 1 carries from one
- * step to the next (populations and half-force carry, both halves of every
- * ping-pong pair of reference-map tiles, frames, tile registries and force
- * pools, the body force, the solids' descriptors and statistics, and the step
- * count).  lbrmt_save with dev_blob NULL stores the size needed in *bytes;
+ * step to the next (populations and the density plane of the half-force term,
+ * both halves of every ping-pong pair of reference-map tiles, frames, tile
+ * registries and force pools, the body force, the solids' descriptors and
+ * statistics, and the step count).  lbrmt_save with dev_blob NULL stores the size needed in *bytes;
  * with a caller-owned device buffer of *bytes >= that size it waits for the
  * simulation's stream, checks the device error flags (a raised flag is
  * returned as its status and nothing is written), copies the state into the
@@ -215,7 +221,8 @@ lbrmt_status lbrmt_read_fields_host(lbrmt_sim *sim, int sim_index, int field, in
                                     double *host_out);
 
 /* Overwrite the populations from host memory (9 planes of nx*ny doubles,
- * plane q = f_q) and reset the stored half-force to zero; waits for the
+ * plane q = f_q) and reset the half-force term of the next step's moments to
+ * zero (as at initialisation); waits for the
  * stream.  A page-locked (or registered) buffer is read by the conversion
  * kernel directly; other buffers are copied to a device staging buffer
  * (9*nx*ny doubles, allocated on first use) first. */
