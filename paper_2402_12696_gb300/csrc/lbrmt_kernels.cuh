@@ -2516,7 +2516,7 @@ __device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *r
 }
 
 template <class R, class S>
-__global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 4 : 2) solid_stats_kernel(SimParams sp, const S *f, const S *carry,
+__global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 3 : 2) solid_stats_kernel(SimParams sp, const S *f, const S *carry,
                                                                     const R *fbody, const R *bfield, const int *reg, const int *reg_solids, const R *pool,
                                                                     const R *xi, const Frame *frames,
                                                                     const SolidDesc *solids, double *out) {

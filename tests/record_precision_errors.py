@@ -1,7 +1,7 @@
 """Write the per-field errors of the full-size 4096^2 mixing parity run into
 profiles/precision_errors_mixing4096.json, keyed by the kernels' source hash.
 
-Usage: python tests/record_precision_errors.py <parity log (JSON lines)>
+Usage: python tests/record_precision_errors.py <parity log (JSON lines)> [output path]
 
 The log is what tests/test_gpu_parity.py and tests/test_gpu_half.py append
 when LBRMT_PARITY_LOG names a file: one line per case, with the relative L-inf
@@ -19,7 +19,7 @@ CASE = "mixing_4096_full/"
 FIELDS = ("rho", "u", "F", "drho", "xi", "xi_band", "label_mismatch")
 
 
-def main(log):
+def main(log, path=None):
     errors = {}
     for line in open(log):
         rec = json.loads(line)
@@ -36,11 +36,12 @@ def main(log):
                         "(xi, xi_band, label_mismatch over 24 sampled solids)",
            "kernels_sha1": hashlib.sha1(src.encode()).hexdigest()[:12],
            "errors": errors}
-    path = os.path.join(ROOT, "profiles", "precision_errors_mixing4096.json")
+    path = path or os.path.join(ROOT, "profiles", "precision_errors_mixing4096.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", path, sorted(errors))
+    return out
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    main(sys.argv[1], sys.argv[2] if len(sys.argv) > 2 else None)

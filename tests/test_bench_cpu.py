@@ -45,3 +45,34 @@ def test_k1_source_hash_covers_only_the_lattice_boltzmann_kernel():
     i = src.index("// K1: fused moments")
     j = src.index("lb_step_kernel", i)
     assert bench.k1_source_sha1(src[:j] + " " + src[j:]) != h
+
+
+def test_precision_error_record_round_trip(tmp_path, monkeypatch):
+    # The per-precision errors of the full-size parity run reach the bench line
+    # through the committed record, and only while the kernels' source hash
+    # still matches the one the record was taken on.
+    import json
+    import bench
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import record_precision_errors as rec
+    log = tmp_path / "parity.jsonl"
+    lines = [{"case": "mixing_4096_full/fp32", "res": {"4": {"rho": 3e-11, "u": 5e-7, "F": 1e-7, "xi": 7e-11,
+                                                            "label_mismatch": 0, "u_abs": 1.0}}},
+             {"case": "mixing_4096_full/fp16", "res": {"4": {"rho": 5e-8, "u": 5e-4, "F": 9e-5}}},
+             {"case": "ldc_disk_64/fp32", "res": {"1": {"rho": 1.0}}}]
+    log.write_text("\n".join(json.dumps(x) for x in lines) + "\n")
+    out = tmp_path / "profiles" / "precision_errors_mixing4096.json"
+    out.parent.mkdir()
+    r = rec.main(str(log), str(out))
+    assert sorted(r["errors"]) == ["fp16", "fp32"]
+    assert r["errors"]["fp32"] == {"rho": 3e-11, "u": 5e-7, "F": 1e-7, "xi": 7e-11, "label_mismatch": 0}
+    # bench reads the record relative to its root: point it at a copy of the tree's kernels
+    csrc = tmp_path / "paper_2402_12696_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = open(os.path.join(ROOT, "paper_2402_12696_gb300", "csrc", "lbrmt_kernels.cuh")).read()
+    (csrc / "lbrmt_kernels.cuh").write_text(src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.precision_errors("fp16") == {"rho": 5e-8, "u": 5e-4, "F": 9e-5}
+    assert bench.precision_errors("bf16") is None
+    (csrc / "lbrmt_kernels.cuh").write_text(src + "\n// edited\n")
+    assert bench.precision_errors("fp16") is None  # stale: taken on other kernels
