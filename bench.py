@@ -356,13 +356,13 @@ REAL_BYTES = {"fp32": 4, "fp64": 8, "fp16": 4, "bf16": 4}    # force pool / refe
 
 
 def band_cells(sc, layers=11):
-    """Band cells B of the survey's byte model: each solid and its extrapolation
+    """Band cells B of the minimal byte model: each solid and its extrapolation
     layers, estimated as pi (r + layers)^2 per disk (at t = 0)."""
     return sum(np.pi * (s["r"] + layers) ** 2 for s in sc["solids"])
 
 
 def k1_bytes(N, prec, active_tiles):
-    """Algorithmic bytes of one K1 launch.  'survey': the populations in and out
+    """Algorithmic bytes of one K1 launch.  'minimal': the populations in and out
     (18 s_f per node) and the stored force density read on the registered tiles
     (2 x 4 B per node there).  'state': everything K1 moves as built -- the
     populations, the density plane read at every node (s_f) and written off
@@ -372,11 +372,11 @@ def k1_bytes(N, prec, active_tiles):
     as large as this one)."""
     sf, sr = STORE_BYTES[prec], REAL_BYTES[prec]
     tn = active_tiles * 256
-    return {"survey": N * 18 * sf + tn * 8, "state": N * 19 * sf + (N - tn) * sf + tn * 10 * sr}
+    return {"minimal": N * 18 * sf + tn * 8, "state": N * 19 * sf + (N - tn) * sf + tn * 10 * sr}
 
 
 def step_bytes(N, prec, sc):
-    """Algorithmic bytes of one whole step on the survey's model: populations
+    """Algorithmic bytes of one whole step on the minimal model: populations
     in and out, and per band cell xi in and out (2 x 2 x 4 B) plus the stored
     force density (8 B)."""
     return N * 18 * STORE_BYTES[prec] + band_cells(sc) * (16 + 8)
@@ -441,7 +441,7 @@ def bench_precisions(args, dev, sc, tile_used, peak):
         out[prec] = {"value": N * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": steps,
                      "ms_per_step": ms / steps,
                      "kernel_ms": {"rmt_solid_kernel": kms[0], "force_kernel": kms[1], "lb_step_kernel": kms[2]},
-                     "k1_frac": kb["survey"] / (kms[2] / 1e3) / 1e9 / peak,
+                     "k1_frac": kb["minimal"] / (kms[2] / 1e3) / 1e9 / peak,
                      "k1_frac_state": kb["state"] / (kms[2] / 1e3) / 1e9 / peak,
                      "step_frac": step_bytes(N, prec, sc) / (ms / steps / 1e3) / 1e9 / peak,
                      "error_vs_oracle": precision_errors(prec)}
@@ -559,7 +559,7 @@ def bench_lbrmt(args):
     sf = STORE_BYTES[args.precision]
     kb = k1_bytes(N, args.precision, nact)
     k1_ms = kms[2]
-    achieved = kb["survey"] / (k1_ms / 1e3) / 1e9
+    achieved = kb["minimal"] / (k1_ms / 1e3) / 1e9
     sbytes = step_bytes(N, args.precision, sc)
     precisions = bench_precisions(args, dev, sc, tile_used, peak) if args.precision_steps > 0 else None
     # DRAM traffic per launch from the committed ncu summary, valid only while the
@@ -608,8 +608,9 @@ def bench_lbrmt(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "lb_step_kernel",
                      "peak_source": peak_kind,
-                     "bytes_model": f"survey: N*18*{sf} + 8*256*active_tiles per launch "
-                                    f"({kb['survey'] / N:.1f} B/LU)",
+                     "bytes_model": f"minimal: N*18*{sf} + 8*256*active_tiles per launch "
+                                    f"({kb['minimal'] / N:.1f} B/LU): populations once in and out, the stored "
+                                    "force density on the registered tiles",
                      "frac_state": kb["state"] / (k1_ms / 1e3) / 1e9 / peak,
                      "bytes_model_state": f"N*19*{sf} + (N - 256*active_tiles)*{sf} + "
                                           f"10*{REAL_BYTES[args.precision]}*256*active_tiles per launch "

@@ -301,7 +301,7 @@ def ldc_convergence(L, tau=0.8, re=100.0, g_over_rho_u2=0.1, t80=2000):
     (time steps ~ L^2, as the paper's 20000 steps at L = 80 and 1.28e6 at 640).
     The run length is t80 (L/80)^2 steps: the paper's full length carries the
     disk against the side wall, where the paper applies a solid-wall contact
-    force that this build does not have, so the study stops at 2000 (L/80)^2
+    force that this library does not implement, so the study stops at 2000 (L/80)^2
     steps, before the disk nears a wall."""
     nu = (tau - 0.5) / 3.0
     U = re * nu / L
