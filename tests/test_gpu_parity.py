@@ -312,6 +312,33 @@ def test_pinned_and_pageable_host_buffers_agree():
     sim.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_population_upload_mid_run_matches_oracle(prec):
+    # Populations uploaded between steps (lbrmt_set_populations_host) replace
+    # the state, and the next step's moments carry no half-force term, as at
+    # initialisation -- on registered tiles (where the term lives in the force
+    # pool) and off them (where it is rebuilt from the density plane) alike.
+    # Both sides take the oracle's own populations after 7 steps, so every
+    # field after 5 more steps must agree as in the plain parity cases.
+    import paper_2402_12696_gb300 as pkg
+    sc = scenarios.settling_small(0)
+    sim = pkg.Simulation(sc, precision=prec)
+    ref = oracle.Oracle(sc)
+    sim.step(7)
+    ref.step(7)
+    f = ref.populations()
+    ref.set_populations(f)
+    sim.set_populations_host(f)
+    sim.step(5)
+    ref.step(5)
+    sim.sync()
+    r = compare(sim, ref, sc)
+    _log(f"upload_mid_run/{prec}", {12: r})
+    _check({12: r}, prec, sc)
+    sim.close()
+    ref.close()
+
+
 def test_deterministic_rerun():
     import paper_2402_12696_gb300 as pkg
     sc = scenarios.mixing_small(0)
