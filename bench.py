@@ -417,6 +417,35 @@ def precision_errors(prec):
         return None
 
 
+def fp64_alu_roofline(N, k1_ms, dev):
+    """FP64 K1 against the FP64 pipe: its FP64 flops per node (DADD + DMUL +
+    2 DFMA thread instructions per node, from the committed ncu record while
+    K1's source is the one counted) over its time, against the peak of two
+    FP64 FMA per SM and clock (GB300's nominal 1.25 TFLOP/s at 152 SMs and
+    2.07 GHz) at the measured maximum SM clock."""
+    import torch
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "lb_step_kernel_mixing2048_fp64_flops.json")))
+        src = open(os.path.join(ROOT, "paper_2402_12696_gb300", "csrc", "lbrmt_kernels.cuh")).read()
+        if rec.get("k1_source_sha1") != k1_source_sha1(src):
+            return None
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+        except Exception:
+            mhz = 2070.0
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = nsm * 2 * 2 * mhz * 1e6 / 1e12
+        achieved = rec["flops_per_node"] * N / (k1_ms / 1e3) / 1e12
+        # the pipe issues two FP64 instructions per SM and clock whatever their kind
+        pipe = rec["fp64_inst_per_node"] * N / (k1_ms / 1e3) / (nsm * 2 * mhz * 1e6)
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "pipe_frac": pipe, "flops_per_node": rec["flops_per_node"],
+                "fp64_inst_per_node": rec["fp64_inst_per_node"],
+                "peak_model": f"{nsm} SMs x 2 FP64 FMA/clk x 2 flop x {mhz:.0f} MHz"}
+    except Exception:
+        return None
+
+
 def bench_precisions(args, dev, sc, tile_used, peak):
     """The same workload and launch configuration in the other precisions: FP64
     arithmetic and storage, FP32 arithmetic with FP16 or BF16 storage."""
@@ -445,6 +474,8 @@ def bench_precisions(args, dev, sc, tile_used, peak):
                      "k1_frac_state": kb["state"] / (kms[2] / 1e3) / 1e9 / peak,
                      "step_frac": step_bytes(N, prec, sc) / (ms / steps / 1e3) / 1e9 / peak,
                      "error_vs_oracle": precision_errors(prec)}
+        if prec == "fp64":
+            out[prec]["k1_alu"] = fp64_alu_roofline(N, kms[2], dev)
     return out
 
 
