@@ -2031,16 +2031,10 @@ __device__ __forceinline__ void classify_region(const SimParams &sp, int r, cons
     busy[r] = any ? 1 : 0;
 }
 
-static __global__ void lb_busy_kernel(SimParams sp, const int *reg_prev, const unsigned char *busy_prev, unsigned char *busy,
-                                      unsigned *err) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < sp.nrx * sp.nty) classify_region(sp, r, reg_prev, busy_prev, busy, err);
-}
-
 // ---------------------------------------------------------------------------
 // K1 with TMA staging: persistent CTAs walk the tiles with a grid stride; one
-// thread loads each tile's 9 population planes and 2 half-force planes with
-// two 3-D bulk tensor copies (boxes tile_x x tile_y x 9 and x 2) into one of
+// thread loads each tile's 9 population planes and its density plane with
+// two 3-D bulk tensor copies (boxes tile_x x tile_y x 9 and x 1) into one of
 // two shared-memory stages, completing on an mbarrier, so the copies of the
 // next tile overlap the collision of the current one.
 // ---------------------------------------------------------------------------
