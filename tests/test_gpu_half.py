@@ -41,6 +41,11 @@ CASES = {
     "settling_small_0": lambda: scenarios.settling_small(0),
     "mixing_small_1": lambda: scenarios.mixing_small(1),
     "contact_pair": lambda: scenarios.contact_pair(gap=0.8, nx=96, ny=64),
+    # a per-node body force (the half-force term rebuilt from the stored density
+    # with the field), the conservative force mode, and non-disk shapes
+    "ldc_body_field_64": lambda: scenarios.adjoint_ldc(64, r=12, body=scenarios.smooth_body_field(0, 64, amp=1e-4)),
+    "settling_small_0_conservative": lambda: dict(scenarios.settling_small(0), force_mode=1),
+    "shapes_small_0": lambda: scenarios.shapes_small(0),
 }
 
 
@@ -85,7 +90,16 @@ def test_half_storage_full_size_mixing(prec):
 
 def _check_half(res, prec, sc):
     us = US[prec]
+    # Density floor of the comparison: next to a moving lid three stored
+    # populations carry the bounce-back term 6 w rho u_w = rho u_w / 6 (w = 1/36),
+    # whose 16-bit rounding alone moves rho by up to rho_f u_w / 2 u_s; a density
+    # deviation smaller than that (the first step of a driven cavity) is
+    # compared against it, as FP32's floor of 1e-4 rho_f (the same effect).
+    rf = sc["rho_f"]
+    floor = max(1e-4 * rf, 0.5 * abs(sc.get("lid_u", 0.0)) * rf)
     for n, r in res.items():
-        for k, c in (("rho", 4), ("u", 4), ("F", 16), ("xi", 2), ("xi_band", 4), ("drho", 4)):
+        for k, c in (("u", 4), ("F", 16), ("xi", 2), ("xi_band", 4), ("drho", 4)):
             assert r[k] <= c * us, (n, k, r[k], c * us, r)
+        rho = r["rho_abs"] / max(r["rho_max"], floor)
+        assert rho <= 4 * us, (n, "rho", rho, 4 * us, r)
         assert r["label_mismatch"] == 0, (n, r)
