@@ -86,7 +86,7 @@ def _batch_scs():
             scenarios.contact_pair(gap=0.8, nx=96, ny=64)]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16", "bf16"])
 def test_batch_members_match_single_runs(prec):
     import paper_2402_12696_gb300 as pkg
     scs = _batch_scs()
