@@ -197,6 +197,24 @@ def contact_pair(gap=1.0, nx=80, ny=48, speed=0.0):
     return sc
 
 
+def ragged_wrap(nx=100, ny=74, walls=False):
+    """A grid no registry tile shape divides, with disks that straddle the
+    periodic boundaries (one across x = 0, one across y = 0 and x = nx, one
+    inside); with walls=True no-slip walls in y instead, gravity, and the disks
+    near the walls without touching them.  Sinusoidal body force, tau 0.7."""
+    if walls:
+        sc = _base(nx, ny, 0, 1, 0.7, gravity=1e-4, name=f"ragged_walls_{nx}x{ny}")
+        sc["solids"].append({"x": 1.5, "y": 14.3, "r": 8.0, "rho_s": 1.4, "G": 0.01})
+        sc["solids"].append({"x": nx - 3.2, "y": ny - 13.6, "r": 7.5, "rho_s": 1.2, "G": 0.02})
+        sc["solids"].append({"x": 0.45 * nx, "y": 0.5 * ny, "r": 9.0, "rho_s": 1.3, "G": 0.015})
+        return sc
+    sc = _base(nx, ny, 0, 0, 0.7, force_kind=2, force_a=(2e-4, 0.0), name=f"ragged_wrap_{nx}x{ny}")
+    sc["solids"].append({"x": 1.3, "y": 0.55 * ny, "r": 8.0, "rho_s": 1.3, "G": 0.01})
+    sc["solids"].append({"x": nx - 2.6, "y": 1.7, "r": 7.0, "rho_s": 1.15, "G": 0.02})
+    sc["solids"].append({"x": 0.5 * nx, "y": 0.3 * ny, "r": 6.5, "rho_s": 1.45, "G": 0.012})
+    return sc
+
+
 def fluid_only(nx, ny, wall_x, wall_y, tau, lid_u=0.0, force_kind=0, force_a=(0.0, 0.0)):
     return _base(nx, ny, wall_x, wall_y, tau, lid_u=lid_u, force_kind=force_kind,
                  force_a=force_a, name="fluid_only")

@@ -46,6 +46,8 @@ SHAPE_CASES = {
     "mixing_small_1": lambda: scenarios.mixing_small(1),
     "contact_pair": lambda: scenarios.contact_pair(gap=0.8, nx=96, ny=64),
     "ragged": lambda: scenarios.fluid_only(100, 60, 1, 0, 0.7, force_kind=1, force_a=(0.0, 2e-5)),
+    "ragged_wrap": lambda: scenarios.ragged_wrap(),
+    "ragged_walls": lambda: scenarios.ragged_wrap(walls=True),
 }
 
 

@@ -75,6 +75,9 @@ CASES = {
     "shapes_small_0": lambda: scenarios.shapes_small(0),
     # force_mode 1: the stress divergence enters the Guo term without rho
     "settling_small_0_conservative": lambda: dict(scenarios.settling_small(0), force_mode=1),
+    # grids no tile shape divides, disks across the periodic boundaries or next to walls
+    "ragged_wrap": lambda: scenarios.ragged_wrap(),
+    "ragged_walls": lambda: scenarios.ragged_wrap(walls=True),
 }
 
 
