@@ -98,7 +98,7 @@ struct SimParams {
     // grid of the solid-fraction table (LamEntry): phi_k = (k - lam_k0) lam_h, lam_h a power of two
     float lam_h, lam_inv_h, eps_lo;  // eps_lo = eps - (float)eps
     int lam_k0;
-    // 16-bit storage: power-of-two scale (and inverse) per population plane and of the carry
+    // 16-bit storage: power-of-two scale (and inverse) per population plane and of the density plane
     float st_scale[9], st_inv[9], ct_scale, ct_inv;
 };
 
@@ -322,7 +322,7 @@ __device__ __forceinline__ R two_diff(R a, R b, R &e) {
 
 // Moments of node (i, j): rho and v = (sum c_q f_q + rho^{n-1} F^{n-1} / 2) / rho.
 // reg/pool: registry and force pool of the step that wrote the populations.
-// rho and v from the stored populations fq, the rest base dro and the carry (cx, cy).
+// rho and v from the stored populations fq, the rest base dro and the half-force term (cx, cy).
 template <class R>
 __device__ __forceinline__ void moments_from(const SimParams &sp, const R (&fq)[9], R dro, R cx, R cy, R &rho, R &u,
                                              R &v) {
@@ -2294,9 +2294,11 @@ struct StatsNode {
     R phi, f[9], pool, cx, cy, st[8];
 };
 // Every load of one queued node, issued before any is used: the populations,
-// carry and rest base (the pool entry is read alongside the registry count and
-// used only if the tile is registered; its address is valid either way), phi,
-// and the 4-neighbour stencil of eta for det F.
+// the half-force term's sources (the pool's half-force and the density plane
+// and body force, one of them used) and the rest base (the pool entries are
+// read alongside the registry count and used only if the tile is registered;
+// their addresses are valid either way), phi, and the 4-neighbour stencil of
+// eta for det F.
 template <class R, class S>
 __device__ __forceinline__ void stats_gather(const SimParams &sp, const S *f, const S *carry, const R *fbody,
                                              const R *bfield, const int *reg, const R *pool, const R *xi, int T,
