@@ -468,7 +468,7 @@ struct Engine {
                                                              (const R *)d.fbody, (const R *)d.bfield,
                                                              d.reg_count[1 - cur], d.reg_solids[1 - cur],
                                                              (const R *)d.pool[1 - cur], (const R *)d.xi[cur],
-                                                             d.frame[cur], d.solids, out);
+                                                             d.frame[cur], d.solids, d.order, out);
         return cudaGetLastError();
     }
 

@@ -2515,11 +2515,12 @@ template <class R, class S>
 __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 3 : 2) solid_stats_kernel(SimParams sp, const S *f, const S *carry,
                                                                     const R *fbody, const R *bfield, const int *reg, const int *reg_solids, const R *pool,
                                                                     const R *xi, const Frame *frames,
-                                                                    const SolidDesc *solids, double *out) {
+                                                                    const SolidDesc *solids, const int *order,
+                                                                    double *out) {
     __shared__ double red[32 * STATS_COLS];
     __shared__ unsigned long long dmax;
     __shared__ int queue[STATS_THREADS / 32][64];  // per warp: < 32 waiting + one round of 32
-    const int s = blockIdx.x;
+    const int s = order ? order[blockIdx.x] : (int)blockIdx.x;  // largest tiles first, as K2
     const SolidDesc sd = solids[s];
     const Frame fr = frames[s];
     const int2 o = make_int2(fr.ox, fr.oy), ow = make_int2(wrapi(fr.ox, sp.nx), wrapi(fr.oy, sp.ny));
