@@ -2423,30 +2423,15 @@ __device__ __forceinline__ bool pair_edge_tau(const R (&ps)[4][4], const R (&pt)
     return true;
 }
 
-// Net contact force on solid s: over the registry tiles around it that also
-// hold another solid t, the divergence (Eq. 3_3_div_solid_stress) of the pair's
-// contact stress at every domain node nearer to s than to t (phi_s < phi_t,
-// half where equal; a node outside t's band is nearer to s), summed over the
-// pairs in FP64 by the CTA's threads.
+// The pair contact divergences of one tile that solid s shares with another
+// (the nodes nearer to s), added to fc; used by contact_force_sum below.
 template <class R>
-__device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *reg, const int *reg_solids, const R *xi,
-                                  const Frame *frames, const SolidDesc *solids, int s, const Frame &fr, double (&fc)[2]) {
-    const SolidDesc sd = solids[s];
-    const R eps = pick<R>(sp.eps, sp.eps_f), eta = pick<R>(sp.eta, sp.eta_f);
-    if (fr.bx0 > fr.bx1) return;
-    int rx0[2], rx1[2], ry0[2], ry1[2];
-    const int nrx = tile_ranges(fr.ox + fr.bx0, fr.ox + fr.bx1, sp.nx, sp.wall_x, sp.lx, sp.ntx, rx0, rx1);
-    const int nry = tile_ranges(fr.oy + fr.by0, fr.oy + fr.by1, sp.ny, sp.wall_y, sp.ly, sp.nty, ry0, ry1);
-    for (int ay = 0; ay < nry; ay++)
-        for (int by = ry0[ay]; by <= ry1[ay]; by++)
-            for (int ax = 0; ax < nrx; ax++)
-                for (int bx = rx0[ax]; bx <= rx1[ax]; bx++) {
-                    const int tile = by * sp.ntx + bx;
+__device__ __forceinline__ void contact_tile_sum(const SimParams &sp, const R *xi, const Frame *frames,
+                                                 const SolidDesc *solids, const int *reg, const int *reg_solids, int s,
+                                                 const SolidDesc &sd, const Frame &fr, R eps, R eta, int tile,
+                                                 double (&fc)[2]) {
+                    const int bx = tile % sp.ntx, by = tile / sp.ntx;
                     const int n = min(reg[tile], sp.kmax);
-                    if (n < 2) continue;  // uniform over the CTA
-                    bool mine = false;
-                    for (int k = 0; k < n; k++) mine = mine || reg_solids[tile * KMAX + k] == s;
-                    if (!mine) continue;
                     for (int lt = threadIdx.x; lt < TILE_N; lt += blockDim.x) {  // the tile's nodes
                     const int i = bx * sp.tx + (lt & (sp.tx - 1)), j = by * sp.ty + (lt >> sp.lx);
                     if (i >= sp.nx || j >= sp.ny) continue;
@@ -2508,7 +2493,74 @@ __device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *r
                         fc[1] += w * (double)((tr[1] - tl[1]) + (tt[2] - tb[2]));
                     }
                     }
-                }
+}
+
+// Net contact force on solid s: over the registry tiles around it that also
+// hold another solid t, the divergence (Eq. 3_3_div_solid_stress) of the pair's
+// contact stress at every domain node nearer to s than to t (phi_s < phi_t,
+// half where equal; a node outside t's band is nearer to s), summed over the
+// pairs in FP64 by the CTA's threads.
+constexpr int CONTACT_CAP = 128;  // tiles a solid shares with another, listed in shared memory
+
+template <class R>
+__device__ __noinline__ void contact_force_sum(const SimParams &sp, const int *reg, const int *reg_solids, const R *xi,
+                                  const Frame *frames, const SolidDesc *solids, int s, const Frame &fr, double (&fc)[2],
+                                  int *ctile /* shared, CONTACT_CAP */, int *nct /* shared */) {
+    const SolidDesc sd = solids[s];
+    const R eps = pick<R>(sp.eps, sp.eps_f), eta = pick<R>(sp.eta, sp.eta_f);
+    if (fr.bx0 > fr.bx1) return;  // uniform over the CTA
+    int rx0[2], rx1[2], ry0[2], ry1[2];
+    const int nrx = tile_ranges(fr.ox + fr.bx0, fr.ox + fr.bx1, sp.nx, sp.wall_x, sp.lx, sp.ntx, rx0, rx1);
+    const int nry = tile_ranges(fr.oy + fr.by0, fr.oy + fr.by1, sp.ny, sp.wall_y, sp.ly, sp.nty, ry0, ry1);
+    // The box's tiles that the solid shares with another, found by the CTA's
+    // threads at once and listed in increasing tile index: the order of the
+    // ranges walked row by row, which the per-thread FP64 sums follow.
+    const int lx0 = nrx > 0 ? rx1[0] - rx0[0] + 1 : 0, lx1 = nrx > 1 ? rx1[1] - rx0[1] + 1 : 0;
+    const int ly0 = nry > 0 ? ry1[0] - ry0[0] + 1 : 0, ly1 = nry > 1 ? ry1[1] - ry0[1] + 1 : 0;
+    const int TXn = lx0 + lx1, ntot = TXn * (ly0 + ly1);
+    if (threadIdx.x == 0) *nct = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < ntot; k += blockDim.x) {
+        const int kx = k % TXn, ky = k / TXn;
+        const int bx = kx < lx0 ? rx0[0] + kx : rx0[1] + (kx - lx0);
+        const int by = ky < ly0 ? ry0[0] + ky : ry0[1] + (ky - ly0);
+        const int tile = by * sp.ntx + bx;
+        const int n = min(reg[tile], sp.kmax);
+        if (n < 2) continue;
+        bool mine = false;
+        for (int m = 0; m < n; m++) mine = mine || reg_solids[tile * KMAX + m] == s;
+        if (mine) {
+            const int pos = atomicAdd(nct, 1);
+            if (pos < CONTACT_CAP) ctile[pos] = tile;
+        }
+    }
+    __syncthreads();
+    const int ncand = *nct;
+    if (ncand > CONTACT_CAP) {  // more than the list holds: every tile of the box in turn, in the same order
+        for (int ay = 0; ay < nry; ay++)
+            for (int by = ry0[ay]; by <= ry1[ay]; by++)
+                for (int ax = 0; ax < nrx; ax++)
+                    for (int bx = rx0[ax]; bx <= rx1[ax]; bx++) {
+                        const int tile = by * sp.ntx + bx;
+                        const int n = min(reg[tile], sp.kmax);
+                        if (n < 2) continue;
+                        bool mine = false;
+                        for (int m = 0; m < n; m++) mine = mine || reg_solids[tile * KMAX + m] == s;
+                        if (mine) contact_tile_sum<R>(sp, xi, frames, solids, reg, reg_solids, s, sd, fr, eps, eta,
+                                                      tile, fc);
+                    }
+        return;
+    }
+    if (threadIdx.x == 0)  // insertion sort of the (short) list
+        for (int a = 1; a < ncand; a++) {
+            const int v = ctile[a];
+            int b = a - 1;
+            while (b >= 0 && ctile[b] > v) { ctile[b + 1] = ctile[b]; b--; }
+            ctile[b + 1] = v;
+        }
+    __syncthreads();
+    for (int c = 0; c < ncand; c++) contact_tile_sum<R>(sp, xi, frames, solids, reg, reg_solids, s, sd, fr, eps, eta,
+                                                        ctile[c], fc);
 }
 
 template <class R, class S>
@@ -2520,6 +2572,7 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 3 : 2) solid_s
     __shared__ double red[32 * STATS_COLS];
     __shared__ unsigned long long dmax;
     __shared__ int queue[STATS_THREADS / 32][64];  // per warp: < 32 waiting + one round of 32
+    __shared__ int ctile[CONTACT_CAP], nct;         // tiles shared with another solid (contact sum)
     const int s = order ? order[blockIdx.x] : (int)blockIdx.x;  // largest tiles first, as K2
     const SolidDesc sd = solids[s];
     const Frame fr = frames[s];
@@ -2594,7 +2647,7 @@ __global__ void __launch_bounds__(STATS_THREADS, sizeof(R) == 4 ? 3 : 2) solid_s
     v[8] = v[9] = 0.0;
     {
         double fc[2] = {0.0, 0.0};
-        contact_force_sum<R>(sp, reg, reg_solids, xi, frames, solids, s, fr, fc);
+        contact_force_sum<R>(sp, reg, reg_solids, xi, frames, solids, s, fr, fc, ctile, &nct);
         v[8] = fc[0];
         v[9] = fc[1];
     }
