@@ -16,6 +16,8 @@ struct LaunchInfo {
     int force_blocks;    // persistent grid of K3
     int force_blocks_ov; // the same in the overlapped step (fewer CTAs per SM)
     int rmt_smem;        // dynamic shared memory of K2
+    int rmt_carve;       // K2's preferred shared-memory carveout (percent), or -1
+    int force_carve_ov;  // the overlapped K3's preferred carveout (percent), or -1
     int force_smem;      // dynamic shared memory of K3
     int rmt_req = 0;      // requested K2 CTA width (0: chosen by configure)
     int rmt_threads = 256; // K2 CTA width in use: 256, or 1024 (FP32 arithmetic only)
@@ -66,6 +68,47 @@ inline cudaError_t launch_prio(void (*kernel)(P...), dim3 grid, dim3 block, size
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
+// The same with a preferred shared-memory carveout (percent of the SM's
+// largest; the driver rounds it up to a carveout it supports), or none (-1).
+template <class... P, class... A>
+inline cudaError_t launch_carve(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int prio,
+                                int carve, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    at[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    at[1].val.sharedMemCarveout = carve < 0 ? 0u : (unsigned)carve;
+    cfg.attrs = at;
+    cfg.numAttrs = carve < 0 ? 1 : 2;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+// Shared-memory carveout steps of this GPU family (KB): the SM's 256 KB of
+// L1/shared storage not carved out for shared memory is L1 cache.
+constexpr int CARVE_STEPS_KB[] = {8, 16, 32, 64, 100, 132, 164, 196, 228};
+// The smallest step that holds need bytes (-1: none up to per_sm).
+inline int carve_step(int need, int per_sm) {
+    for (int kb : CARVE_STEPS_KB)
+        if (kb * 1024 >= need) return kb * 1024 <= per_sm ? kb * 1024 : -1;
+    return -1;
+}
+// A step as a launch's carveout preference: percent of the largest carveout,
+// rounded down, so that the driver, which rounds up to its steps, lands on it.
+inline int carve_percent(int step, int per_sm) { return step > 0 ? (int)(100.0 * step / per_sm) : -1; }
+// The SM's largest carveout and the shared memory reserved per CTA.
+inline void smem_limits(int *per_sm, int *resv) {
+    int dev = 0;
+    *per_sm = *resv = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -92,6 +135,7 @@ template <> inline CUtensorMapDataType tma_dtype<__nv_bfloat16>() { return CU_TE
 // Launch shape of the batched kernels.
 struct BatchLaunch {
     int rmt_blocks, rmt_smem;      // K2: persistent grid, dynamic shared memory (largest solid tile)
+    int rmt_carve;                 // K2's preferred shared-memory carveout (percent), or -1
     int force_blocks, force_smem;  // K3 (widest tile shape)
     // Overlapped batch step, as a single simulation's: the classification and
     // K1 of every member's solid-free regions on a side stream of the lowest
@@ -197,6 +241,45 @@ struct Engine {
         li->tma = true;
     }
 
+    // K2's dynamic shared memory and carveout.  A CTA holds the byte labels of
+    // its tile (tmax^2, padded) and the node lists; min_blocks CTAs on an SM
+    // take min_blocks x (dynamic + static + reserved) of its carveout, and the
+    // rest is L1 cache, which K2's gathers and stencils lean on.  When a lower
+    // carveout step than the one that lists of 8 LIST_CAP bytes need holds
+    // min_blocks CTAs with at least RMT_LIST_MIN_BYTES of lists, the lists take
+    // all of the CTA's share of that step and each launch asks for it.
+    // Otherwise: lists of 8 LIST_CAP bytes and the driver's choice (-1).
+    template <class K>
+    static void rmt_smem_carveout(K kernel, int tmax, int min_blocks, int *smem, int *carve) {
+        const int labs = (tmax * tmax + 15) & ~15;
+        *smem = labs + 8 * LIST_CAP;
+        *carve = -1;
+        int per_sm, resv;
+        smem_limits(&per_sm, &resv);
+        cudaFuncAttributes fa;
+        if (per_sm <= 0 || cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        const int fixed = (int)fa.sharedSizeBytes + resv;
+        const int need_base = min_blocks * (*smem + fixed);
+        for (int kb : CARVE_STEPS_KB) {
+            const int c = kb * 1024;
+            if (c > per_sm || c >= need_base) break;
+            const int dyn = std::min((c / min_blocks - fixed) & ~15, RMT_SMEM_MAX);
+            if (dyn - labs < RMT_LIST_MIN_BYTES) continue;
+            int per = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, RMT_THREADS, dyn) != cudaSuccess ||
+                per < min_blocks) {
+                cudaGetLastError();
+                return;
+            }
+            *smem = dyn;
+            *carve = carve_percent(c, per_sm);
+            return;
+        }
+    }
+
     static cudaError_t configure(const SimParams &sp, const DevState &d, int tmax, LaunchInfo *li) {
         li->tmax = tmax;
         li->rmt_smem = ((tmax * tmax + 15) & ~15) + 8 * LIST_CAP;
@@ -209,6 +292,8 @@ struct Engine {
         cudaError_t e = cudaFuncSetAttribute(rmt_solid_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              RMT_SMEM_MAX);
         if (e != cudaSuccess) return e;
+        rmt_smem_carveout(rmt_solid_kernel<R, S>, tmax, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2, &li->rmt_smem,
+                          &li->rmt_carve);
         int nsm0 = 0, dev0 = 0;
         cudaGetDevice(&dev0);
         cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0);
@@ -234,6 +319,19 @@ struct Engine {
         // CTAs per SM (of four that fit) leave the registers of two K1 CTAs, and
         // the step is shorter although K3 alone takes longer.
         li->force_blocks_ov = nsm * std::min(std::max(per, 1), 3);
+        // With fewer CTAs per SM than fit, the overlapped K3 asks for the
+        // carveout step that holds those only: more L1 beside them.
+        li->force_carve_ov = -1;
+        if (per > 3) {
+            int per_sm, resv;
+            smem_limits(&per_sm, &resv);
+            cudaFuncAttributes fa;
+            if (per_sm > 0 && cudaFuncGetAttributes(&fa, force_kernel<R>) == cudaSuccess)
+                li->force_carve_ov =
+                    carve_percent(carve_step(3 * (li->force_smem + (int)fa.sharedSizeBytes + resv), per_sm), per_sm);
+            else
+                cudaGetLastError();
+        }
         configure_tma(sp, d, li, nsm);
         return cudaSuccess;
     }
@@ -334,6 +432,8 @@ struct Engine {
         cudaError_t e = cudaFuncSetAttribute(rmt_batch_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              RMT_SMEM_MAX);
         if (e != cudaSuccess) return e;
+        rmt_smem_carveout(rmt_batch_kernel<R, S>, tmax, sizeof(R) == 4 ? RMT_MIN_BLOCKS : 2, &bl->rmt_smem,
+                          &bl->rmt_carve);
         e = cudaFuncSetAttribute(force_batch_kernel<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  force_smem_max() * (int)sizeof(R));
         if (e != cudaSuccess) return e;
@@ -363,8 +463,8 @@ struct Engine {
         }
         if (ev) cudaEventRecord(ev[0], st);
         if (n_rmt > 0)
-            launch_prio(rmt_batch_kernel<R, S>, dim3(bl.rmt_blocks), dim3(RMT_THREADS), bl.rmt_smem, st, prio, ds,
-                        rmt_items, n_rmt, parity);
+            launch_carve(rmt_batch_kernel<R, S>, dim3(bl.rmt_blocks), dim3(RMT_THREADS), bl.rmt_smem, st, prio,
+                         bl.rmt_carve, ds, rmt_items, n_rmt, parity);
         if (ev) cudaEventRecord(ev[1], st);
         if (n_rmt > 0)
             launch_prio(force_batch_kernel<R, S>, dim3(bl.force_blocks), dim3(K3_THREADS), bl.force_smem, st, prio, ds,
@@ -386,7 +486,9 @@ struct Engine {
                            int prio = 0) {
         if (li.rmt_threads == RMT_THREADS_BIG)
             launch_prio(rmt_solid_kernel_big<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS_BIG), li.rmt_smem, st, prio, sp, a);
-        else launch_prio(rmt_solid_kernel<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS), li.rmt_smem, st, prio, sp, a);
+        else
+            launch_carve(rmt_solid_kernel<R, S>, dim3(sp.nsolids), dim3(RMT_THREADS), li.rmt_smem, st, prio, li.rmt_carve,
+                         sp, a);
     }
 
     static cudaError_t init(const SimParams &sp, const DevState &d, const LaunchInfo &li, cudaStream_t st) {
@@ -431,9 +533,8 @@ struct Engine {
         }
         if (ev) cudaEventRecord(ev[1], st);
         if (sp.nsolids > 0)
-            launch_prio(force_kernel<R>, dim3(overlap ? li.force_blocks_ov : li.force_blocks), dim3(K3_THREADS),
-                        li.force_smem, st, prio, sp,
-                        force_args(d, q, p));
+            launch_carve(force_kernel<R>, dim3(overlap ? li.force_blocks_ov : li.force_blocks), dim3(K3_THREADS),
+                         li.force_smem, st, prio, overlap ? li.force_carve_ov : -1, sp, force_args(d, q, p));
         if (ev) cudaEventRecord(ev[2], st);
         if (li.tma && li.use_tma)
             lb_tma_kernel<R, S><<<li.lb_blocks, TILE_N, li.lb_smem, st>>>(sp, la, li.tm_f[p], li.tm_c, sp.ntx * sp.nty);

@@ -37,6 +37,7 @@ constexpr int RMT_THREADS = 256;
 #define RMT_MIN_BLOCKS 4
 #endif
 constexpr int LIST_CAP = 2048;              // per-layer target list in shared memory
+constexpr int RMT_LIST_MIN_BYTES = 12288;   // least node-list space (bytes) for which K2 takes a smaller carveout
 constexpr int TILE_SIDE_MAX = 448;          // largest solid tile side (byte labels + lists in shared memory)
 constexpr int RMT_SMEM_MAX = ((TILE_SIDE_MAX * TILE_SIDE_MAX + 15) & ~15) + 8 * LIST_CAP;
 // Force pool, per registered tile, TILE_N values per plane: F_x and F_y of the
@@ -1152,7 +1153,12 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
     const int T = sd.T, TT = T * T;
     const int lane = threadIdx.x & 31;
     signed char *lab = reinterpret_cast<signed char *>(smem);        // -1 free, 0 solid, l layer
-    int *lists = reinterpret_cast<int *>(smem + ((TT + 15) & ~15));  // two per-layer lists of packed (lx, ly)
+    // after the labels, the rest of the launch's dynamic shared memory holds
+    // ints: pass 0's per-warp node lists, then the layer lists
+    int *lists = reinterpret_cast<int *>(smem + ((TT + 15) & ~15));
+    unsigned dsm;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+    const int list_cap = ((int)dsm - ((TT + 15) & ~15)) >> 2;
     const Frame fo = a.frame_out[s];
     const Frame fi = a.init ? fo : a.frame_in[s];
     const int2 oo = make_int2(fo.ox, fo.oy);
@@ -1203,7 +1209,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
         // issued before the arithmetic.  A warp whose segment overflows walks
         // its share node by node instead.
         const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
-        const int seg_cap = (2 * LIST_CAP) / nw;
+        const int seg_cap = list_cap / nw;
         int *seg = lists + warp * seg_cap;
         int nseg = 0;
         BoxWalk wk(bw);
@@ -1267,7 +1273,7 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
         const int x0 = max(sx0 - NL, 0), x1 = min(sx1 + NL, T - 1), y0 = max(sy0 - NL, 0), y1 = min(sy1 + NL, T - 1);
         label_layers_l1(sp, lab, T, sx0, sx1, sy0, sy1, oo, NL, lcnt);
         __syncthreads();
-        listed = list_layers(lab, T, x0, x1, y0, y1, NL, lcnt, loff, lists, 2 * LIST_CAP);
+        listed = list_layers(lab, T, x0, x1, y0, y1, NL, lcnt, loff, lists, list_cap);
     }
     for (int l = 1; l <= NL && sx0 <= sx1; l++) {
         const int nitems = listed ? loff[l + 1] - loff[l] : TT;
