@@ -1212,24 +1212,32 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
         const int seg_cap = list_cap / nw;
         int *seg = lists + warp * seg_cap;
         int nseg = 0;
+        // (four of a thread's items at a time: their phi loads first, then the ballots in item order)
         BoxWalk wk(bw);
-        for (int base = 0; base < bn; base += blockDim.x, wk.next()) {
-            const int kk = base + threadIdx.x;
-            bool hit = false;
-            int entry = 0;
-            if (kk < bn) {
+        for (int base = 0; base < bn; base += 4 * blockDim.x) {
+            R ph[4];
+            int ent[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++, wk.next()) {
                 const int ix = ib0 + wk.c, iy = jb0 + wk.r;
-                const int lx = ix - shx, ly = iy - shy;
-                const R phi = Pi[iy * T + ix];
-                if (phi < eps && domain_cell(sp, oo.x + lx, oo.y + ly)) {
-                    if (lx < 0 || ly < 0 || lx >= T || ly >= T) atomicOr(a.err, ERR_TILE_OVERFLOW);
-                    else { hit = true; entry = ix | (iy << 16); }
-                }
+                ent[q] = ix | (iy << 16);
+                ph[q] = base + q * (int)blockDim.x + (int)threadIdx.x < bn ? Pi[iy * T + ix] : eps;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            const int pos = nseg + __popc(m & ((1u << lane) - 1u));
-            if (hit && pos < seg_cap) seg[pos] = entry;
-            nseg += __popc(m);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                bool hit = false;
+                if (ph[q] < eps) {
+                    const int lx = (ent[q] & 0xffff) - shx, ly = (ent[q] >> 16) - shy;
+                    if (domain_cell(sp, oo.x + lx, oo.y + ly)) {
+                        if (lx < 0 || ly < 0 || lx >= T || ly >= T) atomicOr(a.err, ERR_TILE_OVERFLOW);
+                        else hit = true;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                const int pos = nseg + __popc(m & ((1u << lane) - 1u));
+                if (hit && pos < seg_cap) seg[pos] = ent[q];
+                nseg += __popc(m);
+            }
         }
         __syncwarp();
         if (nseg <= seg_cap) {
