@@ -311,9 +311,13 @@ def bench_shapes(args, dev):
     return out
 
 
-def study_convergence(args):
+CONVERGENCE_WORKLOAD = ("cavity with a disk r = 0.2L at (0.6L, 0.5L), Re 100, tau 0.8, G = 0.1 rho U^2, "
+                        "T = 2000 (L/80)^2 (before the disk nears a wall)")
+
+
+def convergence_rows(levels, precision, steps_scale=1.0):
     """Volume conservation under grid refinement (Sec. 4.1): the cavity with a
-    disk at L = 80, 160, 320, 640 run to the same physical time; max and
+    disk at each L of levels run to the same physical time; max and
     lambda-weighted mean of |det F - 1| over the solid at the end, and the
     observed convergence rates between successive L (the paper reports 9.2 %
     at L = 80, 0.3 % at L = 640 and a rate of about 1.4)."""
@@ -321,10 +325,10 @@ def study_convergence(args):
     import paper_2402_12696_gb300 as pkg
     dev = torch.device("cuda:0")
     rows = []
-    for L in [int(v) for v in args.study_levels.split(",")]:
+    for L in levels:
         sc = scenarios.ldc_convergence(L)
-        steps = sc["steps"] if args.study_steps_scale == 1.0 else int(sc["steps"] * args.study_steps_scale)
-        sim = pkg.Simulation(sc, precision=args.precision, device="cuda:0")
+        steps = sc["steps"] if steps_scale == 1.0 else int(sc["steps"] * steps_scale)
+        sim = pkg.Simulation(sc, precision=precision, device="cuda:0")
         sim.init()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -345,10 +349,14 @@ def study_convergence(args):
         for k in ("max_detF_dev", "mean_detF_dev"):
             if a[k] > 0 and b[k] > 0:
                 b["rate_" + k] = float(np.log(a[k] / b[k]) / np.log(b["L"] / a["L"]))
-    print(json.dumps({"study": "convergence", "workload": "cavity with a disk r = 0.2L at (0.6L, 0.5L), Re 100, "
-                      "tau 0.8, G = 0.1 rho U^2, T = 2000 (L/80)^2 (before the disk nears a wall)",
-                      "precision": args.precision, "rows": rows}),
-          flush=True)
+    return rows
+
+
+def study_convergence(args):
+    """The convergence study alone (all levels of --study-levels), one JSON line."""
+    rows = convergence_rows([int(v) for v in args.study_levels.split(",")], args.precision, args.study_steps_scale)
+    print(json.dumps({"study": "convergence", "workload": CONVERGENCE_WORKLOAD, "precision": args.precision,
+                      "rows": rows}), flush=True)
 
 
 STORE_BYTES = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}   # stored population / carry value
@@ -580,6 +588,11 @@ def bench_lbrmt(args):
     batched = bench_batch(args, dev) if args.batch_steps > 0 and rank == 0 else None
     adjoint = bench_adjoint(args, dev) if args.adjoint_steps > 0 and rank == 0 else None
     shapes = bench_shapes(args, dev) if args.shapes_steps > 0 and rank == 0 else None
+    convergence = None
+    if args.convergence_levels and rank == 0:
+        convergence = {"workload": CONVERGENCE_WORKLOAD, "precision": "fp32",
+                       "rows": convergence_rows([int(v) for v in args.convergence_levels.split(",")], "fp32"),
+                       "note": "the finer level L = 640 (about a minute) runs with --study convergence"}
 
     if rank != 0:
         ranks.close()
@@ -660,6 +673,7 @@ def bench_lbrmt(args):
         "batched": batched,
         "adjoint": adjoint,
         "shapes": shapes,
+        "convergence": convergence,
     }
     print(json.dumps(line), flush=True)
     ranks.close()
@@ -692,6 +706,8 @@ def main():
                     help="run a study instead of the benchmark (prints its own JSON line)")
     ap.add_argument("--study-levels", default="80,160,320,640")
     ap.add_argument("--study-steps-scale", type=float, default=1.0)
+    ap.add_argument("--convergence-levels", default="80,160,320",
+                    help="levels of the convergence study carried by the bench line ('' to skip)")
     ap.add_argument("--shapes-steps", type=int, default=200,
                     help="timed steps of the 506-ellipse workload (0: skip)")
     ap.add_argument("--precision-steps", type=int, default=396,

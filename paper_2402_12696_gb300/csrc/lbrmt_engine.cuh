@@ -303,8 +303,14 @@ struct Engine {
         if (w == 0) w = sizeof(R) == 4 && sp.nsolids > 0 && 2 * sp.nsolids <= nsm0 ? RMT_THREADS_BIG : RMT_THREADS;
         if (w == RMT_THREADS_BIG && sizeof(R) != 4) w = RMT_THREADS;
         li->rmt_threads = w;
-        if (w == RMT_THREADS_BIG)
+        if (w == RMT_THREADS_BIG) {
             e = cudaFuncSetAttribute(rmt_solid_kernel_big<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RMT_SMEM_MAX);
+            // One CTA per solid and at most one per SM: room for node lists of a
+            // tile's size, so that a large solid's advected nodes and layers are
+            // listed instead of walked (its box) or scanned (its tile, per layer).
+            li->rmt_smem = std::max(li->rmt_smem, std::min(((tmax * tmax + 15) & ~15) + 4 * tmax * tmax, RMT_SMEM_MAX));
+            li->rmt_carve = -1;
+        }
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(force_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  force_smem_max() * (int)sizeof(R));
