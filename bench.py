@@ -592,7 +592,7 @@ def bench_lbrmt(args):
     if args.convergence_levels and rank == 0:
         convergence = {"workload": CONVERGENCE_WORKLOAD, "precision": "fp32",
                        "rows": convergence_rows([int(v) for v in args.convergence_levels.split(",")], "fp32"),
-                       "note": "the finer level L = 640 (about a minute) runs with --study convergence"}
+                       "note": "the finer level L = 640 (about 3.5 minutes) runs with --study convergence"}
 
     if rank != 0:
         ranks.close()
