@@ -1205,57 +1205,66 @@ __device__ void rmt_solid(const SimParams &sp, const RmtArgs<R, S> &a, const int
         // (a) each warp lists, in box order, the nodes of its share of the box
         // (items threadIdx.x + m blockDim.x) that lie in the blur zone or the
         // solid, in its own segment of the (not yet used) layer lists; (b) it
-        // then advances them two per lane at a time, every load of both nodes
-        // issued before the arithmetic.  A warp whose segment overflows walks
-        // its share node by node instead.
+        // advances them two per lane at a time, every load of both nodes issued
+        // before the arithmetic -- at the end of its share, or earlier whenever
+        // the segment could overflow, after which the listing goes on.
         const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
         const int seg_cap = list_cap / nw;
         int *seg = lists + warp * seg_cap;
-        int nseg = 0;
-        // (four of a thread's items at a time: their phi loads first, then the ballots in item order)
-        BoxWalk wk(bw);
-        for (int base = 0; base < bn; base += 4 * blockDim.x) {
-            R ph[4];
-            int ent[4];
+        if (seg_cap >= 128) {
+            // (four of a thread's items at a time: their phi loads first, then the
+            // ballots in item order, which add at most 128 entries)
+            int base = 0;
+            do {
+                int nseg = 0;
+                for (; base < bn && nseg <= seg_cap - 128; base += 4 * blockDim.x) {
+                    R ph[4];
+                    int ent[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++, wk.next()) {
-                const int ix = ib0 + wk.c, iy = jb0 + wk.r;
-                ent[q] = ix | (iy << 16);
-                ph[q] = base + q * (int)blockDim.x + (int)threadIdx.x < bn ? Pi[iy * T + ix] : eps;
-            }
+                    for (int q = 0; q < 4; q++) {
+                        const int kk = base + q * (int)blockDim.x + (int)threadIdx.x;
+                        const int ix = ib0 + kk % bw, iy = jb0 + kk / bw;
+                        ent[q] = ix | (iy << 16);
+                        ph[q] = kk < bn ? Pi[iy * T + ix] : eps;
+                    }
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                bool hit = false;
-                if (ph[q] < eps) {
-                    const int lx = (ent[q] & 0xffff) - shx, ly = (ent[q] >> 16) - shy;
-                    if (domain_cell(sp, oo.x + lx, oo.y + ly)) {
-                        if (lx < 0 || ly < 0 || lx >= T || ly >= T) atomicOr(a.err, ERR_TILE_OVERFLOW);
-                        else hit = true;
+                    for (int q = 0; q < 4; q++) {
+                        bool hit = false;
+                        if (ph[q] < eps) {
+                            const int lx = (ent[q] & 0xffff) - shx, ly = (ent[q] >> 16) - shy;
+                            if (domain_cell(sp, oo.x + lx, oo.y + ly)) {
+                                if (lx < 0 || ly < 0 || lx >= T || ly >= T) atomicOr(a.err, ERR_TILE_OVERFLOW);
+                                else hit = true;
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (hit) seg[nseg + __popc(m & ((1u << lane) - 1u))] = ent[q];
+                        nseg += __popc(m);
                     }
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, hit);
-                const int pos = nseg + __popc(m & ((1u << lane) - 1u));
-                if (hit && pos < seg_cap) seg[pos] = ent[q];
-                nseg += __popc(m);
-            }
-        }
-        __syncwarp();
-        if (nseg <= seg_cap) {
-            for (int e = lane; e < nseg; e += 64) {
-                const bool two = e + 32 < nseg;
-                P0Node<R> n1, n2;
-                p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[e], n1);
-                p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[two ? e + 32 : e], n2);
-                p0_finish<R, S>(sp, a, n1, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
-                if (two) p0_finish<R, S>(sp, a, n2, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
-            }
+                __syncwarp();
+                for (int e = lane; e < nseg; e += 64) {
+                    const bool two = e + 32 < nseg;
+                    P0Node<R> n1, n2;
+                    p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[e], n1);
+                    p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, seg[two ? e + 32 : e], n2);
+                    p0_finish<R, S>(sp, a, n1, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
+                    if (two)
+                        p0_finish<R, S>(sp, a, n2, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
+                }
+                __syncwarp();
+            } while (base < bn);
         } else {
+            // segments too small to list four ballots: each thread walks its share
             BoxWalk wk2(bw);
             for (int kk = threadIdx.x; kk < bn; kk += blockDim.x, wk2.next()) {
                 const int ix = ib0 + wk2.c, iy = jb0 + wk2.r;
                 const int lx = ix - shx, ly = iy - shy;
                 if (!(Pi[iy * T + ix] < eps) || !domain_cell(sp, oo.x + lx, oo.y + ly)) continue;
-                if (lx < 0 || ly < 0 || lx >= T || ly >= T) continue;  // flagged in (a)
+                if (lx < 0 || ly < 0 || lx >= T || ly >= T) {
+                    atomicOr(a.err, ERR_TILE_OVERFLOW);
+                    continue;
+                }
                 P0Node<R> nd;
                 p0_gather<R, S>(sp, a, Xi, Yi, Pi, T, oo, shx, shy, ix | (iy << 16), nd);
                 p0_finish<R, S>(sp, a, nd, Xi, Yi, Xo, Yo, lab, T, fi, oo, shx, shy, ddx, ddy, eps, stl, sb);
